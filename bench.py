@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the compressed streamed state-vector path on GB300.
+
+Workload: n = 30 qubits, complex64, chunks of 2^22 amplitudes held
+compressed in pinned host memory (error bound eb), a depth-40 random layered
+circuit (H / RX / RZ on every qubit, then a CNOT on a seeded random pairing
+per layer; 1800 gates). One step = one sv_apply_circuit of that circuit: every
+pass streams all chunks host -> GPU, decodes, applies the fused gates in
+on-chip tiles, re-encodes (with the FP64 norm) and streams them back.
+
+Metric: amplitude-gate updates per second = gates * 2^n / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N under torchrun every rank runs an independent replica of the
+workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+N_QUBITS = 30
+CHUNK_QUBITS = 22
+DEPTH = 40
+EB = 1e-6
+GROUP_QUBITS = 4
+METRIC = "amp-gate updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--eb", type=float, default=EB)
+    p.add_argument("--n", type=int, default=N_QUBITS)
+    p.add_argument("--chunk", type=int, default=CHUNK_QUBITS)
+    p.add_argument("--depth", type=int, default=DEPTH)
+    p.add_argument("--group", type=int, default=GROUP_QUBITS)
+    p.add_argument("--no-extras", action="store_true", help="skip the comparator and baseline legs")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max_sum(world, t_local: float, units_local: float, device=None):
+    """(max over ranks of the step time, sum over ranks of the units)."""
+    if world == 1:
+        return t_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int = 0):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def host_link_peak():
+    """Pinned bulk-copy bandwidth per direction and both at once (GB/s)."""
+    import torch
+    nbytes = 1 << 30
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = {}
+    for name in ("h2d", "d2h"):
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s1):
+                e0.record(s1)
+                if name == "h2d":
+                    d.copy_(h, non_blocking=True)
+                else:
+                    h.copy_(d, non_blocking=True)
+                e1.record(s1)
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        out[name] = best
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, 2 * nbytes / (time.perf_counter() - t0) / 1e9)
+    out["bidir"] = best
+    del h, h2, d, d2
+    torch.cuda.empty_cache()
+    return out
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_2309_16979_gb300 import StateVector
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n, c = args.n, args.chunk
+    gates = W.random_layers(n, args.depth, seed=1 + rank)
+    terms = W.ising(n, seed=4)
+    units_per_step = W.amp_gate_updates(n, gates)
+    link = host_link_peak() if rank == 0 else None
+    hbm_peak, peak_kind = measured_peaks()
+
+    sim = StateVector(n, c, args.eb, dtype="c64", init_index=W.basis_index(n), max_group_qubits=args.group,
+                      profile=True, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.float32, device="cuda")  # 1 GiB > L2
+    for _ in range(args.warmup):
+        sim.apply(gates)
+    s0 = sim.stats()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.apply(gates)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_local = e0.elapsed_time(e1) * 1e-3
+    s1 = sim.stats()
+    t_max, units = reduce_max_sum(world, t_local, units_per_step * args.steps, device="cuda")
+    value = units / t_max
+    ms_per_step = t_max / args.steps * 1e3
+
+    d = {k: s1[k] - s0[k] for k in ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d",
+                                     "bytes_d2h", "t_decode_s", "t_apply_s", "t_encode_s", "n_decode",
+                                     "n_apply", "n_encode", "alg_bytes_decode", "alg_bytes_apply",
+                                     "alg_bytes_encode")}
+    kinds = {"apply": ("t_apply_s", "n_apply", "alg_bytes_apply"),
+             "decode": ("t_decode_s", "n_decode", "alg_bytes_decode"),
+             "encode": ("t_encode_s", "n_encode", "alg_bytes_encode")}
+    top = max(kinds, key=lambda k: d[kinds[k][0]])
+    tk, nk, bk = kinds[top]
+    avg_s = d[tk] / max(1, d[nk])
+    bytes_per_launch = d[bk] / max(1, d[nk])
+    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    traffic = load_traffic(top)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "kernel": f"k_{top}",
+                "peak_source": peak_kind,
+                "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, sum(d[w[0]] for w in kinds.values())), 3)
+                                         for k, v in kinds.items()}}
+    link_bytes = d["bytes_h2d"] + d["bytes_d2h"]
+    per_step = {k: d[k] / args.steps for k in ("passes", "subpasses", "kernel_launches", "bytes_h2d", "bytes_d2h")}
+
+    # e2e: the public call a user makes (apply + read back <H>), host buffers,
+    # every H2D/D2H of the compressed store inside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_steps = max(1, min(2, args.steps))
+    sa = sim.stats()
+    energy = None
+    for _ in range(e_steps):
+        sim.apply(gates)
+        energy = sim.expect(terms)
+    te = (time.perf_counter() - t0) / e_steps
+    sb = sim.stats()
+    e2e = {"value": units_per_step * world / te, "unit": METRIC,
+           "h2d_bytes_per_step": int((sb["bytes_h2d"] - sa["bytes_h2d"]) / e_steps),
+           "d2h_bytes_per_step": int((sb["bytes_d2h"] - sa["bytes_d2h"]) / e_steps + 8),
+           "includes": "sv_apply_circuit + sv_expect(1-D Ising, 59 terms) with the energy read back"}
+    st = sim.stats()
+    gpu_launches = int(d["kernel_launches"])
+    sim.close()
+    del flush
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = comparator(args, gates, terms, energy)
+    out = {
+        "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (fp32 gate arithmetic, fp64 reductions)", "data": "synthetic",
+        "config": {"workload": f"random layered circuit, n={n}, depth={args.depth} ({len(gates)} gates), "
+                               f"complex64, chunk=2^{c}, eb={args.eb}, compressed chunks in pinned host DRAM, "
+                               f"streamed in groups of 2^{args.group} chunks",
+                   "n_qubits": n, "chunk_qubits": c, "abs_error_bound": args.eb, "group_qubits": args.group,
+                   "gates": len(gates), "l2": "state (8 GiB raw) >> L2; streamed groups of 512 MiB > L2",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+        "host_link": {"achieved_gbs": round(link_bytes / (t_local) / 1e9, 1),
+                      "peak_gbs": link, "per_step": per_step},
+        "stored_state": {"compressed_bytes": st["compressed_bytes"], "raw_bytes": st["raw_bytes"],
+                         "ratio": round(st["raw_bytes"] / max(1, st["compressed_bytes"]), 2),
+                         "norm2": st["norm2"], "energy": energy},
+    }
+    out.update(extras)
+    return out
+
+
+def load_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary of that kernel, if any."""
+    path = os.path.join(ROOT, "profiles", f"traffic_k_{kind}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f).get("bytes_per_launch")
+
+
+def comparator(args, gates, terms, energy_c):
+    """The plain uncompressed in-HBM GPU path on the same circuit, and the
+    FP64 CPU oracle on a bounded sample of the workload."""
+    import torch
+    from paper_2309_16979_gb300 import StateVector
+    out = {}
+    n = args.n
+    units = W.amp_gate_updates(n, gates)
+    try:
+        with StateVector(n, mode="uncompressed", dtype="c64", init_index=W.basis_index(n)) as p:
+            p.apply(gates)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.apply(gates)
+            t = time.perf_counter() - t0
+            st = p.stats()
+            # fresh state for the energy at the same circuit as the compressed run
+        with StateVector(n, mode="uncompressed", dtype="c64", init_index=W.basis_index(n)) as p:
+            for _ in range(args.warmup + args.steps + max(1, min(2, args.steps))):
+                p.apply(gates)
+            e_plain = p.expect(terms)
+        out["plain_uncompressed"] = {"value": units / t, "unit": METRIC, "seconds_per_step": t,
+                                     "subpasses_per_step": st["subpasses"] / 2,
+                                     "energy": e_plain, "energy_compressed": energy_c,
+                                     "energy_abs_diff": abs(e_plain - energy_c) if energy_c is not None else None}
+    except Exception as ex:  # noqa: BLE001
+        out["plain_uncompressed"] = {"error": str(ex)}
+    out["cpu_baseline"] = cpu_baseline(args, gates)
+    return out
+
+
+def cpu_baseline(args, gates, target_s=12.0):
+    """FP64 oracle (as it stands) on the host cores: the first K gates of the
+    workload on the full n-qubit complex128 state; amp-gate updates/s."""
+    import oracle
+    n = args.n
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[W.basis_index(n)] = 1.0
+    t0 = time.perf_counter()
+    psi = oracle.apply_gates(n, psi, gates[:1])
+    t1 = time.perf_counter() - t0
+    k = max(1, min(len(gates) - 1, int(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    psi = oracle.apply_gates(n, psi, gates[1:1 + k])
+    dt = time.perf_counter() - t0
+    return {"value": k * (1 << n) / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"gates 2..{k + 1} of the {len(gates)}-gate workload on the full 2^{n} complex128 state "
+                      f"({dt:.1f} s)"}
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as the reference arm, on the same config and metric."""
+    import oracle
+    n = args.n
+    gates = W.random_layers(n, args.depth, seed=1)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[W.basis_index(n)] = 1.0
+    per_step = 4  # gates per step: a bounded sample of the workload
+    times = []
+    g = 0
+    for i in range(args.warmup + args.steps):
+        sample = [gates[(g + j) % len(gates)] for j in range(per_step)]
+        g += per_step
+        t0 = time.perf_counter()
+        psi = oracle.apply_gates(n, psi, sample)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = args.steps * per_step * (1 << n) / t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
+            "data": "synthetic",
+            "config": {"workload": f"random layered circuit, n={n}, depth={args.depth}, complex128 FP64 oracle "
+                                   f"on the host cores", "n_qubits": n},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} consecutive gates of the {len(gates)}-gate workload per step "
+                                       f"on the full 2^{n} state"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * sv.h -- C ABI of the GB300 compressed state-vector simulator.
+ *
+ * Method: MEMQSim (arXiv 2309.16979). The n-qubit state vector is split into
+ * 2^(n-c) chunks of 2^c amplitudes; each chunk is compressed independently
+ * and stored in host memory (Sec. 2, "Offline stage"). Each pass over the
+ * circuit streams chunks to the GPU, updates them there and stores them back
+ * recompressed (Sec. 2, "Online stage", steps (1)-(4) and (6)); whole chunks
+ * are moved with bulk copies and placed by GPU threads (Sec. 2, second
+ * data-movement strategy; Table 1 "Buffer copy").
+ *
+ * In this library decompression and recompression run on the GPU, chunks
+ * move compressed over the host link, and every step of a pass runs in this
+ * library's CUDA kernels (sm_103a).
+ *
+ * Conventions for every call:
+ *   - Qubit 0 is the least-significant bit of an amplitude index.
+ *   - Return value 0 (SV_OK) on success, a negative SV_ERR_* code otherwise;
+ *     nothing is thrown across the ABI. sv_last_error() describes the last
+ *     failure on a handle.
+ *   - Every call is synchronous: when it returns, all GPU work it issued has
+ *     finished and every output buffer is written.
+ *   - Pointers named h_* are host memory, d_* device memory of the handle's
+ *     GPU. Inputs are read during the call only; the caller keeps ownership.
+ *   - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef SV_GB300_SV_H
+#define SV_GB300_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SV_OK 0
+#define SV_ERR_ARG (-1)           /* invalid argument (qubit out of range, bad gate, ...) */
+#define SV_ERR_HOST_OOM (-2)      /* pinned host allocation failed or host budget exceeded */
+#define SV_ERR_DEVICE_OOM (-3)    /* device allocation failed or device budget too small */
+#define SV_ERR_CORRUPT (-4)       /* a compressed chunk stream failed validation */
+#define SV_ERR_TIMEOUT (-5)       /* a host wait on GPU work exceeded sv_config.timeout_s */
+#define SV_ERR_NORM_COLLAPSE (-6) /* norm^2 of the stored state fell below 1e-300 */
+#define SV_ERR_RANGE (-7)         /* a value is outside the quantiser's range (or not finite) */
+#define SV_ERR_CUDA (-8)          /* a CUDA runtime call failed */
+
+/* ------------------------------------------------------------- enumerations */
+enum sv_dtype { SV_C64 = 1, SV_C128 = 2 };       /* amplitude type: complex64 / complex128 */
+enum sv_mode { SV_COMPRESSED = 0, SV_UNCOMPRESSED = 1 };
+
+enum sv_gate_kind {
+    SV_GATE_H = 0, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_S, SV_GATE_SDG, SV_GATE_T,
+    SV_GATE_TDG, SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P, SV_GATE_CNOT, SV_GATE_CZ,
+    SV_GATE_CP, SV_GATE_SWAP, SV_GATE_CUSTOM
+};
+
+/*
+ * One gate. RX/RY/RZ(theta) = exp(-i theta {X,Y,Z} / 2); P(theta) and
+ * CP(theta) = diag(1, e^{i theta}) on the target; CNOT/CZ/CP need at least
+ * one control; any kind may carry up to 2 controls (the gate acts where all
+ * controls are 1). SWAP and 2-target CUSTOM use targets[0..1]; the matrix
+ * row/column index has bit b <-> targets[b]. CUSTOM: mat holds the row-major
+ * 2^ntargets x 2^ntargets complex matrix as (re, im) pairs; it must be unitary
+ * for the error bound of the stored state to mean anything.
+ * param_index >= 0 marks a trainable angle for sv_grad (uncontrolled RX, RY or
+ * RZ only); other calls use theta and ignore param_index.
+ */
+typedef struct sv_gate {
+    uint32_t kind;
+    uint32_t ntargets;
+    uint32_t ncontrols;
+    int32_t param_index;
+    uint32_t targets[2];
+    uint32_t controls[2];
+    double theta;
+    double mat[32];
+} sv_gate;
+
+/* coeff * prod_q sigma_q with sigma = I, X (x bit), Z (z bit), Y (both bits). */
+typedef struct sv_pauli_term {
+    double coeff;
+    uint64_t xmask;
+    uint64_t zmask;
+} sv_pauli_term;
+
+typedef struct sv_config {
+    int32_t dtype;                /* SV_C64 (default) or SV_C128 */
+    int32_t mode;                 /* SV_COMPRESSED (default) or SV_UNCOMPRESSED */
+    uint64_t init_index;          /* initial basis state |init_index> (default 0) */
+    int32_t max_group_qubits;     /* high qubits staged together per pass, g_max >= 2
+                                     (default 4, capped at n - chunk_qubits) */
+    int32_t tile_qubits;          /* qubits of one on-chip tile (0 = default for dtype) */
+    int32_t pipeline_slots;       /* chunk-group buffers in flight, 2..4 (default 3) */
+    int32_t renormalize;          /* 1: scale by 1/||psi|| at the next decode (default 0) */
+    int32_t device;               /* CUDA device ordinal (default 0) */
+    int32_t profile;              /* 1: time every decode / apply / encode launch with CUDA
+                                     events on the compute stream (sv_stats t_*_s); default 0 */
+    uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
+    double timeout_s;             /* limit of every host wait on GPU work (default 600) */
+} sv_config;
+
+typedef struct sv_stats_t {
+    uint64_t passes;              /* chunk passes run since sv_create (streaming sweeps) */
+    uint64_t subpasses;           /* on-chip tile sweeps over staged chunk groups */
+    uint64_t groups;              /* chunk groups processed */
+    uint64_t kernel_launches;     /* kernels launched by this library on this handle */
+    uint64_t bytes_h2d;           /* bytes copied host -> device */
+    uint64_t bytes_d2h;           /* bytes copied device -> host */
+    uint64_t compressed_bytes;    /* current size of the stored state (all chunk streams) */
+    uint64_t raw_bytes;           /* 2^n * sizeof(amplitude) */
+    uint64_t amp_gate_updates;    /* sum over applied gates of 2^n */
+    uint64_t gates_applied;
+    double norm2;                 /* FP64 ||psi||^2 of the stored state after the last pass */
+    double last_call_seconds;     /* wall time of the last sv_apply_circuit / sv_grad */
+    double quant_step;            /* Delta of the codec (0 when uncompressed) */
+    int32_t chunk_qubits;
+    int32_t group_qubits;         /* g_max in use */
+    /* with sv_config.profile: summed CUDA-event durations of the kernels, their
+       launch counts, and their algorithmic HBM bytes (what each launch must read
+       and write at least: compressed streams, amplitudes) */
+    double t_decode_s, t_apply_s, t_encode_s;
+    uint64_t n_decode, n_apply, n_encode;
+    uint64_t alg_bytes_decode, alg_bytes_apply, alg_bytes_encode;
+} sv_stats_t;
+
+typedef struct sv_state sv_state; /* opaque, owned by the library */
+
+/* Fill *cfg with the defaults listed above. */
+void sv_config_default(sv_config* cfg);
+
+/*
+ * Create an n-qubit state |init_index> split into chunks of 2^chunk_qubits
+ * amplitudes (Sec. 2, "Offline stage": partition the state vector into
+ * chunks compressed independently and stored in CPU memory).
+ *   n:               1..40 qubits.
+ *   chunk_qubits:    8..n (compressed mode); ignored in uncompressed mode.
+ *   abs_error_bound: eb > 0, pointwise bound on |x - xhat| for every real and
+ *                    imaginary part stored; the codec step is the largest
+ *                    power of two <= 2 eb. complex64 needs eb >= 2^-24,
+ *                    complex128 eb >= 2^-30 (SV_ERR_RANGE otherwise). Ignored
+ *                    in uncompressed mode.
+ *   cfg:             NULL for defaults.
+ *   out:             receives the handle; *out is NULL on failure.
+ * Allocates pinned host memory for the compressed store and device memory
+ * for the staging pipeline (or the whole state when uncompressed).
+ */
+int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* cfg, sv_state** out);
+
+/*
+ * Apply gates[0..ngates) in order (Sec. 2, "Online stage": the circuit is
+ * partitioned into stages; each stage is one pass over all chunks, streamed
+ * to the GPU, updated and stored back recompressed).
+ *   gates:  host array; copied during the call. SWAPs relabel qubits and
+ *           move no data.
+ * Errors: SV_ERR_ARG (invalid gate; the state is unchanged), SV_ERR_RANGE /
+ * SV_ERR_CORRUPT / SV_ERR_CUDA / SV_ERR_TIMEOUT (the state is undefined and
+ * the handle should be destroyed).
+ */
+int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t ngates);
+
+/*
+ * *out_re = sum_j coeff_j <psi|P_j|psi> accumulated in FP64 (the
+ * expectation value of a Pauli sum on the stored state; imaginary parts cancel
+ * for real coefficients). Masks use logical qubits. Terms whose x-masks
+ * differ on the high (inter-chunk) qubits pair different chunks and take one
+ * streaming sweep per distinct high x-mask.
+ */
+int sv_expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
+
+/*
+ * Read amplitudes of logical basis indices idx[0..m) into
+ * out_interleaved[2i], [2i+1] = (re, im) as FP64 (values as stored, i.e.
+ * decompressed). All pointers are host memory. Indices must be < 2^n.
+ */
+int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out_interleaved);
+
+/* Same as sv_amplitudes for the logical indices first .. first+count-1. */
+int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_interleaved);
+
+/*
+ * Energy and gradient by the adjoint method (Jones & Gacon, arXiv
+ * 2009.02823; not part of MEMQSim): resets the state to |init_index>,
+ * applies the circuit with theta[param_index] as the angle of every
+ * parameterised gate, forms lambda = H psi, then sweeps the circuit in
+ * reverse applying U_k^dagger to psi and lambda and accumulating
+ * grad[p] += Im<lambda_k|G_k|psi_k> in FP64 for every gate k with
+ * param_index p (G = X, Y, Z for RX, RY, RZ).
+ *   theta: host, nparams values. H: host Pauli terms. energy: host double.
+ *   grad:  host, nparams doubles (overwritten).
+ * On return the stored state is U(theta)|init_index> rebuilt from the forward
+ * sweep when the state is compressed, or psi_0 after the reverse sweep when
+ * uncompressed (call sv_apply_circuit to continue from a known state).
+ */
+int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* theta, size_t nparams,
+            const sv_pauli_term* H, size_t nterms, double* energy, double* grad);
+
+/*
+ * The chunk passes sv_apply_circuit would run, computed on the host only (no
+ * GPU is touched). The paper partitions the circuit into stages but gives no
+ * algorithm (Sec. 2, "Offline stage" / "Online stage"); a pass here holds the
+ * gates whose non-diagonal targets lie in the chunk_qubits low qubits plus at
+ * most max_group_qubits staged high qubits, and gates move ahead only past
+ * gates on disjoint qubits.
+ *   gates, ngates:  host gate list (validated as in sv_apply_circuit; SWAPs
+ *                   relabel qubits and do not appear in the order).
+ *   order:          host, >= ngates slots: indices of the executed gates in
+ *                   execution order.
+ *   pass_of:        host, >= ngates slots: pass of each entry of order.
+ *   staged:         host, >= ngates slots: bit mask of the physical high
+ *                   qubits staged by each pass.
+ *   out_executed, out_passes, out_subpasses: host, counts (sub-passes are the
+ *                   on-chip tile sweeps after fusion, tile_qubits 0 = default).
+ * Errors: SV_ERR_ARG for invalid sizes or gates.
+ */
+int sv_plan(int n, int chunk_qubits, int max_group_qubits, int tile_qubits, const sv_gate* gates,
+            size_t ngates, int32_t* order, int32_t* pass_of, uint64_t* staged, size_t* out_executed,
+            size_t* out_passes, size_t* out_subpasses);
+
+/* Counters and sizes of the handle. */
+int sv_stats(const sv_state* s, sv_stats_t* out);
+
+/* Human-readable description of the last error on s (never NULL; "" if none).
+ * With s == NULL, the last error of a failed sv_create on this thread. */
+const char* sv_last_error(const sv_state* s);
+
+/* Release all host and device memory of s. NULL is accepted. */
+void sv_destroy(sv_state* s);
+
+/* --------------------------------------------------------------- the codec
+ * Chunk codec used by the store (the paper names no compressor; Sec. 2
+ * claims a state-of-the-art one). Stream format, little-endian:
+ *   0  u32 magic 0x31435653 ("SVC1")     4  u16 version = 1
+ *   6  u8 dtype (1 c64, 2 c128)          7  u8 c
+ *   8  i32 k (step Delta = 2^k)          12 u32 nblocks = 2 * 2^c / 256
+ *   16 u32 total_words                   20..31 zero
+ *   32 u8 width[nblocks], i32 anchor[nblocks], u32 offset[nblocks+1], each
+ *      section padded to 16 bytes; then u32 payload[total_words].
+ * Blocks 0..nblocks/2-1 hold the real parts of amplitudes 256b..256b+255,
+ * the rest the imaginary parts. Per block: q_j = rint(x_j / Delta) (ties to
+ * even), anchor = q_0, r_0 = 0, r_j = q_j - q_{j-1}, zigzag z = 2r (r >= 0)
+ * or -2r-1, width = bit length of max z, value j in bits [j w, j w + w) of
+ * the block's 8 w words, offset[b+1] = offset[b] + 8 w_b.
+ */
+
+/* Largest stream size for a chunk of 2^chunk_qubits amplitudes (0 if out of range). */
+size_t sv_codec_max_bytes(int chunk_qubits);
+
+/*
+ * Encode one chunk on the GPU.
+ *   dtype: SV_C64 / SV_C128. chunk_qubits: 8..30. eb: as in sv_create.
+ *   d_amps:   device, 2^chunk_qubits interleaved complex amplitudes.
+ *   d_stream: device, capacity cap bytes (>= sv_codec_max_bytes for safety;
+ *             SV_ERR_ARG if the stream would not fit).
+ *   h_nbytes: host, receives the stream length.
+ * Allocates and frees device scratch (packed-block staging) on every call.
+ * Errors: SV_ERR_RANGE (a value outside the quantiser's range or not finite).
+ */
+int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
+                    size_t cap, size_t* h_nbytes);
+
+/*
+ * Decode one chunk stream of nbytes bytes (device) into d_amps (device,
+ * 2^chunk_qubits interleaved complex). SV_ERR_CORRUPT if the stream fails
+ * validation (magic, sizes, widths <= 32, offsets consistent with widths).
+ */
+int sv_codec_decode(int dtype, int chunk_qubits, const void* d_stream, size_t nbytes, void* d_amps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_GB300_SV_H */

@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 from typing import List, Optional, Sequence, Tuple
@@ -27,7 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -1,0 +1,174 @@
+"""GB300 compressed state-vector simulator (MEMQSim, arXiv 2309.16979).
+
+Python binding over the C ABI of include/sv.h. Every step of a pass -- chunk
+streaming, decode, gate application, encode, reductions, the adjoint sweep --
+runs in the CUDA library libsvgb300.so; this module only marshals arguments.
+
+    from paper_2309_16979_gb300 import StateVector
+    sv = StateVector(30, chunk_qubits=22, eb=1e-6)
+    sv.apply(gates)
+    e = sv.expect(terms)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _abi
+from ._abi import SV_C64, SV_C128, SV_COMPRESSED, SV_UNCOMPRESSED, SvError, load
+
+__all__ = ["StateVector", "SvError", "codec_encode", "codec_decode", "codec_max_bytes", "load",
+           "SV_C64", "SV_C128", "SV_COMPRESSED", "SV_UNCOMPRESSED"]
+
+
+def _check(code: int, what: str, handle=None):
+    if code != 0:
+        detail = _abi.load().sv_last_error(handle)
+        raise SvError(code, what, detail.decode() if detail else "")
+
+
+class StateVector:
+    """An n-qubit state stored as compressed chunks in pinned host memory
+    (mode="compressed") or whole in HBM (mode="uncompressed")."""
+
+    def __init__(self, n: int, chunk_qubits: int = 0, eb: float = 1e-6, dtype: str = "c64",
+                 mode: str = "compressed", init_index: int = 0, max_group_qubits: int = 4,
+                 tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
+                 host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
+                 profile: bool = False):
+        L = load()
+        cfg = _abi.SvConfig()
+        L.sv_config_default(C.byref(cfg))
+        cfg.dtype = SV_C64 if dtype == "c64" else SV_C128
+        cfg.mode = SV_COMPRESSED if mode == "compressed" else SV_UNCOMPRESSED
+        cfg.init_index = init_index
+        cfg.max_group_qubits = max_group_qubits
+        cfg.tile_qubits = tile_qubits
+        cfg.pipeline_slots = pipeline_slots
+        cfg.renormalize = int(renormalize)
+        cfg.host_budget_bytes = host_budget_bytes
+        cfg.timeout_s = timeout_s
+        cfg.device = device
+        cfg.profile = int(profile)
+        h = C.c_void_p()
+        _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
+        self._h = h
+        self.n = n
+        self.dtype = dtype
+        self.mode = mode
+
+    # ------------------------------------------------------------ calls
+    def apply(self, gates: Sequence) -> None:
+        arr = _abi.gates_to_c(gates)
+        _check(load().sv_apply_circuit(self._h, C.addressof(arr), len(gates)), "sv_apply_circuit", self._h)
+
+    def expect(self, terms: Sequence) -> float:
+        arr = _abi.terms_to_c(terms)
+        out = C.c_double(0.0)
+        _check(load().sv_expect(self._h, C.addressof(arr), len(terms), C.byref(out)), "sv_expect", self._h)
+        return out.value
+
+    def amplitudes(self, idx) -> np.ndarray:
+        idx = np.ascontiguousarray(idx, dtype=np.uint64)
+        out = np.empty(2 * idx.size, dtype=np.float64)
+        _check(load().sv_amplitudes(self._h, idx.ctypes.data, idx.size, out.ctypes.data), "sv_amplitudes",
+               self._h)
+        return out.view(np.complex128)
+
+    def amplitudes_range(self, first: int, count: int) -> np.ndarray:
+        out = np.empty(2 * count, dtype=np.float64)
+        _check(load().sv_amplitudes_range(self._h, first, count, out.ctypes.data), "sv_amplitudes_range",
+               self._h)
+        return out.view(np.complex128)
+
+    def state(self) -> np.ndarray:
+        return self.amplitudes_range(0, 1 << self.n)
+
+    def grad(self, gates: Sequence, theta: Sequence[float], terms: Sequence):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        g = np.zeros(th.size, dtype=np.float64)
+        ga = _abi.gates_to_c(gates)
+        ta = _abi.terms_to_c(terms)
+        e = C.c_double(0.0)
+        _check(load().sv_grad(self._h, C.addressof(ga), len(gates), th.ctypes.data, th.size, C.addressof(ta),
+                              len(terms), C.byref(e), g.ctypes.data), "sv_grad", self._h)
+        return e.value, g
+
+    def stats(self) -> dict:
+        st = _abi.SvStats()
+        _check(load().sv_stats(self._h, C.byref(st)), "sv_stats", self._h)
+        return {f: getattr(st, f) for f, _ in _abi.SvStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().sv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, tile_qubits: int = 0) -> dict:
+    """Host-only pass plan (sv_plan): execution order, pass of each gate,
+    staged high-qubit mask per pass, and pass / sub-pass counts."""
+    L = load()
+    ng = len(gates)
+    arr = _abi.gates_to_c(gates)
+    order = np.zeros(max(1, ng), dtype=np.int32)
+    pass_of = np.zeros(max(1, ng), dtype=np.int32)
+    staged = np.zeros(max(1, ng), dtype=np.uint64)
+    ex, npass, nsub = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+    _check(L.sv_plan(n, chunk_qubits, max_group_qubits, tile_qubits, C.addressof(arr), ng, order.ctypes.data,
+                     pass_of.ctypes.data, staged.ctypes.data, C.byref(ex), C.byref(npass), C.byref(nsub)),
+           "sv_plan", None)
+    k = ex.value
+    return {"order": order[:k].tolist(), "pass_of": pass_of[:k].tolist(),
+            "staged": [int(x) for x in staged[:npass.value]], "passes": npass.value, "subpasses": nsub.value}
+
+
+# ------------------------------------------------------------------ codec
+
+def codec_max_bytes(chunk_qubits: int) -> int:
+    return load().sv_codec_max_bytes(chunk_qubits)
+
+
+def codec_encode(d_amps, eb: float, d_stream=None):
+    """Encode one chunk held in a CUDA tensor (complex64/complex128, 2^c
+    elements). Returns (stream tensor uint8 on the device, nbytes)."""
+    import torch
+    c = int(d_amps.numel()).bit_length() - 1
+    dt = SV_C64 if d_amps.dtype == torch.complex64 else SV_C128
+    cap = codec_max_bytes(c)
+    if d_stream is None:
+        d_stream = torch.empty(cap, dtype=torch.uint8, device=d_amps.device)
+    nb = C.c_size_t(0)
+    torch.cuda.synchronize(d_amps.device)
+    code = load().sv_codec_encode(dt, c, eb, d_amps.data_ptr(), d_stream.data_ptr(), d_stream.numel(),
+                                  C.byref(nb))
+    if code:
+        raise SvError(code, "sv_codec_encode")
+    return d_stream, nb.value
+
+
+def codec_decode(d_stream, nbytes: int, c: int, dtype="c64", out=None):
+    import torch
+    dt = SV_C64 if dtype == "c64" else SV_C128
+    if out is None:
+        out = torch.empty(1 << c, dtype=torch.complex64 if dt == SV_C64 else torch.complex128,
+                          device=d_stream.device)
+    torch.cuda.synchronize(d_stream.device)
+    code = load().sv_codec_decode(dt, c, d_stream.data_ptr(), nbytes, out.data_ptr())
+    if code:
+        raise SvError(code, "sv_codec_decode")
+    return out

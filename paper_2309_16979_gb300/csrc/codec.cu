@@ -1,0 +1,422 @@
+// codec.cu -- GPU chunk codec (decode / encode) for the compressed store.
+//
+// MEMQSim (Sec. 2, "Offline stage") compresses each chunk of the state vector
+// independently and stores it in CPU memory; the online stage decompresses
+// chunks, updates them and recompresses them (steps (1) and (6)). The paper
+// names no compressor. This codec is an error-bounded linear quantiser with
+// 1-D Lorenzo prediction inside 256-value blocks and fixed-length bit packing
+// per block with prefix-sum block offsets; the stream format is documented in
+// include/sv.h.
+//
+// Design for sm_103a:
+//   * one warp owns one 256-amplitude block pair (the real-part block and the
+//     imaginary-part block of the same amplitudes), so amplitudes are read and
+//     written as interleaved complex values with 16-byte vector accesses;
+//   * the step is a power of two, so x * 2^-k and q * 2^k are exact in the
+//     amplitude's own precision: no FP64 on the complex64 path and no rounding
+//     difference to any IEEE implementation;
+//   * Lorenzo residuals cross lanes with one shuffle, block widths come from a
+//     warp max-reduction, and decode rebuilds q with a warp scan;
+//   * packing goes through shared memory (atomicOr of each value's w bits),
+//     then 16-byte stores to a per-block staging slot; a one-CTA-per-chunk scan
+//     turns widths into offsets, and a compaction kernel moves each block's
+//     8*w words to its final offset.
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+__device__ __forceinline__ uint32_t ld32(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+template <typename R> __device__ __forceinline__ R pow2(int e);
+template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
+template <> __device__ __forceinline__ double pow2<double>(int e)
+{
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+template <typename R> __device__ __forceinline__ int32_t round_q(R y);
+template <> __device__ __forceinline__ int32_t round_q<float>(float y) { return __float2int_rn(y); }
+template <> __device__ __forceinline__ int32_t round_q<double>(double y) { return __double2int_rn(y); }
+
+template <typename R> __device__ __forceinline__ R from_q(int32_t q);
+template <> __device__ __forceinline__ float from_q<float>(int32_t q) { return __int2float_rn(q); }
+template <> __device__ __forceinline__ double from_q<double>(int32_t q) { return (double)q; }
+
+template <typename R> struct QLimit;
+template <> struct QLimit<float> { static constexpr float v = 16777215.0f; };     // 2^24 - 1
+template <> struct QLimit<double> { static constexpr double v = 1073741823.0; };  // 2^30 - 1
+
+// load / store 8 consecutive amplitudes of one lane
+__device__ __forceinline__ void load8(const float2* p, float (&re)[8], float (&im)[8])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        float4 v = p4[h];
+        re[2 * h] = v.x; im[2 * h] = v.y; re[2 * h + 1] = v.z; im[2 * h + 1] = v.w;
+    }
+}
+__device__ __forceinline__ void load8(const double2* p, double (&re)[8], double (&im)[8])
+{
+#pragma unroll
+    for (int m = 0; m < 8; m++) { double2 v = p[m]; re[m] = v.x; im[m] = v.y; }
+}
+__device__ __forceinline__ void store8(float2* p, const float (&re)[8], const float (&im)[8])
+{
+    float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int h = 0; h < 4; h++) p4[h] = make_float4(re[2 * h], im[2 * h], re[2 * h + 1], im[2 * h + 1]);
+}
+__device__ __forceinline__ void store8(double2* p, const double (&re)[8], const double (&im)[8])
+{
+#pragma unroll
+    for (int m = 0; m < 8; m++) p[m] = make_double2(re[m], im[m]);
+}
+
+// ----------------------------------------------------------------- decode
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_decode(const uint8_t* __restrict__ in, size_t stride, int c, int dtype, uint64_t nwarps,
+         GroupIn gin, typename V2<R>::T* __restrict__ amps, R scale, int* err)
+{
+    __shared__ __align__(16) uint32_t sbuf[8][2][264];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * 8 + wib;
+    if (gw >= nwarps) return;
+    const CodecLayout L = codec_layout(c);
+    const int sh = c - 8;
+    const uint32_t r = (uint32_t)(gw >> sh);
+    const uint32_t bp = (uint32_t)(gw & ((1ull << sh) - 1));
+    const uint8_t* s = in + (size_t)r * stride;
+    const uint64_t nbytes = gin.bytes[r];
+
+    bool ok = nbytes >= L.p_off && nbytes <= stride;
+    int k = 0;
+    uint32_t total = 0;
+    if (ok) {
+        const uint32_t h0 = ld32(s), h1 = ld32(s + 4), nbh = ld32(s + 12);
+        k = (int32_t)ld32(s + 8);
+        total = ld32(s + 16);
+        ok = h0 == kMagic && (h1 & 0xffffu) == 1u && ((h1 >> 16) & 0xffu) == (uint32_t)dtype &&
+             (h1 >> 24) == (uint32_t)c && k <= 0 && k >= -60 && nbh == L.nb &&
+             L.p_off + 4ull * total <= nbytes;
+    }
+    uint32_t w[2] = {0, 0}, off[2] = {0, 0};
+    int32_t anc[2] = {0, 0};
+    if (ok) {
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            const uint32_t b = p ? bp + L.bpc : bp;
+            w[p] = s[L.w_off + b];
+            off[p] = ld32(s + L.o_off + 4ull * b);
+            const uint32_t nxt = ld32(s + L.o_off + 4ull * (b + 1));
+            anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
+            ok = ok && w[p] <= 32u && nxt - off[p] == 8u * w[p] &&
+                 L.p_off + 4ull * ((uint64_t)off[p] + 8ull * w[p]) <= nbytes;
+        }
+        if (bp == 0) ok = ok && ld32(s + L.o_off) == 0u && ld32(s + L.o_off + 4ull * L.nb) == total;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrCorrupt);
+        return;
+    }
+
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        if (w[p] == 0) continue;
+        const uint4* src = reinterpret_cast<const uint4*>(s + L.p_off + 4ull * off[p]);
+        uint4* dst = reinterpret_cast<uint4*>(sbuf[wib][p]);
+        for (uint32_t i = lane; i < 2 * w[p]; i += 32) dst[i] = src[i];
+        if (lane == 0) sbuf[wib][p][8 * w[p]] = 0u;
+    }
+    __syncwarp();
+
+    const R delta = pow2<R>(k);
+    R x[2][8];
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const uint32_t ww = w[p];
+        const uint32_t mask = ww >= 32u ? FULL : ((1u << ww) - 1u);
+        uint32_t v[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            const uint32_t j = 8u * lane + m;
+            uint32_t z = 0;
+            if (ww) {
+                const uint32_t pos = j * ww;
+                z = __funnelshift_r(sbuf[wib][p][pos >> 5], sbuf[wib][p][(pos >> 5) + 1], pos & 31) & mask;
+            }
+            uint32_t rr = (z >> 1) ^ (0u - (z & 1u));
+            v[m] = (j == 0) ? 0u : rr;
+        }
+#pragma unroll
+        for (int m = 1; m < 8; m++) v[m] += v[m - 1];
+        const uint32_t tot = v[7];
+        uint32_t incl = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const uint32_t base = (uint32_t)anc[p] + (incl - tot);
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            R val = from_q<R>((int32_t)(base + v[m])) * delta;
+            if (scale != (R)1) val *= scale;
+            x[p][m] = val;
+        }
+    }
+    store8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x[0], x[1]);
+}
+
+// ----------------------------------------------------------------- encode
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_encode_blocks(const typename V2<R>::T* __restrict__ amps, int c, uint64_t nwarps, int k,
+                uint8_t* __restrict__ out, size_t stride, uint32_t* __restrict__ sparse,
+                unsigned long long* __restrict__ blocksq, int* err)
+{
+    __shared__ __align__(16) uint32_t pk[8][2][260];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * 8 + wib;
+    if (gw >= nwarps) return;
+    const CodecLayout L = codec_layout(c);
+    const int sh = c - 8;
+    const uint32_t r = (uint32_t)(gw >> sh);
+    const uint32_t bp = (uint32_t)(gw & ((1ull << sh) - 1));
+
+    R x[2][8];
+    load8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x[0], x[1]);
+
+    const R inv = pow2<R>(-k);
+    const R qmax = QLimit<R>::v;
+    int32_t q[2][8];
+    bool bad = false;
+    unsigned long long ss = 0;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            R y = x[p][m] * inv;  // exact: inv is a power of two
+            if (!(fabs(y) <= qmax)) { bad = true; y = (R)0; }
+            q[p][m] = round_q<R>(y);
+            ss += (unsigned long long)((long long)q[p][m] * (long long)q[p][m]);
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, kErrRange);
+
+    uint32_t* pkw = &pk[wib][0][0];
+    for (int i = lane; i < 2 * 260; i += 32) pkw[i] = 0u;
+    __syncwarp();
+
+    uint32_t wpl[2];
+    int32_t anchor[2];
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const int32_t prev = __shfl_up_sync(FULL, q[p][7], 1);
+        uint32_t z[8], mx = 0;
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            int32_t rr;
+            if (m == 0) rr = (lane == 0) ? 0 : q[p][0] - prev;
+            else rr = q[p][m] - q[p][m - 1];
+            z[m] = ((uint32_t)rr << 1) ^ (uint32_t)(rr >> 31);
+            mx = max(mx, z[m]);
+        }
+        mx = __reduce_max_sync(FULL, mx);
+        const uint32_t w = mx ? 32u - (uint32_t)__clz(mx) : 0u;
+        if (w) {
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                const uint32_t pos = (8u * lane + m) * w;
+                const uint32_t wi = pos >> 5, bit = pos & 31;
+                atomicOr(&pk[wib][p][wi], z[m] << bit);
+                if (bit + w > 32u) atomicOr(&pk[wib][p][wi + 1], z[m] >> (32u - bit));
+            }
+        }
+        wpl[p] = w;
+        anchor[p] = __shfl_sync(FULL, q[p][0], 0);
+    }
+    __syncwarp();
+
+    uint8_t* so = out + (size_t)r * stride;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const uint32_t b = p ? bp + L.bpc : bp;
+        const uint32_t w = wpl[p];
+        uint4* dst = reinterpret_cast<uint4*>(sparse + ((uint64_t)r * L.nb + b) * 256ull);
+        const uint4* srcv = reinterpret_cast<const uint4*>(pk[wib][p]);
+        for (uint32_t i = lane; i < 2 * w; i += 32) dst[i] = srcv[i];
+        if (lane == 0) {
+            so[L.w_off + b] = (uint8_t)w;
+            *reinterpret_cast<int32_t*>(so + L.a_off + 4ull * b) = anchor[p];
+        }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) ss += __shfl_down_sync(FULL, ss, d);
+    if (lane == 0) blocksq[(uint64_t)r * L.bpc + bp] = ss;
+}
+
+// One CTA per chunk: widths -> offsets (exclusive scan of 8*w), header,
+// zeroed padding, and the chunk's record {bytes, sum q^2}.
+__global__ void __launch_bounds__(1024)
+k_encode_scan(uint8_t* __restrict__ out, size_t stride, int c, int dtype, int k,
+              const unsigned long long* __restrict__ blocksq, ChunkOut* __restrict__ co)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ unsigned long long qsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t r = blockIdx.x;
+    uint8_t* so = out + (size_t)r * stride;
+    const CodecLayout L = codec_layout(c);
+    const uint32_t nb = L.nb;
+    const uint32_t per = (nb + 1023) / 1024;
+    const uint32_t b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
+
+    uint32_t local = 0;
+    for (uint32_t b = b0; b < b1; b++) local += 8u * so[L.w_off + b];
+    uint32_t incl = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t v = wsum[lane], vi = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, vi, d);
+            if (lane >= d) vi += t;
+        }
+        wsum[lane] = vi - v;  // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    uint32_t run = wsum[wid] + incl - local;
+    for (uint32_t b = b0; b < b1; b++) {
+        *reinterpret_cast<uint32_t*>(so + L.o_off + 4ull * b) = run;
+        run += 8u * so[L.w_off + b];
+    }
+    if (b1 == nb && b0 < b1) *reinterpret_cast<uint32_t*>(so + L.o_off + 4ull * nb) = run;
+
+    // sum of q^2 over the chunk's block pairs
+    const uint32_t bpc = L.bpc, per2 = (bpc + 1023) / 1024;
+    const uint32_t p0 = min(bpc, tid * per2), p1 = min(bpc, p0 + per2);
+    unsigned long long s2 = 0;
+    for (uint32_t b = p0; b < p1; b++) s2 += blocksq[(uint64_t)r * bpc + b];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) s2 += __shfl_down_sync(FULL, s2, d);
+    if (lane == 0) qsum[wid] = s2;
+    __syncthreads();
+
+    if (tid == 0) {
+        unsigned long long tot2 = 0;
+        for (int i = 0; i < 32; i++) tot2 += qsum[i];
+        // total words = offset[nb]
+        const uint32_t total = *reinterpret_cast<const uint32_t*>(so + L.o_off + 4ull * nb);
+        uint32_t* h = reinterpret_cast<uint32_t*>(so);
+        h[0] = kMagic;
+        h[1] = 1u | ((uint32_t)dtype << 16) | ((uint32_t)c << 24);
+        h[2] = (uint32_t)k;
+        h[3] = nb;
+        h[4] = total;
+        h[5] = h[6] = h[7] = 0u;
+        for (size_t i = L.w_off + nb; i < L.a_off; i++) so[i] = 0;
+        for (size_t i = L.a_off + 4ull * nb; i < L.o_off; i++) so[i] = 0;
+        for (size_t i = L.o_off + 4ull * (nb + 1); i < L.p_off; i++) so[i] = 0;
+        co[r].bytes = L.p_off + 4ull * total;
+        co[r].sumsq = tot2;
+    }
+}
+
+// One warp per block: move the block's 8*w packed words to payload + offset[b].
+__global__ void __launch_bounds__(256)
+k_encode_compact(uint8_t* __restrict__ out, size_t stride, int c, uint64_t nwarps,
+                 const uint32_t* __restrict__ sparse)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * 8 + wib;
+    if (gw >= nwarps) return;
+    const CodecLayout L = codec_layout(c);
+    const int sh = c - 7;
+    const uint32_t r = (uint32_t)(gw >> sh);
+    const uint32_t b = (uint32_t)(gw & ((1ull << sh) - 1));
+    uint8_t* so = out + (size_t)r * stride;
+    const uint32_t w = so[L.w_off + b];
+    if (w == 0) return;
+    const uint32_t off = *reinterpret_cast<const uint32_t*>(so + L.o_off + 4ull * b);
+    const uint4* src = reinterpret_cast<const uint4*>(sparse + ((uint64_t)r * L.nb + b) * 256ull);
+    uint4* dst = reinterpret_cast<uint4*>(so + L.p_off + 4ull * off);
+    for (uint32_t i = lane; i < 2 * w; i += 32) dst[i] = src[i];
+}
+
+template <typename R>
+__global__ void k_fill_basis(typename V2<R>::T* amps, uint64_t count, int64_t one_at)
+{
+    using T = typename V2<R>::T;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        T v;
+        v.x = ((int64_t)i == one_at) ? (R)1 : (R)0;
+        v.y = (R)0;
+        amps[i] = v;
+    }
+}
+
+inline unsigned blocks_for_warps(uint64_t nwarps) { return (unsigned)((nwarps + 7) / 8); }
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_decode(const uint8_t* in, size_t stride, int c, int dtype, int nchunks,
+                          const GroupIn& gin, void* amps, double scale, int* err, cudaStream_t st)
+{
+    const uint64_t nwarps = (uint64_t)nchunks << (c - 8);
+    k_decode<R><<<blocks_for_warps(nwarps), 256, 0, st>>>(
+        in, stride, c, dtype, nwarps, gin, static_cast<typename V2<R>::T*>(amps), (R)scale, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks, uint8_t* out,
+                          size_t stride, uint32_t* sparse, unsigned long long* blocksq,
+                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches)
+{
+    const uint64_t nw = (uint64_t)nchunks << (c - 8);
+    k_encode_blocks<R><<<blocks_for_warps(nw), 256, 0, st>>>(
+        static_cast<const typename V2<R>::T*>(amps), c, nw, k, out, stride, sparse, blocksq, err);
+    k_encode_scan<<<nchunks, 1024, 0, st>>>(out, stride, c, dtype, k, blocksq, chunk_out);
+    const uint64_t nw2 = (uint64_t)nchunks << (c - 7);
+    k_encode_compact<<<blocks_for_warps(nw2), 256, 0, st>>>(out, stride, c, nw2, sparse);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)std::min<uint64_t>((count + 255) / 256, 152ull * 16);
+    k_fill_basis<R><<<blocks, 256, 0, st>>>(static_cast<typename V2<R>::T*>(amps), count, one_at);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_decode<float>(const uint8_t*, size_t, int, int, int, const GroupIn&, void*,
+                                          double, int*, cudaStream_t);
+template cudaError_t launch_decode<double>(const uint8_t*, size_t, int, int, int, const GroupIn&, void*,
+                                           double, int*, cudaStream_t);
+template cudaError_t launch_encode<float>(const void*, int, int, int, int, uint8_t*, size_t, uint32_t*,
+                                          unsigned long long*, ChunkOut*, int*, cudaStream_t, int*);
+template cudaError_t launch_encode<double>(const void*, int, int, int, int, uint8_t*, size_t, uint32_t*,
+                                           unsigned long long*, ChunkOut*, int*, cudaStream_t, int*);
+template cudaError_t launch_fill_basis<float>(void*, uint64_t, int64_t, cudaStream_t);
+template cudaError_t launch_fill_basis<double>(void*, uint64_t, int64_t, cudaStream_t);
+
+}  // namespace sv

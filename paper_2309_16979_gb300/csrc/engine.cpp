@@ -1,0 +1,842 @@
+// engine.cpp -- execution of planned passes (MEMQSim Sec. 2, "Online stage").
+//
+// Compressed mode: for each pass, chunk groups stream through a pipeline of
+// pipeline_slots device buffers on three CUDA streams:
+//   h2d  : compressed chunk streams, pinned host -> device (one bulk copy per
+//          chunk, the paper's buffer strategy, Table 1)
+//   comp : decode -> tile sub-passes -> encode, then the group's chunk sizes
+//          device -> pinned host
+//   d2h  : compressed chunk streams device -> pinned host, issued one group
+//          later, once the sizes are on the host
+// so that while group i is computed, group i+1 is copied in and group i-1
+// copied out. Chunks written by a pass go to the second pinned arena; the
+// arenas swap at the end of the pass.
+// Uncompressed mode keeps the whole state in HBM and runs the sub-passes
+// over it directly.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "engine.h"
+
+namespace sv {
+
+// ------------------------------------------------------------------ errors
+int fail(sv_state* s, int code, const std::string& msg)
+{
+    if (s) s->err = msg;
+    return code;
+}
+
+int cuda_fail(sv_state* s, cudaError_t e, const char* where)
+{
+    return fail(s, SV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int wait_event(sv_state* s, cudaEvent_t ev)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return SV_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(s, e, "cudaEventQuery");
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > s->cfg.timeout_s) return fail(s, SV_ERR_TIMEOUT, "timed out waiting for GPU work");
+    }
+}
+
+int wait_stream(sv_state* s, cudaStream_t st)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return SV_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(s, e, "cudaStreamQuery");
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > s->cfg.timeout_s) return fail(s, SV_ERR_TIMEOUT, "timed out waiting for GPU work");
+    }
+}
+
+int sync_all(sv_state* s)
+{
+    int r;
+    if ((r = wait_stream(s, s->s_h2d))) return r;
+    if ((r = wait_stream(s, s->s_comp))) return r;
+    if ((r = wait_stream(s, s->s_d2h))) return r;
+    return SV_OK;
+}
+
+// read and clear the device error word
+int check_device_error(sv_state* s)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->s_comp);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read error word");
+    int r = wait_stream(s, s->s_comp);
+    if (r) return r;
+    if (h) {
+        cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s_comp);
+        wait_stream(s, s->s_comp);
+        if (h & kErrCorrupt) return fail(s, SV_ERR_CORRUPT, "compressed chunk stream failed validation");
+        if (h & kErrRange) return fail(s, SV_ERR_RANGE, "amplitude outside the quantiser range or not finite");
+    }
+    return SV_OK;
+}
+
+// ------------------------------------------------------------------ store
+uint8_t* arena_alloc(sv_state* s, Arena& a, uint64_t bytes)
+{
+    const uint64_t need = (bytes + 255) & ~uint64_t(255);
+    while (true) {
+        if (a.si < a.segs.size()) {
+            Segment& g = a.segs[a.si];
+            if (a.off + need <= g.cap) {
+                uint8_t* p = g.ptr + a.off;
+                a.off += need;
+                return p;
+            }
+            a.si++;
+            a.off = 0;
+            continue;
+        }
+        const size_t cap = std::max<size_t>(a.seg_bytes, need);
+        if (s->cfg.host_budget_bytes && s->pinned_bytes + cap > s->cfg.host_budget_bytes) return nullptr;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, cap, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        s->pinned_bytes += cap;
+        a.segs.push_back({static_cast<uint8_t*>(p), cap});
+    }
+}
+
+void arena_free(Arena& a)
+{
+    for (auto& g : a.segs) cudaFreeHost(g.ptr);
+    a.segs.clear();
+    a.reset();
+}
+
+// ------------------------------------------------------------- profiling
+// With sv_config.profile, kernel launches on the compute stream are bracketed
+// by CUDA events; durations are read once the pass has synchronised.
+enum { PROF_DECODE = 0, PROF_APPLY = 1, PROF_ENCODE = 2 };
+
+static int prof_begin(sv_state* s)
+{
+    if (!s->cfg.profile) return -1;
+    const size_t i = s->prof_used;
+    while (s->prof_ev.size() < 2 * (i + 1)) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+        s->prof_ev.push_back(ev);
+    }
+    if (s->prof_rec.size() < i + 1) s->prof_rec.resize(i + 1);
+    cudaEventRecord(s->prof_ev[2 * i], s->s_comp);
+    s->prof_used++;
+    return (int)i;
+}
+
+static void prof_end(sv_state* s, int i, int kind, uint64_t bytes)
+{
+    if (i < 0) return;
+    cudaEventRecord(s->prof_ev[2 * i + 1], s->s_comp);
+    s->prof_rec[i] = {kind, bytes};
+}
+
+static void prof_collect(sv_state* s)
+{
+    for (size_t i = 0; i < s->prof_used; i++) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const auto& r = s->prof_rec[i];
+        if (r.kind == PROF_DECODE) { s->st.t_decode_s += ms * 1e-3; s->st.n_decode++; s->st.alg_bytes_decode += r.bytes; }
+        if (r.kind == PROF_APPLY) { s->st.t_apply_s += ms * 1e-3; s->st.n_apply++; s->st.alg_bytes_apply += r.bytes; }
+        if (r.kind == PROF_ENCODE) { s->st.t_encode_s += ms * 1e-3; s->st.n_encode++; s->st.alg_bytes_encode += r.bytes; }
+    }
+    s->prof_used = 0;
+}
+
+// ----------------------------------------------------------- op upload
+template <typename R>
+int upload_ops(sv_state* s, const std::vector<DevOp<R>>& ops)
+{
+    const size_t bytes = std::max<size_t>(1, ops.size()) * sizeof(DevOp<R>);
+    if (bytes > s->ops_cap) {
+        if (s->d_ops) {
+            wait_stream(s, s->s_comp);
+            cudaFree(s->d_ops);
+            s->d_ops = nullptr;
+        }
+        size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+        cudaError_t e = cudaMalloc(&s->d_ops, cap);
+        if (e != cudaSuccess) return cuda_fail(s, e, "cudaMalloc(ops)");
+        s->ops_cap = cap;
+    }
+    if (!ops.empty()) {
+        cudaError_t e = cudaMemcpyAsync(s->d_ops, ops.data(), ops.size() * sizeof(DevOp<R>), cudaMemcpyHostToDevice,
+                                        s->s_comp);
+        if (e != cudaSuccess) return cuda_fail(s, e, "upload ops");
+    }
+    return SV_OK;
+}
+
+// Device form of a pass: every sub-pass's tile descriptor and op range.
+template <typename R>
+struct DevPass {
+    std::vector<TileDesc> td;
+    std::vector<int> off, cnt;
+    std::vector<DevOp<R>> ops;
+};
+
+template <typename R>
+static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t, int l)
+{
+    DevPass<R> dp;
+    for (const SubPlan& sp : subs) {
+        TileDesc td = tile_desc(sp.T, L, t, l);
+        dp.td.push_back(td);
+        dp.off.push_back((int)dp.ops.size());
+        dev_ops<R>(sp, td, dp.ops, nullptr, nullptr);
+        dp.cnt.push_back((int)dp.ops.size() - dp.off.back());
+    }
+    return dp;
+}
+
+// Tile shape over L local positions: t tile qubits of which the low l are
+// always included; at least two tile positions stay free for the mixing
+// targets of a gate unless the tile covers every local position.
+void tile_shape(int L, int tq, int lq, int& t, int& l)
+{
+    t = std::min(tq, L);
+    if (t < L) {
+        t = std::min(L, std::max(t, 3));
+        l = std::max(1, std::min(lq, t - 2));
+    } else {
+        l = std::max(1, std::min(lq, t));
+    }
+}
+
+static inline uint64_t deposit(uint64_t v, const std::vector<int>& pos)
+{
+    uint64_t r = 0;
+    for (size_t i = 0; i < pos.size(); i++)
+        if ((v >> i) & 1) r |= 1ull << pos[i];
+    return r;
+}
+
+// --------------------------------------------------- compressed streaming
+template <typename R>
+int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp)
+{
+    const int c = s->c, g = (int)pp.S.size();
+    const int L = c + g;
+    int t, l;
+    tile_shape(L, s->tq, s->lq, t, l);
+    const std::vector<HOp> hops = local_ops(gates, pp.gates, c, pp.S, false);
+    const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
+    const DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
+    int r = upload_ops<R>(s, dp.ops);
+    if (r) return r;
+    const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
+
+    // chunk-index bit positions of staged and fixed high qubits
+    std::vector<int> spos, fpos;
+    for (int q = c; q < s->n; q++) {
+        if (std::find(pp.S.begin(), pp.S.end(), q) != pp.S.end()) spos.push_back(q - c);
+        else fpos.push_back(q - c);
+    }
+    const uint64_t ngroups = 1ull << fpos.size();
+    const int gch = 1 << g;
+    const int NS = s->nslots;
+    std::vector<std::vector<uint64_t>> slot_chunks(NS);
+    std::vector<int> slot_prof(NS, -1);
+    Arena& out_arena = s->arena[1 - s->cur_arena];
+    out_arena.reset();
+    double norm2 = 0;
+    const double delta2 = std::ldexp(1.0, 2 * s->k);
+
+    auto issue = [&](uint64_t gi) -> int {
+        const int slot = (int)(gi % NS);
+        const uint64_t base = deposit(gi, fpos);
+        auto& ch = slot_chunks[slot];
+        ch.resize(gch);
+        GroupIn gin{};
+        cudaError_t e;
+        if (s->slot_used[slot]) {
+            if ((e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0))) return cuda_fail(s, e, "wait comp");
+        }
+        for (int j = 0; j < gch; j++) {
+            const uint64_t k = base | deposit((uint64_t)j, spos);
+            ch[j] = k;
+            const ChunkRef& cr = s->cur[k];
+            gin.bytes[j] = (uint32_t)cr.bytes;
+            e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                s->s_h2d);
+            if (e) return cuda_fail(s, e, "H2D chunk");
+            s->st.bytes_h2d += cr.bytes;
+        }
+        if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d))) return cuda_fail(s, e, "record h2d");
+        if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0))) return cuda_fail(s, e, "wait h2d");
+        if (s->slot_used[slot]) {
+            if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0))) return cuda_fail(s, e, "wait d2h");
+        }
+        const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
+        uint64_t in_bytes = 0;
+        for (int j = 0; j < gch; j++) in_bytes += gin.bytes[j];
+        int pi = prof_begin(s);
+        if ((e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gin, s->d_amps, s->scale, s->d_err,
+                                  s->s_comp)))
+            return cuda_fail(s, e, "decode");
+        prof_end(s, pi, PROF_DECODE, in_bytes + amp_bytes);
+        s->st.kernel_launches++;
+        const uint64_t gbase = base << c;
+        for (size_t i = 0; i < dp.td.size(); i++) {
+            pi = prof_begin(s);
+            if ((e = launch_apply<R>(s->d_amps, dp.td[i], d_ops + dp.off[i], dp.cnt[i], gbase, s->s_comp)))
+                return cuda_fail(s, e, "apply");
+            prof_end(s, pi, PROF_APPLY, 2 * amp_bytes);
+            s->st.kernel_launches++;
+        }
+        int launches = 0;
+        pi = prof_begin(s);
+        slot_prof[slot] = pi;
+        if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)))
+            return cuda_fail(s, e, "encode");
+        prof_end(s, pi, PROF_ENCODE, amp_bytes);
+        s->st.kernel_launches += launches;
+        if ((e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
+                                 s->s_comp)))
+            return cuda_fail(s, e, "D2H sizes");
+        if ((e = cudaEventRecord(s->ev_comp[slot], s->s_comp))) return cuda_fail(s, e, "record comp");
+        s->slot_used[slot] = true;
+        s->st.groups++;
+        s->st.subpasses += dp.td.size();
+        return SV_OK;
+    };
+
+    auto finish = [&](uint64_t gi) -> int {
+        const int slot = (int)(gi % NS);
+        int rr = wait_event(s, s->ev_comp[slot]);
+        if (rr) return rr;
+        cudaError_t e;
+        for (int j = 0; j < gch; j++) {
+            const uint64_t k = slot_chunks[slot][j];
+            const ChunkOut co = s->h_co[slot][j];
+            if (co.bytes > s->stride) return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
+            uint8_t* dst = arena_alloc(s, out_arena, co.bytes);
+            if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
+            e = cudaMemcpyAsync(dst, s->d_out[slot] + (size_t)j * s->stride, co.bytes, cudaMemcpyDeviceToHost,
+                                s->s_d2h);
+            if (e) return cuda_fail(s, e, "D2H chunk");
+            s->nxt[k] = {dst, co.bytes};
+            s->st.bytes_d2h += co.bytes;
+            if (slot_prof[slot] >= 0) s->prof_rec[slot_prof[slot]].bytes += co.bytes;
+            norm2 += (double)co.sumsq * delta2;
+        }
+        if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h))) return cuda_fail(s, e, "record d2h");
+        return SV_OK;
+    };
+
+    for (uint64_t gi = 0; gi <= ngroups; gi++) {
+        if (gi < ngroups && (r = issue(gi))) return r;
+        if (gi >= 1 && (r = finish(gi - 1))) return r;
+    }
+    if ((r = sync_all(s))) return r;
+    prof_collect(s);
+    if ((r = check_device_error(s))) return r;
+    s->cur.swap(s->nxt);
+    s->cur_arena = 1 - s->cur_arena;
+    uint64_t total = 0;
+    for (const ChunkRef& cr : s->cur) total += cr.bytes;
+    s->st.compressed_bytes = total;
+    s->st.norm2 = norm2;
+    s->st.passes++;
+    if (norm2 < 1e-300) return fail(s, SV_ERR_NORM_COLLAPSE, "norm of the stored state collapsed to zero");
+    s->scale = s->cfg.renormalize ? 1.0 / std::sqrt(norm2) : 1.0;
+    return SV_OK;
+}
+
+// ------------------------------------------------------------ uncompressed
+template <typename R>
+int run_pass_uncompressed(sv_state* s, void* state, const std::vector<PGate>& gates, const std::vector<int>& ids)
+{
+    const int L = s->n;
+    int t, l;
+    tile_shape(L, s->tq, s->lq, t, l);
+    const std::vector<int> noS;
+    const std::vector<HOp> hops = local_ops(gates, ids, L, noS, false);
+    const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
+    const DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
+    int r = upload_ops<R>(s, dp.ops);
+    if (r) return r;
+    const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
+    const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
+    for (size_t i = 0; i < dp.td.size(); i++) {
+        const int pi = prof_begin(s);
+        cudaError_t e = launch_apply<R>(state, dp.td[i], d_ops + dp.off[i], dp.cnt[i], 0, s->s_comp);
+        if (e) return cuda_fail(s, e, "apply");
+        prof_end(s, pi, PROF_APPLY, 2 * amp_bytes);
+        s->st.kernel_launches++;
+    }
+    s->st.subpasses += dp.td.size();
+    s->st.passes++;
+    r = wait_stream(s, s->s_comp);
+    prof_collect(s);
+    return r;
+}
+
+template <typename R>
+int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
+{
+    if (gates.empty()) return SV_OK;
+    if (s->mode == SV_UNCOMPRESSED) {
+        std::vector<int> ids(gates.size());
+        for (size_t i = 0; i < gates.size(); i++) ids[i] = (int)i;
+        return run_pass_uncompressed<R>(s, s->d_state, gates, ids);
+    }
+    const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
+    for (const PassPlan& pp : passes) {
+        int r = run_pass_compressed<R>(s, gates, pp);
+        if (r) return r;
+    }
+    return SV_OK;
+}
+
+// --------------------------------------------------------------- init
+template <typename R>
+int init_state(sv_state* s)
+{
+    cudaError_t e;
+    const uint64_t init = s->cfg.init_index;
+    if (s->mode == SV_UNCOMPRESSED) {
+        if ((e = launch_fill_basis<R>(s->d_state, 1ull << s->n, (int64_t)init, s->s_comp)))
+            return cuda_fail(s, e, "fill");
+        s->st.kernel_launches++;
+        s->st.norm2 = 1.0;
+        return wait_stream(s, s->s_comp);
+    }
+    const int c = s->c;
+    const uint64_t nchunks = 1ull << s->nh;
+    const uint64_t cs = 1ull << c;
+    // encode one all-zero chunk (slot 0) and the chunk holding the basis amplitude (slot 1)
+    const int nenc = nchunks > 1 ? 2 : 1;
+    if ((e = launch_fill_basis<R>(s->d_amps, cs * nenc, (int64_t)(nenc == 2 ? cs + (init & (cs - 1)) : init),
+                                  s->s_comp)))
+        return cuda_fail(s, e, "fill");
+    int launches = 1;
+    if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, nenc, s->d_out[0], s->stride, s->d_sparse,
+                              s->d_blocksq, s->d_co[0], s->d_err, s->s_comp, &launches)))
+        return cuda_fail(s, e, "encode");
+    s->st.kernel_launches += launches;
+    if ((e = cudaMemcpyAsync(s->h_co[0], s->d_co[0], sizeof(ChunkOut) * nenc, cudaMemcpyDeviceToHost, s->s_comp)))
+        return cuda_fail(s, e, "D2H sizes");
+    int r = wait_stream(s, s->s_comp);
+    if (r) return r;
+    if ((r = check_device_error(s))) return r;
+    std::vector<std::vector<uint8_t>> streams(nenc);
+    for (int j = 0; j < nenc; j++) {
+        streams[j].resize(s->h_co[0][j].bytes);
+        if ((e = cudaMemcpy(streams[j].data(), s->d_out[0] + (size_t)j * s->stride, streams[j].size(),
+                            cudaMemcpyDeviceToHost)))
+            return cuda_fail(s, e, "D2H init stream");
+        s->st.bytes_d2h += streams[j].size();
+    }
+    Arena& a = s->arena[s->cur_arena];
+    a.reset();
+    const uint64_t init_chunk = init >> c;
+    uint64_t total = 0;
+    for (uint64_t k = 0; k < nchunks; k++) {
+        const std::vector<uint8_t>& src = (nenc == 1 || k == init_chunk) ? streams[nenc - 1] : streams[0];
+        uint8_t* dst = arena_alloc(s, a, src.size());
+        if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
+        std::memcpy(dst, src.data(), src.size());
+        s->cur[k] = {dst, src.size()};
+        total += src.size();
+    }
+    s->st.compressed_bytes = total;
+    s->st.norm2 = 1.0;
+    s->scale = 1.0;
+    return SV_OK;
+}
+
+// ----------------------------------------------------- read-only staging
+// Stage chunks ks[0..m) (m <= 2^gmax) into d_amps slots 0..m-1 (decoded).
+template <typename R>
+int stage_chunks(sv_state* s, const std::vector<uint64_t>& ks)
+{
+    GroupIn gin{};
+    cudaError_t e;
+    const int m = (int)ks.size();
+    for (int j = 0; j < m; j++) {
+        const ChunkRef& cr = s->cur[ks[j]];
+        gin.bytes[j] = (uint32_t)cr.bytes;
+        if ((e = cudaMemcpyAsync(s->d_in[0] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                 s->s_comp)))
+            return cuda_fail(s, e, "H2D chunk");
+        s->st.bytes_h2d += cr.bytes;
+    }
+    if ((e = launch_decode<R>(s->d_in[0], s->stride, s->c, s->dtype, m, gin, s->d_amps, s->scale, s->d_err,
+                              s->s_comp)))
+        return cuda_fail(s, e, "decode");
+    s->st.kernel_launches++;
+    return SV_OK;
+}
+
+static inline uint64_t to_physical(const std::vector<int>& perm, uint64_t logical)
+{
+    uint64_t p = 0;
+    for (size_t q = 0; q < perm.size(); q++)
+        if ((logical >> q) & 1) p |= 1ull << perm[q];
+    return p;
+}
+
+template <typename R>
+int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
+{
+    const uint64_t dim = 1ull << s->n;
+    for (size_t i = 0; i < m; i++)
+        if (idx[i] >= dim) return fail(s, SV_ERR_ARG, "amplitude index out of range");
+    if (m == 0) return SV_OK;
+    const size_t batch = std::min<size_t>(m, (size_t)1 << 22);
+    uint64_t *d_loc = nullptr, *d_dst = nullptr;
+    double* d_out = nullptr;
+    cudaError_t e;
+    int r = SV_OK;
+    if ((e = cudaMalloc(&d_loc, batch * 8)) || (e = cudaMalloc(&d_dst, batch * 8)) ||
+        (e = cudaMalloc(&d_out, batch * 16))) {
+        cudaFree(d_loc); cudaFree(d_dst); cudaFree(d_out);
+        return cuda_fail(s, e, "cudaMalloc(gather)");
+    }
+    std::vector<uint64_t> loc, dst;
+    for (size_t b0 = 0; b0 < m && !r; b0 += batch) {
+        const size_t nb = std::min(batch, m - b0);
+        if (s->mode == SV_UNCOMPRESSED) {
+            loc.resize(nb);
+            dst.resize(nb);
+            for (size_t i = 0; i < nb; i++) { loc[i] = to_physical(s->perm, idx[b0 + i]); dst[i] = i; }
+            if ((e = cudaMemcpyAsync(d_loc, loc.data(), nb * 8, cudaMemcpyHostToDevice, s->s_comp)) ||
+                (e = cudaMemcpyAsync(d_dst, dst.data(), nb * 8, cudaMemcpyHostToDevice, s->s_comp)) ||
+                (e = launch_gather<R>(s->d_state, d_loc, d_dst, nb, d_out, s->s_comp))) {
+                r = cuda_fail(s, e, "gather");
+                break;
+            }
+            s->st.kernel_launches++;
+        } else {
+            // bucket requests by chunk
+            std::vector<std::pair<uint64_t, uint64_t>> req(nb);  // (physical, position)
+            for (size_t i = 0; i < nb; i++) req[i] = {to_physical(s->perm, idx[b0 + i]), i};
+            std::sort(req.begin(), req.end());
+            const int gcap = 1 << std::min(s->gmax, s->nh);
+            size_t i = 0;
+            while (i < nb && !r) {
+                std::vector<uint64_t> ks;
+                loc.clear();
+                dst.clear();
+                while (i < nb) {
+                    const uint64_t k = req[i].first >> s->c;
+                    if (ks.empty() || ks.back() != k) {
+                        if ((int)ks.size() == gcap) break;
+                        ks.push_back(k);
+                    }
+                    loc.push_back(((uint64_t)(ks.size() - 1) << s->c) | (req[i].first & ((1ull << s->c) - 1)));
+                    dst.push_back(req[i].second);
+                    i++;
+                }
+                if ((r = stage_chunks<R>(s, ks))) break;
+                if ((e = cudaMemcpyAsync(d_loc, loc.data(), loc.size() * 8, cudaMemcpyHostToDevice, s->s_comp)) ||
+                    (e = cudaMemcpyAsync(d_dst, dst.data(), dst.size() * 8, cudaMemcpyHostToDevice, s->s_comp)) ||
+                    (e = launch_gather<R>(s->d_amps, d_loc, d_dst, loc.size(), d_out, s->s_comp))) {
+                    r = cuda_fail(s, e, "gather");
+                    break;
+                }
+                s->st.kernel_launches++;
+                // loc/dst are host vectors reused next round: wait before overwriting them
+                if ((r = wait_stream(s, s->s_comp))) break;
+            }
+        }
+        if (r) break;
+        if ((e = cudaMemcpyAsync(out + 2 * b0, d_out, nb * 16, cudaMemcpyDeviceToHost, s->s_comp))) {
+            r = cuda_fail(s, e, "D2H amplitudes");
+            break;
+        }
+        r = wait_stream(s, s->s_comp);
+    }
+    if (!r) r = check_device_error(s);
+    cudaFree(d_loc);
+    cudaFree(d_dst);
+    cudaFree(d_out);
+    return r;
+}
+
+// ------------------------------------------------------------ expectation
+static PauliDev pauli_dev(const sv_pauli_term& t, uint64_t xl, uint64_t zl, uint64_t zg, double scale)
+{
+    PauliDev p{};
+    p.coeff = t.coeff * scale;
+    p.xl = xl;
+    p.zl = zl;
+    p.zg = zg;
+    p.ny = __builtin_popcountll(t.xmask & t.zmask) & 3;
+    return p;
+}
+
+static uint64_t mask_to_physical(const std::vector<int>& perm, uint64_t m) { return to_physical(perm, m); }
+
+template <typename R>
+int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re)
+{
+    *out_re = 0;
+    if (nterms == 0) return SV_OK;
+    const uint64_t dim_mask = (s->n >= 64) ? ~0ull : ((1ull << s->n) - 1);
+    for (size_t i = 0; i < nterms; i++)
+        if ((terms[i].xmask | terms[i].zmask) & ~dim_mask) return fail(s, SV_ERR_ARG, "Pauli mask out of range");
+    // physical masks
+    std::vector<sv_pauli_term> phys(nterms);
+    for (size_t i = 0; i < nterms; i++) {
+        phys[i] = terms[i];
+        phys[i].xmask = mask_to_physical(s->perm, terms[i].xmask);
+        phys[i].zmask = mask_to_physical(s->perm, terms[i].zmask);
+    }
+    cudaError_t e;
+    const int c = s->mode == SV_UNCOMPRESSED ? s->n : s->c;
+    const uint64_t lowmask = (c >= 64) ? ~0ull : ((1ull << c) - 1);
+    const int nblocks = reduce_blocks_for(1ull << c);
+    // group by the high part of x
+    std::vector<uint64_t> xhs;
+    for (auto& t : phys) xhs.push_back(t.xmask >> c);
+    std::sort(xhs.begin(), xhs.end());
+    xhs.erase(std::unique(xhs.begin(), xhs.end()), xhs.end());
+    PauliDev* d_terms = nullptr;
+    double *d_part = nullptr, *d_acc = nullptr;
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * nterms)) ||
+        (e = cudaMalloc(&d_part, sizeof(double) * nterms * nblocks)) || (e = cudaMalloc(&d_acc, sizeof(double) * nterms))) {
+        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+        return cuda_fail(s, e, "cudaMalloc(expect)");
+    }
+    int r = SV_OK;
+    cudaMemsetAsync(d_acc, 0, sizeof(double) * nterms, s->s_comp);
+    std::vector<PauliDev> hd;
+    size_t acc_off = 0;
+    std::vector<std::pair<size_t, size_t>> acc_map;  // (term index, slot in d_acc)
+    for (uint64_t xh : xhs) {
+        hd.clear();
+        std::vector<size_t> tid;
+        const double pair_scale = xh ? 2.0 : 1.0;
+        for (size_t i = 0; i < nterms; i++) {
+            if ((phys[i].xmask >> c) != xh) continue;
+            hd.push_back(pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, phys[i].zmask & ~lowmask,
+                                   pair_scale));
+            tid.push_back(i);
+        }
+        const int nt = (int)hd.size();
+        if ((e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * nt, cudaMemcpyHostToDevice, s->s_comp))) {
+            r = cuda_fail(s, e, "upload terms");
+            break;
+        }
+        if (s->mode == SV_UNCOMPRESSED) {
+            if ((e = launch_pauli_partials<R>(s->d_state, s->d_state, s->n, 0, d_terms, nt, d_part, nblocks, s->s_comp)) ||
+                (e = launch_sum_partials(d_part, nt, nblocks, d_acc + acc_off, s->s_comp))) {
+                r = cuda_fail(s, e, "pauli");
+                break;
+            }
+            s->st.kernel_launches += 2;
+        } else {
+            // units: chunk k (xh == 0) or pairs (k, k ^ xh) with k < k ^ xh
+            const uint64_t nch = 1ull << s->nh;
+            std::vector<uint64_t> units;
+            for (uint64_t k = 0; k < nch; k++)
+                if (xh == 0 || k < (k ^ xh)) units.push_back(k);
+            const size_t per = xh ? (size_t)(1 << (s->gmax - 1)) : (size_t)(1 << s->gmax);
+            for (size_t u0 = 0; u0 < units.size() && !r; u0 += per) {
+                const size_t nu = std::min(per, units.size() - u0);
+                std::vector<uint64_t> ks;
+                for (size_t u = 0; u < nu; u++) {
+                    ks.push_back(units[u0 + u]);
+                    if (xh) ks.push_back(units[u0 + u] ^ xh);
+                }
+                if ((r = stage_chunks<R>(s, ks))) break;
+                const size_t cb = sizeof(R) * 2ull << s->c;
+                for (size_t u = 0; u < nu; u++) {
+                    const uint8_t* A = static_cast<const uint8_t*>(s->d_amps) + (xh ? 2 * u : u) * cb;
+                    const uint8_t* B = xh ? A + cb : A;
+                    if ((e = launch_pauli_partials<R>(A, B, s->c, units[u0 + u] << s->c, d_terms, nt, d_part, nblocks,
+                                                      s->s_comp)) ||
+                        (e = launch_sum_partials(d_part, nt, nblocks, d_acc + acc_off, s->s_comp))) {
+                        r = cuda_fail(s, e, "pauli");
+                        break;
+                    }
+                    s->st.kernel_launches += 2;
+                }
+            }
+            if (r) break;
+        }
+        for (int j = 0; j < nt; j++) acc_map.push_back({tid[j], acc_off + j});
+        acc_off += nt;
+        // hd is reused next round: the upload above is stream-ordered before the next upload
+    }
+    if (!r) {
+        std::vector<double> acc(nterms);
+        if ((e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * nterms, cudaMemcpyDeviceToHost, s->s_comp)))
+            r = cuda_fail(s, e, "D2H expect");
+        else if (!(r = wait_stream(s, s->s_comp))) {
+            std::vector<double> per_term(nterms, 0.0);
+            for (auto& pm : acc_map) per_term[pm.first] = acc[pm.second];
+            double sum = 0;
+            for (size_t i = 0; i < nterms; i++) sum += per_term[i];
+            *out_re = sum;
+        }
+    }
+    if (!r) r = check_device_error(s);
+    cudaFree(d_terms);
+    cudaFree(d_part);
+    cudaFree(d_acc);
+    return r;
+}
+
+// --------------------------------------------------------------- adjoint
+template <typename R>
+int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
+                      size_t nterms, double* energy, double* grad)
+{
+    cudaError_t e;
+    const int n = s->n;
+    const size_t vbytes = sizeof(R) * 2ull << n;
+    if (!s->d_lam) {
+        if ((e = cudaMalloc(&s->d_lam, vbytes))) return cuda_fail(s, e, "cudaMalloc(lambda)");
+    }
+    int r = init_state<R>(s);
+    if (r) return r;
+    std::vector<int> ids(gates.size());
+    for (size_t i = 0; i < gates.size(); i++) ids[i] = (int)i;
+    if ((r = run_pass_uncompressed<R>(s, s->d_state, gates, ids))) return r;
+    // lambda = H psi (physical masks)
+    std::vector<PauliDev> hd;
+    for (size_t i = 0; i < nterms; i++) {
+        sv_pauli_term t = H[i];
+        const uint64_t x = mask_to_physical(s->perm, t.xmask), z = mask_to_physical(s->perm, t.zmask);
+        hd.push_back(pauli_dev(t, x, z, 0, 1.0));
+    }
+    PauliDev* d_terms = nullptr;
+    double *d_part = nullptr, *d_acc = nullptr, *d_gpart = nullptr;
+    const int nblocks = reduce_blocks_for(1ull << n);
+    // reverse sweep plan
+    std::vector<int> rids(gates.size());
+    for (size_t i = 0; i < gates.size(); i++) rids[i] = (int)(gates.size() - 1 - i);
+    std::vector<PGate> inv(gates.size());
+    for (size_t i = 0; i < gates.size(); i++) {
+        inv[i] = gates[i];
+        const int K = 1 << gates[i].nt;
+        for (int a = 0; a < K; a++)
+            for (int b = 0; b < K; b++) inv[i].m[a * K + b] = std::conj(gates[i].m[b * K + a]);
+    }
+    const int L = n;
+    int t, l;
+    tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
+    const std::vector<int> noS;
+    const std::vector<HOp> hops = local_ops(inv, rids, L, noS, true);
+    const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
+    std::vector<TileDesc> tds;
+    std::vector<int> offs, cnts, slot_params;
+    std::vector<DevOp<R>> ops;
+    std::vector<int> slot_base;
+    int max_slots = 0;
+    for (const SubPlan& sp : subs) {
+        TileDesc td = tile_desc(sp.T, L, t, l);
+        tds.push_back(td);
+        offs.push_back((int)ops.size());
+        slot_base.push_back((int)slot_params.size());
+        int base = 0;
+        dev_ops<R>(sp, td, ops, &base, &slot_params);
+        max_slots = std::max(max_slots, base);
+        cnts.push_back((int)ops.size() - offs.back());
+    }
+    const uint64_t ntiles = 1ull << (L - t);
+    const size_t nslots_total = slot_params.size();
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms))) ||
+        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
+        (e = cudaMalloc(&d_acc, sizeof(double) * (1 + std::max<size_t>(1, nslots_total)))) ||
+        (e = cudaMalloc(&d_gpart, sizeof(double) * std::max(1, max_slots) * ntiles))) {
+        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc); cudaFree(d_gpart);
+        return cuda_fail(s, e, "cudaMalloc(grad)");
+    }
+    do {
+        if (nterms &&
+            (e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * nterms, cudaMemcpyHostToDevice, s->s_comp))) {
+            r = cuda_fail(s, e, "upload H");
+            break;
+        }
+        if ((e = launch_hamiltonian<R>(s->d_state, s->d_lam, n, d_terms, (int)nterms, s->s_comp))) {
+            r = cuda_fail(s, e, "hamiltonian");
+            break;
+        }
+        cudaMemsetAsync(d_acc, 0, sizeof(double) * (1 + nslots_total), s->s_comp);
+        if ((e = launch_dot<R>(s->d_state, s->d_lam, 1ull << n, d_part, nblocks, s->s_comp)) ||
+            (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp))) {
+            r = cuda_fail(s, e, "energy");
+            break;
+        }
+        s->st.kernel_launches += 3;
+        if ((r = upload_ops<R>(s, ops))) break;
+        const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
+        for (size_t i = 0; i < tds.size(); i++) {
+            if ((e = launch_adjoint<R>(s->d_state, s->d_lam, tds[i], d_ops + offs[i], cnts[i], 0, d_gpart, ntiles,
+                                       s->s_comp))) {
+                r = cuda_fail(s, e, "adjoint");
+                break;
+            }
+            s->st.kernel_launches++;
+            const int nsl = (i + 1 < tds.size() ? slot_base[i + 1] : (int)nslots_total) - slot_base[i];
+            if (nsl > 0) {
+                if ((e = launch_sum_partials(d_gpart, nsl, (int)ntiles, d_acc + 1 + slot_base[i], s->s_comp))) {
+                    r = cuda_fail(s, e, "grad reduce");
+                    break;
+                }
+                s->st.kernel_launches++;
+            }
+        }
+        if (r) break;
+        s->st.subpasses += tds.size();
+        std::vector<double> acc(1 + nslots_total);
+        if ((e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s->s_comp))) {
+            r = cuda_fail(s, e, "D2H grad");
+            break;
+        }
+        if ((r = wait_stream(s, s->s_comp))) break;
+        *energy = acc[0];
+        for (size_t p = 0; p < nparams; p++) grad[p] = 0;
+        for (size_t j = 0; j < nslots_total; j++) grad[slot_params[j]] += acc[1 + j];
+    } while (0);
+    cudaFree(d_terms);
+    cudaFree(d_part);
+    cudaFree(d_acc);
+    cudaFree(d_gpart);
+    if (!r) r = check_device_error(s);
+    return r;
+}
+
+template int apply_circuit<float>(sv_state*, const std::vector<PGate>&);
+template int apply_circuit<double>(sv_state*, const std::vector<PGate>&);
+template int init_state<float>(sv_state*);
+template int init_state<double>(sv_state*);
+template int amplitudes<float>(sv_state*, const uint64_t*, size_t, double*);
+template int amplitudes<double>(sv_state*, const uint64_t*, size_t, double*);
+template int expect<float>(sv_state*, const sv_pauli_term*, size_t, double*);
+template int expect<double>(sv_state*, const sv_pauli_term*, size_t, double*);
+template int grad_uncompressed<float>(sv_state*, const std::vector<PGate>&, size_t, const sv_pauli_term*, size_t,
+                                      double*, double*);
+template int grad_uncompressed<double>(sv_state*, const std::vector<PGate>&, size_t, const sv_pauli_term*, size_t,
+                                       double*, double*);
+
+}  // namespace sv

@@ -1,0 +1,27 @@
+// engine.h -- pass execution entry points used by the C ABI (api.cpp).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+namespace sv {
+
+int fail(sv_state* s, int code, const std::string& msg);
+int cuda_fail(sv_state* s, cudaError_t e, const char* where);
+int wait_stream(sv_state* s, cudaStream_t st);
+int sync_all(sv_state* s);
+int check_device_error(sv_state* s);
+void arena_free(Arena& a);
+void tile_shape(int L, int tq, int lq, int& t, int& l);
+
+template <typename R> int init_state(sv_state* s);
+template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& gates);
+template <typename R> int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out);
+template <typename R> int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
+template <typename R>
+int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
+                      size_t nterms, double* energy, double* grad);
+
+}  // namespace sv

@@ -1,0 +1,331 @@
+// plan.cpp -- circuit partitioning for the compressed state-vector method.
+//
+// MEMQSim (Sec. 2, "Offline stage") partitions the input circuit into stages
+// and the state vector into independently compressed chunks; the online stage
+// sweeps all chunks once per stage. The paper gives no partitioning
+// algorithm. Here a stage ("pass") is a set of gates whose mixing qubits --
+// the targets of non-diagonal gates -- lie in the c low (intra-chunk) qubits
+// plus at most g_max staged high qubits S; diagonal gates and controls never
+// mix, so they fit any pass. Inside a pass, the same greedy rule splits the
+// gates into tile sub-passes whose mixing qubits fit one on-chip tile.
+#include <algorithm>
+#include <cmath>
+
+#include "runtime.h"
+
+namespace sv {
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+bool kind_is_diag(int kind)
+{
+    switch (kind) {
+        case SV_GATE_Z: case SV_GATE_S: case SV_GATE_SDG: case SV_GATE_T: case SV_GATE_TDG:
+        case SV_GATE_RZ: case SV_GATE_P: case SV_GATE_CZ: case SV_GATE_CP:
+            return true;
+        default:
+            return false;
+    }
+}
+
+void gate_matrix(int kind, double theta, const double* custom, int nt, cd* m)
+{
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    const cd I(0, 1);
+    for (int i = 0; i < 16; i++) m[i] = 0;
+    switch (kind) {
+        case SV_GATE_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; break;
+        case SV_GATE_X: case SV_GATE_CNOT: m[1] = 1; m[2] = 1; break;
+        case SV_GATE_Y: m[1] = -I; m[2] = I; break;
+        case SV_GATE_Z: case SV_GATE_CZ: m[0] = 1; m[3] = -1; break;
+        case SV_GATE_S: m[0] = 1; m[3] = I; break;
+        case SV_GATE_SDG: m[0] = 1; m[3] = -I; break;
+        case SV_GATE_T: m[0] = 1; m[3] = cd(r2, r2); break;
+        case SV_GATE_TDG: m[0] = 1; m[3] = cd(r2, -r2); break;
+        case SV_GATE_RX: m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
+        case SV_GATE_RY: m[0] = c; m[1] = -s; m[2] = s; m[3] = c; break;
+        case SV_GATE_RZ: m[0] = cd(c, -s); m[3] = cd(c, s); break;
+        case SV_GATE_P: case SV_GATE_CP: m[0] = 1; m[3] = cd(std::cos(theta), std::sin(theta)); break;
+        case SV_GATE_SWAP: m[0] = 1; m[6] = 1; m[9] = 1; m[15] = 1; break;
+        case SV_GATE_CUSTOM: {
+            const int K = 1 << nt;
+            for (int i = 0; i < K * K; i++) m[i] = cd(custom[2 * i], custom[2 * i + 1]);
+            break;
+        }
+        default: break;
+    }
+}
+
+static uint64_t qubit_mask(const PGate& g)
+{
+    uint64_t m = 0;
+    for (int i = 0; i < g.nt; i++) m |= 1ull << g.t[i];
+    for (int i = 0; i < g.nc; i++) m |= 1ull << g.c[i];
+    return m;
+}
+
+static uint64_t mixing_mask(const PGate& g)
+{
+    if (g.diag) return 0;
+    uint64_t m = 0;
+    for (int i = 0; i < g.nt; i++) m |= 1ull << g.t[i];
+    return m;
+}
+
+std::vector<PassPlan> plan_passes(const std::vector<PGate>& g, int n, int c, int gmax)
+{
+    std::vector<PassPlan> passes;
+    const uint64_t high = (n > c) ? (((n >= 64) ? ~0ull : ((1ull << n) - 1)) & ~((1ull << c) - 1)) : 0;
+    const int nh = n - c;
+    const int gsz = std::min(gmax, nh);
+    std::vector<int> remaining(g.size());
+    for (size_t i = 0; i < g.size(); i++) remaining[i] = (int)i;
+    while (!remaining.empty()) {
+        uint64_t S = 0, blocked = 0;
+        PassPlan pp;
+        std::vector<int> deferred;
+        for (int gi : remaining) {
+            const uint64_t qm = qubit_mask(g[gi]);
+            if (qm & blocked) {
+                deferred.push_back(gi);
+                blocked |= qm;
+                continue;
+            }
+            const uint64_t need = mixing_mask(g[gi]) & high & ~S;
+            if (popc(S | need) <= gsz) {
+                S |= need;
+                pp.gates.push_back(gi);
+            } else {
+                deferred.push_back(gi);
+                blocked |= qm;
+            }
+        }
+        // stage exactly gsz high qubits: pad with the lowest unused ones
+        for (int q = c; q < n && popc(S) < gsz; q++) S |= 1ull << q;
+        for (int q = c; q < n; q++)
+            if ((S >> q) & 1) pp.S.push_back(q);
+        passes.push_back(std::move(pp));
+        remaining.swap(deferred);
+    }
+    if (passes.empty()) {  // empty circuit: nothing to do
+    }
+    return passes;
+}
+
+std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& ids, int c,
+                           const std::vector<int>& S, bool adjoint)
+{
+    auto loc = [&](int q) -> int {
+        if (q < c) return q;
+        for (size_t j = 0; j < S.size(); j++)
+            if (S[j] == q) return c + (int)j;
+        return -1;
+    };
+    std::vector<HOp> out;
+    out.reserve(ids.size());
+    for (int gi : ids) {
+        const PGate& G = g[gi];
+        HOp op;
+        for (int i = 0; i < G.nc; i++) {
+            const int p = loc(G.c[i]);
+            if (p >= 0) { op.cL |= 1ull << p; op.qL |= 1ull << p; }
+            else { op.cG |= 1ull << G.c[i]; op.qG |= 1ull << G.c[i]; }
+        }
+        if (G.diag) {
+            op.type = OP_DIAG;
+            for (int i = 0; i < G.nt; i++) {
+                const int p = loc(G.t[i]);
+                op.dsrc[i] = p >= 0 ? p : kGlobalSrc + G.t[i];
+                if (p >= 0) op.qL |= 1ull << p;
+                else op.qG |= 1ull << G.t[i];
+            }
+            const int K = 1 << G.nt;
+            for (int v = 0; v < 4; v++) op.m[v] = (v < K) ? G.m[v * K + v] : cd(1, 0);
+            if (G.nt == 1) { op.m[2] = op.m[0]; op.m[3] = op.m[1]; }
+        } else {
+            op.type = G.nt == 1 ? OP_DENSE1 : OP_DENSE2;
+            for (int i = 0; i < G.nt; i++) {
+                const int p = loc(G.t[i]);
+                op.t[i] = p;  // mixing targets are always local in a valid pass
+                op.qL |= 1ull << p;
+                op.mixL |= 1ull << p;
+            }
+            for (int i = 0; i < 16; i++) op.m[i] = G.m[i];
+        }
+        if (adjoint && G.param >= 0) {
+            op.param = G.param;
+            op.gen = G.kind == SV_GATE_RX ? 1 : G.kind == SV_GATE_RY ? 2 : 3;
+            const int p = loc(G.t[0]);
+            op.mixL |= 1ull << p;  // the generator's pairs must be tile-local
+            if (op.type == OP_DIAG) op.t[0] = p;
+        }
+        out.push_back(op);
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------- fusion
+static bool same_controls(const HOp& a, const HOp& b) { return a.cL == b.cL && a.cG == b.cG; }
+
+static void mat2_mul(const cd* b, const cd* a, cd* out)  // out = b * a (2x2)
+{
+    cd r[4];
+    r[0] = b[0] * a[0] + b[1] * a[2];
+    r[1] = b[0] * a[1] + b[1] * a[3];
+    r[2] = b[2] * a[0] + b[3] * a[2];
+    r[3] = b[2] * a[1] + b[3] * a[3];
+    for (int i = 0; i < 4; i++) out[i] = r[i];
+}
+
+// 1-bit diagonal on a local position
+static bool diag1_local(const HOp& o, int& pos)
+{
+    if (o.type != OP_DIAG || o.dsrc[1] != -1 || o.dsrc[0] < 0 || o.dsrc[0] >= kGlobalSrc) return false;
+    pos = o.dsrc[0];
+    return true;
+}
+
+// Merge b (applied after a) into a when both act on the same single target
+// with the same controls; returns false if they cannot be merged.
+static bool try_fuse(HOp& a, const HOp& b)
+{
+    if (a.param >= 0 || b.param >= 0 || !same_controls(a, b)) return false;
+    int pa = -1, pb = -1;
+    const bool ad = diag1_local(a, pa), bd = diag1_local(b, pb);
+    if (a.type == OP_DENSE1) pa = a.t[0];
+    if (b.type == OP_DENSE1) pb = b.t[0];
+    if ((a.type != OP_DENSE1 && !ad) || (b.type != OP_DENSE1 && !bd) || pa != pb) return false;
+    cd A[4], B[4];
+    if (ad) { A[0] = a.m[0]; A[1] = 0; A[2] = 0; A[3] = a.m[1]; }
+    else for (int i = 0; i < 4; i++) A[i] = a.m[i];
+    if (bd) { B[0] = b.m[0]; B[1] = 0; B[2] = 0; B[3] = b.m[1]; }
+    else for (int i = 0; i < 4; i++) B[i] = b.m[i];
+    cd M[4];
+    mat2_mul(B, A, M);
+    if (ad && bd) {
+        a.m[0] = M[0]; a.m[1] = M[3]; a.m[2] = M[0]; a.m[3] = M[3];
+    } else {
+        a.type = OP_DENSE1;
+        a.t[0] = pa;
+        a.dsrc[0] = a.dsrc[1] = -1;
+        a.mixL |= 1ull << pa;
+        for (int i = 0; i < 4; i++) a.m[i] = M[i];
+    }
+    a.qL |= b.qL;
+    a.qG |= b.qG;
+    return true;
+}
+
+std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse)
+{
+    std::vector<SubPlan> subs;
+    const uint64_t low = (l >= 64) ? ~0ull : ((1ull << l) - 1);
+    std::vector<int> remaining(ops.size());
+    for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
+    while (!remaining.empty()) {
+        uint64_t T = low, bL = 0, bG = 0;
+        SubPlan sp;
+        std::vector<int> deferred;
+        for (int oi : remaining) {
+            const HOp& o = ops[oi];
+            if ((o.qL & bL) || (o.qG & bG)) {
+                deferred.push_back(oi);
+                bL |= o.qL;
+                bG |= o.qG;
+                continue;
+            }
+            const uint64_t need = o.mixL & ~T;
+            if (popc(T | need) <= t) {
+                T |= need;
+                if (fuse && !sp.ops.empty() && try_fuse(sp.ops.back(), o)) continue;
+                sp.ops.push_back(o);
+            } else {
+                deferred.push_back(oi);
+                bL |= o.qL;
+                bG |= o.qG;
+            }
+        }
+        if (sp.ops.empty() && !deferred.empty() && deferred.size() == remaining.size()) {
+            // no op fits a tile (cannot happen when t - l >= 2): stop instead of looping
+            subs.clear();
+            return subs;
+        }
+        for (int p = 0; p < L && popc(T) < t; p++) T |= 1ull << p;
+        sp.T = T;
+        subs.push_back(std::move(sp));
+        remaining.swap(deferred);
+    }
+    return subs;
+}
+
+TileDesc tile_desc(uint64_t T, int L, int t, int l)
+{
+    TileDesc td{};
+    td.t = t;
+    td.l = l;
+    td.L = L;
+    int h = 0, o = 0;
+    for (int p = 0; p < L; p++) {
+        if ((T >> p) & 1) {
+            if (p >= l) td.hpos[h++] = (int8_t)p;
+        } else {
+            td.opos[o++] = (int8_t)p;
+        }
+    }
+    td.nout = o;
+    return td;
+}
+
+template <typename R>
+void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, int* grad_slot_base,
+             std::vector<int>* slot_params)
+{
+    // local position -> tile bit
+    int tpos[64];
+    for (int p = 0; p < 64; p++) tpos[p] = -1;
+    for (int p = 0; p < td.l; p++) tpos[p] = p;
+    for (int i = 0; i < td.t - td.l; i++) tpos[td.hpos[i]] = td.l + i;
+    for (const HOp& o : sp.ops) {
+        DevOp<R> d{};
+        d.type = o.type;
+        d.grad_slot = -1;
+        d.gen = 0;
+        d.d0 = d.d1 = SRC_NONE;
+        for (int p = 0; p < 64; p++) {
+            if (!((o.cL >> p) & 1)) continue;
+            if (tpos[p] >= 0) d.cmask_tile |= 1u << tpos[p];
+            else d.cmask_local |= 1ull << p;
+        }
+        d.cmask_global = o.cG;
+        if (o.type == OP_DIAG) {
+            int32_t* dst[2] = {&d.d0, &d.d1};
+            for (int i = 0; i < 2; i++) {
+                const int s = o.dsrc[i];
+                if (s < 0) *dst[i] = SRC_NONE;
+                else if (s >= kGlobalSrc) *dst[i] = SRC_GLOBAL + (s - kGlobalSrc);
+                else if (tpos[s] >= 0) *dst[i] = SRC_TILE + tpos[s];
+                else *dst[i] = SRC_LOCAL + s;
+            }
+            for (int v = 0; v < 4; v++) { d.m[2 * v] = (R)o.m[v].real(); d.m[2 * v + 1] = (R)o.m[v].imag(); }
+            if (o.param >= 0) d.t0 = tpos[o.t[0]];
+        } else {
+            d.t0 = tpos[o.t[0]];
+            d.t1 = o.type == OP_DENSE2 ? tpos[o.t[1]] : 0;
+            const int K = o.type == OP_DENSE2 ? 4 : 2;
+            for (int i = 0; i < K * K; i++) { d.m[2 * i] = (R)o.m[i].real(); d.m[2 * i + 1] = (R)o.m[i].imag(); }
+        }
+        if (o.param >= 0 && grad_slot_base) {
+            d.grad_slot = (*grad_slot_base)++;
+            d.gen = o.gen;
+            if (slot_params) slot_params->push_back(o.param);
+        }
+        out.push_back(d);
+    }
+}
+
+template void dev_ops<float>(const SubPlan&, const TileDesc&, std::vector<DevOp<float>>&, int*, std::vector<int>*);
+template void dev_ops<double>(const SubPlan&, const TileDesc&, std::vector<DevOp<double>>&, int*,
+                              std::vector<int>*);
+
+}  // namespace sv

@@ -1,0 +1,229 @@
+// reduce.cu -- FP64 reductions over staged amplitudes: Pauli-sum expectation
+// values, <a|b> dot products, the amplitude gather behind sv_amplitudes, and
+// lambda = H psi for the adjoint gradient.
+//
+// Reductions are deterministic: each CTA covers a fixed index range, each
+// thread first sums a few products in the amplitude precision, the per-thread
+// sums are added in FP64 in a fixed tree, and per-CTA partials are summed in
+// FP64 in index order by a final one-CTA-per-term kernel.
+#include <algorithm>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kThreads = 256;
+constexpr int kPerThread = 16;  // products summed in amplitude precision before FP64
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; w++) s += red[w];
+    return s;
+}
+
+// partials[t * nblocks + block] = Re sum_{i in block range} conj(B[i ^ xl]) * phase_t(i) * A[i]
+// phase_t(i) = i^ny * (-1)^(popcount(i & zl) + popcount(gbase & zg)).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pauli(const typename V2<R>::T* __restrict__ A, const typename V2<R>::T* __restrict__ B, uint64_t count,
+        uint64_t gbase, const PauliDev* __restrict__ terms, int nterms, double* __restrict__ partials)
+{
+    __shared__ double red[kThreads / 32];
+    const uint64_t per_block = (count + gridDim.x - 1) / gridDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * per_block;
+    const uint64_t i1 = min(count, i0 + per_block);
+    for (int tt = 0; tt < nterms; tt++) {
+        const PauliDev P = terms[tt];
+        const int gsign = __popcll(gbase & P.zg) & 1;
+        double acc = 0;
+        R sub = (R)0;
+        int cnt = 0;
+        for (uint64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+            const typename V2<R>::T a = A[i], b = B[i ^ P.xl];
+            // Re(conj(b) * a) and Im(conj(b) * a)
+            const R re = b.x * a.x + b.y * a.y;
+            const R im = b.x * a.y - b.y * a.x;
+            R v;
+            switch (P.ny & 3) {  // multiply by i^ny, keep the real part
+                case 0: v = re; break;
+                case 1: v = -im; break;
+                case 2: v = -re; break;
+                default: v = im; break;
+            }
+            if ((__popcll(i & P.zl) + gsign) & 1) v = -v;
+            sub += v;
+            if (++cnt == kPerThread) {
+                acc += (double)sub;
+                sub = (R)0;
+                cnt = 0;
+            }
+        }
+        acc += (double)sub;
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) partials[(uint64_t)tt * gridDim.x + blockIdx.x] = s * P.coeff;
+    }
+}
+
+// out[t] += sum over blocks of partials[t * nblocks + b], one CTA per term, fixed order
+__global__ void __launch_bounds__(kThreads)
+k_sum_partials(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
+{
+    __shared__ double red[kThreads / 32];
+    const int tt = blockIdx.x;
+    double acc = 0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) acc += partials[(uint64_t)tt * nblocks + b];
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) out[tt] += s;
+}
+
+template <typename R>
+__global__ void k_gather(const typename V2<R>::T* __restrict__ amps, const uint64_t* __restrict__ local_idx,
+                         const uint64_t* __restrict__ dest, uint64_t m, double* __restrict__ out)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const typename V2<R>::T a = amps[local_idx[i]];
+        const uint64_t d = dest[i];
+        out[2 * d] = (double)a.x;
+        out[2 * d + 1] = (double)a.y;
+    }
+}
+
+// lam[k] = sum_t coeff_t * phase_t(k ^ x_t) * psi[k ^ x_t]
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_hamiltonian(const typename V2<R>::T* __restrict__ psi, typename V2<R>::T* __restrict__ lam, uint64_t count,
+              const PauliDev* __restrict__ terms, int nterms)
+{
+    using T = typename V2<R>::T;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        R ar = (R)0, ai = (R)0;
+        for (int tt = 0; tt < nterms; tt++) {
+            const PauliDev& P = terms[tt];
+            const uint64_t src = k ^ P.xl;
+            const T v = psi[src];
+            R vr = v.x, vi = v.y, tr;
+            switch (P.ny & 3) {
+                case 1: tr = vr; vr = -vi; vi = tr; break;   // * i
+                case 2: vr = -vr; vi = -vi; break;
+                case 3: tr = vr; vr = vi; vi = -tr; break;   // * -i
+                default: break;
+            }
+            const R c = (__popcll(src & P.zl) & 1) ? (R)(-P.coeff) : (R)P.coeff;
+            ar += c * vr;
+            ai += c * vi;
+        }
+        T o;
+        o.x = ar;
+        o.y = ai;
+        lam[k] = o;
+    }
+}
+
+// partials[block] = Re sum conj(A[i]) B[i] over the block's range (FP64 accumulation)
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_dot(const typename V2<R>::T* __restrict__ A, const typename V2<R>::T* __restrict__ B, uint64_t count,
+      double* __restrict__ partials)
+{
+    __shared__ double red[kThreads / 32];
+    const uint64_t per_block = (count + gridDim.x - 1) / gridDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * per_block;
+    const uint64_t i1 = min(count, i0 + per_block);
+    double acc = 0;
+    R sub = (R)0;
+    int cnt = 0;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+        const typename V2<R>::T a = A[i], b = B[i];
+        sub += a.x * b.x + a.y * b.y;
+        if (++cnt == kPerThread) {
+            acc += (double)sub;
+            sub = (R)0;
+            cnt = 0;
+        }
+    }
+    acc += (double)sub;
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+}  // namespace
+
+int reduce_blocks_for(uint64_t count)
+{
+    const uint64_t want = (count + kThreads * 64 - 1) / (kThreads * 64);
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, 152ull * 8));
+}
+
+template <typename R>
+cudaError_t launch_pauli_partials(const void* A, const void* B, int Lbits, uint64_t gbase, const PauliDev* terms,
+                                  int nterms, double* partials, int nblocks, cudaStream_t st)
+{
+    using T = typename V2<R>::T;
+    k_pauli<R><<<nblocks, kThreads, 0, st>>>(static_cast<const T*>(A), static_cast<const T*>(B), 1ull << Lbits,
+                                            gbase, terms, nterms, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks, double* out, cudaStream_t st)
+{
+    k_sum_partials<<<nterms, kThreads, 0, st>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uint64_t* dest, uint64_t m,
+                          double* out, cudaStream_t st)
+{
+    if (m == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((m + 255) / 256, 152ull * 16);
+    k_gather<R><<<blocks, 256, 0, st>>>(static_cast<const typename V2<R>::T*>(amps), local_idx, dest, m, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev* terms, int nterms,
+                               cudaStream_t st)
+{
+    using T = typename V2<R>::T;
+    const uint64_t count = 1ull << n;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((count + kThreads - 1) / kThreads, 152ull * 32);
+    k_hamiltonian<R><<<blocks, kThreads, 0, st>>>(static_cast<const T*>(psi), static_cast<T*>(lam), count, terms,
+                                                 nterms);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* partials, int nblocks, cudaStream_t st)
+{
+    using T = typename V2<R>::T;
+    k_dot<R><<<nblocks, kThreads, 0, st>>>(static_cast<const T*>(A), static_cast<const T*>(B), count, partials);
+    return cudaGetLastError();
+}
+
+#define SV_INST(R)                                                                                              \
+    template cudaError_t launch_pauli_partials<R>(const void*, const void*, int, uint64_t, const PauliDev*, int, \
+                                                  double*, int, cudaStream_t);                                  \
+    template cudaError_t launch_gather<R>(const void*, const uint64_t*, const uint64_t*, uint64_t, double*,     \
+                                          cudaStream_t);                                                        \
+    template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \
+    template cudaError_t launch_dot<R>(const void*, const void*, uint64_t, double*, int, cudaStream_t);
+SV_INST(float)
+SV_INST(double)
+#undef SV_INST
+
+}  // namespace sv

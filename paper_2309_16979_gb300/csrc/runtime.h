@@ -1,0 +1,140 @@
+// runtime.h -- host runtime of the compressed state-vector simulator: gate
+// representation, pass planning, the pinned compressed chunk store and the
+// state handle behind the C ABI in include/sv.h.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+#include "sv_internal.h"
+
+namespace sv {
+
+using cd = std::complex<double>;
+
+// A validated gate on physical qubits (SWAPs already absorbed).
+struct PGate {
+    int kind = 0;
+    int nt = 1, nc = 0;
+    int t[2] = {0, 0};
+    int c[2] = {0, 0};
+    double theta = 0;
+    int param = -1;
+    bool diag = false;
+    cd m[16];
+};
+
+// Matrix of a gate kind on its targets (row-major 2^nt x 2^nt, FP64).
+void gate_matrix(int kind, double theta, const double* custom, int nt, cd* m);
+bool kind_is_diag(int kind);
+
+// Host op in a pass's local coordinates (before tiling).
+constexpr int kGlobalSrc = 1000;  // diag source >= kGlobalSrc: global qubit (src - kGlobalSrc)
+
+struct HOp {
+    int type = OP_DENSE1;
+    int t[2] = {0, 0};             // local positions of dense targets
+    int dsrc[2] = {-1, -1};        // diag entry-index bit sources: local position or kGlobalSrc + q
+    uint64_t cL = 0, cG = 0;       // controls: local positions / global qubits
+    cd m[16];
+    int param = -1;                // adjoint: parameter index
+    int gen = 0;                   // adjoint: 1 X, 2 Y, 3 Z
+    uint64_t qL = 0, qG = 0;       // every qubit the op touches (for ordering)
+    uint64_t mixL = 0;             // local positions that must be tile bits
+};
+
+struct SubPlan {
+    uint64_t T = 0;                // tile positions (local)
+    std::vector<HOp> ops;
+};
+
+struct PassPlan {
+    std::vector<int> S;            // staged high qubits (physical), ascending
+    std::vector<int> gates;        // indices into the physical gate list
+    std::vector<SubPlan> subs;
+};
+
+// Chunk-level passes: gates in order, each pass holding the gates whose
+// mixing high qubits fit in g_max staged qubits; gates are moved ahead only
+// past gates on disjoint qubits.
+std::vector<PassPlan> plan_passes(const std::vector<PGate>& g, int n, int c, int gmax);
+
+// Translate a pass's gates to local ops: low qubits 0..c-1 keep their
+// position, S[j] becomes position c + j, other qubits are global.
+std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& ids, int c,
+                           const std::vector<int>& S, bool adjoint);
+
+// Tile sub-passes over L local positions (tiles of t qubits containing 0..l-1).
+std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse);
+
+// Tile descriptor and device ops of one sub-pass.
+TileDesc tile_desc(uint64_t T, int L, int t, int l);
+template <typename R>
+void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, int* grad_slot_base,
+             std::vector<int>* slot_params);
+
+// ------------------------------------------------------------- the store
+struct Segment {
+    uint8_t* ptr = nullptr;
+    size_t cap = 0;
+};
+
+struct Arena {
+    std::vector<Segment> segs;
+    size_t si = 0, off = 0;
+    size_t seg_bytes = 0;
+    void reset() { si = 0; off = 0; }
+};
+
+struct ChunkRef {
+    uint8_t* ptr = nullptr;
+    uint64_t bytes = 0;
+};
+
+}  // namespace sv
+
+// The opaque handle of the C ABI.
+struct sv_state {
+    int n = 0, c = 0, dtype = SV_C64, mode = SV_COMPRESSED;
+    double eb = 0;
+    int k = 0;                      // codec step exponent
+    sv_config cfg{};
+    int gmax = 4, tq = 12, lq = 5, nslots = 3;
+    int nh = 0;                     // high qubits n - c
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    // compressed store and staging
+    size_t stride = 0;              // device slot stride per chunk stream
+    std::vector<sv::ChunkRef> cur, nxt;
+    sv::Arena arena[2];
+    int cur_arena = 0;
+    uint64_t pinned_bytes = 0;
+    uint8_t* d_in[4] = {};
+    uint8_t* d_out[4] = {};
+    sv::ChunkOut* d_co[4] = {};
+    sv::ChunkOut* h_co[4] = {};
+    cudaEvent_t ev_h2d[4] = {}, ev_comp[4] = {}, ev_d2h[4] = {};
+    bool slot_used[4] = {};
+    void* d_amps = nullptr;
+    uint32_t* d_sparse = nullptr;
+    unsigned long long* d_blocksq = nullptr;
+    int* d_err = nullptr;
+    // uncompressed state / adjoint vectors
+    void* d_state = nullptr;
+    void* d_lam = nullptr;
+    // device op list
+    void* d_ops = nullptr;
+    size_t ops_cap = 0;
+    // logical -> physical qubit
+    std::vector<int> perm;
+    double scale = 1.0;             // decode scale (renormalisation)
+    sv_stats_t st{};
+    std::string err;
+    // profiling: event pairs around kernel launches on s_comp, read at pass end
+    struct ProfRec { int kind; uint64_t bytes; };
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<ProfRec> prof_rec;
+    size_t prof_used = 0;
+};

@@ -1,0 +1,148 @@
+// sv_internal.h -- types shared by the CUDA kernels and the host runtime.
+//
+// Terminology (MEMQSim, Sec. 2): the state vector is split into chunks of
+// 2^c amplitudes; a pass ("stage") streams every chunk through the GPU once.
+// A pass stages groups of 2^g chunks that differ only in the pass's staged
+// high qubits S, so that gates mixing those qubits act inside one group. In a
+// group, the local index of an amplitude is (slot << c) | low bits; local
+// qubit positions are 0..c-1 for the low qubits and c..c+g-1 for S.
+// Inside a group, a tile is the 2^t amplitudes that vary over t local
+// positions T with all other local bits fixed; a sub-pass sweeps every tile
+// of a group once, applying all of its gates in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace sv {
+
+// ------------------------------------------------------------------ codec
+constexpr uint32_t kMagic = 0x31435653u;  // "SVC1"
+constexpr int kBlock = 256;               // values per codec block
+
+struct CodecLayout {
+    uint32_t nb;      // blocks, both planes
+    uint32_t bpc;     // block pairs (256 amplitudes each) per chunk
+    size_t w_off, a_off, o_off, p_off;
+    size_t max_bytes; // metadata + worst-case payload (32 bits per value)
+};
+
+__host__ __device__ inline size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline CodecLayout codec_layout(int c)
+{
+    CodecLayout L;
+    L.nb = (uint32_t)((2ull << c) >> 8);
+    L.bpc = L.nb / 2;
+    L.w_off = 32;
+    L.a_off = L.w_off + pad16(L.nb);
+    L.o_off = L.a_off + pad16(4ull * L.nb);
+    L.p_off = L.o_off + pad16(4ull * (L.nb + 1));
+    L.max_bytes = L.p_off + (size_t)L.nb * 1024;
+    return L;
+}
+
+// device -> host record of one encoded chunk
+struct ChunkOut {
+    uint64_t bytes;   // stream length
+    uint64_t sumsq;   // sum of q^2 over the chunk (exact; norm^2 = sumsq * Delta^2)
+};
+
+enum : int { kErrCorrupt = 1, kErrRange = 2 };
+
+// --------------------------------------------------------------- gate ops
+enum OpType : int32_t { OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG = 2 };
+
+// A bit source of a diagonal gate's index: tile-local bit, local bit outside
+// the tile, or a global (fixed per group) bit.
+enum : int32_t { SRC_NONE = -1, SRC_TILE = 0, SRC_LOCAL = 64, SRC_GLOBAL = 128 };
+
+template <typename R>
+struct DevOp {
+    int32_t type;          // OpType
+    int32_t t0, t1;        // tile-local bit positions of dense targets
+    int32_t d0, d1;        // diagonal entry-index bit sources (SRC_* + position)
+    uint32_t cmask_tile;   // controls on tile-local bits
+    uint64_t cmask_local;  // controls on local bits outside the tile
+    uint64_t cmask_global; // controls on global bits fixed per group
+    int32_t grad_slot;     // adjoint: >= 0 -> gradient term taken before this op
+    int32_t gen;           // adjoint generator on t0 / d0: 1 = X, 2 = Y, 3 = Z
+    R m[32];               // dense1: 2x2, dense2: 4x4, diag: 4 entries; (re, im) pairs
+};
+
+constexpr int kMaxTileQubits = 13;
+constexpr int kMaxLocalQubits = 48;
+
+struct TileDesc {
+    int32_t t;                  // tile qubits
+    int32_t l;                  // low local bits 0..l-1 always in the tile (rows are 2^l contiguous)
+    int32_t L;                  // local qubits of the buffer (c + g, or n when uncompressed)
+    int32_t nout;               // L - t
+    int8_t hpos[kMaxTileQubits];          // local positions of tile bits l..t-1
+    int8_t opos[kMaxLocalQubits];         // local positions outside the tile (ascending)
+};
+
+// per-group staging parameters for decode
+constexpr int kMaxGroupChunks = 256;
+
+struct GroupIn {
+    uint32_t bytes[kMaxGroupChunks];      // stream length of each staged chunk
+};
+
+// ------------------------------------------------------------ launchers
+// All launchers enqueue on `st` and return cudaGetLastError().
+
+template <typename R>
+cudaError_t launch_decode(const uint8_t* in, size_t stride, int c, int dtype, int nchunks,
+                          const GroupIn& gin, void* amps, double scale, int* err, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks, uint8_t* out,
+                          size_t stride, uint32_t* sparse, unsigned long long* blocksq,
+                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches);
+
+template <typename R>
+cudaError_t launch_apply(void* amps, const TileDesc& td, const DevOp<R>* ops, int nops,
+                         uint64_t gbase, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st);
+
+// sum_t coeff_t <A| P_t |B> pieces; see reduce.cu
+struct PauliDev {
+    double coeff;
+    uint64_t xl;      // x-mask on the buffer's local bits
+    uint64_t zl;      // z-mask on local bits
+    uint64_t zg;      // z-mask on global bits fixed per unit (phase sign)
+    int32_t ny;       // number of Y factors mod 4
+    int32_t pad;
+};
+
+template <typename R>
+cudaError_t launch_pauli_partials(const void* A, const void* B, int Lbits, uint64_t gbase,
+                                  const PauliDev* terms, int nterms, double* partials, int nblocks,
+                                  cudaStream_t st);
+
+cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks, double* out,
+                                cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uint64_t* dest,
+                          uint64_t m, double* out, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev* terms, int nterms,
+                               cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_adjoint(void* psi, void* lam, const TileDesc& td, const DevOp<R>* ops, int nops,
+                           uint64_t gbase, double* gpart, uint64_t tile_stride, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* partials,
+                       int nblocks, cudaStream_t st);
+
+int reduce_blocks_for(uint64_t count);
+
+}  // namespace sv

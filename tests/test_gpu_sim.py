@@ -1,0 +1,216 @@
+"""GPU state-vector path vs the FP64 oracle, through the C ABI.
+
+Uncompressed complex128: relative L2 <= 1e-12. Uncompressed complex64:
+within the FP32 arithmetic bound of gpu_util.fp32_tol. Compressed: within the
+quantisation bound of gpu_util.compressed_l2_bound (one re-quantisation per
+pass, unitaries preserve error norms), plus the closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import compressed_l2_bound, fp32_tol, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def SV():
+    from paper_2309_16979_gb300 import StateVector
+    return StateVector
+
+
+def _circuits(n):
+    return {
+        "ghz": W.ghz(n),
+        "qft": W.qft(n),
+        "layers": W.random_layers(n, 6, seed=4),
+        "clifford": W.random_clifford_rz(n, 6, max(1, n // 3), seed=5),
+        "mixed": W.random_mixed(n, 150, seed=6),
+    }
+
+
+@pytest.mark.parametrize("name", ["ghz", "qft", "layers", "clifford", "mixed"])
+@pytest.mark.parametrize("n", [3, 9, 14])
+def test_uncompressed_c128_matches_oracle(SV, name, n):
+    gates = _circuits(n)[name]
+    init = W.basis_index(n)
+    want = oracle.run(n, gates, init=init)
+    with SV(n, mode="uncompressed", dtype="c128", init_index=init) as s:
+        s.apply(gates)
+        got = s.state()
+    assert rel_l2(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["ghz", "qft", "layers", "clifford", "mixed"])
+@pytest.mark.parametrize("n", [5, 13, 16])
+def test_uncompressed_c64_matches_oracle(SV, name, n):
+    gates = _circuits(n)[name]
+    want = oracle.run(n, gates, init=3)
+    with SV(n, mode="uncompressed", dtype="c64", init_index=3) as s:
+        s.apply(gates)
+        got = s.state()
+    assert rel_l2(got, want) <= fp32_tol(len(gates))
+
+
+@pytest.mark.parametrize("tile", [2, 5, 8, 13])
+def test_tile_sizes_agree(SV, tile):
+    n = 14
+    gates = W.random_mixed(n, 120, seed=9)
+    want = oracle.run(n, gates)
+    with SV(n, mode="uncompressed", dtype="c128", tile_qubits=tile) as s:
+        s.apply(gates)
+        assert rel_l2(s.state(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("name", ["ghz", "qft", "layers", "clifford", "mixed"])
+@pytest.mark.parametrize("n,c,g", [(12, 8, 2), (14, 9, 3), (16, 10, 4), (10, 10, 2)])
+def test_compressed_within_quantisation_bound(SV, dtype, name, n, c, g):
+    gates = _circuits(n)[name]
+    init = W.basis_index(n, seed=7)
+    want = oracle.run(n, gates, init=init)
+    eb = 1e-6
+    with SV(n, c, eb, dtype=dtype, init_index=init, max_group_qubits=g) as s:
+        s.apply(gates)
+        got = s.state()
+        st = s.stats()
+    bound = compressed_l2_bound(n, eb, st["passes"], len(gates), dtype)
+    assert np.linalg.norm(got - want) <= bound, (st["passes"], np.linalg.norm(got - want), bound)
+    assert abs(st["norm2"] - np.vdot(got, got).real) <= 1e-9
+
+
+def test_compressed_config0_workloads(SV):
+    """n=16 complex128, chunk 2^10, eb 1e-6: QFT of a seeded basis state and 20
+    random layers, checked against the oracle."""
+    n = 16
+    x = W.basis_index(n)
+    for gates in (W.qft(n), W.random_layers(n, 20, seed=1)):
+        want = oracle.run(n, gates, init=x)
+        with SV(n, 10, 1e-6, dtype="c128", init_index=x) as s:
+            s.apply(gates)
+            got = s.state()
+            st = s.stats()
+        assert np.linalg.norm(got - want) <= compressed_l2_bound(n, 1e-6, st["passes"], len(gates), "c128")
+        fid = abs(np.vdot(want, got)) ** 2 / np.vdot(got, got).real
+        assert fid > 1 - 1e-3
+
+
+def test_ghz_and_qft_closed_forms_compressed(SV):
+    n, c = 18, 10
+    with SV(n, c, 1e-6, max_group_qubits=3) as s:
+        s.apply(W.ghz(n))
+        a = s.amplitudes([0, (1 << n) - 1, 1, 12345])
+    assert abs(a[0] - 2 ** -0.5) <= 1e-5 and abs(a[1] - 2 ** -0.5) <= 1e-5
+    assert abs(a[2]) == 0 and abs(a[3]) == 0
+    x = W.basis_index(n)
+    with SV(n, c, 1e-7, init_index=x) as s:
+        s.apply(W.qft(n))
+        k = np.array([0, 1, 777, 4095, (1 << n) - 1], dtype=np.uint64)
+        got = s.amplitudes(k)
+        st = s.stats()
+    want = np.exp(2j * np.pi * x * k.astype(float) / (1 << n)) / np.sqrt(1 << n)
+    assert np.abs(got - want).max() <= compressed_l2_bound(n, 1e-7, st["passes"], len(W.qft(n)))
+
+
+def test_swap_relabels_logical_order(SV):
+    n = 10
+    gates = [W.Gate("X", (0,)), W.Gate("H", (3,)), W.Gate("SWAP", (0, 9)), W.Gate("RY", (9,), theta=0.4),
+             W.Gate("SWAP", (3, 5)), W.Gate("CNOT", (2,), (5,))]
+    want = oracle.run(n, gates)
+    for mode in ("uncompressed", "compressed"):
+        with SV(n, 8, 1e-7, mode=mode, dtype="c128") as s:
+            s.apply(gates)
+            assert np.abs(s.state() - want).max() < 1e-6
+
+
+def test_sequential_calls_accumulate(SV):
+    n = 12
+    g1, g2 = W.random_layers(n, 3, seed=1), W.random_layers(n, 3, seed=2)
+    want = oracle.run(n, g1 + g2)
+    with SV(n, 8, 1e-7, dtype="c128", max_group_qubits=2) as s:
+        s.apply(g1)
+        s.apply(g2)
+        st = s.stats()
+        assert np.linalg.norm(s.state() - want) <= compressed_l2_bound(n, 1e-7, st["passes"], 0, "c128")
+        assert st["gates_applied"] == len(g1) + len(g2)
+
+
+@pytest.mark.parametrize("mode", ["uncompressed", "compressed"])
+def test_expectation_values(SV, mode):
+    n = 12
+    gates = W.random_layers(n, 5, seed=3)
+    terms = W.ising(n) + W.random_pauli_sum(n, 20, seed=4)
+    psi = oracle.run(n, gates)
+    with SV(n, 8, 1e-8, mode=mode, dtype="c128", max_group_qubits=2) as s:
+        s.apply(gates)
+        got = s.expect(terms)
+        st = s.stats()
+        # against the oracle on the state the GPU holds (pure reduction check)
+        held = s.state()
+    assert abs(got - oracle.expect(n, held, terms)) <= 1e-12 * sum(abs(t.coeff) for t in terms) + 1e-12
+    # and against the exact state, within what the stored-state error allows
+    err = np.linalg.norm(held - psi)
+    assert abs(got - oracle.expect(n, psi, terms)) <= 2 * err * sum(abs(t.coeff) for t in terms) + 1e-12
+
+
+def test_expectation_closed_forms(SV):
+    n = 14
+    with SV(n, 8, 1e-6, max_group_qubits=2) as s:
+        s.apply(W.ghz(n))
+        assert abs(s.expect([W.PauliTerm(1.0, 0, (1 << 2) | (1 << 13))]) - 1) < 1e-5
+        assert abs(s.expect([W.PauliTerm(1.0, (1 << n) - 1, 0)]) - 1) < 1e-5
+        assert abs(s.expect([W.PauliTerm(1.0, 0, 1 << 11)])) < 1e-5
+
+
+def test_amplitude_indices_and_errors(SV):
+    from paper_2309_16979_gb300 import SvError
+    n = 11
+    gates = W.random_mixed(n, 60, seed=2)
+    want = oracle.run(n, gates)
+    idx = np.random.default_rng(0).integers(0, 1 << n, 500)
+    with SV(n, 8, 1e-7, dtype="c128") as s:
+        s.apply(gates)
+        got = s.amplitudes(idx)
+        assert np.abs(got - want[idx]).max() < 1e-5
+        with pytest.raises(SvError):
+            s.amplitudes([1 << n])
+        with pytest.raises(SvError):
+            s.apply([W.Gate("H", (n,))])
+        # a rejected circuit leaves the state unchanged
+        assert np.abs(s.amplitudes(idx) - got).max() == 0
+
+
+def test_create_argument_errors(SV):
+    from paper_2309_16979_gb300 import SvError
+    with pytest.raises(SvError):
+        SV(12, 7, 1e-6)
+    with pytest.raises(SvError):
+        SV(12, 8, 1e-9)  # complex64 quantiser range
+    with pytest.raises(SvError):
+        SV(12, 8, 1e-6, max_group_qubits=1)
+
+
+def test_pipeline_slots_agree(SV):
+    n = 14
+    gates = W.random_layers(n, 4, seed=8)
+    outs = []
+    for slots in (2, 3, 4):
+        with SV(n, 8, 1e-6, pipeline_slots=slots, max_group_qubits=2) as s:
+            s.apply(gates)
+            outs.append(s.state())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_compressed_store_is_byte_exact_with_oracle_codec(SV):
+    """After a circuit, re-encoding the stored (decoded) state chunk by chunk
+    with the oracle codec gives amplitudes equal to what the GPU decodes."""
+    n, c = 13, 9
+    gates = W.random_layers(n, 3, seed=11)
+    with SV(n, c, 1e-5) as s:
+        s.apply(gates)
+        held = s.state().astype(np.complex64)
+    again = oracle.compress_roundtrip(held, c, 1e-5)
+    assert np.array_equal(again, held)

@@ -1,0 +1,97 @@
+"""Host-side pass planning (sv_plan, no GPU): the execution order is a valid
+reordering of the circuit (checked by running both orders through the FP64
+oracle), every pass's mixing high qubits are staged, and pass counts of
+circuits with a known structure."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def sv():
+    from paper_2309_16979_gb300 import build
+    build.build()
+    import paper_2309_16979_gb300 as sv
+    return sv
+
+
+DIAG = {"Z", "S", "SDG", "T", "TDG", "RZ", "P", "CZ", "CP"}
+
+
+def _mixing(g):
+    if g.kind in DIAG:
+        return set()
+    return set(g.targets)
+
+
+@pytest.mark.parametrize("family", ["layers", "clifford", "mixed", "qft_noswap", "ghz"])
+@pytest.mark.parametrize("n,c,gmax", [(10, 6, 2), (12, 8, 3), (11, 9, 2)])
+def test_plan_is_valid_reordering(sv, family, n, c, gmax):
+    gates = {
+        "layers": W.random_layers(n, 6, seed=2),
+        "clifford": W.random_clifford_rz(n, 6, 3, seed=2),
+        "mixed": [g for g in W.random_mixed(n, 150, seed=2) if g.kind != "SWAP"],
+        "qft_noswap": W.qft(n, swaps=False),
+        "ghz": W.ghz(n),
+    }[family]
+    p = sv.plan(n, c, gates, max_group_qubits=gmax)
+    assert sorted(p["order"]) == list(range(len(gates)))
+    assert p["pass_of"] == sorted(p["pass_of"])
+    nh = n - c
+    for k, gi in enumerate(p["order"]):
+        high_mix = {q for q in _mixing(gates[gi]) if q >= c}
+        staged = p["staged"][p["pass_of"][k]]
+        assert all((staged >> q) & 1 for q in high_mix)
+    for m in p["staged"]:
+        assert bin(m).count("1") == min(gmax, nh)
+        assert m & ((1 << c) - 1) == 0
+    rng = np.random.default_rng(1)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    a = oracle.apply_gates(n, psi0, gates)
+    b = oracle.apply_gates(n, psi0, [gates[i] for i in p["order"]])
+    assert np.abs(a - b).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,c,gmax", [(30, 22, 4), (36, 26, 4), (36, 26, 5), (16, 10, 2), (12, 12, 4)])
+def test_ghz_pass_count(sv, n, c, gmax):
+    p = sv.plan(n, c, W.ghz(n), max_group_qubits=gmax)
+    want = max(1, -(-(n - c) // gmax))
+    assert p["passes"] == want
+
+
+def test_diagonal_gates_never_force_a_pass(sv):
+    n, c = 20, 10
+    gates = [W.Gate("H", (q,)) for q in range(c)]
+    gates += [W.Gate("RZ", (q,), theta=0.1 * q) for q in range(n)]
+    gates += [W.Gate("CZ", (q,), (q + 1,)) for q in range(n - 1)]
+    gates += [W.Gate("CNOT", (q - 10,), (q,)) for q in range(c, n)]  # high controls, low targets
+    p = sv.plan(n, c, gates, max_group_qubits=2)
+    assert p["passes"] == 1
+
+
+def test_swaps_relabel_without_passes(sv):
+    n, c = 14, 8
+    gates = [W.Gate("SWAP", (0, 13)), W.Gate("H", (0,))]   # logical 0 now lives on physical 13
+    p = sv.plan(n, c, gates, max_group_qubits=2)
+    assert p["order"] == [1] and p["passes"] == 1
+    assert (p["staged"][0] >> 13) & 1
+
+
+def test_invalid_gates_rejected(sv):
+    with pytest.raises(sv.SvError):
+        sv.plan(8, 8, [W.Gate("H", (8,))])
+    with pytest.raises(sv.SvError):
+        sv.plan(8, 8, [W.Gate("CNOT", (1,), (1,))])
+    with pytest.raises(sv.SvError):
+        sv.plan(8, 8, [W.Gate("H", (1,))], max_group_qubits=1)
+
+
+def test_subpass_counts_small_tiles_terminate(sv):
+    n = 16
+    gates = W.random_mixed(n, 200, seed=4)
+    gates = [g for g in gates if g.kind != "SWAP"]
+    for tile in (2, 3, 5, 8, 13):
+        p = sv.plan(n, 10, gates, max_group_qubits=3, tile_qubits=tile)
+        assert p["subpasses"] >= p["passes"] >= 1
