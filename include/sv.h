@@ -260,6 +260,40 @@ int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, 
                     size_t cap, size_t* h_nbytes);
 
 /*
+ * sv_codec_encode without any device allocation (the paper has no
+ * counterpart; this is a convenience of this library).
+ *
+ * Who needs it: code that must not allocate GPU memory while it runs -- for
+ * example a process whose device memory is already carved up by another
+ * allocator (so a raw cudaMalloc would fail or fragment it), or a
+ * latency-sensitive loop that cannot afford the device-wide synchronisation
+ * that cudaMalloc / cudaFree imply. sv_codec_encode allocates and frees its
+ * staging buffers on every call; this variant uses one staging area that is
+ * part of the library image instead.
+ *
+ * Limits and behaviour:
+ *   - chunk_qubits must be 8..SV_NOALLOC_MAX_CHUNK_QUBITS (20); larger chunks
+ *     return SV_ERR_ARG. The staging area is a file-scope device array of
+ *     8 MiB + 32 KiB + 256 bytes that every GPU which loads the library keeps
+ *     until the process exits.
+ *   - cap must be >= sv_codec_max_bytes(chunk_qubits) (SV_ERR_ARG otherwise):
+ *     the stream is written in place, with no temporary.
+ *   - The first call on a device looks up the staging area's device address
+ *     for that device (once per device, with that device made current); make
+ *     that first call before any stream capture on that device.
+ *   - All calls share the one staging area, which keeps the last call's
+ *     contents. Calls are synchronous, so calls from one thread never
+ *     overlap; calls from several host threads that overlap on the GPU race
+ *     on the staging area and must be serialised by the caller.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ * Arguments, output and errors are those of sv_codec_encode; the stream is
+ * byte-identical to sv_codec_encode's.
+ */
+#define SV_NOALLOC_MAX_CHUNK_QUBITS 20
+int sv_codec_encode_noalloc(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
+                            size_t cap, size_t* h_nbytes);
+
+/*
  * Decode one chunk stream of nbytes bytes (device) into d_amps (device,
  * 2^chunk_qubits interleaved complex). SV_ERR_CORRUPT if the stream fails
  * validation (magic, sizes, widths <= 32, offsets consistent with widths).

@@ -56,7 +56,8 @@ class SvStats(C.Structure):
 # every entry point declared in include/sv.h
 EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "sv_amplitudes",
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
-           "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan")
+           "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
+           "sv_codec_encode_noalloc")
 
 _lib = None
 
@@ -107,6 +108,8 @@ def load() -> C.CDLL:
     L.sv_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, SZ, P, P, P, C.POINTER(SZ), C.POINTER(SZ),
                           C.POINTER(SZ)]
     L.sv_plan.restype = C.c_int
+    L.sv_codec_encode_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
+    L.sv_codec_encode_noalloc.restype = C.c_int
     _lib = L
     return L
 
