@@ -1,16 +1,20 @@
 #!/usr/bin/env python
 """Throughput of the compressed streamed state-vector path on GB300.
 
-Workload: n = 30 qubits, complex64, chunks of 2^22 amplitudes held
-compressed in pinned host memory (error bound eb), a depth-40 random layered
-circuit (H / RX / RZ on every qubit, then a CNOT on a seeded random pairing
-per layer; 1800 gates). One step = one sv_apply_circuit of that circuit: every
-pass streams all chunks host -> GPU, decodes, applies the fused gates in
-on-chip tiles, re-encodes (with the FP64 norm) and streams them back.
+Default workload (the configuration the headline metric is quoted on):
+n = 30 qubits, complex64, chunks of 2^22 amplitudes held compressed in pinned
+host memory (error bound 1e-6), a depth-40 random layered circuit (H / RX / RZ
+on every qubit, then a CNOT on a seeded random pairing per layer; 1800
+gates), streamed through the GPU in groups of 2^4 chunks. One step = one
+sv_apply_circuit of that circuit: every pass streams all chunks host -> GPU,
+decodes, applies the fused gates in on-chip tiles, re-encodes (with the FP64
+norm) and streams them back.
 
 Metric: amplitude-gate updates per second = gates * 2^n / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload {c1-layers,c1-ghz,c1-qft,c0-qft,c0-layers,
+                              c2-ghz,c2-qft,c2-clifford,c3-grad,c4-grad}
 
 With --gpus N under torchrun every rank runs an independent replica of the
 workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
@@ -35,12 +39,21 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-N_QUBITS = 30
-CHUNK_QUBITS = 22
-DEPTH = 40
-EB = 1e-6
-GROUP_QUBITS = 4
 METRIC = "amp-gate updates/s"
+
+# name -> (n, chunk qubits, eb, dtype, group qubits, circuit, extra)
+WORKLOADS = {
+    "c1-layers": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="layers", depth=40),
+    "c1-ghz": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="ghz"),
+    "c1-qft": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="qft"),
+    "c0-qft": dict(n=16, c=10, eb=1e-6, dtype="c128", group=4, circuit="qft"),
+    "c0-layers": dict(n=16, c=10, eb=1e-6, dtype="c128", group=4, circuit="layers", depth=20),
+    "c2-ghz": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="ghz"),
+    "c2-qft": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="qft"),
+    "c2-clifford": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="clifford", depth=30),
+    "c3-grad": dict(n=24, c=24, eb=0.0, dtype="c64", group=4, circuit="hea", layers=10, mode="uncompressed"),
+    "c4-grad": dict(n=32, c=24, eb=1e-6, dtype="c64", group=4, circuit="hea", layers=8, sets=16),
+}
 
 
 def parse():
@@ -49,17 +62,52 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--eb", type=float, default=EB)
-    p.add_argument("--n", type=int, default=N_QUBITS)
-    p.add_argument("--chunk", type=int, default=CHUNK_QUBITS)
-    p.add_argument("--depth", type=int, default=DEPTH)
-    p.add_argument("--group", type=int, default=GROUP_QUBITS)
+    p.add_argument("--workload", default="c1-layers", choices=sorted(WORKLOADS))
+    p.add_argument("--eb", type=float, default=None)
+    p.add_argument("--n", type=int, default=None)
+    p.add_argument("--chunk", type=int, default=None)
+    p.add_argument("--depth", type=int, default=None)
+    p.add_argument("--group", type=int, default=None)
+    p.add_argument("--sets", type=int, default=None, help="parameter sets for c4-grad")
     p.add_argument("--no-extras", action="store_true", help="skip the comparator and baseline legs")
-    return p.parse_args()
+    a = p.parse_args()
+    w = dict(WORKLOADS[a.workload])
+    for k, v in (("eb", a.eb), ("n", a.n), ("c", a.chunk), ("depth", a.depth), ("group", a.group),
+                 ("sets", a.sets)):
+        if v is not None:
+            w[k] = v
+    if w["c"] > w["n"]:
+        w["c"] = w["n"]
+    a.w = w
+    return a
+
+
+def make_circuit(w, seed=1):
+    n = w["n"]
+    if w["circuit"] == "layers":
+        return W.random_layers(n, w["depth"], seed=seed)
+    if w["circuit"] == "ghz":
+        return W.ghz(n)
+    if w["circuit"] == "qft":
+        return W.qft(n)
+    if w["circuit"] == "clifford":
+        return W.random_clifford_rz(n, w["depth"], 10, seed=seed)
+    raise ValueError(w["circuit"])
+
+
+def describe(w, ngates):
+    if w["circuit"] == "hea":
+        return (f"adjoint gradient, hardware-efficient ansatz n={w['n']}, {w['layers']} layers, 1-D Ising, "
+                f"{w['dtype']}, " + ("uncompressed in HBM" if w.get("mode") == "uncompressed" else
+                                     f"compressed chunks 2^{w['c']}, eb={w['eb']}"))
+    name = {"layers": f"random layered circuit depth {w.get('depth')}", "ghz": "GHZ", "qft": "QFT on a seeded basis state",
+            "clifford": f"random Clifford+RZ depth {w.get('depth')} (40% of slots on the 10 high qubits)"}[w["circuit"]]
+    return (f"{name}, n={w['n']} ({ngates} gates), {w['dtype']}, chunk=2^{w['c']}, eb={w['eb']}, compressed chunks "
+            f"in pinned host DRAM, streamed in groups of 2^{w['group']} chunks")
 
 
 # ------------------------------------------------------------ distributed
-def dist_init(args):
+def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
@@ -180,7 +228,7 @@ def host_link_peak():
                 e1.record(s1)
             e1.synchronize()
             best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-        out[name] = best
+        out[name] = round(best, 1)
     best = 0.0
     for _ in range(3):
         torch.cuda.synchronize()
@@ -191,33 +239,61 @@ def host_link_peak():
             h2.copy_(d2, non_blocking=True)
         torch.cuda.synchronize()
         best = max(best, 2 * nbytes / (time.perf_counter() - t0) / 1e9)
-    out["bidir"] = best
+    out["bidir"] = round(best, 1)
     del h, h2, d, d2
     torch.cuda.empty_cache()
     return out
 
 
-def flush_l2(buf):
-    buf.add_(1)
+def load_traffic(kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", f"traffic_k_{kind}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f).get("bytes_per_launch")
+
+
+def roofline_from_stats(d):
+    hbm_peak, peak_kind = measured_peaks()
+    kinds = {"apply": ("t_apply_s", "n_apply", "alg_bytes_apply"),
+             "decode": ("t_decode_s", "n_decode", "alg_bytes_decode"),
+             "encode": ("t_encode_s", "n_encode", "alg_bytes_encode")}
+    total = sum(d[v[0]] for v in kinds.values())
+    top = max(kinds, key=lambda k: d[kinds[k][0]])
+    tk, nk, bk = kinds[top]
+    avg_s = d[tk] / max(1, d[nk])
+    bytes_per_launch = d[bk] / max(1, d[nk])
+    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": load_traffic(top), "kernel": f"k_{top}",
+            "peak_source": f"{peak_kind} (copy)", "launches": int(d[nk]),
+            "avg_launch_ms": round(avg_s * 1e3, 4), "alg_bytes_per_launch": int(bytes_per_launch),
+            "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, total), 3) for k, v in kinds.items()}}
+
+
+STAT_KEYS = ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d", "bytes_d2h", "t_decode_s", "t_apply_s",
+             "t_encode_s", "n_decode", "n_apply", "n_encode", "alg_bytes_decode", "alg_bytes_apply",
+             "alg_bytes_encode")
 
 
 # ------------------------------------------------------------ our arm
-def run_ours(args, rank, world):
+def run_apply(args, rank, world):
     import torch
     from paper_2309_16979_gb300 import StateVector
 
+    w = args.w
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    n, c = args.n, args.chunk
-    gates = W.random_layers(n, args.depth, seed=1 + rank)
+    n, c = w["n"], w["c"]
+    gates = make_circuit(w, seed=1 + rank)
     terms = W.ising(n, seed=4)
     units_per_step = W.amp_gate_updates(n, gates)
     link = host_link_peak() if rank == 0 else None
-    hbm_peak, peak_kind = measured_peaks()
+    init = W.basis_index(n)
 
-    sim = StateVector(n, c, args.eb, dtype="c64", init_index=W.basis_index(n), max_group_qubits=args.group,
-                      profile=True, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.float32, device="cuda")  # 1 GiB > L2
+    sim = StateVector(n, c, w["eb"], dtype=w["dtype"], init_index=init, max_group_qubits=w["group"], profile=True,
+                      device=dev)
     for _ in range(args.warmup):
         sim.apply(gates)
     s0 = sim.stats()
@@ -239,31 +315,13 @@ def run_ours(args, rank, world):
     s1 = sim.stats()
     t_max, units = reduce_max_sum(world, t_local, units_per_step * args.steps, device="cuda")
     value = units / t_max
-    ms_per_step = t_max / args.steps * 1e3
-
-    d = {k: s1[k] - s0[k] for k in ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d",
-                                     "bytes_d2h", "t_decode_s", "t_apply_s", "t_encode_s", "n_decode",
-                                     "n_apply", "n_encode", "alg_bytes_decode", "alg_bytes_apply",
-                                     "alg_bytes_encode")}
-    kinds = {"apply": ("t_apply_s", "n_apply", "alg_bytes_apply"),
-             "decode": ("t_decode_s", "n_decode", "alg_bytes_decode"),
-             "encode": ("t_encode_s", "n_encode", "alg_bytes_encode")}
-    top = max(kinds, key=lambda k: d[kinds[k][0]])
-    tk, nk, bk = kinds[top]
-    avg_s = d[tk] / max(1, d[nk])
-    bytes_per_launch = d[bk] / max(1, d[nk])
-    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
-    traffic = load_traffic(top)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "kernel": f"k_{top}",
-                "peak_source": peak_kind,
-                "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, sum(d[w[0]] for w in kinds.values())), 3)
-                                         for k, v in kinds.items()}}
+    d = {k: s1[k] - s0[k] for k in STAT_KEYS}
+    roofline = roofline_from_stats(d)
     link_bytes = d["bytes_h2d"] + d["bytes_d2h"]
     per_step = {k: d[k] / args.steps for k in ("passes", "subpasses", "kernel_launches", "bytes_h2d", "bytes_d2h")}
 
-    # e2e: the public call a user makes (apply + read back <H>), host buffers,
-    # every H2D/D2H of the compressed store inside the timed region
+    # e2e: the public calls a user makes (apply + read back <H>), host buffers,
+    # every H2D / D2H of the compressed store inside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e_steps = max(1, min(2, args.steps))
@@ -277,84 +335,83 @@ def run_ours(args, rank, world):
     e2e = {"value": units_per_step * world / te, "unit": METRIC,
            "h2d_bytes_per_step": int((sb["bytes_h2d"] - sa["bytes_h2d"]) / e_steps),
            "d2h_bytes_per_step": int((sb["bytes_d2h"] - sa["bytes_d2h"]) / e_steps + 8),
-           "includes": "sv_apply_circuit + sv_expect(1-D Ising, 59 terms) with the energy read back"}
+           "includes": f"sv_apply_circuit + sv_expect(1-D Ising, {len(terms)} terms) with the energy read back"}
     st = sim.stats()
+    quality = state_quality(sim, w, gates, init, args.warmup + args.steps + e_steps)
     gpu_launches = int(d["kernel_launches"])
     sim.close()
-    del flush
 
-    extras = {}
-    if rank == 0 and not args.no_extras:
-        extras = comparator(args, gates, terms, energy)
     out = {
         "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 (fp32 gate arithmetic, fp64 reductions)", "data": "synthetic",
-        "config": {"workload": f"random layered circuit, n={n}, depth={args.depth} ({len(gates)} gates), "
-                               f"complex64, chunk=2^{c}, eb={args.eb}, compressed chunks in pinned host DRAM, "
-                               f"streamed in groups of 2^{args.group} chunks",
-                   "n_qubits": n, "chunk_qubits": c, "abs_error_bound": args.eb, "group_qubits": args.group,
-                   "gates": len(gates), "l2": "state (8 GiB raw) >> L2; streamed groups of 512 MiB > L2",
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{w['dtype']} (FP32 gate arithmetic for c64, FP64 reductions)"
+        if w["dtype"] == "c64" else "c128 (FP64)", "data": "synthetic",
+        "config": {"workload": describe(w, len(gates)), "n_qubits": n, "chunk_qubits": c, "abs_error_bound": w["eb"],
+                   "group_qubits": w["group"], "gates": len(gates),
+                   "l2": "inputs larger than L2: every pass streams the whole state; groups of 2^(c+g) amplitudes",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": gpu_launches,
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clk,
-        "host_link": {"achieved_gbs": round(link_bytes / (t_local) / 1e9, 1),
-                      "peak_gbs": link, "per_step": per_step},
+        "host_link": {"achieved_gbs": round(link_bytes / t_local / 1e9, 1), "peak_gbs": link,
+                      "frac_of_bidir": round(link_bytes / t_local / 1e9 / link["bidir"], 3) if link else None,
+                      "per_step": per_step},
         "stored_state": {"compressed_bytes": st["compressed_bytes"], "raw_bytes": st["raw_bytes"],
                          "ratio": round(st["raw_bytes"] / max(1, st["compressed_bytes"]), 2),
-                         "norm2": st["norm2"], "energy": energy},
+                         "norm2": st["norm2"], "energy": energy, **quality},
     }
-    out.update(extras)
+    if rank == 0 and not args.no_extras and w["n"] <= 32:
+        out.update(comparator(args, gates, terms, energy, applies=args.warmup + args.steps + e_steps))
     return out
 
 
-def load_traffic(kind):
-    """DRAM bytes per launch from the committed ncu summary of that kernel, if any."""
-    path = os.path.join(ROOT, "profiles", f"traffic_k_{kind}.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        return json.load(f).get("bytes_per_launch")
+def state_quality(sim, w, gates, init, applies):
+    """Closed-form fidelity where the circuit has one (GHZ; QFT applied once)."""
+    n = w["n"]
+    if w["circuit"] == "ghz" and applies % 2 == 1:
+        a = sim.amplitudes([0, (1 << n) - 1])
+        norm2 = sim.stats()["norm2"]
+        return {"fidelity_closed_form": float(abs((a[0] + a[1]) / math.sqrt(2)) ** 2 / max(norm2, 1e-300))}
+    return {}
 
 
-def comparator(args, gates, terms, energy_c):
+def comparator(args, gates, terms, energy_c, applies):
     """The plain uncompressed in-HBM GPU path on the same circuit, and the
-    FP64 CPU oracle on a bounded sample of the workload."""
+    FP64 oracle on a bounded sample of the workload."""
     import torch
     from paper_2309_16979_gb300 import StateVector
+    w = args.w
     out = {}
-    n = args.n
+    n = w["n"]
     units = W.amp_gate_updates(n, gates)
     try:
-        with StateVector(n, mode="uncompressed", dtype="c64", init_index=W.basis_index(n)) as p:
-            p.apply(gates)  # warm-up
+        with StateVector(n, mode="uncompressed", dtype=w["dtype"], init_index=W.basis_index(n), profile=True) as p:
+            for _ in range(applies):
+                p.apply(gates)
+            e_plain = p.expect(terms)
+            s0 = p.stats()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p.apply(gates)
             t = time.perf_counter() - t0
-            st = p.stats()
-            # fresh state for the energy at the same circuit as the compressed run
-        with StateVector(n, mode="uncompressed", dtype="c64", init_index=W.basis_index(n)) as p:
-            for _ in range(args.warmup + args.steps + max(1, min(2, args.steps))):
-                p.apply(gates)
-            e_plain = p.expect(terms)
+            s1 = p.stats()
+        d = {k: s1[k] - s0[k] for k in STAT_KEYS}
         out["plain_uncompressed"] = {"value": units / t, "unit": METRIC, "seconds_per_step": t,
-                                     "subpasses_per_step": st["subpasses"] / 2,
-                                     "energy": e_plain, "energy_compressed": energy_c,
+                                     "subpasses_per_step": d["subpasses"], "roofline": roofline_from_stats(d),
+                                     "energy_after_same_applies": e_plain, "energy_compressed": energy_c,
                                      "energy_abs_diff": abs(e_plain - energy_c) if energy_c is not None else None}
     except Exception as ex:  # noqa: BLE001
         out["plain_uncompressed"] = {"error": str(ex)}
-    out["cpu_baseline"] = cpu_baseline(args, gates)
+    out["cpu_baseline"] = cpu_baseline(w, gates)
     return out
 
 
-def cpu_baseline(args, gates, target_s=12.0):
-    """FP64 oracle (as it stands) on the host cores: the first K gates of the
+def cpu_baseline(w, gates, target_s=12.0):
+    """FP64 oracle (as it stands) on the host cores: consecutive gates of the
     workload on the full n-qubit complex128 state; amp-gate updates/s."""
     import oracle
-    n = args.n
+    n = w["n"]
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[W.basis_index(n)] = 1.0
     t0 = time.perf_counter()
@@ -369,12 +426,63 @@ def cpu_baseline(args, gates, target_s=12.0):
                       f"({dt:.1f} s)"}
 
 
+def run_grad(args, rank, world):
+    """Adjoint gradient seconds per step (configs 3 and 4)."""
+    import torch
+    from paper_2309_16979_gb300 import StateVector
+    w = args.w
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = w["n"]
+    gates, npar = W.hea(n, w["layers"])
+    terms = W.ising(n, seed=4)
+    sets = w.get("sets", 1)
+    thetas = [W.normal_params(npar, seed=(3 if sets == 1 else 100 + i)) for i in range(max(1, sets))]
+    mode = w.get("mode", "compressed")
+    sim = StateVector(n, w["c"], w["eb"] or 1e-6, dtype=w["dtype"], mode=mode, max_group_qubits=w["group"], device=dev)
+    for i in range(args.warmup):
+        sim.grad(gates, thetas[i % len(thetas)], terms)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    results = []
+    for i in range(args.steps):
+        results.append(sim.grad(gates, thetas[i % len(thetas)], terms))
+    torch.cuda.synchronize()
+    t_local = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    barrier(world)
+    t_max, _ = reduce_max_sum(world, t_local, 1.0, device="cuda")
+    st = sim.stats()
+    sim.close()
+    errors = []
+    if not args.no_extras and rank == 0:
+        # FP64 reference: the uncompressed complex128 GPU adjoint (pinned to the oracle at small n)
+        ref = StateVector(n, mode="uncompressed", dtype="c128", device=dev)
+        for i in range(min(args.steps, len(thetas))):
+            e_r, g_r = ref.grad(gates, thetas[i], terms)
+            e, g = results[i]
+            errors.append({"set": i, "energy_err": abs(e - e_r), "grad_max_err": float(np.abs(g - g_r).max()),
+                           "grad_rel_l2": float(np.linalg.norm(g - g_r) / max(np.linalg.norm(g_r), 1e-300))})
+        ref.close()
+    return {"metric": "adjoint grad s/step", "value": t_max, "unit": "s/step", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+            "config": {"workload": describe(w, len(gates)), "n_qubits": n, "params": npar, "gates": len(gates),
+                       "parameter_sets": len(thetas), "parallelism": f"replicas x{world}"},
+            "gpu_launches": None, "clocks": clk, "passes_total": st["passes"],
+            "errors_vs_fp64_gpu_adjoint": errors}
+
+
 # ------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as the reference arm, on the same config and metric."""
     import oracle
-    n = args.n
-    gates = W.random_layers(n, args.depth, seed=1)
+    w = args.w
+    n = w["n"]
+    gates = make_circuit(w, seed=1) if w["circuit"] != "hea" else W.hea(n, w["layers"])[0]
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[W.basis_index(n)] = 1.0
     per_step = 4  # gates per step: a bounded sample of the workload
@@ -383,8 +491,9 @@ def run_reference(args, rank, world):
     for i in range(args.warmup + args.steps):
         sample = [gates[(g + j) % len(gates)] for j in range(per_step)]
         g += per_step
+        th = None
         t0 = time.perf_counter()
-        psi = oracle.apply_gates(n, psi, sample)
+        psi = oracle.apply_gates(n, psi, sample, th)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -394,22 +503,21 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
             "data": "synthetic",
-            "config": {"workload": f"random layered circuit, n={n}, depth={args.depth}, complex128 FP64 oracle "
-                                   f"on the host cores", "n_qubits": n},
+            "config": {"workload": describe(w, len(gates)) + "; FP64 oracle on the host cores", "n_qubits": n},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"{per_step} consecutive gates of the {len(gates)}-gate workload per step "
-                                       f"on the full 2^{n} state"},
+                                       f"on the full 2^{n} complex128 state"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     args = parse()
-    rank, world = dist_init(args)
+    rank, world = dist_init()
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)), flush=True)
         return
-    out = run_ours(args, rank, world)
+    out = run_grad(args, rank, world) if args.w["circuit"] == "hea" else run_apply(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -96,6 +96,10 @@ typedef struct sv_config {
     int32_t device;               /* CUDA device ordinal (default 0) */
     int32_t profile;              /* 1: time every decode / apply / encode launch with CUDA
                                      events on the compute stream (sv_stats t_*_s); default 0 */
+    int32_t fuse_codec;           /* 1 (default): decode inside the first tile sub-pass and
+                                     encode inside the last when their tiles hold whole codec
+                                     blocks; 0: separate decode / encode kernels */
+    int32_t reserved1;
     uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
@@ -188,9 +192,14 @@ int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_i
  * param_index p (G = X, Y, Z for RX, RY, RZ).
  *   theta: host, nparams values. H: host Pauli terms. energy: host double.
  *   grad:  host, nparams doubles (overwritten).
- * On return the stored state is U(theta)|init_index> rebuilt from the forward
- * sweep when the state is compressed, or psi_0 after the reverse sweep when
- * uncompressed (call sv_apply_circuit to continue from a known state).
+ * Compressed states keep lambda as a second compressed chunk store and run
+ * the reverse sweep pass by pass over both stores (re-encoding both after
+ * every pass); lambda is built one chunk at a time from the source chunks
+ * k ^ xh of every distinct high x-mask xh, which must number at most
+ * 2^max_group_qubits (SV_ERR_ARG otherwise).
+ * On return the stored state is psi_0 as left by the reverse sweep (|init_index>
+ * up to rounding and, when compressed, quantisation error); call sv_create or
+ * sv_apply_circuit from a known state to continue.
  */
 int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* theta, size_t nparams,
             const sv_pauli_term* H, size_t nterms, double* energy, double* grad);

@@ -37,7 +37,7 @@ class StateVector:
                  mode: str = "compressed", init_index: int = 0, max_group_qubits: int = 4,
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
-                 profile: bool = False):
+                 profile: bool = False, fuse_codec: bool = True):
         L = load()
         cfg = _abi.SvConfig()
         L.sv_config_default(C.byref(cfg))
@@ -52,6 +52,7 @@ class StateVector:
         cfg.timeout_s = timeout_s
         cfg.device = device
         cfg.profile = int(profile)
+        cfg.fuse_codec = int(fuse_codec)
         h = C.c_void_p()
         _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
         self._h = h

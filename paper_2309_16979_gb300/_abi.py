@@ -37,7 +37,8 @@ class SvConfig(C.Structure):
     _fields_ = [("dtype", C.c_int32), ("mode", C.c_int32), ("init_index", C.c_uint64),
                 ("max_group_qubits", C.c_int32), ("tile_qubits", C.c_int32),
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
-                ("profile", C.c_int32), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
+                ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("reserved1", C.c_int32),
+                ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 
 class SvStats(C.Structure):

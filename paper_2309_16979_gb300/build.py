@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libsvgb300.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["codec.cu", "apply.cu", "reduce.cu", "noalloc.cu", "plan.cpp", "engine.cpp", "api.cpp"]
+SOURCES = ["codec.cu", "apply.cu", "apply_phase.cu", "reduce.cu", "noalloc.cu", "plan.cpp", "engine.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

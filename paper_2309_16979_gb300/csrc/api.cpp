@@ -115,6 +115,10 @@ void release(sv_state* s)
         cudaFree(s->d_out[i]);
         cudaFree(s->d_co[i]);
         if (s->h_co[i]) cudaFreeHost(s->h_co[i]);
+        cudaFree(s->d_in2[i]);
+        cudaFree(s->d_out2[i]);
+        cudaFree(s->d_co2[i]);
+        if (s->h_co2[i]) cudaFreeHost(s->h_co2[i]);
         if (s->ev_h2d[i]) cudaEventDestroy(s->ev_h2d[i]);
         if (s->ev_comp[i]) cudaEventDestroy(s->ev_comp[i]);
         if (s->ev_d2h[i]) cudaEventDestroy(s->ev_d2h[i]);
@@ -127,8 +131,11 @@ void release(sv_state* s)
     cudaFree(s->d_lam);
     cudaFree(s->d_ops);
     for (cudaEvent_t ev : s->prof_ev) cudaEventDestroy(ev);
+    cudaFree(s->d_amps2);
     arena_free(s->arena[0]);
     arena_free(s->arena[1]);
+    arena_free(s->larena[0]);
+    arena_free(s->larena[1]);
     if (s->s_comp) cudaStreamDestroy(s->s_comp);
     if (s->s_h2d) cudaStreamDestroy(s->s_h2d);
     if (s->s_d2h) cudaStreamDestroy(s->s_d2h);
@@ -198,6 +205,7 @@ void sv_config_default(sv_config* cfg)
     cfg->renormalize = 0;
     cfg->device = 0;
     cfg->host_budget_bytes = 0;
+    cfg->fuse_codec = 1;
     cfg->timeout_s = 600.0;
 }
 
@@ -252,7 +260,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     s->k = k;
     s->gmax = cfg.max_group_qubits;
     s->nslots = cfg.pipeline_slots;
-    s->tq = cfg.tile_qubits ? cfg.tile_qubits : (cfg.dtype == SV_C64 ? 12 : 11);
+    s->tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
     s->lq = 5;
     s->perm.resize(n);
     for (int q = 0; q < n; q++) s->perm[q] = q;
@@ -340,16 +348,18 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
     s->err.clear();
     for (size_t p = 0; p < nparams; p++)
         if (!std::isfinite(theta[p])) return fail(s, SV_ERR_ARG, "theta not finite");
-    if (s->mode != SV_UNCOMPRESSED)
-        return fail(s, SV_ERR_ARG, "sv_grad needs an uncompressed state in this build");
     const double t0 = now_s();
     for (int q = 0; q < s->n; q++) s->perm[q] = q;
     std::vector<PGate> pg;
     int r = lower(s, gates, ngates, theta, nparams, true, pg);
     if (r) return r;
     cudaSetDevice(s->cfg.device);
-    r = s->dtype == SV_C64 ? grad_uncompressed<float>(s, pg, nparams, H, nterms, energy, grad)
-                           : grad_uncompressed<double>(s, pg, nparams, H, nterms, energy, grad);
+    if (s->mode == SV_UNCOMPRESSED)
+        r = s->dtype == SV_C64 ? grad_uncompressed<float>(s, pg, nparams, H, nterms, energy, grad)
+                               : grad_uncompressed<double>(s, pg, nparams, H, nterms, energy, grad);
+    else
+        r = s->dtype == SV_C64 ? grad_compressed<float>(s, pg, nparams, H, nterms, energy, grad)
+                               : grad_compressed<double>(s, pg, nparams, H, nterms, energy, grad);
     s->st.last_call_seconds = now_s() - t0;
     return r;
 }

@@ -21,159 +21,64 @@
 //     then 16-byte stores to a per-block staging slot; a one-CTA-per-chunk scan
 //     turns widths into offsets, and a compaction kernel moves each block's
 //     8*w words to its final offset.
-#include "sv_internal.h"
+#include <algorithm>
+
+#include "codec_dev.cuh"
 
 namespace sv {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename R> struct V2;
-template <> struct V2<float> { using T = float2; };
-template <> struct V2<double> { using T = double2; };
-
-__device__ __forceinline__ uint32_t ld32(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-template <typename R> __device__ __forceinline__ R pow2(int e);
-template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
-template <> __device__ __forceinline__ double pow2<double>(int e)
-{
-    return __longlong_as_double((long long)(1023 + e) << 52);
-}
-
-template <typename R> __device__ __forceinline__ int32_t round_q(R y);
-template <> __device__ __forceinline__ int32_t round_q<float>(float y) { return __float2int_rn(y); }
-template <> __device__ __forceinline__ int32_t round_q<double>(double y) { return __double2int_rn(y); }
-
-template <typename R> __device__ __forceinline__ R from_q(int32_t q);
-template <> __device__ __forceinline__ float from_q<float>(int32_t q) { return __int2float_rn(q); }
-template <> __device__ __forceinline__ double from_q<double>(int32_t q) { return (double)q; }
-
-template <typename R> struct QLimit;
-template <> struct QLimit<float> { static constexpr float v = 16777215.0f; };     // 2^24 - 1
-template <> struct QLimit<double> { static constexpr double v = 1073741823.0; };  // 2^30 - 1
+using codec::FULL;
+template <typename R> using V2 = codec::V2<R>;
 
 // load / store 8 consecutive amplitudes of one lane
-__device__ __forceinline__ void load8(const float2* p, float (&re)[8], float (&im)[8])
+__device__ __forceinline__ void load8(const float2* p, float (&x)[2][8])
 {
     const float4* p4 = reinterpret_cast<const float4*>(p);
 #pragma unroll
     for (int h = 0; h < 4; h++) {
-        float4 v = p4[h];
-        re[2 * h] = v.x; im[2 * h] = v.y; re[2 * h + 1] = v.z; im[2 * h + 1] = v.w;
+        const float4 v = p4[h];
+        x[0][2 * h] = v.x; x[1][2 * h] = v.y; x[0][2 * h + 1] = v.z; x[1][2 * h + 1] = v.w;
     }
 }
-__device__ __forceinline__ void load8(const double2* p, double (&re)[8], double (&im)[8])
+__device__ __forceinline__ void load8(const double2* p, double (&x)[2][8])
 {
 #pragma unroll
-    for (int m = 0; m < 8; m++) { double2 v = p[m]; re[m] = v.x; im[m] = v.y; }
+    for (int m = 0; m < 8; m++) { const double2 v = p[m]; x[0][m] = v.x; x[1][m] = v.y; }
 }
-__device__ __forceinline__ void store8(float2* p, const float (&re)[8], const float (&im)[8])
+__device__ __forceinline__ void store8(float2* p, const float (&x)[2][8])
 {
     float4* p4 = reinterpret_cast<float4*>(p);
 #pragma unroll
-    for (int h = 0; h < 4; h++) p4[h] = make_float4(re[2 * h], im[2 * h], re[2 * h + 1], im[2 * h + 1]);
+    for (int h = 0; h < 4; h++) p4[h] = make_float4(x[0][2 * h], x[1][2 * h], x[0][2 * h + 1], x[1][2 * h + 1]);
 }
-__device__ __forceinline__ void store8(double2* p, const double (&re)[8], const double (&im)[8])
+__device__ __forceinline__ void store8(double2* p, const double (&x)[2][8])
 {
 #pragma unroll
-    for (int m = 0; m < 8; m++) p[m] = make_double2(re[m], im[m]);
+    for (int m = 0; m < 8; m++) p[m] = make_double2(x[0][m], x[1][m]);
 }
 
 // ----------------------------------------------------------------- decode
+// one warp per block pair of the group's chunk streams
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_decode(const uint8_t* __restrict__ in, size_t stride, int c, int dtype, uint64_t nwarps,
-         GroupIn gin, typename V2<R>::T* __restrict__ amps, R scale, int* err)
+k_decode(const uint8_t* __restrict__ in, size_t stride, int c, int dtype, uint64_t nwarps, GroupIn gin,
+         typename V2<R>::T* __restrict__ amps, R scale, int* err)
 {
     __shared__ __align__(16) uint32_t sbuf[8][2][264];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t gw = (uint64_t)blockIdx.x * 8 + wib;
     if (gw >= nwarps) return;
-    const CodecLayout L = codec_layout(c);
     const int sh = c - 8;
     const uint32_t r = (uint32_t)(gw >> sh);
     const uint32_t bp = (uint32_t)(gw & ((1ull << sh) - 1));
-    const uint8_t* s = in + (size_t)r * stride;
-    const uint64_t nbytes = gin.bytes[r];
-
-    bool ok = nbytes >= L.p_off && nbytes <= stride;
-    int k = 0;
-    uint32_t total = 0;
-    if (ok) {
-        const uint32_t h0 = ld32(s), h1 = ld32(s + 4), nbh = ld32(s + 12);
-        k = (int32_t)ld32(s + 8);
-        total = ld32(s + 16);
-        ok = h0 == kMagic && (h1 & 0xffffu) == 1u && ((h1 >> 16) & 0xffu) == (uint32_t)dtype &&
-             (h1 >> 24) == (uint32_t)c && k <= 0 && k >= -60 && nbh == L.nb &&
-             L.p_off + 4ull * total <= nbytes;
-    }
-    uint32_t w[2] = {0, 0}, off[2] = {0, 0};
-    int32_t anc[2] = {0, 0};
-    if (ok) {
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const uint32_t b = p ? bp + L.bpc : bp;
-            w[p] = s[L.w_off + b];
-            off[p] = ld32(s + L.o_off + 4ull * b);
-            const uint32_t nxt = ld32(s + L.o_off + 4ull * (b + 1));
-            anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
-            ok = ok && w[p] <= 32u && nxt - off[p] == 8u * w[p] &&
-                 L.p_off + 4ull * ((uint64_t)off[p] + 8ull * w[p]) <= nbytes;
-        }
-        if (bp == 0) ok = ok && ld32(s + L.o_off) == 0u && ld32(s + L.o_off + 4ull * L.nb) == total;
-    }
-    if (!ok) {
+    R x[2][8];
+    if (!codec::decode_pair<R>(in + (size_t)r * stride, gin.bytes[r], stride, c, dtype, bp, sbuf[wib], scale, x,
+                               lane)) {
         if (lane == 0) atomicOr(err, kErrCorrupt);
         return;
     }
-
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        if (w[p] == 0) continue;
-        const uint4* src = reinterpret_cast<const uint4*>(s + L.p_off + 4ull * off[p]);
-        uint4* dst = reinterpret_cast<uint4*>(sbuf[wib][p]);
-        for (uint32_t i = lane; i < 2 * w[p]; i += 32) dst[i] = src[i];
-        if (lane == 0) sbuf[wib][p][8 * w[p]] = 0u;
-    }
-    __syncwarp();
-
-    const R delta = pow2<R>(k);
-    R x[2][8];
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        const uint32_t ww = w[p];
-        const uint32_t mask = ww >= 32u ? FULL : ((1u << ww) - 1u);
-        uint32_t v[8];
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            const uint32_t j = 8u * lane + m;
-            uint32_t z = 0;
-            if (ww) {
-                const uint32_t pos = j * ww;
-                z = __funnelshift_r(sbuf[wib][p][pos >> 5], sbuf[wib][p][(pos >> 5) + 1], pos & 31) & mask;
-            }
-            uint32_t rr = (z >> 1) ^ (0u - (z & 1u));
-            v[m] = (j == 0) ? 0u : rr;
-        }
-#pragma unroll
-        for (int m = 1; m < 8; m++) v[m] += v[m - 1];
-        const uint32_t tot = v[7];
-        uint32_t incl = tot;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += t;
-        }
-        const uint32_t base = (uint32_t)anc[p] + (incl - tot);
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            R val = from_q<R>((int32_t)(base + v[m])) * delta;
-            if (scale != (R)1) val *= scale;
-            x[p][m] = val;
-        }
-    }
-    store8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x[0], x[1]);
+    store8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x);
 }
 
 // ----------------------------------------------------------------- encode
@@ -191,77 +96,10 @@ k_encode_blocks(const typename V2<R>::T* __restrict__ amps, int c, uint64_t nwar
     const int sh = c - 8;
     const uint32_t r = (uint32_t)(gw >> sh);
     const uint32_t bp = (uint32_t)(gw & ((1ull << sh) - 1));
-
     R x[2][8];
-    load8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x[0], x[1]);
-
-    const R inv = pow2<R>(-k);
-    const R qmax = QLimit<R>::v;
-    int32_t q[2][8];
-    bool bad = false;
-    unsigned long long ss = 0;
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            R y = x[p][m] * inv;  // exact: inv is a power of two
-            if (!(fabs(y) <= qmax)) { bad = true; y = (R)0; }
-            q[p][m] = round_q<R>(y);
-            ss += (unsigned long long)((long long)q[p][m] * (long long)q[p][m]);
-        }
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, kErrRange);
-
-    uint32_t* pkw = &pk[wib][0][0];
-    for (int i = lane; i < 2 * 260; i += 32) pkw[i] = 0u;
-    __syncwarp();
-
-    uint32_t wpl[2];
-    int32_t anchor[2];
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        const int32_t prev = __shfl_up_sync(FULL, q[p][7], 1);
-        uint32_t z[8], mx = 0;
-#pragma unroll
-        for (int m = 0; m < 8; m++) {
-            int32_t rr;
-            if (m == 0) rr = (lane == 0) ? 0 : q[p][0] - prev;
-            else rr = q[p][m] - q[p][m - 1];
-            z[m] = ((uint32_t)rr << 1) ^ (uint32_t)(rr >> 31);
-            mx = max(mx, z[m]);
-        }
-        mx = __reduce_max_sync(FULL, mx);
-        const uint32_t w = mx ? 32u - (uint32_t)__clz(mx) : 0u;
-        if (w) {
-#pragma unroll
-            for (int m = 0; m < 8; m++) {
-                const uint32_t pos = (8u * lane + m) * w;
-                const uint32_t wi = pos >> 5, bit = pos & 31;
-                atomicOr(&pk[wib][p][wi], z[m] << bit);
-                if (bit + w > 32u) atomicOr(&pk[wib][p][wi + 1], z[m] >> (32u - bit));
-            }
-        }
-        wpl[p] = w;
-        anchor[p] = __shfl_sync(FULL, q[p][0], 0);
-    }
-    __syncwarp();
-
-    uint8_t* so = out + (size_t)r * stride;
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        const uint32_t b = p ? bp + L.bpc : bp;
-        const uint32_t w = wpl[p];
-        uint4* dst = reinterpret_cast<uint4*>(sparse + ((uint64_t)r * L.nb + b) * 256ull);
-        const uint4* srcv = reinterpret_cast<const uint4*>(pk[wib][p]);
-        for (uint32_t i = lane; i < 2 * w; i += 32) dst[i] = srcv[i];
-        if (lane == 0) {
-            so[L.w_off + b] = (uint8_t)w;
-            *reinterpret_cast<int32_t*>(so + L.a_off + 4ull * b) = anchor[p];
-        }
-    }
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) ss += __shfl_down_sync(FULL, ss, d);
-    if (lane == 0) blocksq[(uint64_t)r * L.bpc + bp] = ss;
+    load8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x);
+    codec::encode_pair<R>(x, c, k, bp, out + (size_t)r * stride, sparse + (uint64_t)r * L.nb * 256ull,
+                          blocksq + (uint64_t)r * L.bpc + bp, pk[wib], err, lane);
 }
 
 // One CTA per chunk: widths -> offsets (exclusive scan of 8*w), header,
@@ -393,10 +231,18 @@ cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks
     const uint64_t nw = (uint64_t)nchunks << (c - 8);
     k_encode_blocks<R><<<blocks_for_warps(nw), 256, 0, st>>>(
         static_cast<const typename V2<R>::T*>(amps), c, nw, k, out, stride, sparse, blocksq, err);
+    if (launches) *launches += 1;
+    return launch_encode_finish(c, dtype, k, nchunks, out, stride, sparse, blocksq, chunk_out, st, launches);
+}
+
+cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* out, size_t stride,
+                                 const uint32_t* sparse, const unsigned long long* blocksq, ChunkOut* chunk_out,
+                                 cudaStream_t st, int* launches)
+{
     k_encode_scan<<<nchunks, 1024, 0, st>>>(out, stride, c, dtype, k, blocksq, chunk_out);
     const uint64_t nw2 = (uint64_t)nchunks << (c - 7);
     k_encode_compact<<<blocks_for_warps(nw2), 256, 0, st>>>(out, stride, c, nw2, sparse);
-    if (launches) *launches += 3;
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 

@@ -168,10 +168,11 @@ static void prof_collect(sv_state* s)
 }
 
 // ----------------------------------------------------------- op upload
-template <typename R>
-int upload_ops(sv_state* s, const std::vector<DevOp<R>>& ops)
+// Copy a pass's op tables (concatenated, 256-byte aligned sections) to the
+// device buffer d_ops on the compute stream, growing the buffer if needed.
+static int upload_blob(sv_state* s, const std::vector<uint8_t>& blob)
 {
-    const size_t bytes = std::max<size_t>(1, ops.size()) * sizeof(DevOp<R>);
+    const size_t bytes = std::max<size_t>(1, blob.size());
     if (bytes > s->ops_cap) {
         if (s->d_ops) {
             wait_stream(s, s->s_comp);
@@ -183,34 +184,93 @@ int upload_ops(sv_state* s, const std::vector<DevOp<R>>& ops)
         if (e != cudaSuccess) return cuda_fail(s, e, "cudaMalloc(ops)");
         s->ops_cap = cap;
     }
-    if (!ops.empty()) {
-        cudaError_t e = cudaMemcpyAsync(s->d_ops, ops.data(), ops.size() * sizeof(DevOp<R>), cudaMemcpyHostToDevice,
-                                        s->s_comp);
+    if (!blob.empty()) {
+        cudaError_t e = cudaMemcpyAsync(s->d_ops, blob.data(), blob.size(), cudaMemcpyHostToDevice, s->s_comp);
         if (e != cudaSuccess) return cuda_fail(s, e, "upload ops");
     }
     return SV_OK;
 }
 
-// Device form of a pass: every sub-pass's tile descriptor and op range.
+template <typename V>
+static size_t append_section(std::vector<uint8_t>& blob, const std::vector<V>& v)
+{
+    const size_t off = (blob.size() + 255) & ~size_t(255);
+    blob.resize(off + v.size() * sizeof(V));
+    if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(V));
+    return off;
+}
+
+template <typename R>
+int upload_ops(sv_state* s, const std::vector<DevOp<R>>& ops)
+{
+    std::vector<uint8_t> blob;
+    append_section(blob, ops);
+    return upload_blob(s, blob);
+}
+
+// Device form of a pass: every sub-pass's tile descriptor and its op range,
+// as generic shared-memory ops or, on 2^12 tiles, as register phases.
 template <typename R>
 struct DevPass {
     std::vector<TileDesc> td;
     std::vector<int> off, cnt;
     std::vector<DevOp<R>> ops;
+    bool use_phases = false;
+    bool fuse_decode = false;  // first sub-pass decodes the chunk streams
+    bool fuse_encode = false;  // last sub-pass encodes the block pairs
+    std::vector<int> ph_off, ph_cnt;
+    std::vector<Phase> phases;
+    std::vector<PhaseOp<R>> pops;
+    size_t ops_at = 0, phases_at = 0, pops_at = 0;  // byte offsets in the uploaded blob
 };
 
 template <typename R>
-static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t, int l)
+static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t, int l, bool fuse_decode = false,
+                                 bool fuse_encode = false)
 {
     DevPass<R> dp;
-    for (const SubPlan& sp : subs) {
-        TileDesc td = tile_desc(sp.T, L, t, l);
+    dp.use_phases = (t == kPhaseTileQubits && l == 5);
+    dp.fuse_decode = dp.use_phases && fuse_decode;
+    dp.fuse_encode = dp.use_phases && fuse_encode;
+    for (size_t si = 0; si < subs.size(); si++) {
+        const SubPlan& sp = subs[si];
+        // sub-passes that fuse the codec use rows of whole block pairs (l = 8)
+        const bool codec_rows = dp.use_phases && ((si == 0 && dp.fuse_decode) || (si + 1 == subs.size() && dp.fuse_encode));
+        TileDesc td = tile_desc(sp.T, L, t, codec_rows ? 8 : l);
         dp.td.push_back(td);
         dp.off.push_back((int)dp.ops.size());
-        dev_ops<R>(sp, td, dp.ops, nullptr, nullptr);
+        dp.ph_off.push_back((int)dp.phases.size());
+        if (dp.use_phases) dev_phases<R>(sp, td, dp.phases, dp.pops);
+        else dev_ops<R>(sp, td, dp.ops, nullptr, nullptr);
         dp.cnt.push_back((int)dp.ops.size() - dp.off.back());
+        dp.ph_cnt.push_back((int)dp.phases.size() - dp.ph_off.back());
     }
     return dp;
+}
+
+template <typename R>
+static int upload_pass(sv_state* s, DevPass<R>& dp)
+{
+    std::vector<uint8_t> blob;
+    dp.ops_at = append_section(blob, dp.ops);
+    dp.phases_at = append_section(blob, dp.phases);
+    dp.pops_at = append_section(blob, dp.pops);
+    return upload_blob(s, blob);
+}
+
+// launch sub-pass i of an uploaded pass on a buffer of 2^L local amplitudes
+template <typename R>
+static cudaError_t launch_subpass(sv_state* s, const DevPass<R>& dp, size_t i, void* amps, uint64_t gbase,
+                                  const FuseArgs* fa = nullptr)
+{
+    const uint8_t* base = static_cast<const uint8_t*>(s->d_ops);
+    static const FuseArgs none{};
+    if (dp.use_phases)
+        return launch_apply_phases<R>(amps, dp.td[i], reinterpret_cast<const Phase*>(base + dp.phases_at) + dp.ph_off[i],
+                                      dp.ph_cnt[i], reinterpret_cast<const PhaseOp<R>*>(base + dp.pops_at), gbase,
+                                      fa ? *fa : none, s->s_comp);
+    return launch_apply<R>(amps, dp.td[i], reinterpret_cast<const DevOp<R>*>(base + dp.ops_at) + dp.off[i], dp.cnt[i],
+                           gbase, s->s_comp);
 }
 
 // Tile shape over L local positions: t tile qubits of which the low l are
@@ -244,11 +304,23 @@ int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const Pass
     int t, l;
     tile_shape(L, s->tq, s->lq, t, l);
     const std::vector<HOp> hops = local_ops(gates, pp.gates, c, pp.S, false);
-    const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
-    const DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
-    int r = upload_ops<R>(s, dp.ops);
+    std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
+    if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+    // Fuse the decode into the first sub-pass when a plan whose first tile
+    // holds whole block pairs (local bits 0..7) needs no extra sub-pass, and
+    // the encode into the last sub-pass when its tile holds them.
+    bool fdec = false, fenc = false;
+    if (t == kPhaseTileQubits && l == 5 && c >= 8 && !subs.empty() && s->cfg.fuse_codec) {
+        std::vector<SubPlan> alt = plan_subpasses(hops, L, t, l, true, 8);
+        if (!alt.empty() && alt.size() <= subs.size()) {
+            subs.swap(alt);
+            fdec = true;
+        }
+        fenc = (subs.back().T & 0xffull) == 0xffull;
+    }
+    DevPass<R> dp = build_dev_pass<R>(subs, L, t, l, fdec, fenc);
+    int r = upload_pass<R>(s, dp);
     if (r) return r;
-    const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
 
     // chunk-index bit positions of staged and fixed high qubits
     std::vector<int> spos, fpos;
@@ -294,27 +366,54 @@ int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const Pass
         const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
         uint64_t in_bytes = 0;
         for (int j = 0; j < gch; j++) in_bytes += gin.bytes[j];
-        int pi = prof_begin(s);
-        if ((e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gin, s->d_amps, s->scale, s->d_err,
-                                  s->s_comp)))
-            return cuda_fail(s, e, "decode");
-        prof_end(s, pi, PROF_DECODE, in_bytes + amp_bytes);
-        s->st.kernel_launches++;
-        const uint64_t gbase = base << c;
-        for (size_t i = 0; i < dp.td.size(); i++) {
+        int pi = -1;
+        if (!dp.fuse_decode) {
             pi = prof_begin(s);
-            if ((e = launch_apply<R>(s->d_amps, dp.td[i], d_ops + dp.off[i], dp.cnt[i], gbase, s->s_comp)))
-                return cuda_fail(s, e, "apply");
-            prof_end(s, pi, PROF_APPLY, 2 * amp_bytes);
+            if ((e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gin, s->d_amps, s->scale, s->d_err,
+                                      s->s_comp)))
+                return cuda_fail(s, e, "decode");
+            prof_end(s, pi, PROF_DECODE, in_bytes + amp_bytes);
+            s->st.kernel_launches++;
+        }
+        const uint64_t gbase = base << c;
+        FuseArgs fa;
+        fa.c = c;
+        fa.dtype = s->dtype;
+        fa.k = s->k;
+        fa.scale = s->scale;
+        fa.in = s->d_in[slot];
+        fa.in_stride = s->stride;
+        fa.gin = gin;
+        fa.out = s->d_out[slot];
+        fa.out_stride = s->stride;
+        fa.sparse = s->d_sparse;
+        fa.blocksq = s->d_blocksq;
+        fa.err = s->d_err;
+        slot_prof[slot] = -1;
+        for (size_t i = 0; i < dp.td.size(); i++) {
+            fa.decode = (i == 0 && dp.fuse_decode) ? 1 : 0;
+            fa.encode = (i + 1 == dp.td.size() && dp.fuse_encode) ? 1 : 0;
+            pi = prof_begin(s);
+            if ((e = launch_subpass<R>(s, dp, i, s->d_amps, gbase, &fa))) return cuda_fail(s, e, "apply");
+            // algorithmic bytes: what the launch reads (stream or amplitudes) and writes
+            // (amplitudes; a fused encode's stream bytes are added once known)
+            prof_end(s, pi, PROF_APPLY, (fa.decode ? in_bytes : amp_bytes) + (fa.encode ? 0 : amp_bytes));
+            if (fa.encode) slot_prof[slot] = pi;
             s->st.kernel_launches++;
         }
         int launches = 0;
-        pi = prof_begin(s);
-        slot_prof[slot] = pi;
-        if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)))
-            return cuda_fail(s, e, "encode");
-        prof_end(s, pi, PROF_ENCODE, amp_bytes);
+        if (dp.fuse_encode) {
+            if ((e = launch_encode_finish(c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse, s->d_blocksq,
+                                          s->d_co[slot], s->s_comp, &launches)))
+                return cuda_fail(s, e, "encode");
+        } else {
+            pi = prof_begin(s);
+            slot_prof[slot] = pi;
+            if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
+                                      s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)))
+                return cuda_fail(s, e, "encode");
+            prof_end(s, pi, PROF_ENCODE, amp_bytes);
+        }
         s->st.kernel_launches += launches;
         if ((e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
                                  s->s_comp)))
@@ -378,14 +477,14 @@ int run_pass_uncompressed(sv_state* s, void* state, const std::vector<PGate>& ga
     const std::vector<int> noS;
     const std::vector<HOp> hops = local_ops(gates, ids, L, noS, false);
     const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
-    const DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
-    int r = upload_ops<R>(s, dp.ops);
+    if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+    DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
+    int r = upload_pass<R>(s, dp);
     if (r) return r;
-    const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
     const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
     for (size_t i = 0; i < dp.td.size(); i++) {
         const int pi = prof_begin(s);
-        cudaError_t e = launch_apply<R>(state, dp.td[i], d_ops + dp.off[i], dp.cnt[i], 0, s->s_comp);
+        cudaError_t e = launch_subpass<R>(s, dp, i, state, 0);
         if (e) return cuda_fail(s, e, "apply");
         prof_end(s, pi, PROF_APPLY, 2 * amp_bytes);
         s->st.kernel_launches++;
@@ -826,6 +925,311 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
     return r;
 }
 
+// ----------------------------------------------------- compressed adjoint
+// Adjoint gradient with psi and lambda = H psi both held as compressed chunk
+// stores in pinned host memory. The reverse sweep runs the forward plan's
+// passes in reverse order, each pass's gates reversed and daggered, streaming
+// the chunk groups of both vectors through the GPU.
+template <typename R>
+static int ensure_lambda_store(sv_state* s)
+{
+    if (s->d_amps2) return SV_OK;
+    const int gsz = std::min(s->gmax, s->nh);
+    const uint64_t gch = 1ull << gsz;
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->d_amps2, ((sizeof(R) * 2) << s->c) * gch))) {
+        cudaGetLastError();
+        return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the lambda group buffer failed");
+    }
+    for (int i = 0; i < s->nslots; i++) {
+        if ((e = cudaMalloc(&s->d_in2[i], s->stride * gch)) || (e = cudaMalloc(&s->d_out2[i], s->stride * gch)) ||
+            (e = cudaMalloc(&s->d_co2[i], sizeof(ChunkOut) * gch))) {
+            cudaGetLastError();
+            return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the lambda staging slots failed");
+        }
+        if ((e = cudaHostAlloc(&s->h_co2[i], sizeof(ChunkOut) * gch, cudaHostAllocDefault)))
+            return fail(s, SV_ERR_HOST_OOM, "pinned allocation failed");
+    }
+    const uint64_t nchunks = 1ull << s->nh;
+    s->lcur.assign(nchunks, ChunkRef{});
+    s->lnxt.assign(nchunks, ChunkRef{});
+    s->larena[0].seg_bytes = s->larena[1].seg_bytes = s->arena[0].seg_bytes;
+    return SV_OK;
+}
+
+// lambda = H psi, one output chunk at a time from the staged source chunks
+// k ^ xh (one per distinct high x-mask); adds Re<psi_k|lambda_k> to *d_energy.
+template <typename R>
+static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, PauliDev* d_terms, double* d_part,
+                        int nblocks, double* d_energy)
+{
+    const int c = s->c;
+    const uint64_t lowmask = (1ull << c) - 1;
+    std::vector<uint64_t> X{0};
+    for (const auto& t : phys) X.push_back(t.xmask >> c);
+    std::sort(X.begin(), X.end());
+    X.erase(std::unique(X.begin(), X.end()), X.end());
+    const size_t gcap = (size_t)1 << std::min(s->gmax, s->nh);
+    if (X.size() > gcap)
+        return fail(s, SV_ERR_ARG, "more distinct high x-masks than chunks in a staging group (raise max_group_qubits)");
+    Arena& la = s->larena[s->lcur_arena];
+    la.reset();
+    const uint64_t nch = 1ull << s->nh;
+    std::vector<PauliDev> hd(phys.size());
+    cudaError_t e;
+    for (uint64_t k = 0; k < nch; k++) {
+        std::vector<uint64_t> ks;
+        for (uint64_t xh : X) ks.push_back(k ^ xh);
+        int r = stage_chunks<R>(s, ks);
+        if (r) return r;
+        for (size_t i = 0; i < phys.size(); i++) {
+            const uint64_t xh = phys[i].xmask >> c;
+            const size_t slot = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
+            const uint64_t src_chunk = k ^ xh;
+            const int hs = __builtin_popcountll(src_chunk & (phys[i].zmask >> c)) & 1;
+            hd[i] = pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, 0, hs ? -1.0 : 1.0);
+            hd[i].pad = (int32_t)slot;
+        }
+        if (!hd.empty() &&
+            (e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice, s->s_comp)))
+            return cuda_fail(s, e, "upload terms");
+        int launches = 0;
+        if ((e = launch_ham_chunk<R>(s->d_amps, s->d_amps2, c, d_terms, (int)hd.size(), s->s_comp)) ||
+            (e = launch_dot<R>(s->d_amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
+            (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
+            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->k, 1, s->d_out2[0], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co2[0], s->d_err, s->s_comp, &launches)) ||
+            (e = cudaMemcpyAsync(s->h_co2[0], s->d_co2[0], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)))
+            return cuda_fail(s, e, "lambda chunk");
+        s->st.kernel_launches += 3 + launches;
+        if ((r = wait_stream(s, s->s_comp))) return r;
+        const uint64_t bytes = s->h_co2[0][0].bytes;
+        uint8_t* dst = arena_alloc(s, la, bytes);
+        if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the lambda store failed");
+        if ((e = cudaMemcpyAsync(dst, s->d_out2[0], bytes, cudaMemcpyDeviceToHost, s->s_comp)))
+            return cuda_fail(s, e, "D2H lambda chunk");
+        s->st.bytes_d2h += bytes;
+        s->lcur[k] = {dst, bytes};
+    }
+    return wait_stream(s, s->s_comp);
+}
+
+// One reverse pass over (psi, lambda): gradient partials and U^dagger on both.
+template <typename R>
+static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& inv, const PassPlan& pp,
+                                       double* d_gpart, size_t gpart_cap, double* d_acc,
+                                       std::vector<int>& slot_params)
+{
+    const int c = s->c, g = (int)pp.S.size();
+    const int L = c + g;
+    int t, l;
+    tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
+    std::vector<int> rids(pp.gates.rbegin(), pp.gates.rend());
+    const std::vector<HOp> hops = local_ops(inv, rids, c, pp.S, true);
+    const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
+    if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+    std::vector<TileDesc> tds;
+    std::vector<int> offs, cnts, gslot, nsl;
+    std::vector<DevOp<R>> ops;
+    for (const SubPlan& sp : subs) {
+        TileDesc td = tile_desc(sp.T, L, t, l);
+        tds.push_back(td);
+        offs.push_back((int)ops.size());
+        gslot.push_back((int)slot_params.size());
+        int base = 0;
+        dev_ops<R>(sp, td, ops, &base, &slot_params);
+        nsl.push_back(base);
+        cnts.push_back((int)ops.size() - offs.back());
+    }
+    const uint64_t ntiles = 1ull << (L - t);
+    for (int v : nsl)
+        if ((uint64_t)v * ntiles > gpart_cap) return fail(s, SV_ERR_ARG, "gradient partial buffer too small");
+    int r = upload_ops<R>(s, ops);
+    if (r) return r;
+    const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
+
+    std::vector<int> spos, fpos;
+    for (int q = c; q < s->n; q++) {
+        if (std::find(pp.S.begin(), pp.S.end(), q) != pp.S.end()) spos.push_back(q - c);
+        else fpos.push_back(q - c);
+    }
+    const uint64_t ngroups = 1ull << fpos.size();
+    const int gch = 1 << g;
+    const int NS = s->nslots;
+    std::vector<std::vector<uint64_t>> slot_chunks(NS);
+    Arena& pa = s->arena[1 - s->cur_arena];
+    Arena& la = s->larena[1 - s->lcur_arena];
+    pa.reset();
+    la.reset();
+
+    auto issue = [&](uint64_t gi) -> int {
+        const int slot = (int)(gi % NS);
+        const uint64_t base = deposit(gi, fpos);
+        auto& ch = slot_chunks[slot];
+        ch.resize(gch);
+        GroupIn gp{}, gl{};
+        cudaError_t e;
+        if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0)))
+            return cuda_fail(s, e, "wait comp");
+        for (int j = 0; j < gch; j++) {
+            const uint64_t k = base | deposit((uint64_t)j, spos);
+            ch[j] = k;
+            gp.bytes[j] = (uint32_t)s->cur[k].bytes;
+            gl.bytes[j] = (uint32_t)s->lcur[k].bytes;
+            if ((e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, s->cur[k].ptr, s->cur[k].bytes,
+                                     cudaMemcpyHostToDevice, s->s_h2d)) ||
+                (e = cudaMemcpyAsync(s->d_in2[slot] + (size_t)j * s->stride, s->lcur[k].ptr, s->lcur[k].bytes,
+                                     cudaMemcpyHostToDevice, s->s_h2d)))
+                return cuda_fail(s, e, "H2D chunk");
+            s->st.bytes_h2d += s->cur[k].bytes + s->lcur[k].bytes;
+        }
+        if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0)))
+            return cuda_fail(s, e, "record h2d");
+        if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0)))
+            return cuda_fail(s, e, "wait d2h");
+        if ((e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gp, s->d_amps, 1.0, s->d_err, s->s_comp)) ||
+            (e = launch_decode<R>(s->d_in2[slot], s->stride, c, s->dtype, gch, gl, s->d_amps2, 1.0, s->d_err,
+                                  s->s_comp)))
+            return cuda_fail(s, e, "decode");
+        s->st.kernel_launches += 2;
+        const uint64_t gbase = base << c;
+        for (size_t i = 0; i < tds.size(); i++) {
+            if ((e = launch_adjoint<R>(s->d_amps, s->d_amps2, tds[i], d_ops + offs[i], cnts[i], gbase, d_gpart, ntiles,
+                                       s->s_comp)))
+                return cuda_fail(s, e, "adjoint");
+            s->st.kernel_launches++;
+            if (nsl[i] > 0) {
+                if ((e = launch_sum_partials(d_gpart, nsl[i], (int)ntiles, d_acc + 1 + gslot[i], s->s_comp)))
+                    return cuda_fail(s, e, "grad reduce");
+                s->st.kernel_launches++;
+            }
+        }
+        int launches = 0;
+        if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)) ||
+            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->k, gch, s->d_out2[slot], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches)) ||
+            (e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
+                                 s->s_comp)) ||
+            (e = cudaMemcpyAsync(s->h_co2[slot], s->d_co2[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
+                                 s->s_comp)) ||
+            (e = cudaEventRecord(s->ev_comp[slot], s->s_comp)))
+            return cuda_fail(s, e, "encode");
+        s->st.kernel_launches += launches;
+        s->slot_used[slot] = true;
+        s->st.groups++;
+        s->st.subpasses += tds.size();
+        return SV_OK;
+    };
+    auto finish = [&](uint64_t gi) -> int {
+        const int slot = (int)(gi % NS);
+        int rr = wait_event(s, s->ev_comp[slot]);
+        if (rr) return rr;
+        cudaError_t e;
+        for (int j = 0; j < gch; j++) {
+            const uint64_t k = slot_chunks[slot][j];
+            const ChunkOut cp = s->h_co[slot][j], cl = s->h_co2[slot][j];
+            if (cp.bytes > s->stride || cl.bytes > s->stride)
+                return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
+            uint8_t* dp = arena_alloc(s, pa, cp.bytes);
+            uint8_t* dl = arena_alloc(s, la, cl.bytes);
+            if (!dp || !dl) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
+            if ((e = cudaMemcpyAsync(dp, s->d_out[slot] + (size_t)j * s->stride, cp.bytes, cudaMemcpyDeviceToHost,
+                                     s->s_d2h)) ||
+                (e = cudaMemcpyAsync(dl, s->d_out2[slot] + (size_t)j * s->stride, cl.bytes, cudaMemcpyDeviceToHost,
+                                     s->s_d2h)))
+                return cuda_fail(s, e, "D2H chunk");
+            s->nxt[k] = {dp, cp.bytes};
+            s->lnxt[k] = {dl, cl.bytes};
+            s->st.bytes_d2h += cp.bytes + cl.bytes;
+        }
+        if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h))) return cuda_fail(s, e, "record d2h");
+        return SV_OK;
+    };
+    for (uint64_t gi = 0; gi <= ngroups; gi++) {
+        if (gi < ngroups && (r = issue(gi))) return r;
+        if (gi >= 1 && (r = finish(gi - 1))) return r;
+    }
+    if ((r = sync_all(s))) return r;
+    if ((r = check_device_error(s))) return r;
+    s->cur.swap(s->nxt);
+    s->lcur.swap(s->lnxt);
+    s->cur_arena = 1 - s->cur_arena;
+    s->lcur_arena = 1 - s->lcur_arena;
+    s->st.passes++;
+    return SV_OK;
+}
+
+template <typename R>
+int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
+                    size_t nterms, double* energy, double* grad)
+{
+    int r = ensure_lambda_store<R>(s);
+    if (r) return r;
+    if ((r = init_state<R>(s))) return r;
+    const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
+    for (const PassPlan& pp : passes)
+        if ((r = run_pass_compressed<R>(s, gates, pp))) return r;
+    std::vector<sv_pauli_term> phys(nterms);
+    for (size_t i = 0; i < nterms; i++) {
+        phys[i] = H[i];
+        phys[i].xmask = mask_to_physical(s->perm, H[i].xmask);
+        phys[i].zmask = mask_to_physical(s->perm, H[i].zmask);
+    }
+    std::vector<PGate> inv(gates.size());
+    size_t nparam_gates = 0;
+    for (size_t i = 0; i < gates.size(); i++) {
+        inv[i] = gates[i];
+        const int K = 1 << gates[i].nt;
+        for (int a = 0; a < K; a++)
+            for (int b = 0; b < K; b++) inv[i].m[a * K + b] = std::conj(gates[i].m[b * K + a]);
+        if (gates[i].param >= 0) nparam_gates++;
+    }
+    const int nblocks = reduce_blocks_for(1ull << s->c);
+    const int L = s->c + std::min(s->gmax, s->nh);
+    int t, l;
+    tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
+    const size_t gpart_cap = std::max<size_t>(1, nparam_gates) << (L - t);
+    PauliDev* d_terms = nullptr;
+    double *d_part = nullptr, *d_acc = nullptr, *d_gpart = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms))) ||
+        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
+        (e = cudaMalloc(&d_acc, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)))) ||
+        (e = cudaMalloc(&d_gpart, sizeof(double) * gpart_cap))) {
+        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc); cudaFree(d_gpart);
+        return cuda_fail(s, e, "cudaMalloc(grad)");
+    }
+    std::vector<int> slot_params;
+    do {
+        cudaMemsetAsync(d_acc, 0, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)), s->s_comp);
+        if ((r = build_lambda<R>(s, phys, d_terms, d_part, nblocks, d_acc))) break;
+        for (size_t p = passes.size(); p-- > 0;)
+            if ((r = run_pass_adjoint_compressed<R>(s, inv, passes[p], d_gpart, gpart_cap, d_acc, slot_params)))
+                break;
+        if (r) break;
+        std::vector<double> acc(1 + slot_params.size());
+        if ((e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s->s_comp))) {
+            r = cuda_fail(s, e, "D2H grad");
+            break;
+        }
+        if ((r = wait_stream(s, s->s_comp))) break;
+        *energy = acc[0];
+        for (size_t p = 0; p < nparams; p++) grad[p] = 0;
+        for (size_t j = 0; j < slot_params.size(); j++) grad[slot_params[j]] += acc[1 + j];
+    } while (0);
+    cudaFree(d_terms);
+    cudaFree(d_part);
+    cudaFree(d_acc);
+    cudaFree(d_gpart);
+    if (!r) r = check_device_error(s);
+    return r;
+}
+
+template int grad_compressed<float>(sv_state*, const std::vector<PGate>&, size_t, const sv_pauli_term*, size_t,
+                                    double*, double*);
+template int grad_compressed<double>(sv_state*, const std::vector<PGate>&, size_t, const sv_pauli_term*, size_t,
+                                     double*, double*);
 template int apply_circuit<float>(sv_state*, const std::vector<PGate>&);
 template int apply_circuit<double>(sv_state*, const std::vector<PGate>&);
 template int init_state<float>(sv_state*);

@@ -21,6 +21,9 @@ template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& g
 template <typename R> int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out);
 template <typename R> int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
 template <typename R>
+int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
+                    size_t nterms, double* energy, double* grad);
+template <typename R>
 int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
                       size_t nterms, double* energy, double* grad);
 

@@ -217,14 +217,16 @@ static bool try_fuse(HOp& a, const HOp& b)
     return true;
 }
 
-std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse)
+std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
 {
     std::vector<SubPlan> subs;
     const uint64_t low = (l >= 64) ? ~0ull : ((1ull << l) - 1);
+    const int fl = first_l > 0 ? std::min(first_l, t) : l;
+    const uint64_t first_low = (fl >= 64) ? ~0ull : ((1ull << fl) - 1);
     std::vector<int> remaining(ops.size());
     for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
-        uint64_t T = low, bL = 0, bG = 0;
+        uint64_t T = subs.empty() ? first_low : low, bL = 0, bG = 0;
         SubPlan sp;
         std::vector<int> deferred;
         for (int oi : remaining) {
@@ -323,6 +325,117 @@ void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, 
         out.push_back(d);
     }
 }
+
+// --------------------------------------------------------- register phases
+static int classify_2x2(const cd* m)
+{
+    if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) return POP_SWAP;
+    bool real = true, rx = true;
+    for (int i = 0; i < 4; i++)
+        if (m[i].imag() != 0) real = false;
+    if (m[0].imag() != 0 || m[3].imag() != 0 || m[1].real() != 0 || m[2].real() != 0) rx = false;
+    if (real) return POP_REAL;
+    if (rx) return POP_RXLIKE;
+    return POP_GENERIC;
+}
+
+template <typename R>
+void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out)
+{
+    int tbit[64];  // local position -> tile bit (-1 outside the tile)
+    for (int p = 0; p < 64; p++) tbit[p] = -1;
+    for (int p = 0; p < td.l; p++) tbit[p] = p;
+    for (int i = 0; i < td.t - td.l; i++) tbit[td.hpos[i]] = td.l + i;
+    const int nops = (int)sp.ops.size();
+    std::vector<uint32_t> mix(nops, 0);
+    for (int i = 0; i < nops; i++) {
+        const HOp& o = sp.ops[i];
+        for (int p = 0; p < 64; p++)
+            if ((o.mixL >> p) & 1) mix[i] |= 1u << tbit[p];
+    }
+    std::vector<int> remaining(nops);
+    for (int i = 0; i < nops; i++) remaining[i] = i;
+    while (!remaining.empty()) {
+        uint32_t Rm = 0;
+        uint64_t bL = 0, bG = 0;
+        std::vector<int> placed, deferred;
+        for (int oi : remaining) {
+            const HOp& o = sp.ops[oi];
+            if ((o.qL & bL) || (o.qG & bG)) {
+                deferred.push_back(oi);
+                bL |= o.qL;
+                bG |= o.qG;
+                continue;
+            }
+            if (popc(Rm | mix[oi]) <= kPhaseRegBits) {
+                Rm |= mix[oi];
+                placed.push_back(oi);
+            } else {
+                deferred.push_back(oi);
+                bL |= o.qL;
+                bG |= o.qG;
+            }
+        }
+        for (int b = 0; b < td.t && popc(Rm) < kPhaseRegBits; b++) Rm |= 1u << b;
+        Phase ph{};
+        int reg_of[32];
+        for (int b = 0; b < 32; b++) reg_of[b] = -1;
+        int j = 0;
+        for (int b = 0; b < td.t; b++)
+            if ((Rm >> b) & 1) { ph.rpos[j] = (int8_t)b; reg_of[b] = j++; }
+        // thread bits 0..3 on tile bits of distinct residues mod 4 (bank spread), then the rest
+        bool used[32] = {};
+        int k = 0;
+        for (int r = 0; r < 4; r++)
+            for (int b = r; b < td.t; b += 4)
+                if (!((Rm >> b) & 1) && !used[b]) { ph.tpos[k++] = (int8_t)b; used[b] = true; break; }
+        for (int b = 0; b < td.t; b++)
+            if (!((Rm >> b) & 1) && !used[b]) { ph.tpos[k++] = (int8_t)b; used[b] = true; }
+        ph.op_begin = (int)out.size();
+        for (int oi : placed) {
+            const HOp& o = sp.ops[oi];
+            PhaseOp<R> d{};
+            d.d0 = d.d1 = -1;
+            for (int p = 0; p < 64; p++) {
+                if (!((o.cL >> p) & 1)) continue;
+                const int b = tbit[p];
+                if (b < 0) d.cmask_local |= 1ull << p;
+                else if (reg_of[b] >= 0) d.cmask_reg |= 1u << reg_of[b];
+                else d.cmask_tile |= 1u << b;
+            }
+            d.cmask_global = o.cG;
+            if (o.type == OP_DIAG) {
+                d.type = POP_DIAG;
+                int32_t* dst[2] = {&d.d0, &d.d1};
+                for (int i = 0; i < 2; i++) {
+                    const int s = o.dsrc[i];
+                    if (s < 0) *dst[i] = -1;
+                    else if (s >= kGlobalSrc) *dst[i] = PSRC_GLOBAL + (s - kGlobalSrc);
+                    else if (tbit[s] < 0) *dst[i] = PSRC_LOCAL + s;
+                    else if (reg_of[tbit[s]] >= 0) *dst[i] = PSRC_REG + reg_of[tbit[s]];
+                    else *dst[i] = PSRC_TILE + tbit[s];
+                }
+                for (int v = 0; v < 4; v++) { d.m[2 * v] = (R)o.m[v].real(); d.m[2 * v + 1] = (R)o.m[v].imag(); }
+            } else if (o.type == OP_DENSE1) {
+                d.type = classify_2x2(o.m);
+                d.r0 = reg_of[tbit[o.t[0]]];
+                for (int i = 0; i < 4; i++) { d.m[2 * i] = (R)o.m[i].real(); d.m[2 * i + 1] = (R)o.m[i].imag(); }
+            } else {
+                d.type = POP_DENSE2;
+                d.r0 = reg_of[tbit[o.t[0]]];
+                d.r1 = reg_of[tbit[o.t[1]]];
+                for (int i = 0; i < 16; i++) { d.m[2 * i] = (R)o.m[i].real(); d.m[2 * i + 1] = (R)o.m[i].imag(); }
+            }
+            out.push_back(d);
+        }
+        ph.op_count = (int)out.size() - ph.op_begin;
+        phases.push_back(ph);
+        remaining.swap(deferred);
+    }
+}
+
+template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&);
+template void dev_phases<double>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<double>>&);
 
 template void dev_ops<float>(const SubPlan&, const TileDesc&, std::vector<DevOp<float>>&, int*, std::vector<int>*);
 template void dev_ops<double>(const SubPlan&, const TileDesc&, std::vector<DevOp<double>>&, int*,

@@ -134,6 +134,43 @@ k_hamiltonian(const typename V2<R>::T* __restrict__ psi, typename V2<R>::T* __re
     }
 }
 
+// One output chunk of lambda = H psi on compressed chunks: the source chunks
+// k ^ xh of every distinct high x-mask are staged side by side (slot s at
+// s << c); term t reads slot terms[t].pad, its low x-mask flips local bits,
+// and the sign from its z-mask on the source chunk's high bits is already in
+// its coefficient.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_ham_chunk(const typename V2<R>::T* __restrict__ psi_slots, typename V2<R>::T* __restrict__ lam, int c,
+            const PauliDev* __restrict__ terms, int nterms)
+{
+    using T = typename V2<R>::T;
+    const uint64_t count = 1ull << c;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        R ar = (R)0, ai = (R)0;
+        for (int tt = 0; tt < nterms; tt++) {
+            const PauliDev& P = terms[tt];
+            const uint64_t src = k ^ P.xl;
+            const T v = psi_slots[((uint64_t)P.pad << c) + src];
+            R vr = v.x, vi = v.y, tr;
+            switch (P.ny & 3) {
+                case 1: tr = vr; vr = -vi; vi = tr; break;
+                case 2: vr = -vr; vi = -vi; break;
+                case 3: tr = vr; vr = vi; vi = -tr; break;
+                default: break;
+            }
+            const R cf = (__popcll(src & P.zl) & 1) ? (R)(-P.coeff) : (R)P.coeff;
+            ar += cf * vr;
+            ai += cf * vi;
+        }
+        T o;
+        o.x = ar;
+        o.y = ai;
+        lam[k] = o;
+    }
+}
+
 // partials[block] = Re sum conj(A[i]) B[i] over the block's range (FP64 accumulation)
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
@@ -208,6 +245,18 @@ cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev
 }
 
 template <typename R>
+cudaError_t launch_ham_chunk(const void* psi_slots, void* lam, int c, const PauliDev* terms, int nterms,
+                             cudaStream_t st)
+{
+    using T = typename V2<R>::T;
+    const uint64_t count = 1ull << c;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((count + kThreads - 1) / kThreads, 152ull * 32);
+    k_ham_chunk<R><<<blocks, kThreads, 0, st>>>(static_cast<const T*>(psi_slots), static_cast<T*>(lam), c, terms,
+                                               nterms);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* partials, int nblocks, cudaStream_t st)
 {
     using T = typename V2<R>::T;
@@ -221,7 +270,8 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
     template cudaError_t launch_gather<R>(const void*, const uint64_t*, const uint64_t*, uint64_t, double*,     \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \
-    template cudaError_t launch_dot<R>(const void*, const void*, uint64_t, double*, int, cudaStream_t);
+    template cudaError_t launch_dot<R>(const void*, const void*, uint64_t, double*, int, cudaStream_t);     \
+    template cudaError_t launch_ham_chunk<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);
 SV_INST(float)
 SV_INST(double)
 #undef SV_INST

@@ -68,13 +68,18 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
                            const std::vector<int>& S, bool adjoint);
 
 // Tile sub-passes over L local positions (tiles of t qubits containing 0..l-1).
-std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse);
+// first_l > 0: the first sub-pass's tile must contain local bits 0..first_l-1.
+std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l = 0);
 
 // Tile descriptor and device ops of one sub-pass.
 TileDesc tile_desc(uint64_t T, int L, int t, int l);
 template <typename R>
 void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, int* grad_slot_base,
              std::vector<int>* slot_params);
+
+// Register phases of one sub-pass on a 2^12 tile (apply_phase.cu).
+template <typename R>
+void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out);
 
 // ------------------------------------------------------------- the store
 struct Segment {
@@ -124,6 +129,16 @@ struct sv_state {
     // uncompressed state / adjoint vectors
     void* d_state = nullptr;
     void* d_lam = nullptr;
+    // compressed adjoint: lambda = H psi as a second compressed chunk store with
+    // its own arenas and staging (allocated at the first compressed sv_grad)
+    std::vector<sv::ChunkRef> lcur, lnxt;
+    sv::Arena larena[2];
+    int lcur_arena = 0;
+    uint8_t* d_in2[4] = {};
+    uint8_t* d_out2[4] = {};
+    sv::ChunkOut* d_co2[4] = {};
+    sv::ChunkOut* h_co2[4] = {};
+    void* d_amps2 = nullptr;
     // device op list
     void* d_ops = nullptr;
     size_t ops_cap = 0;

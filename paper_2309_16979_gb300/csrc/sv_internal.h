@@ -71,6 +71,43 @@ struct DevOp {
     R m[32];               // dense1: 2x2, dense2: 4x4, diag: 4 entries; (re, im) pairs
 };
 
+// Register-phase form of a sub-pass (tiles of exactly kPhaseTileQubits
+// qubits, 256 threads, 16 amplitudes per thread): a phase keeps 4 tile
+// qubits in registers and applies every op whose mixing qubits are among
+// them; phases exchange amplitudes through shared memory.
+constexpr int kPhaseTileQubits = 12;
+constexpr int kPhaseRegBits = 4;
+
+enum PhaseOpType : int32_t {
+    POP_GENERIC = 0,  // 2x2 complex matrix on register bit r0
+    POP_REAL = 1,     // 2x2 real matrix
+    POP_RXLIKE = 2,   // real diagonal, imaginary off-diagonal: [[a, ib], [ic, d]]
+    POP_SWAP = 3,     // X: exchange the pair
+    POP_DENSE2 = 4,   // 4x4 complex matrix on register bits (r0, r1)
+    POP_DIAG = 5      // diagonal, entry index from up to two bit sources
+};
+// bit sources of a phase diagonal: register bit, thread (non-register tile) bit,
+// local bit outside the tile, global bit fixed per group
+enum : int32_t { PSRC_REG = 0, PSRC_TILE = 16, PSRC_LOCAL = 64, PSRC_GLOBAL = 128 };
+
+template <typename R>
+struct PhaseOp {
+    int32_t type;
+    int32_t r0, r1;         // register bits of dense targets
+    int32_t d0, d1;         // diagonal bit sources (PSRC_* + index) or -1
+    uint32_t cmask_reg;     // controls among register bits
+    uint32_t cmask_tile;    // controls among non-register tile bits (tile-bit mask)
+    uint64_t cmask_local;   // controls on local bits outside the tile
+    uint64_t cmask_global;  // controls on global bits fixed per group
+    R m[32];
+};
+
+struct Phase {
+    int32_t op_begin, op_count;
+    int8_t rpos[kPhaseRegBits];                          // register bit j <-> tile bit rpos[j]
+    int8_t tpos[kPhaseTileQubits - kPhaseRegBits];       // thread bit j <-> tile bit tpos[j]
+};
+
 constexpr int kMaxTileQubits = 13;
 constexpr int kMaxLocalQubits = 48;
 
@@ -106,6 +143,34 @@ template <typename R>
 cudaError_t launch_apply(void* amps, const TileDesc& td, const DevOp<R>* ops, int nops,
                          uint64_t gbase, cudaStream_t st);
 
+// Optional fusion of the chunk codec into a tile sub-pass (tiles whose rows
+// are whole 256-amplitude block pairs, i.e. l = 8): decode the group's chunk
+// streams straight into shared memory instead of reading amplitudes, and/or
+// encode the tile's block pairs (widths, anchors, packed staging, sum q^2)
+// instead of writing amplitudes; launch_encode_finish then completes the
+// streams (offset scan, header, compaction).
+struct FuseArgs {
+    int32_t decode = 0, encode = 0;
+    int32_t c = 0, dtype = 0, k = 0;
+    double scale = 1.0;
+    const uint8_t* in = nullptr;
+    size_t in_stride = 0;
+    GroupIn gin{};
+    uint8_t* out = nullptr;
+    size_t out_stride = 0;
+    uint32_t* sparse = nullptr;
+    unsigned long long* blocksq = nullptr;
+    int* err = nullptr;
+};
+
+template <typename R>
+cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* phases, int nphases,
+                                const PhaseOp<R>* ops, uint64_t gbase, const FuseArgs& fa, cudaStream_t st);
+
+cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* out, size_t stride,
+                                 const uint32_t* sparse, const unsigned long long* blocksq, ChunkOut* chunk_out,
+                                 cudaStream_t st, int* launches);
+
 template <typename R>
 cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st);
 
@@ -138,6 +203,10 @@ cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev
 template <typename R>
 cudaError_t launch_adjoint(void* psi, void* lam, const TileDesc& td, const DevOp<R>* ops, int nops,
                            uint64_t gbase, double* gpart, uint64_t tile_stride, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_ham_chunk(const void* psi_slots, void* lam, int c, const PauliDev* terms, int nterms,
+                             cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* partials,

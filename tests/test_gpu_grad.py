@@ -68,3 +68,48 @@ def test_autograd_function(SV):
     e_o, g_o = oracle.adjoint(n, gates, theta.detach().numpy(), terms)
     assert abs(e.item() - e_o) < 1e-12
     assert np.abs(theta.grad.numpy() - 2 * g_o).max() < 1e-11
+
+
+@pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
+def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
+    """psi and lambda both as compressed chunk stores. Each re-encoding moves
+    every stored real number by <= eb (L2 <= sqrt(2 * 2^n) eb); a gradient
+    term Im<lambda|G|psi> then moves by at most |lambda| |d psi| + |d lambda|
+    with |lambda| <= sum |c|, so
+    |d g| <= (sum|c| * P + P_rev + 1) sqrt(2 * 2^n) eb (+ arithmetic)."""
+    n, c, g = 12, 8, 3
+    gates, npar = W.hea(n, 2)
+    theta = W.normal_params(npar, seed=6)
+    terms = W.ising(n)
+    e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=3)
+    with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g) as s:
+        e, gr = s.grad(gates, theta, terms)
+        st = s.stats()
+    P = st["passes"]  # forward + reverse passes
+    scale = sum(abs(t.coeff) for t in terms)
+    q = np.sqrt(2.0 * (1 << n)) * eb
+    arith = 0.0 if dtype == "c128" else 64 * 2.0 ** -24 * len(gates) * scale
+    assert abs(e - e_o) <= (scale * P + 1) * q + arith + 1e-12
+    assert np.abs(gr - g_o).max() <= (scale * P + P + 1) * q + arith + 1e-12
+
+
+def test_compressed_adjoint_agrees_with_uncompressed_gpu(SV):
+    n = 13
+    gates, npar = W.hea(n, 2)
+    theta = W.normal_params(npar, seed=9)
+    terms = W.ising(n)
+    with SV(n, mode="uncompressed", dtype="c128") as s:
+        e_u, g_u = s.grad(gates, theta, terms)
+    with SV(n, 9, 1e-9, dtype="c128", max_group_qubits=4) as s:
+        e_c, g_c = s.grad(gates, theta, terms)
+    assert abs(e_c - e_u) < 1e-4 and np.abs(g_c - g_u).max() < 1e-4
+
+
+def test_compressed_adjoint_rejects_too_many_high_x_masks(SV):
+    from paper_2309_16979_gb300 import SvError
+    n, c = 12, 8
+    gates, npar = W.hea(n, 1)
+    terms = [W.PauliTerm(1.0, 1 << q, 0) for q in range(n)] + [W.PauliTerm(0.5, (1 << 11) | (1 << 8), 0)]
+    with SV(n, c, 1e-6, max_group_qubits=2) as s:
+        with pytest.raises(SvError):
+            s.grad(gates, W.normal_params(npar), terms)

@@ -214,3 +214,31 @@ def test_compressed_store_is_byte_exact_with_oracle_codec(SV):
         held = s.state().astype(np.complex64)
     again = oracle.compress_roundtrip(held, c, 1e-5)
     assert np.array_equal(again, held)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_fused_codec_agrees_with_separate_kernels(SV, dtype):
+    """Decode inside the first tile sub-pass / encode inside the last gives the
+    same stored state, within the quantisation bound, as separate kernels."""
+    n, c = 16, 9
+    gates = W.random_layers(n, 6, seed=12)
+    want = oracle.run(n, gates, init=5)
+    outs = []
+    for fuse in (True, False):
+        with SV(n, c, 1e-6, dtype=dtype, init_index=5, max_group_qubits=3, fuse_codec=fuse) as s:
+            s.apply(gates)
+            outs.append((s.state(), s.stats()))
+    for got, st in outs:
+        assert np.linalg.norm(got - want) <= compressed_l2_bound(n, 1e-6, st["passes"], len(gates), dtype)
+    assert outs[0][1]["kernel_launches"] < outs[1][1]["kernel_launches"]
+
+
+def test_phase_kernel_every_gate_kind_and_control(SV):
+    """Register-phase tiles (2^12 amplitudes) on every gate kind with controls
+    inside, outside and across tiles, complex128 at 1e-12."""
+    n = 15
+    gates = W.random_mixed(n, 400, seed=21)
+    want = oracle.run(n, gates, init=77)
+    with SV(n, mode="uncompressed", dtype="c128", init_index=77) as s:
+        s.apply(gates)
+        assert rel_l2(s.state(), want) <= 1e-12
