@@ -192,7 +192,9 @@ int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_i
  * param_index p (G = X, Y, Z for RX, RY, RZ).
  *   theta: host, nparams values. H: host Pauli terms. energy: host double.
  *   grad:  host, nparams doubles (overwritten).
- * Compressed states keep lambda as a second compressed chunk store and run
+ * Compressed states keep lambda as a second compressed chunk store (its
+ * quantisation step is the state's times the smallest power of two >= sum
+ * |coeff|, since |lambda_i| <= ||H|| <= sum |coeff|) and run
  * the reverse sweep pass by pass over both stores (re-encoding both after
  * every pass); lambda is built one chunk at a time from the source chunks
  * k ^ xh of every distinct high x-mask xh, which must number at most
@@ -225,6 +227,17 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
 int sv_plan(int n, int chunk_qubits, int max_group_qubits, int tile_qubits, const sv_gate* gates,
             size_t ngates, int32_t* order, int32_t* pass_of, uint64_t* staged, size_t* out_executed,
             size_t* out_passes, size_t* out_subpasses);
+
+/*
+ * Copy the compressed stream of chunk k (physical chunk index, 0 <=
+ * k < 2^(n - chunk_qubits)) of the stored state into h_buf (host, cap bytes);
+ * *h_nbytes receives its length (also when cap is too small, which returns
+ * SV_ERR_ARG). The stream is in the format of sv_codec_* (Sec. 2 "Offline
+ * stage": chunks stored compressed in CPU memory). SV_ERR_ARG in uncompressed
+ * mode. Physical chunk bits are logical qubits only while no SWAP has been
+ * applied.
+ */
+int sv_chunk_stream(const sv_state* s, uint64_t k, void* h_buf, size_t cap, size_t* h_nbytes);
 
 /* Counters and sizes of the handle. */
 int sv_stats(const sv_state* s, sv_stats_t* out);

@@ -97,6 +97,15 @@ class StateVector:
                               len(terms), C.byref(e), g.ctypes.data), "sv_grad", self._h)
         return e.value, g
 
+    def chunk_stream(self, k: int) -> bytes:
+        """The compressed stream of physical chunk k as stored in host memory."""
+        L = load()
+        nb = C.c_size_t(0)
+        L.sv_chunk_stream(self._h, k, None, 0, C.byref(nb))
+        buf = (C.c_uint8 * max(1, nb.value))()
+        _check(L.sv_chunk_stream(self._h, k, buf, nb.value, C.byref(nb)), "sv_chunk_stream", self._h)
+        return bytes(buf)[:nb.value]
+
     def stats(self) -> dict:
         st = _abi.SvStats()
         _check(load().sv_stats(self._h, C.byref(st)), "sv_stats", self._h)

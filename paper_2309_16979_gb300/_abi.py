@@ -58,7 +58,7 @@ class SvStats(C.Structure):
 EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "sv_amplitudes",
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
-           "sv_codec_encode_noalloc")
+           "sv_codec_encode_noalloc", "sv_chunk_stream")
 
 _lib = None
 
@@ -111,6 +111,8 @@ def load() -> C.CDLL:
     L.sv_plan.restype = C.c_int
     L.sv_codec_encode_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
     L.sv_codec_encode_noalloc.restype = C.c_int
+    L.sv_chunk_stream.argtypes = [P, C.c_uint64, P, SZ, C.POINTER(SZ)]
+    L.sv_chunk_stream.restype = C.c_int
     _lib = L
     return L
 

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "engine.h"
@@ -13,6 +14,10 @@ using namespace sv;
 namespace {
 
 thread_local std::string g_create_error;
+
+// Calls that apply gates use the module's constant-memory op tables: they
+// run one at a time per process (each call is synchronous).
+std::mutex g_apply_mu;
 
 double now_s()
 {
@@ -297,7 +302,10 @@ int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t ngates)
         return r;
     }
     cudaSetDevice(s->cfg.device);
-    r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg) : apply_circuit<double>(s, pg);
+    {
+        std::lock_guard<std::mutex> lock(g_apply_mu);
+        r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg) : apply_circuit<double>(s, pg);
+    }
     if (!r) {
         s->st.amp_gate_updates += (uint64_t)ngates << s->n;
         s->st.gates_applied += ngates;
@@ -354,6 +362,7 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
     int r = lower(s, gates, ngates, theta, nparams, true, pg);
     if (r) return r;
     cudaSetDevice(s->cfg.device);
+    std::lock_guard<std::mutex> lock(g_apply_mu);
     if (s->mode == SV_UNCOMPRESSED)
         r = s->dtype == SV_C64 ? grad_uncompressed<float>(s, pg, nparams, H, nterms, energy, grad)
                                : grad_uncompressed<double>(s, pg, nparams, H, nterms, energy, grad);
@@ -408,6 +417,16 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
     *out_executed = k;
     *out_passes = passes.size();
     *out_subpasses = subs;
+    return SV_OK;
+}
+
+int sv_chunk_stream(const sv_state* s, uint64_t k, void* h_buf, size_t cap, size_t* h_nbytes)
+{
+    if (!s || !h_nbytes || s->mode != SV_COMPRESSED || k >= s->cur.size()) return SV_ERR_ARG;
+    const ChunkRef& cr = s->cur[k];
+    *h_nbytes = cr.bytes;
+    if (!h_buf || cap < cr.bytes) return SV_ERR_ARG;
+    std::memcpy(h_buf, cr.ptr, cr.bytes);
     return SV_OK;
 }
 

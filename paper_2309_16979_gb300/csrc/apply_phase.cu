@@ -4,22 +4,28 @@
 //
 // One CTA of 256 threads owns one tile of 4096 amplitudes at a time. The tile
 // is read from HBM once (16-byte vectors along contiguous rows) into shared
-// memory and written back once. In between, the sub-pass's gates run in
-// phases: in a phase every thread holds the 16 amplitudes that vary over four
-// tile qubits (the phase's register qubits) and applies, in registers, every
-// gate whose mixing qubits are among them; the other eight tile bits are the
-// thread's index. Controls and diagonal bits on non-register tile bits are
-// per-thread constants, those outside the tile per-CTA constants.
+// memory and written back once -- or, when the codec is fused, decoded from /
+// encoded to the compressed chunk streams. In between, the sub-pass's gates
+// run in phases: in a phase every thread holds the 16 amplitudes that vary
+// over four tile qubits (the phase's register qubits) and applies, in
+// registers, every gate whose mixing qubits are among them; the other eight
+// tile bits are the thread's index. Controls and diagonal bits on
+// non-register tile bits are per-thread constants, those outside the tile
+// per-CTA constants.
 //
-// Shared memory is XOR-swizzled: amplitude i sits at i ^ (((i >> 4) ^ (i >> 8))
-// & 15), so the 16 lanes of a half-warp, whose four low thread bits the host
-// maps to tile bits of four different residues mod 4, hit 16 different bank
-// pairs whatever the register qubits are.
+// Per-gate cost is kept to the arithmetic: the sub-pass's phases and ops are
+// staged in shared memory once per CTA; each op is one record whose dense
+// `code` selects, through one jump table, code specialised at compile time
+// for its form (X exchange, real 2x2, RX-like 2x2, general 2x2, diagonals),
+// target register bit and whether it has register controls (a host-computed
+// 16-bit mask of the register indices that take part).
 //
-// Common 2x2 gates have cheaper forms: X (pair exchange, no arithmetic),
-// real matrices (H, RY, products: 4 multiply-adds per amplitude) and
-// [[a, ib], [ic, d]] with real a..d (RX-like), against 8 for a general
-// complex matrix; diagonal gates cost one complex product per amplitude.
+// Shared memory is XOR-swizzled: amplitude i sits at swz(i) = i ^ (((i >> 4)
+// ^ (i >> 8)) & 15), so the 16 lanes of a half-warp, whose four low thread
+// bits the host maps to tile bits of four different residues mod 4, hit 16
+// different bank pairs whatever the register qubits are. swz is linear over
+// XOR, so a phase's element address is swz(thread bits) ^ sroff[m], with the
+// sixteen register offsets pre-swizzled on the host.
 #include <algorithm>
 
 #include "codec_dev.cuh"
@@ -32,31 +38,44 @@ constexpr int kT = kPhaseTileQubits;  // 12
 constexpr int kN = 1 << kT;           // 4096 amplitudes per tile
 constexpr int kRegs = 1 << kPhaseRegBits;
 constexpr int kPhaseLowBits = 5;
+constexpr int kCodecWords = 2 * 264;    // per-warp codec staging (decode payload / encode packing)
+constexpr int kMaxStagedOps = 256;      // ops staged in shared memory per launch
+constexpr int kMaxStagedPhases = 64;    // phases staged in shared memory per launch
 
 template <typename R> struct V2;
 template <> struct V2<float> { using T = float2; };
 template <> struct V2<double> { using T = double2; };
 
+// Phase and op tables of the current pass in constant memory: read with a
+// warp-uniform index they are uniform values, so the per-op dispatch is a
+// uniform branch. Passes whose tables do not fit use the shared-memory path.
+__constant__ Phase c_phases[kConstPhases];
+__constant__ PhaseOp<float> c_ops_f[kConstOpsF];
+__constant__ PhaseOp<double> c_ops_d[kConstOpsD];
+
+template <typename R> __device__ __forceinline__ const PhaseOp<R>& cop(int i);
+template <> __device__ __forceinline__ const PhaseOp<float>& cop<float>(int i) { return c_ops_f[i]; }
+template <> __device__ __forceinline__ const PhaseOp<double>& cop<double>(int i) { return c_ops_d[i]; }
+
 __device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
 
-template <typename T, typename R>
-__device__ __forceinline__ T cmul(R ar, R ai, T b)
+__device__ __forceinline__ uint32_t const_bit(uint8_t s, uint32_t tb, uint64_t base, uint64_t gbase)
 {
-    T o;
-    o.x = ar * b.x - ai * b.y;
-    o.y = ar * b.y + ai * b.x;
-    return o;
+    if (s == kSrcNone) return 0;
+    if (s < 0x40) return (tb >> s) & 1u;
+    if (s < 0x80) return (uint32_t)((base >> (s - 0x40)) & 1ull);
+    return (uint32_t)((gbase >> (s - 0x80)) & 1ull);
 }
 
-// ---------------------------------------------------- 2x2 forms on bit B
-template <int B, typename T, typename R>
-__device__ __forceinline__ void d1_generic(T (&a)[kRegs], const R* m, uint32_t rm)
+// ------------------------------------------------------ 2x2 forms on bit B
+template <int B, bool C, typename T, typename R>
+__device__ __forceinline__ void f_generic(T (&a)[kRegs], const R* m, uint32_t am)
 {
     const R m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3], m4 = m[4], m5 = m[5], m6 = m[6], m7 = m[7];
 #pragma unroll
     for (int i = 0; i < kRegs; i++) {
         if (i & (1 << B)) continue;
-        if ((i & rm) != rm) continue;
+        if (C && !((am >> i) & 1u)) continue;
         const int j = i | (1 << B);
         const T x = a[i], y = a[j];
         T o0, o1;
@@ -69,14 +88,14 @@ __device__ __forceinline__ void d1_generic(T (&a)[kRegs], const R* m, uint32_t r
     }
 }
 
-template <int B, typename T, typename R>
-__device__ __forceinline__ void d1_real(T (&a)[kRegs], const R* m, uint32_t rm)
+template <int B, bool C, typename T, typename R>
+__device__ __forceinline__ void f_real(T (&a)[kRegs], const R* m, uint32_t am)
 {
     const R m0 = m[0], m2 = m[2], m4 = m[4], m6 = m[6];
 #pragma unroll
     for (int i = 0; i < kRegs; i++) {
         if (i & (1 << B)) continue;
-        if ((i & rm) != rm) continue;
+        if (C && !((am >> i) & 1u)) continue;
         const int j = i | (1 << B);
         const T x = a[i], y = a[j];
         T o0, o1;
@@ -90,14 +109,14 @@ __device__ __forceinline__ void d1_real(T (&a)[kRegs], const R* m, uint32_t rm)
 }
 
 // [[p, i q], [i r, s]] with real p, q, r, s (m[0] = p, m[3] = q, m[5] = r, m[6] = s)
-template <int B, typename T, typename R>
-__device__ __forceinline__ void d1_rx(T (&a)[kRegs], const R* m, uint32_t rm)
+template <int B, bool C, typename T, typename R>
+__device__ __forceinline__ void f_rx(T (&a)[kRegs], const R* m, uint32_t am)
 {
     const R p = m[0], q = m[3], r = m[5], s = m[6];
 #pragma unroll
     for (int i = 0; i < kRegs; i++) {
         if (i & (1 << B)) continue;
-        if ((i & rm) != rm) continue;
+        if (C && !((am >> i) & 1u)) continue;
         const int j = i | (1 << B);
         const T x = a[i], y = a[j];
         T o0, o1;
@@ -110,13 +129,13 @@ __device__ __forceinline__ void d1_rx(T (&a)[kRegs], const R* m, uint32_t rm)
     }
 }
 
-template <int B, typename T>
-__device__ __forceinline__ void d1_swap(T (&a)[kRegs], uint32_t rm)
+template <int B, bool C, typename T, typename R>
+__device__ __forceinline__ void f_swap(T (&a)[kRegs], const R*, uint32_t am)
 {
 #pragma unroll
     for (int i = 0; i < kRegs; i++) {
         if (i & (1 << B)) continue;
-        if ((i & rm) != rm) continue;
+        if (C && !((am >> i) & 1u)) continue;
         const int j = i | (1 << B);
         const T x = a[i];
         a[i] = a[j];
@@ -124,13 +143,64 @@ __device__ __forceinline__ void d1_swap(T (&a)[kRegs], uint32_t rm)
     }
 }
 
+template <typename T, typename R>
+__device__ __forceinline__ T cmul(R er, R ei, T x)
+{
+    T o;
+    o.x = er * x.x - ei * x.y;
+    o.y = er * x.y + ei * x.x;
+    return o;
+}
+
+// diagonal whose entry index has one register bit B; the other index bit is
+// constant per thread and selects the pair of factors
+template <int B, bool C, typename T, typename R>
+__device__ __forceinline__ void f_diag1(T (&a)[kRegs], const PhaseOp<R>& op, uint32_t tb, uint64_t base,
+                                        uint64_t gbase)
+{
+    const uint32_t cb = const_bit(op.csrc, tb, base, gbase);
+    const uint32_t lo = op.rsel ? cb : (cb << 1), hi = op.rsel ? (cb | 2u) : ((cb << 1) | 1u);
+    const R lr = op.m[2 * lo], li = op.m[2 * lo + 1], hr = op.m[2 * hi], hv = op.m[2 * hi + 1];
+    const uint32_t am = op.amask;
+#pragma unroll
+    for (int i = 0; i < kRegs; i++) {
+        if (C && !((am >> i) & 1u)) continue;
+        a[i] = (i & (1 << B)) ? cmul<T, R>(hr, hv, a[i]) : cmul<T, R>(lr, li, a[i]);
+    }
+}
+
+template <int B0, int B1, bool C, typename T, typename R>
+__device__ __forceinline__ void f_diag2(T (&a)[kRegs], const R* m, uint32_t am)
+{
+#pragma unroll
+    for (int i = 0; i < kRegs; i++) {
+        if (C && !((am >> i) & 1u)) continue;
+        const int v = ((i >> B0) & 1) | (((i >> B1) & 1) << 1);
+        a[i] = cmul<T, R>(m[2 * v], m[2 * v + 1], a[i]);
+    }
+}
+
+template <bool C, typename T, typename R>
+__device__ __forceinline__ void f_diagt(T (&a)[kRegs], const PhaseOp<R>& op, uint32_t tb, uint64_t base,
+                                        uint64_t gbase)
+{
+    const uint32_t v = const_bit(op.csrc, tb, base, gbase) | (const_bit(op.csrc1, tb, base, gbase) << 1);
+    const R er = op.m[2 * v], ei = op.m[2 * v + 1];
+    const uint32_t am = op.amask;
+#pragma unroll
+    for (int i = 0; i < kRegs; i++) {
+        if (C && !((am >> i) & 1u)) continue;
+        a[i] = cmul<T, R>(er, ei, a[i]);
+    }
+}
+
 template <int B0, int B1, typename T, typename R>
-__device__ __forceinline__ void d2(T (&a)[kRegs], const R* m, uint32_t rm)
+__device__ __forceinline__ void f_dense2(T (&a)[kRegs], const R* m, uint32_t am)
 {
 #pragma unroll
     for (int i = 0; i < kRegs; i++) {
         if (i & ((1 << B0) | (1 << B1))) continue;
-        if ((i & rm) != rm) continue;
+        if (!((am >> i) & 1u)) continue;
         int idx[4];
         T v[4];
 #pragma unroll
@@ -154,92 +224,146 @@ __device__ __forceinline__ void d2(T (&a)[kRegs], const R* m, uint32_t rm)
     }
 }
 
+// 4x4 ops are rare (two-target custom gates): they run out of line on the
+// thread's own 16 shared-memory slots, so the register array is never
+// addressed and stays in registers on the common path.
 template <typename T, typename R>
-__device__ __forceinline__ void apply_d1(int type, int r0, T (&a)[kRegs], const R* m, uint32_t rm)
+__device__ __noinline__ void apply_dense2_smem(uint32_t bits, T* s, const uint16_t* sroff, uint32_t stb, const R* m,
+                                               uint32_t am)
 {
-#define SV_D1_CASE(B)                                          \
-    case B:                                                    \
-        if (type == POP_SWAP) d1_swap<B>(a, rm);               \
-        else if (type == POP_REAL) d1_real<B>(a, m, rm);       \
-        else if (type == POP_RXLIKE) d1_rx<B>(a, m, rm);       \
-        else d1_generic<B>(a, m, rm);                          \
-        break;
-    switch (r0) {
-        SV_D1_CASE(0)
-        SV_D1_CASE(1)
-        SV_D1_CASE(2)
-        SV_D1_CASE(3)
-        default: break;
-    }
-#undef SV_D1_CASE
-}
-
-template <typename T, typename R>
-__device__ __forceinline__ void apply_d2(int r0, int r1, T (&a)[kRegs], const R* m, uint32_t rm)
-{
-    switch (r0 * 4 + r1) {
-        case 1: d2<0, 1>(a, m, rm); break;
-        case 2: d2<0, 2>(a, m, rm); break;
-        case 3: d2<0, 3>(a, m, rm); break;
-        case 4: d2<1, 0>(a, m, rm); break;
-        case 6: d2<1, 2>(a, m, rm); break;
-        case 7: d2<1, 3>(a, m, rm); break;
-        case 8: d2<2, 0>(a, m, rm); break;
-        case 9: d2<2, 1>(a, m, rm); break;
-        case 11: d2<2, 3>(a, m, rm); break;
-        case 12: d2<3, 0>(a, m, rm); break;
-        case 13: d2<3, 1>(a, m, rm); break;
-        case 14: d2<3, 2>(a, m, rm); break;
-        default: break;
-    }
-}
-
-// constant part of a diagonal source; sets reg_bit (or -1) for register sources
-__device__ __forceinline__ uint32_t diag_src(int32_t src, uint32_t tb, uint64_t base, uint64_t gbase, int& reg_bit)
-{
-    reg_bit = -1;
-    if (src < 0) return 0;
-    if (src < PSRC_TILE) { reg_bit = src - PSRC_REG; return 0; }
-    if (src < PSRC_LOCAL) return (tb >> (src - PSRC_TILE)) & 1u;
-    if (src < PSRC_GLOBAL) return (uint32_t)((base >> (src - PSRC_LOCAL)) & 1ull);
-    return (uint32_t)((gbase >> (src - PSRC_GLOBAL)) & 1ull);
-}
-
-template <typename T, typename R>
-__device__ __forceinline__ void apply_diag(const PhaseOp<R>& op, T (&a)[kRegs], uint32_t tb, uint64_t base,
-                                           uint64_t gbase, uint32_t rm)
-{
-    int rb0, rb1;
-    const uint32_t c0 = diag_src(op.d0, tb, base, gbase, rb0);
-    const uint32_t c1 = diag_src(op.d1, tb, base, gbase, rb1);
-    const R e0r = op.m[0], e0i = op.m[1], e1r = op.m[2], e1i = op.m[3];
-    const R e2r = op.m[4], e2i = op.m[5], e3r = op.m[6], e3i = op.m[7];
+    T a[kRegs];
 #pragma unroll
-    for (int i = 0; i < kRegs; i++) {
-        if ((i & rm) != rm) continue;
-        const uint32_t b0 = rb0 >= 0 ? ((uint32_t)i >> rb0) & 1u : c0;
-        const uint32_t b1 = rb1 >= 0 ? ((uint32_t)i >> rb1) & 1u : c1;
-        const uint32_t v = b0 | (b1 << 1);
-        const R er = v == 0 ? e0r : v == 1 ? e1r : v == 2 ? e2r : e3r;
-        const R ei = v == 0 ? e0i : v == 1 ? e1i : v == 2 ? e2i : e3i;
-        a[i] = cmul<T, R>(er, ei, a[i]);
+    for (int i = 0; i < kRegs; i++) a[i] = s[stb ^ sroff[i]];
+    switch (bits) {  // b1 * 4 + b0
+        case 0x4: f_dense2<0, 1, T, R>(a, m, am); break;
+        case 0x8: f_dense2<0, 2, T, R>(a, m, am); break;
+        case 0xc: f_dense2<0, 3, T, R>(a, m, am); break;
+        case 0x1: f_dense2<1, 0, T, R>(a, m, am); break;
+        case 0x9: f_dense2<1, 2, T, R>(a, m, am); break;
+        case 0xd: f_dense2<1, 3, T, R>(a, m, am); break;
+        case 0x2: f_dense2<2, 0, T, R>(a, m, am); break;
+        case 0x6: f_dense2<2, 1, T, R>(a, m, am); break;
+        case 0xe: f_dense2<2, 3, T, R>(a, m, am); break;
+        case 0x3: f_dense2<3, 0, T, R>(a, m, am); break;
+        case 0x7: f_dense2<3, 1, T, R>(a, m, am); break;
+        case 0xb: f_dense2<3, 2, T, R>(a, m, am); break;
+        default: break;
+    }
+#pragma unroll
+    for (int i = 0; i < kRegs; i++) s[stb ^ sroff[i]] = a[i];
+}
+
+// Fused codec steps, out of line: they run once per row, not per gate.
+template <typename T, typename R>
+__device__ __noinline__ void decode_row(T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw, int lane)
+{
+    const uint64_t cmask = (1ull << fa.c) - 1;
+    const uint32_t r = (uint32_t)(li >> fa.c);
+    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
+    R x[2][8];
+    if (!codec::decode_pair<R>(fa.in + (size_t)r * fa.in_stride, fa.gin.bytes[r], fa.in_stride, fa.c, fa.dtype, bp,
+                               reinterpret_cast<uint32_t(*)[264]>(cw), (R)fa.scale, x, lane)) {
+        if (lane == 0) atomicOr(fa.err, kErrCorrupt);
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[0][m] = x[1][m] = (R)0;
+    }
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        T v;
+        v.x = x[0][m];
+        v.y = x[1][m];
+        s[swz(rw * 256u + 8u * lane + m)] = v;
     }
 }
 
-// Dynamic shared memory: the tile, then per-warp codec staging (decode
-// payload words / encode packing buffer, 2 x 264 words per warp).
-constexpr int kCodecWords = 2 * 264;
+template <typename T, typename R>
+__device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw,
+                                        int lane)
+{
+    const CodecLayout CL = codec_layout(fa.c);
+    const uint64_t cmask = (1ull << fa.c) - 1;
+    const uint32_t r = (uint32_t)(li >> fa.c);
+    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
+    R x[2][8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const T v = s[swz(rw * 256u + 8u * lane + m)];
+        x[0][m] = v.x;
+        x[1][m] = v.y;
+    }
+    codec::encode_pair<R>(x, fa.c, fa.k, bp, fa.out + (size_t)r * fa.out_stride,
+                          fa.sparse + (uint64_t)r * CL.nb * 256ull, fa.blocksq + (uint64_t)r * CL.bpc + bp,
+                          reinterpret_cast<uint32_t(*)[260]>(cw), fa.err, lane);
+}
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
+// Apply one staged op to the thread's 16 register amplitudes: one jump
+// table over the dense op code (4x4 ops go through the thread's shared slots).
+template <typename T, typename R>
+__device__ __forceinline__ void apply_op(const PhaseOp<R>& op, T (&a)[kRegs], uint32_t tb, uint64_t base,
+                                         uint64_t gbase, const R* __restrict__ dense2, T* s, const uint16_t* sroff,
+                                         uint32_t stb)
+{
+    const uint32_t am = op.amask;
+    const R* m = op.m;
+#define SV_D1(K, FN)                                            \
+    case K * 8 + 0: FN<0, false, T, R>(a, m, am); break;        \
+    case K * 8 + 1: FN<1, false, T, R>(a, m, am); break;        \
+    case K * 8 + 2: FN<2, false, T, R>(a, m, am); break;        \
+    case K * 8 + 3: FN<3, false, T, R>(a, m, am); break;        \
+    case K * 8 + 4: FN<0, true, T, R>(a, m, am); break;         \
+    case K * 8 + 5: FN<1, true, T, R>(a, m, am); break;         \
+    case K * 8 + 6: FN<2, true, T, R>(a, m, am); break;         \
+    case K * 8 + 7: FN<3, true, T, R>(a, m, am); break;
+#define SV_DG1(B, C) \
+    case PK_DIAG1 * 8 + (C ? 4 : 0) + B: f_diag1<B, C, T, R>(a, op, tb, base, gbase); break;
+#define SV_D2(B0, B1)                                                                        \
+    case kCodeDiag2 + B1 * 4 + B0: f_diag2<B0, B1, false, T, R>(a, m, am); break;            \
+    case kCodeDiag2 + 16 + B1 * 4 + B0: f_diag2<B0, B1, true, T, R>(a, m, am); break;
+    switch (op.code) {
+        SV_D1(PK_GENERIC, f_generic)
+        SV_D1(PK_REAL, f_real)
+        SV_D1(PK_RX, f_rx)
+        SV_D1(PK_SWAP, f_swap)
+        SV_DG1(0, false) SV_DG1(1, false) SV_DG1(2, false) SV_DG1(3, false)
+        SV_DG1(0, true) SV_DG1(1, true) SV_DG1(2, true) SV_DG1(3, true)
+        SV_D2(0, 1) SV_D2(0, 2) SV_D2(0, 3) SV_D2(1, 0) SV_D2(1, 2) SV_D2(1, 3)
+        SV_D2(2, 0) SV_D2(2, 1) SV_D2(2, 3) SV_D2(3, 0) SV_D2(3, 1) SV_D2(3, 2)
+        case kCodeDiagT: f_diagt<false, T, R>(a, op, tb, base, gbase); break;
+        case kCodeDiagT + 1: f_diagt<true, T, R>(a, op, tb, base, gbase); break;
+        case kCodeDense2: {
+#pragma unroll
+            for (int i = 0; i < kRegs; i++) s[stb ^ sroff[i]] = a[i];
+            apply_dense2_smem<T, R>(op.pad, s, sroff, stb, dense2 + 32ull * op.aux, am);
+#pragma unroll
+            for (int i = 0; i < kRegs; i++) a[i] = s[stb ^ sroff[i]];
+            break;
+        }
+        default: break;
+    }
+#undef SV_D1
+#undef SV_DG1
+#undef SV_D2
+}
+
+template <typename R, bool CT>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
 k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* __restrict__ phases, int nphases,
-               const PhaseOp<R>* __restrict__ ops, uint64_t gbase, uint64_t ntiles, FuseArgs fa)
+               const PhaseOp<R>* __restrict__ ops, int op0, int nops, const CtaCtrl* __restrict__ ctl,
+               const R* __restrict__ dense2, uint64_t gbase, uint64_t ntiles, FuseArgs fa, int ph_base)
 {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     T* s = reinterpret_cast<T*>(smem);
-    uint32_t* cw = reinterpret_cast<uint32_t*>(smem + (sizeof(T) << kT));
+    const bool ph_staged = !CT && nphases <= kMaxStagedPhases;
+    const bool op_staged = !CT && nops <= kMaxStagedOps;
+    unsigned char* p = smem + (sizeof(T) << kT);
+    Phase* sph = reinterpret_cast<Phase*>(p);
+    p += ph_staged ? sizeof(Phase) * (size_t)nphases : 0;
+    PhaseOp<R>* sops = reinterpret_cast<PhaseOp<R>*>(p);
+    p += op_staged ? sizeof(PhaseOp<R>) * (size_t)nops : 0;
+    uint32_t* cw = reinterpret_cast<uint32_t*>(p);
     __shared__ uint64_t rowoff[1 << (kT - kPhaseLowBits)];
+    __shared__ uint64_t tile_opos[kMaxLocalQubits];
     const int l = td.l;  // 5 (rows of 32 amplitudes) or 8 (rows = codec block pairs)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nrows = 1u << (kT - l), rmask = (1u << l) - 1u;
@@ -249,34 +373,30 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
             if ((rw >> i) & 1u) off |= 1ull << td.hpos[i];
         rowoff[rw] = off;
     }
-    const uint64_t cmask = (1ull << fa.c) - 1;
+    for (int i = threadIdx.x; i < td.nout; i += kThreads) tile_opos[i] = 1ull << td.opos[i];
+    if (ph_staged) {
+        const uint4* src = reinterpret_cast<const uint4*>(phases);
+        uint4* dst = reinterpret_cast<uint4*>(sph);
+        const int nvec = (int)(sizeof(Phase) * (size_t)nphases / 16);
+        for (int i = threadIdx.x; i < nvec; i += kThreads) dst[i] = src[i];
+    }
+    if (op_staged) {
+        const uint4* src = reinterpret_cast<const uint4*>(ops + op0);
+        uint4* dst = reinterpret_cast<uint4*>(sops);
+        const int nvec = (int)(sizeof(PhaseOp<R>) * (size_t)nops / 16);
+        for (int i = threadIdx.x; i < nvec; i += kThreads) dst[i] = src[i];
+    }
+    const Phase* phb = ph_staged ? sph : phases;
+    const PhaseOp<R>* opb = op_staged ? sops : ops + op0;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
         uint64_t base = 0;
         for (int i = 0; i < td.nout; i++)
-            if ((tile >> i) & 1ull) base |= 1ull << td.opos[i];
-        __syncthreads();
+            if ((tile >> i) & 1ull) base |= tile_opos[i];
         if (fa.decode) {
             // compressed streams -> shared: one warp per 256-amplitude block pair (row)
-            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32) {
-                const uint64_t li = base + rowoff[rw];
-                const uint32_t r = (uint32_t)(li >> fa.c);
-                const uint32_t bp = (uint32_t)((li & cmask) >> 8);
-                R x[2][8];
-                if (!codec::decode_pair<R>(fa.in + (size_t)r * fa.in_stride, fa.gin.bytes[r], fa.in_stride, fa.c,
-                                           fa.dtype, bp, reinterpret_cast<uint32_t(*)[264]>(cw + wid * kCodecWords),
-                                           (R)fa.scale, x, lane)) {
-                    if (lane == 0) atomicOr(fa.err, kErrCorrupt);
-#pragma unroll
-                    for (int m = 0; m < 8; m++) x[0][m] = x[1][m] = (R)0;
-                }
-#pragma unroll
-                for (int m = 0; m < 8; m++) {
-                    T v;
-                    v.x = x[0][m];
-                    v.y = x[1][m];
-                    s[swz(rw * 256u + 8u * lane + m)] = v;
-                }
-            }
+            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
+                decode_row<T, R>(s, rw, fa, base + rowoff[rw], cw + wid * kCodecWords, lane);
         } else {
             // HBM -> shared: 2 amplitudes (16 bytes for complex64) per access along rows
             for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
@@ -296,53 +416,32 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
         }
         __syncthreads();
         for (int ph = 0; ph < nphases; ph++) {
-            const Phase P = phases[ph];
+            const Phase& P = CT ? c_phases[ph_base + ph] : phb[ph];
             uint32_t tb = 0;
 #pragma unroll
             for (int j = 0; j < kT - kPhaseRegBits; j++) tb |= ((threadIdx.x >> j) & 1u) << P.tpos[j];
-            uint32_t roff[kRegs];
-#pragma unroll
-            for (int m = 0; m < kRegs; m++) {
-                uint32_t o = 0;
-#pragma unroll
-                for (int j = 0; j < kPhaseRegBits; j++)
-                    if ((m >> j) & 1) o |= 1u << P.rpos[j];
-                roff[m] = o;
-            }
+            const uint32_t stb = swz(tb);
             T a[kRegs];
 #pragma unroll
-            for (int m = 0; m < kRegs; m++) a[m] = s[swz(tb | roff[m])];
-            for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
-                const PhaseOp<R>& op = ops[oi];
-                if ((base & op.cmask_local) != op.cmask_local || (gbase & op.cmask_global) != op.cmask_global) continue;
-                if ((tb & op.cmask_tile) != op.cmask_tile) continue;
-                const uint32_t rm = op.cmask_reg;
-                if (op.type == POP_DIAG) apply_diag<T, R>(op, a, tb, base, gbase, rm);
-                else if (op.type == POP_DENSE2) apply_d2<T, R>(op.r0, op.r1, a, op.m, rm);
-                else apply_d1<T, R>(op.type, op.r0, a, op.m, rm);
+            for (int m = 0; m < kRegs; m++) a[m] = s[stb ^ P.sroff[m]];
+            const int oe = P.op_begin - op0 + P.op_count;
+            for (int oi = P.op_begin - op0; oi < oe; oi++) {
+                const PhaseOp<R>& op = CT ? cop<R>(op0 + oi) : opb[oi];
+                if (op.flags) {
+                    const CtaCtrl cc = ctl[op.aux];
+                    if ((base & cc.cl) != cc.cl || (gbase & cc.cg) != cc.cg) continue;
+                }
+                if ((tb & op.tmask) != op.tmask) continue;
+                apply_op<T, R>(op, a, tb, base, gbase, dense2, s, P.sroff, stb);
             }
 #pragma unroll
-            for (int m = 0; m < kRegs; m++) s[swz(tb | roff[m])] = a[m];
+            for (int m = 0; m < kRegs; m++) s[stb ^ P.sroff[m]] = a[m];
             __syncthreads();
         }
         if (fa.encode) {
             // shared -> codec: one warp per block pair; packed words go to the staging slots
-            const CodecLayout CL = codec_layout(fa.c);
-            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32) {
-                const uint64_t li = base + rowoff[rw];
-                const uint32_t r = (uint32_t)(li >> fa.c);
-                const uint32_t bp = (uint32_t)((li & cmask) >> 8);
-                R x[2][8];
-#pragma unroll
-                for (int m = 0; m < 8; m++) {
-                    const T v = s[swz(rw * 256u + 8u * lane + m)];
-                    x[0][m] = v.x;
-                    x[1][m] = v.y;
-                }
-                codec::encode_pair<R>(x, fa.c, fa.k, bp, fa.out + (size_t)r * fa.out_stride,
-                                      fa.sparse + (uint64_t)r * CL.nb * 256ull, fa.blocksq + (uint64_t)r * CL.bpc + bp,
-                                      reinterpret_cast<uint32_t(*)[260]>(cw + wid * kCodecWords), fa.err, lane);
-            }
+            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
+                encode_row<T, R>(s, rw, fa, base + rowoff[rw], cw + wid * kCodecWords, lane);
         } else {
             for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
                 const uint32_t i = 2 * e;
@@ -361,30 +460,72 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
 
 }  // namespace
 
+template <typename R> struct ConstOps;
+template <> struct ConstOps<float> { static constexpr int cap = kConstOpsF; };
+template <> struct ConstOps<double> { static constexpr int cap = kConstOpsD; };
+
 template <typename R>
-cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* phases, int nphases,
-                                const PhaseOp<R>* ops, uint64_t gbase, const FuseArgs& fa, cudaStream_t st)
+bool upload_const_tables(const Phase* phases, int nphases, const PhaseOp<R>* ops, int nops, cudaStream_t st)
+{
+    if (nphases > kConstPhases || nops > ConstOps<R>::cap) return false;
+    if (nphases &&
+        cudaMemcpyToSymbolAsync(c_phases, phases, sizeof(Phase) * nphases, 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return false;
+    if (nops) {
+        cudaError_t e = sizeof(R) == 4
+                            ? cudaMemcpyToSymbolAsync(c_ops_f, ops, sizeof(PhaseOp<R>) * nops, 0, cudaMemcpyHostToDevice, st)
+                            : cudaMemcpyToSymbolAsync(c_ops_d, ops, sizeof(PhaseOp<R>) * nops, 0, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return false;
+    }
+    return true;
+}
+
+template <typename R, bool CT>
+static cudaError_t launch_impl(void* amps, const TileDesc& td, const Phase* phases, int nphases, const PhaseOp<R>* ops,
+                               int op0, int nops, const CtaCtrl* ctl, const R* dense2, uint64_t gbase,
+                               const FuseArgs& fa, cudaStream_t st, int ph_base)
 {
     static bool attr_set = false;
-    const size_t smem = (sizeof(typename V2<R>::T) << kT) + sizeof(uint32_t) * kCodecWords * (kThreads / 32);
+    using T = typename V2<R>::T;
+    const size_t codec_bytes = sizeof(uint32_t) * kCodecWords * (kThreads / 32);
+    const size_t max_smem = (sizeof(T) << kT) + sizeof(Phase) * kMaxStagedPhases + sizeof(PhaseOp<R>) * kMaxStagedOps +
+                            codec_bytes;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_phases<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_apply_phases<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)max_smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (td.l != 5 && td.l != 8) return cudaErrorInvalidValue;
-    if ((fa.decode || fa.encode) && td.l != 8) return cudaErrorInvalidValue;
+    const size_t smem = (sizeof(T) << kT) +
+                        (!CT && nphases <= kMaxStagedPhases ? sizeof(Phase) * (size_t)nphases : 0) +
+                        (!CT && nops <= kMaxStagedOps ? sizeof(PhaseOp<R>) * (size_t)nops : 0) +
+                        ((fa.decode || fa.encode) ? codec_bytes : 0);
     const uint64_t ntiles = 1ull << (td.L - kT);
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, 152ull * 32);
-    k_apply_phases<R><<<grid, kThreads, smem, st>>>(static_cast<typename V2<R>::T*>(amps), td, phases, nphases, ops,
-                                                    gbase, ntiles, fa);
+    k_apply_phases<R, CT><<<grid, kThreads, smem, st>>>(static_cast<T*>(amps), td, phases, nphases, ops, op0, nops,
+                                                        ctl, dense2, gbase, ntiles, fa, ph_base);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_apply_phases<float>(void*, const TileDesc&, const Phase*, int, const PhaseOp<float>*,
-                                                uint64_t, const FuseArgs&, cudaStream_t);
+template <typename R>
+cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* phases, int nphases,
+                                const PhaseOp<R>* ops, int op0, int nops, const CtaCtrl* ctl, const R* dense2,
+                                uint64_t gbase, const FuseArgs& fa, cudaStream_t st, int ph_base)
+{
+    if (td.l != 5 && td.l != 8) return cudaErrorInvalidValue;
+    if ((fa.decode || fa.encode) && td.l != 8) return cudaErrorInvalidValue;
+    if (ph_base >= 0)
+        return launch_impl<R, true>(amps, td, phases, nphases, ops, op0, nops, ctl, dense2, gbase, fa, st, ph_base);
+    return launch_impl<R, false>(amps, td, phases, nphases, ops, op0, nops, ctl, dense2, gbase, fa, st, -1);
+}
+
+template bool upload_const_tables<float>(const Phase*, int, const PhaseOp<float>*, int, cudaStream_t);
+template bool upload_const_tables<double>(const Phase*, int, const PhaseOp<double>*, int, cudaStream_t);
+template cudaError_t launch_apply_phases<float>(void*, const TileDesc&, const Phase*, int, const PhaseOp<float>*, int,
+                                                int, const CtaCtrl*, const float*, uint64_t, const FuseArgs&,
+                                                cudaStream_t, int);
 template cudaError_t launch_apply_phases<double>(void*, const TileDesc&, const Phase*, int, const PhaseOp<double>*,
-                                                 uint64_t, const FuseArgs&, cudaStream_t);
+                                                 int, int, const CtaCtrl*, const double*, uint64_t, const FuseArgs&,
+                                                 cudaStream_t, int);
 
 }  // namespace sv

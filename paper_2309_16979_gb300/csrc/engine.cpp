@@ -216,12 +216,15 @@ struct DevPass {
     std::vector<int> off, cnt;
     std::vector<DevOp<R>> ops;
     bool use_phases = false;
+    bool const_tables = false; // phase / op tables uploaded to constant memory
     bool fuse_decode = false;  // first sub-pass decodes the chunk streams
     bool fuse_encode = false;  // last sub-pass encodes the block pairs
     std::vector<int> ph_off, ph_cnt;
     std::vector<Phase> phases;
     std::vector<PhaseOp<R>> pops;
-    size_t ops_at = 0, phases_at = 0, pops_at = 0;  // byte offsets in the uploaded blob
+    std::vector<CtaCtrl> ctl;
+    std::vector<R> d2m;
+    size_t ops_at = 0, phases_at = 0, pops_at = 0, ctl_at = 0, d2m_at = 0;  // byte offsets in the uploaded blob
 };
 
 template <typename R>
@@ -240,7 +243,7 @@ static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t,
         dp.td.push_back(td);
         dp.off.push_back((int)dp.ops.size());
         dp.ph_off.push_back((int)dp.phases.size());
-        if (dp.use_phases) dev_phases<R>(sp, td, dp.phases, dp.pops);
+        if (dp.use_phases) dev_phases<R>(sp, td, dp.phases, dp.pops, dp.ctl, dp.d2m);
         else dev_ops<R>(sp, td, dp.ops, nullptr, nullptr);
         dp.cnt.push_back((int)dp.ops.size() - dp.off.back());
         dp.ph_cnt.push_back((int)dp.phases.size() - dp.ph_off.back());
@@ -255,7 +258,14 @@ static int upload_pass(sv_state* s, DevPass<R>& dp)
     dp.ops_at = append_section(blob, dp.ops);
     dp.phases_at = append_section(blob, dp.phases);
     dp.pops_at = append_section(blob, dp.pops);
-    return upload_blob(s, blob);
+    dp.ctl_at = append_section(blob, dp.ctl);
+    dp.d2m_at = append_section(blob, dp.d2m);
+    int r = upload_blob(s, blob);
+    if (r) return r;
+    // phase / op tables also go to constant memory when they fit (uniform dispatch)
+    dp.const_tables = dp.use_phases && upload_const_tables<R>(dp.phases.data(), (int)dp.phases.size(),
+                                                              dp.pops.data(), (int)dp.pops.size(), s->s_comp);
+    return SV_OK;
 }
 
 // launch sub-pass i of an uploaded pass on a buffer of 2^L local amplitudes
@@ -265,10 +275,16 @@ static cudaError_t launch_subpass(sv_state* s, const DevPass<R>& dp, size_t i, v
 {
     const uint8_t* base = static_cast<const uint8_t*>(s->d_ops);
     static const FuseArgs none{};
-    if (dp.use_phases)
-        return launch_apply_phases<R>(amps, dp.td[i], reinterpret_cast<const Phase*>(base + dp.phases_at) + dp.ph_off[i],
-                                      dp.ph_cnt[i], reinterpret_cast<const PhaseOp<R>*>(base + dp.pops_at), gbase,
-                                      fa ? *fa : none, s->s_comp);
+    if (dp.use_phases) {
+        const int p0 = dp.ph_off[i], pn = dp.ph_cnt[i];
+        const int op0 = pn ? dp.phases[p0].op_begin : 0;
+        const int nops = pn ? dp.phases[p0 + pn - 1].op_begin + dp.phases[p0 + pn - 1].op_count - op0 : 0;
+        return launch_apply_phases<R>(amps, dp.td[i], reinterpret_cast<const Phase*>(base + dp.phases_at) + p0, pn,
+                                      reinterpret_cast<const PhaseOp<R>*>(base + dp.pops_at), op0, nops,
+                                      reinterpret_cast<const CtaCtrl*>(base + dp.ctl_at),
+                                      reinterpret_cast<const R*>(base + dp.d2m_at), gbase, fa ? *fa : none, s->s_comp,
+                                      dp.const_tables ? p0 : -1);
+    }
     return launch_apply<R>(amps, dp.td[i], reinterpret_cast<const DevOp<R>*>(base + dp.ops_at) + dp.off[i], dp.cnt[i],
                            gbase, s->s_comp);
 }
@@ -997,7 +1013,7 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         if ((e = launch_ham_chunk<R>(s->d_amps, s->d_amps2, c, d_terms, (int)hd.size(), s->s_comp)) ||
             (e = launch_dot<R>(s->d_amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
-            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->k, 1, s->d_out2[0], s->stride, s->d_sparse,
+            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, 1, s->d_out2[0], s->stride, s->d_sparse,
                                   s->d_blocksq, s->d_co2[0], s->d_err, s->s_comp, &launches)) ||
             (e = cudaMemcpyAsync(s->h_co2[0], s->d_co2[0], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)))
             return cuda_fail(s, e, "lambda chunk");
@@ -1107,7 +1123,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
         int launches = 0;
         if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
                                   s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)) ||
-            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->k, gch, s->d_out2[slot], s->stride, s->d_sparse,
+            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, gch, s->d_out2[slot], s->stride, s->d_sparse,
                                   s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches)) ||
             (e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
                                  s->s_comp)) ||
@@ -1203,6 +1219,13 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     std::vector<int> slot_params;
     do {
         cudaMemsetAsync(d_acc, 0, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)), s->s_comp);
+        // lambda = H psi has |lambda_i| <= ||H|| <= sum |c|: its store quantises with the
+        // step scaled by the next power of two of sum |c|, keeping q in range
+        double csum = 0;
+        for (size_t i = 0; i < nterms; i++) csum += std::fabs(H[i].coeff);
+        int up = 0;
+        while (std::ldexp(1.0, up) < csum && up < 40) up++;
+        s->kl = std::min(0, s->k + up);
         if ((r = build_lambda<R>(s, phys, d_terms, d_part, nblocks, d_acc))) break;
         for (size_t p = passes.size(); p-- > 0;)
             if ((r = run_pass_adjoint_compressed<R>(s, inv, passes[p], d_gpart, gpart_cap, d_acc, slot_params)))

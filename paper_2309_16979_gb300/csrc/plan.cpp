@@ -329,18 +329,19 @@ void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, 
 // --------------------------------------------------------- register phases
 static int classify_2x2(const cd* m)
 {
-    if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) return POP_SWAP;
+    if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) return PK_SWAP;
     bool real = true, rx = true;
     for (int i = 0; i < 4; i++)
         if (m[i].imag() != 0) real = false;
     if (m[0].imag() != 0 || m[3].imag() != 0 || m[1].real() != 0 || m[2].real() != 0) rx = false;
-    if (real) return POP_REAL;
-    if (rx) return POP_RXLIKE;
-    return POP_GENERIC;
+    if (real) return PK_REAL;
+    if (rx) return PK_RX;
+    return PK_GENERIC;
 }
 
 template <typename R>
-void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out)
+void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out,
+                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m)
 {
     int tbit[64];  // local position -> tile bit (-1 outside the tile)
     for (int p = 0; p < 64; p++) tbit[p] = -1;
@@ -392,41 +393,85 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
         for (int b = 0; b < td.t; b++)
             if (!((Rm >> b) & 1) && !used[b]) { ph.tpos[k++] = (int8_t)b; used[b] = true; }
         ph.op_begin = (int)out.size();
+        // constant bit source byte of a local position / global qubit (see kSrcNone)
+        auto csrc_of = [&](int s) -> uint8_t {
+            if (s < 0) return kSrcNone;
+            if (s >= kGlobalSrc) return (uint8_t)(0x80 + (s - kGlobalSrc));
+            if (tbit[s] < 0) return (uint8_t)(0x40 + s);
+            return (uint8_t)tbit[s];
+        };
         for (int oi : placed) {
             const HOp& o = sp.ops[oi];
             PhaseOp<R> d{};
-            d.d0 = d.d1 = -1;
+            d.csrc = d.csrc1 = kSrcNone;
+            uint32_t creg = 0;
+            CtaCtrl cc{0, 0};
             for (int p = 0; p < 64; p++) {
                 if (!((o.cL >> p) & 1)) continue;
                 const int b = tbit[p];
-                if (b < 0) d.cmask_local |= 1ull << p;
-                else if (reg_of[b] >= 0) d.cmask_reg |= 1u << reg_of[b];
-                else d.cmask_tile |= 1u << b;
+                if (b < 0) cc.cl |= 1ull << p;
+                else if (reg_of[b] >= 0) creg |= 1u << reg_of[b];
+                else d.tmask |= (uint16_t)(1u << b);
             }
-            d.cmask_global = o.cG;
+            cc.cg = o.cG;
+            if (cc.cl || cc.cg) {
+                d.flags = 1;
+                d.aux = (uint32_t)ctl.size();
+                ctl.push_back(cc);
+            }
+            uint32_t kind, b0 = 0, b1 = 0, excl = 0;
             if (o.type == OP_DIAG) {
-                d.type = POP_DIAG;
-                int32_t* dst[2] = {&d.d0, &d.d1};
-                for (int i = 0; i < 2; i++) {
-                    const int s = o.dsrc[i];
-                    if (s < 0) *dst[i] = -1;
-                    else if (s >= kGlobalSrc) *dst[i] = PSRC_GLOBAL + (s - kGlobalSrc);
-                    else if (tbit[s] < 0) *dst[i] = PSRC_LOCAL + s;
-                    else if (reg_of[tbit[s]] >= 0) *dst[i] = PSRC_REG + reg_of[tbit[s]];
-                    else *dst[i] = PSRC_TILE + tbit[s];
+                const int s0 = o.dsrc[0], s1 = o.dsrc[1];
+                const int r0 = (s0 >= 0 && s0 < kGlobalSrc && tbit[s0] >= 0) ? reg_of[tbit[s0]] : -1;
+                const int r1 = (s1 >= 0 && s1 < kGlobalSrc && tbit[s1] >= 0) ? reg_of[tbit[s1]] : -1;
+                if (r0 >= 0 && r1 >= 0) {
+                    kind = PK_DIAG2; b0 = r0; b1 = r1;
+                } else if (r0 >= 0 || r1 >= 0) {
+                    kind = PK_DIAG1;
+                    b0 = r0 >= 0 ? r0 : r1;
+                    d.rsel = r0 >= 0 ? 0 : 1;
+                    d.csrc = csrc_of(r0 >= 0 ? s1 : s0);
+                } else {
+                    kind = PK_DIAGT;
+                    d.csrc = csrc_of(s0);
+                    d.csrc1 = csrc_of(s1);
                 }
                 for (int v = 0; v < 4; v++) { d.m[2 * v] = (R)o.m[v].real(); d.m[2 * v + 1] = (R)o.m[v].imag(); }
             } else if (o.type == OP_DENSE1) {
-                d.type = classify_2x2(o.m);
-                d.r0 = reg_of[tbit[o.t[0]]];
+                kind = (uint32_t)classify_2x2(o.m);
+                b0 = reg_of[tbit[o.t[0]]];
+                excl = 1u << b0;  // pairs are enumerated from their b0 = 0 member
                 for (int i = 0; i < 4; i++) { d.m[2 * i] = (R)o.m[i].real(); d.m[2 * i + 1] = (R)o.m[i].imag(); }
             } else {
-                d.type = POP_DENSE2;
-                d.r0 = reg_of[tbit[o.t[0]]];
-                d.r1 = reg_of[tbit[o.t[1]]];
-                for (int i = 0; i < 16; i++) { d.m[2 * i] = (R)o.m[i].real(); d.m[2 * i + 1] = (R)o.m[i].imag(); }
+                kind = PK_DENSE2;
+                b0 = reg_of[tbit[o.t[0]]];
+                b1 = reg_of[tbit[o.t[1]]];
+                excl = (1u << b0) | (1u << b1);
+                d.aux = (uint32_t)(d2m.size() / 32);
+                for (int i = 0; i < 16; i++) { d2m.push_back((R)o.m[i].real()); d2m.push_back((R)o.m[i].imag()); }
+            }
+            // register indices that take part: every control bit set (pair/quad leaders only for dense ops)
+            uint32_t am = 0;
+            for (uint32_t i = 0; i < 16; i++)
+                if (!(i & excl) && (i & creg) == creg) am |= 1u << i;
+            d.amask = (uint16_t)am;
+            const uint32_t ctrl = creg != 0 ? 1u : 0u;
+            if (kind <= PK_DIAG1) d.code = (uint16_t)(kind * 8 + ctrl * 4 + b0);
+            else if (kind == PK_DIAG2) d.code = (uint16_t)(kCodeDiag2 + ctrl * 16 + b1 * 4 + b0);
+            else if (kind == PK_DIAGT) d.code = (uint16_t)(kCodeDiagT + ctrl);
+            else {
+                d.code = (uint16_t)kCodeDense2;
+                d.pad = (uint16_t)(b1 * 4 + b0);
             }
             out.push_back(d);
+        }
+        // swizzled shared-memory offset of each register index (the swizzle is
+        // linear over XOR, so the device adds the thread's part with one XOR)
+        for (int m = 0; m < 16; m++) {
+            uint32_t o = 0;
+            for (int q = 0; q < kPhaseRegBits; q++)
+                if ((m >> q) & 1) o |= 1u << ph.rpos[q];
+            ph.sroff[m] = (uint16_t)(o ^ (((o >> 4) ^ (o >> 8)) & 15u));
         }
         ph.op_count = (int)out.size() - ph.op_begin;
         phases.push_back(ph);
@@ -434,8 +479,10 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
     }
 }
 
-template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&);
-template void dev_phases<double>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<double>>&);
+template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&,
+                                std::vector<CtaCtrl>&, std::vector<float>&);
+template void dev_phases<double>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<double>>&,
+                                 std::vector<CtaCtrl>&, std::vector<double>&);
 
 template void dev_ops<float>(const SubPlan&, const TileDesc&, std::vector<DevOp<float>>&, int*, std::vector<int>*);
 template void dev_ops<double>(const SubPlan&, const TileDesc&, std::vector<DevOp<double>>&, int*,

@@ -79,7 +79,8 @@ void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, 
 
 // Register phases of one sub-pass on a 2^12 tile (apply_phase.cu).
 template <typename R>
-void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out);
+void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out,
+                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m);
 
 // ------------------------------------------------------------- the store
 struct Segment {
@@ -106,6 +107,7 @@ struct sv_state {
     int n = 0, c = 0, dtype = SV_C64, mode = SV_COMPRESSED;
     double eb = 0;
     int k = 0;                      // codec step exponent
+    int kl = 0;                     // step exponent of the lambda store (k + ceil(log2 sum|c|))
     sv_config cfg{};
     int gmax = 4, tq = 12, lq = 5, nslots = 3;
     int nh = 0;                     // high qubits n - c

@@ -78,35 +78,56 @@ struct DevOp {
 constexpr int kPhaseTileQubits = 12;
 constexpr int kPhaseRegBits = 4;
 
-enum PhaseOpType : int32_t {
-    POP_GENERIC = 0,  // 2x2 complex matrix on register bit r0
-    POP_REAL = 1,     // 2x2 real matrix
-    POP_RXLIKE = 2,   // real diagonal, imaginary off-diagonal: [[a, ib], [ic, d]]
-    POP_SWAP = 3,     // X: exchange the pair
-    POP_DENSE2 = 4,   // 4x4 complex matrix on register bits (r0, r1)
-    POP_DIAG = 5      // diagonal, entry index from up to two bit sources
+// Op kinds of a phase. A phase op's `code` is dense, so one jump-table
+// dispatch selects code specialised at compile time:
+//   kinds PK_GENERIC..PK_DIAG1 (one register bit b0): code = kind * 8 + ctrl * 4 + b0
+//   PK_DIAG2 (register bits b0, b1):                  code = 40 + ctrl * 16 + b1 * 4 + b0
+//   PK_DIAGT:                                          code = 72 + ctrl
+//   PK_DENSE2 (register bits b0, b1):                  code = 74, bits in `pad` (b1 * 4 + b0)
+// where ctrl says the op has controls among the register bits.
+enum PhaseOpKind : uint32_t {
+    PK_GENERIC = 0,  // 2x2 complex matrix on register bit b0
+    PK_REAL = 1,     // 2x2 real matrix
+    PK_RX = 2,       // [[p, i q], [i r, s]] with real p, q, r, s
+    PK_SWAP = 3,     // X: exchange the pair
+    PK_DIAG1 = 4,    // diagonal whose entry index has one register bit b0
+    PK_DIAG2 = 5,    // diagonal whose entry index bits are register bits (b0, b1)
+    PK_DIAGT = 6,    // diagonal whose entry index is constant per thread
+    PK_DENSE2 = 7    // 4x4 complex matrix on register bits (b0, b1), matrix in a side table
 };
-// bit sources of a phase diagonal: register bit, thread (non-register tile) bit,
-// local bit outside the tile, global bit fixed per group
-enum : int32_t { PSRC_REG = 0, PSRC_TILE = 16, PSRC_LOCAL = 64, PSRC_GLOBAL = 128 };
+constexpr uint32_t kCodeDiag2 = 40, kCodeDiagT = 72, kCodeDense2 = 74;
+// A constant bit source byte: 0xff none, 0..15 tile bit (a thread bit in the
+// phase), 0x40 + p local bit p outside the tile, 0x80 + q global bit q.
+constexpr uint8_t kSrcNone = 0xff;
 
 template <typename R>
 struct PhaseOp {
-    int32_t type;
-    int32_t r0, r1;         // register bits of dense targets
-    int32_t d0, d1;         // diagonal bit sources (PSRC_* + index) or -1
-    uint32_t cmask_reg;     // controls among register bits
-    uint32_t cmask_tile;    // controls among non-register tile bits (tile-bit mask)
-    uint64_t cmask_local;   // controls on local bits outside the tile
-    uint64_t cmask_global;  // controls on global bits fixed per group
-    R m[32];
+    uint16_t code;
+    uint16_t amask;  // register controls: bit i set = register index i takes part
+    uint16_t tmask;  // controls on thread (non-register tile) bits
+    uint8_t flags;   // bit 0: controls outside the tile, entry `aux` of the CTA control table
+    uint8_t csrc;    // PK_DIAG1: source of the entry-index bit that is not the register bit;
+                     // PK_DIAGT: source of entry-index bit 0
+    uint8_t csrc1;   // PK_DIAGT: source of entry-index bit 1
+    uint8_t rsel;    // PK_DIAG1: which entry-index bit (0 or 1) is the register bit
+    uint16_t pad;
+    uint32_t aux;    // CTA control table entry / PK_DENSE2 matrix index
+    R m[8];          // 2x2 matrix or 4 diagonal entries, (re, im) pairs
+};
+
+struct CtaCtrl {
+    uint64_t cl;  // local bits outside the tile that must be 1
+    uint64_t cg;  // global bits (fixed per group) that must be 1
 };
 
 struct Phase {
+    uint16_t sroff[1 << kPhaseRegBits];                  // swizzled tile offset of register index m
     int32_t op_begin, op_count;
     int8_t rpos[kPhaseRegBits];                          // register bit j <-> tile bit rpos[j]
     int8_t tpos[kPhaseTileQubits - kPhaseRegBits];       // thread bit j <-> tile bit tpos[j]
+    uint32_t pad[3];
 };
+static_assert(sizeof(Phase) == 64, "phase records are 64 bytes");
 
 constexpr int kMaxTileQubits = 13;
 constexpr int kMaxLocalQubits = 48;
@@ -163,9 +184,23 @@ struct FuseArgs {
     int* err = nullptr;
 };
 
+// Capacity of the constant-memory phase / op tables (one pass at a time).
+constexpr int kConstPhases = 128;
+constexpr int kConstOpsF = 640;
+constexpr int kConstOpsD = 256;
+
+// Copy a pass's phase and op tables to constant memory (stream-ordered);
+// returns false (nothing copied) when they do not fit.
+template <typename R>
+bool upload_const_tables(const Phase* phases, int nphases, const PhaseOp<R>* ops, int nops, cudaStream_t st);
+
+// ph_base >= 0: the sub-pass's phases start at c_phases[ph_base] and its ops
+// are read from the constant op table (upload_const_tables); otherwise from
+// `phases` / `ops` in device memory.
 template <typename R>
 cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* phases, int nphases,
-                                const PhaseOp<R>* ops, uint64_t gbase, const FuseArgs& fa, cudaStream_t st);
+                                const PhaseOp<R>* ops, int op0, int nops, const CtaCtrl* ctl, const R* dense2,
+                                uint64_t gbase, const FuseArgs& fa, cudaStream_t st, int ph_base = -1);
 
 cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* out, size_t stride,
                                  const uint32_t* sparse, const unsigned long long* blocksq, ChunkOut* chunk_out,

@@ -72,11 +72,12 @@ def test_autograd_function(SV):
 
 @pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
 def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
-    """psi and lambda both as compressed chunk stores. Each re-encoding moves
-    every stored real number by <= eb (L2 <= sqrt(2 * 2^n) eb); a gradient
-    term Im<lambda|G|psi> then moves by at most |lambda| |d psi| + |d lambda|
-    with |lambda| <= sum |c|, so
-    |d g| <= (sum|c| * P + P_rev + 1) sqrt(2 * 2^n) eb (+ arithmetic)."""
+    """psi and lambda both as compressed chunk stores. Each re-encoding of psi
+    moves every stored real number by <= eb (L2 <= sqrt(2 * 2^n) eb = q); the
+    lambda store's step is scaled by the next power of two of sum|c| (< 2
+    sum|c|), so its re-encodings move it by < 2 sum|c| q. A gradient term
+    Im<lambda|G|psi> moves by at most |lambda| |d psi| + |d lambda| with
+    |lambda| <= sum|c|: |d g| <= sum|c| (P + 2 (P + 1)) q (+ arithmetic)."""
     n, c, g = 12, 8, 3
     gates, npar = W.hea(n, 2)
     theta = W.normal_params(npar, seed=6)
@@ -89,8 +90,8 @@ def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
     scale = sum(abs(t.coeff) for t in terms)
     q = np.sqrt(2.0 * (1 << n)) * eb
     arith = 0.0 if dtype == "c128" else 64 * 2.0 ** -24 * len(gates) * scale
-    assert abs(e - e_o) <= (scale * P + 1) * q + arith + 1e-12
-    assert np.abs(gr - g_o).max() <= (scale * P + P + 1) * q + arith + 1e-12
+    assert abs(e - e_o) <= scale * P * q + arith + 1e-12
+    assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
 
 
 def test_compressed_adjoint_agrees_with_uncompressed_gpu(SV):
