@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--group", type=int, default=None)
     p.add_argument("--sets", type=int, default=None, help="parameter sets for c4-grad")
     p.add_argument("--no-extras", action="store_true", help="skip the comparator and baseline legs")
+    p.add_argument("--jit", type=int, default=1, choices=[0, 1],
+                   help="1: sub-pass kernels generated per gate sequence (default); 0: table-driven kernel")
     a = p.parse_args()
     w = dict(WORKLOADS[a.workload])
     for k, v in (("eb", a.eb), ("n", a.n), ("c", a.chunk), ("depth", a.depth), ("group", a.group),
@@ -274,7 +276,7 @@ def roofline_from_stats(d):
 
 STAT_KEYS = ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d", "bytes_d2h", "t_decode_s", "t_apply_s",
              "t_encode_s", "n_decode", "n_apply", "n_encode", "alg_bytes_decode", "alg_bytes_apply",
-             "alg_bytes_encode")
+             "alg_bytes_encode", "jit_launches")
 
 
 # ------------------------------------------------------------ our arm
@@ -293,7 +295,7 @@ def run_apply(args, rank, world):
     init = W.basis_index(n)
 
     sim = StateVector(n, c, w["eb"], dtype=w["dtype"], init_index=init, max_group_qubits=w["group"], profile=True,
-                      device=dev)
+                      device=dev, jit=bool(args.jit))
     for _ in range(args.warmup):
         sim.apply(gates)
     s0 = sim.stats()
@@ -351,6 +353,9 @@ def run_apply(args, rank, world):
                    "l2": "inputs larger than L2: every pass streams the whole state; groups of 2^(c+g) amplitudes",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": gpu_launches,
+        "kernels": {"generated": bool(args.jit), "compiled": st["jit_kernels_compiled"],
+                    "compile_s_before_timing": round(st["t_jit_compile_s"], 3),
+                    "generated_launches_per_step": d["jit_launches"] / args.steps},
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clk,
@@ -386,7 +391,8 @@ def comparator(args, gates, terms, energy_c, applies):
     n = w["n"]
     units = W.amp_gate_updates(n, gates)
     try:
-        with StateVector(n, mode="uncompressed", dtype=w["dtype"], init_index=W.basis_index(n), profile=True) as p:
+        with StateVector(n, mode="uncompressed", dtype=w["dtype"], init_index=W.basis_index(n), profile=True,
+                         jit=bool(args.jit)) as p:
             for _ in range(applies):
                 p.apply(gates)
             e_plain = p.expect(terms)

@@ -99,7 +99,11 @@ typedef struct sv_config {
     int32_t fuse_codec;           /* 1 (default): decode inside the first tile sub-pass and
                                      encode inside the last when their tiles hold whole codec
                                      blocks; 0: separate decode / encode kernels */
-    int32_t reserved1;
+    int32_t jit;                  /* 1 (default): every sub-pass on 2^12-amplitude tiles runs a kernel
+                                     generated for its gate sequence and compiled at run time with
+                                     NVRTC (cached per process, keyed by structure, not angles);
+                                     0: the table-driven phase kernel. Compilation errors fail the
+                                     call with SV_ERR_CUDA. */
     uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
@@ -126,6 +130,10 @@ typedef struct sv_stats_t {
     double t_decode_s, t_apply_s, t_encode_s;
     uint64_t n_decode, n_apply, n_encode;
     uint64_t alg_bytes_decode, alg_bytes_apply, alg_bytes_encode;
+    /* run-time generated sub-pass kernels: compiled by this handle's calls, their
+       launches, and the wall time spent generating, compiling and loading them */
+    uint64_t jit_kernels_compiled, jit_launches;
+    double t_jit_compile_s;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
@@ -205,6 +213,26 @@ int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_i
  */
 int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* theta, size_t nparams,
             const sv_pauli_term* H, size_t nterms, double* energy, double* grad);
+
+/*
+ * The CUDA C++ sources of the sub-pass kernels sv_apply_circuit would
+ * generate and compile at run time for this circuit (sv_config.jit), computed
+ * on the host only (no GPU is touched). The paper has no counterpart: this
+ * exposes the library's own code generator for inspection and testing.
+ *   n, chunk_qubits: as in sv_create (chunk_qubits ignored when cfg->mode is
+ *                    SV_UNCOMPRESSED).
+ *   cfg:             NULL for defaults; dtype, mode, max_group_qubits,
+ *                    tile_qubits and fuse_codec are used.
+ *   gates, ngates:   host gate list, validated as in sv_apply_circuit.
+ *   buf, cap:        host buffer receiving the sources, each terminated by a
+ *                    NUL byte, in launch order; NULL to query the size only.
+ *   needed:          receives the bytes required; nkernels the number of
+ *                    kernels (a sub-pass that cannot be specialised yields an
+ *                    empty source and runs the table-driven kernel).
+ * Errors: SV_ERR_ARG for invalid sizes or gates, or cap < *needed.
+ */
+int sv_jit_sources(int n, int chunk_qubits, const sv_config* cfg, const sv_gate* gates, size_t ngates, char* buf,
+                   size_t cap, size_t* needed, size_t* nkernels);
 
 /*
  * The chunk passes sv_apply_circuit would run, computed on the host only (no

@@ -37,7 +37,8 @@ class StateVector:
                  mode: str = "compressed", init_index: int = 0, max_group_qubits: int = 4,
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
-                 profile: bool = False, fuse_codec: bool = True):
+                 profile: bool = False, fuse_codec: bool = True,
+                 jit: bool = True):
         L = load()
         cfg = _abi.SvConfig()
         L.sv_config_default(C.byref(cfg))
@@ -53,6 +54,7 @@ class StateVector:
         cfg.device = device
         cfg.profile = int(profile)
         cfg.fuse_codec = int(fuse_codec)
+        cfg.jit = int(jit)
         h = C.c_void_p()
         _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
         self._h = h
@@ -145,6 +147,29 @@ def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, 
     k = ex.value
     return {"order": order[:k].tolist(), "pass_of": pass_of[:k].tolist(),
             "staged": [int(x) for x in staged[:npass.value]], "passes": npass.value, "subpasses": nsub.value}
+
+
+def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", mode: str = "compressed",
+                max_group_qubits: int = 4, tile_qubits: int = 0, fuse_codec: bool = True) -> list:
+    """Host-only: the CUDA C++ sources of the sub-pass kernels sv_apply_circuit
+    would generate for this circuit (sv_jit_sources), in launch order."""
+    L = load()
+    cfg = _abi.SvConfig()
+    L.sv_config_default(C.byref(cfg))
+    cfg.dtype = SV_C64 if dtype == "c64" else SV_C128
+    cfg.mode = SV_COMPRESSED if mode == "compressed" else SV_UNCOMPRESSED
+    cfg.max_group_qubits = max_group_qubits
+    cfg.tile_qubits = tile_qubits
+    cfg.fuse_codec = int(fuse_codec)
+    arr = _abi.gates_to_c(gates)
+    need, nk = C.c_size_t(0), C.c_size_t(0)
+    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), None, 0, C.byref(need),
+                            C.byref(nk)), "sv_jit_sources", None)
+    buf = C.create_string_buffer(max(1, need.value))
+    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), buf, need.value,
+                            C.byref(need), C.byref(nk)), "sv_jit_sources", None)
+    parts = buf.raw[:need.value].split(b"\0")[:nk.value]
+    return [x.decode() for x in parts]
 
 
 # ------------------------------------------------------------------ codec

@@ -37,7 +37,7 @@ class SvConfig(C.Structure):
     _fields_ = [("dtype", C.c_int32), ("mode", C.c_int32), ("init_index", C.c_uint64),
                 ("max_group_qubits", C.c_int32), ("tile_qubits", C.c_int32),
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
-                ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("reserved1", C.c_int32),
+                ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("jit", C.c_int32),
                 ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 
@@ -51,14 +51,16 @@ class SvStats(C.Structure):
                 ("t_decode_s", C.c_double), ("t_apply_s", C.c_double), ("t_encode_s", C.c_double),
                 ("n_decode", C.c_uint64), ("n_apply", C.c_uint64), ("n_encode", C.c_uint64),
                 ("alg_bytes_decode", C.c_uint64), ("alg_bytes_apply", C.c_uint64),
-                ("alg_bytes_encode", C.c_uint64)]
+                ("alg_bytes_encode", C.c_uint64),
+                ("jit_kernels_compiled", C.c_uint64), ("jit_launches", C.c_uint64),
+                ("t_jit_compile_s", C.c_double)]
 
 
 # every entry point declared in include/sv.h
 EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "sv_amplitudes",
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
-           "sv_codec_encode_noalloc", "sv_chunk_stream")
+           "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources")
 
 _lib = None
 
@@ -113,6 +115,9 @@ def load() -> C.CDLL:
     L.sv_codec_encode_noalloc.restype = C.c_int
     L.sv_chunk_stream.argtypes = [P, C.c_uint64, P, SZ, C.POINTER(SZ)]
     L.sv_chunk_stream.restype = C.c_int
+    L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_char_p, SZ, C.POINTER(SZ),
+                                 C.POINTER(SZ)]
+    L.sv_jit_sources.restype = C.c_int
     _lib = L
     return L
 

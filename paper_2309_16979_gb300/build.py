@@ -18,21 +18,48 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libsvgb300.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["codec.cu", "apply.cu", "apply_phase.cu", "reduce.cu", "noalloc.cu", "plan.cpp", "engine.cpp", "api.cpp"]
+SOURCES = ["codec.cu", "apply.cu", "apply_phase.cu", "reduce.cu", "noalloc.cu", "plan.cpp", "engine.cpp", "api.cpp",
+           "jit.cpp"]
+# device headers embedded into the library for the kernels it generates and
+# compiles at run time (jit.cpp)
+JIT_HEADERS = ["sv_dev_types.h", "codec_dev.cuh", "tile_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 
 def _flags():
     return ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-            "-I", INCLUDE, "-I", CSRC] + ARCH
+            "-I", INCLUDE, "-I", CSRC, "-I", BUILD] + ARCH
+
+
+def _write_jit_embed() -> str:
+    """Write _build/jit_embed.inc: the JIT device headers as raw string
+    literals (rewritten only when their text changes)."""
+    path = os.path.join(BUILD, "jit_embed.inc")
+    parts = ["// generated by build.py from " + ", ".join(JIT_HEADERS) + "\n"]
+    names, texts = [], []
+    for i, h in enumerate(JIT_HEADERS):
+        text = open(os.path.join(CSRC, h)).read()
+        tag = f"SVJ{i}"
+        assert f"){tag}\"" not in text
+        names.append(f'"{h}"')
+        texts.append(f'R"{tag}({text}){tag}"')
+    parts.append(f"static constexpr int kJitHeaderCount = {len(JIT_HEADERS)};\n")
+    parts.append("static const char* const kJitHeaderNames[] = {" + ", ".join(names) + "};\n")
+    parts.append("static const char* const kJitHeaders[] = {\n" + ",\n".join(texts) + "};\n")
+    content = "".join(parts)
+    if not os.path.exists(path) or open(path).read() != content:
+        with open(path, "w") as f:
+            f.write(content)
+    return path
 
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "sv.h"))
+    deps.append(os.path.join(BUILD, "jit_embed.inc"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [NVCC] + _flags() + ["-c", path, "-o", obj]
@@ -59,6 +86,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             os.remove(OUT)
         with open(stamp, "w") as f:
             f.write(arch + "\n")
+    _write_jit_embed()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if (not force and os.path.exists(OUT)

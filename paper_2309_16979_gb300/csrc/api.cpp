@@ -211,6 +211,7 @@ void sv_config_default(sv_config* cfg)
     cfg->device = 0;
     cfg->host_budget_bytes = 0;
     cfg->fuse_codec = 1;
+    cfg->jit = 1;
     cfg->timeout_s = 600.0;
 }
 
@@ -417,6 +418,47 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
     *out_executed = k;
     *out_passes = passes.size();
     *out_subpasses = subs;
+    return SV_OK;
+}
+
+int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, size_t ngates, char* buf, size_t cap,
+                   size_t* needed, size_t* nkernels)
+{
+    sv_config cfg;
+    sv_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (n < 1 || n > 40 || (ngates && !gates) || !needed || !nkernels) return SV_ERR_ARG;
+    if (cfg.mode == SV_COMPRESSED && (c < 8 || c > n)) return SV_ERR_ARG;
+    if (cfg.tile_qubits && (cfg.tile_qubits < 2 || cfg.tile_qubits > kMaxTileQubits)) return SV_ERR_ARG;
+    sv_state tmp;
+    tmp.n = n;
+    tmp.c = cfg.mode == SV_COMPRESSED ? c : n;
+    tmp.mode = cfg.mode;
+    tmp.dtype = cfg.dtype;
+    tmp.cfg = cfg;
+    tmp.gmax = cfg.max_group_qubits;
+    tmp.tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
+    tmp.lq = 5;
+    tmp.perm.resize(n);
+    for (int q = 0; q < n; q++) tmp.perm[q] = q;
+    std::vector<PGate> pg;
+    int r = lower(&tmp, gates, ngates, nullptr, 0, false, pg);
+    std::vector<std::string> src;
+    if (!r) r = cfg.dtype == SV_C128 ? jit_sources<double>(&tmp, pg, src) : jit_sources<float>(&tmp, pg, src);
+    if (r) {
+        g_create_error = tmp.err;
+        return r;
+    }
+    size_t total = 0;
+    for (const std::string& x : src) total += x.size() + 1;
+    *needed = total;
+    *nkernels = src.size();
+    if (!buf) return SV_OK;
+    if (cap < total) return SV_ERR_ARG;
+    for (const std::string& x : src) {
+        std::memcpy(buf, x.c_str(), x.size() + 1);
+        buf += x.size() + 1;
+    }
     return SV_OK;
 }
 

@@ -16,35 +16,30 @@
 // Per-gate cost is kept to the arithmetic: the sub-pass's phases and ops are
 // staged in shared memory once per CTA; each op is one record whose dense
 // `code` selects, through one jump table, code specialised at compile time
-// for its form (X exchange, real 2x2, RX-like 2x2, general 2x2, diagonals),
+// for its form (real 2x2, RX-like 2x2, general 2x2, diagonals),
 // target register bit and whether it has register controls (a host-computed
 // 16-bit mask of the register indices that take part).
 //
-// Shared memory is XOR-swizzled: amplitude i sits at swz(i) = i ^ (((i >> 4)
-// ^ (i >> 8)) & 15), so the 16 lanes of a half-warp, whose four low thread
-// bits the host maps to tile bits of four different residues mod 4, hit 16
-// different bank pairs whatever the register qubits are. swz is linear over
-// XOR, so a phase's element address is swz(thread bits) ^ sroff[m], with the
-// sixteen register offsets pre-swizzled on the host.
+// Shared memory holds the tile XOR-swizzled (tile_dev.cuh); a phase's element
+// address is swz(thread bits) ^ sroff[m], the sixteen register offsets
+// pre-swizzled on the host.
 #include <algorithm>
 
-#include "codec_dev.cuh"
+#include "sv_internal.h"
+#include "tile_dev.cuh"
 
 namespace sv {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kT = kPhaseTileQubits;  // 12
-constexpr int kN = 1 << kT;           // 4096 amplitudes per tile
+using tile::kThreads;
+using tile::kT;
+using tile::kN;
+using tile::kCodecWords;
+using tile::swz;
+using tile::V2;
 constexpr int kRegs = 1 << kPhaseRegBits;
-constexpr int kPhaseLowBits = 5;
-constexpr int kCodecWords = 2 * 264;    // per-warp codec staging (decode payload / encode packing)
 constexpr int kMaxStagedOps = 256;      // ops staged in shared memory per launch
 constexpr int kMaxStagedPhases = 64;    // phases staged in shared memory per launch
-
-template <typename R> struct V2;
-template <> struct V2<float> { using T = float2; };
-template <> struct V2<double> { using T = double2; };
 
 // Phase and op tables of the current pass in constant memory: read with a
 // warp-uniform index they are uniform values, so the per-op dispatch is a
@@ -56,8 +51,6 @@ __constant__ PhaseOp<double> c_ops_d[kConstOpsD];
 template <typename R> __device__ __forceinline__ const PhaseOp<R>& cop(int i);
 template <> __device__ __forceinline__ const PhaseOp<float>& cop<float>(int i) { return c_ops_f[i]; }
 template <> __device__ __forceinline__ const PhaseOp<double>& cop<double>(int i) { return c_ops_d[i]; }
-
-__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
 
 __device__ __forceinline__ uint32_t const_bit(uint8_t s, uint32_t tb, uint64_t base, uint64_t gbase)
 {
@@ -126,20 +119,6 @@ __device__ __forceinline__ void f_rx(T (&a)[kRegs], const R* m, uint32_t am)
         o1.y = s * y.y + r * x.x;
         a[i] = o0;
         a[j] = o1;
-    }
-}
-
-template <int B, bool C, typename T, typename R>
-__device__ __forceinline__ void f_swap(T (&a)[kRegs], const R*, uint32_t am)
-{
-#pragma unroll
-    for (int i = 0; i < kRegs; i++) {
-        if (i & (1 << B)) continue;
-        if (C && !((am >> i) & 1u)) continue;
-        const int j = i | (1 << B);
-        const T x = a[i];
-        a[i] = a[j];
-        a[j] = x;
     }
 }
 
@@ -253,49 +232,6 @@ __device__ __noinline__ void apply_dense2_smem(uint32_t bits, T* s, const uint16
     for (int i = 0; i < kRegs; i++) s[stb ^ sroff[i]] = a[i];
 }
 
-// Fused codec steps, out of line: they run once per row, not per gate.
-template <typename T, typename R>
-__device__ __noinline__ void decode_row(T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw, int lane)
-{
-    const uint64_t cmask = (1ull << fa.c) - 1;
-    const uint32_t r = (uint32_t)(li >> fa.c);
-    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
-    R x[2][8];
-    if (!codec::decode_pair<R>(fa.in + (size_t)r * fa.in_stride, fa.gin.bytes[r], fa.in_stride, fa.c, fa.dtype, bp,
-                               reinterpret_cast<uint32_t(*)[264]>(cw), (R)fa.scale, x, lane)) {
-        if (lane == 0) atomicOr(fa.err, kErrCorrupt);
-#pragma unroll
-        for (int m = 0; m < 8; m++) x[0][m] = x[1][m] = (R)0;
-    }
-#pragma unroll
-    for (int m = 0; m < 8; m++) {
-        T v;
-        v.x = x[0][m];
-        v.y = x[1][m];
-        s[swz(rw * 256u + 8u * lane + m)] = v;
-    }
-}
-
-template <typename T, typename R>
-__device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw,
-                                        int lane)
-{
-    const CodecLayout CL = codec_layout(fa.c);
-    const uint64_t cmask = (1ull << fa.c) - 1;
-    const uint32_t r = (uint32_t)(li >> fa.c);
-    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
-    R x[2][8];
-#pragma unroll
-    for (int m = 0; m < 8; m++) {
-        const T v = s[swz(rw * 256u + 8u * lane + m)];
-        x[0][m] = v.x;
-        x[1][m] = v.y;
-    }
-    codec::encode_pair<R>(x, fa.c, fa.k, bp, fa.out + (size_t)r * fa.out_stride,
-                          fa.sparse + (uint64_t)r * CL.nb * 256ull, fa.blocksq + (uint64_t)r * CL.bpc + bp,
-                          reinterpret_cast<uint32_t(*)[260]>(cw), fa.err, lane);
-}
-
 // Apply one staged op to the thread's 16 register amplitudes: one jump
 // table over the dense op code (4x4 ops go through the thread's shared slots).
 template <typename T, typename R>
@@ -323,7 +259,6 @@ __device__ __forceinline__ void apply_op(const PhaseOp<R>& op, T (&a)[kRegs], ui
         SV_D1(PK_GENERIC, f_generic)
         SV_D1(PK_REAL, f_real)
         SV_D1(PK_RX, f_rx)
-        SV_D1(PK_SWAP, f_swap)
         SV_DG1(0, false) SV_DG1(1, false) SV_DG1(2, false) SV_DG1(3, false)
         SV_DG1(0, true) SV_DG1(1, true) SV_DG1(2, true) SV_DG1(3, true)
         SV_D2(0, 1) SV_D2(0, 2) SV_D2(0, 3) SV_D2(1, 0) SV_D2(1, 2) SV_D2(1, 3)
@@ -362,18 +297,8 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
     PhaseOp<R>* sops = reinterpret_cast<PhaseOp<R>*>(p);
     p += op_staged ? sizeof(PhaseOp<R>) * (size_t)nops : 0;
     uint32_t* cw = reinterpret_cast<uint32_t*>(p);
-    __shared__ uint64_t rowoff[1 << (kT - kPhaseLowBits)];
-    __shared__ uint64_t tile_opos[kMaxLocalQubits];
-    const int l = td.l;  // 5 (rows of 32 amplitudes) or 8 (rows = codec block pairs)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t nrows = 1u << (kT - l), rmask = (1u << l) - 1u;
-    for (uint32_t rw = threadIdx.x; rw < nrows; rw += kThreads) {
-        uint64_t off = 0;
-        for (int i = 0; i < kT - l; i++)
-            if ((rw >> i) & 1u) off |= 1ull << td.hpos[i];
-        rowoff[rw] = off;
-    }
-    for (int i = threadIdx.x; i < td.nout; i += kThreads) tile_opos[i] = 1ull << td.opos[i];
+    __shared__ tile::Rows rt;
+    tile::setup_rows(rt, td);
     if (ph_staged) {
         const uint4* src = reinterpret_cast<const uint4*>(phases);
         uint4* dst = reinterpret_cast<uint4*>(sph);
@@ -390,30 +315,9 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
     const PhaseOp<R>* opb = op_staged ? sops : ops + op0;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        uint64_t base = 0;
-        for (int i = 0; i < td.nout; i++)
-            if ((tile >> i) & 1ull) base |= tile_opos[i];
-        if (fa.decode) {
-            // compressed streams -> shared: one warp per 256-amplitude block pair (row)
-            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
-                decode_row<T, R>(s, rw, fa, base + rowoff[rw], cw + wid * kCodecWords, lane);
-        } else {
-            // HBM -> shared: 2 amplitudes (16 bytes for complex64) per access along rows
-            for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
-                const uint32_t i = 2 * e;
-                const T* g = amps + base + rowoff[i >> l] + (i & rmask);
-                T x0, x1;
-                if (sizeof(R) == 4) {
-                    const float4 v = *reinterpret_cast<const float4*>(g);
-                    x0.x = v.x; x0.y = v.y; x1.x = v.z; x1.y = v.w;
-                } else {
-                    x0 = g[0];
-                    x1 = g[1];
-                }
-                s[swz(i)] = x0;
-                s[swz(i + 1)] = x1;
-            }
-        }
+        const uint64_t base = tile::tile_base(rt, td, tile);
+        if (fa.decode) tile::load_tile<T, R, true>(s, amps, rt, td, base, fa, cw);
+        else tile::load_tile<T, R, false>(s, amps, rt, td, base, fa, cw);
         __syncthreads();
         for (int ph = 0; ph < nphases; ph++) {
             const Phase& P = CT ? c_phases[ph_base + ph] : phb[ph];
@@ -438,23 +342,8 @@ k_apply_phases(typename V2<R>::T* __restrict__ amps, TileDesc td, const Phase* _
             for (int m = 0; m < kRegs; m++) s[stb ^ P.sroff[m]] = a[m];
             __syncthreads();
         }
-        if (fa.encode) {
-            // shared -> codec: one warp per block pair; packed words go to the staging slots
-            for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
-                encode_row<T, R>(s, rw, fa, base + rowoff[rw], cw + wid * kCodecWords, lane);
-        } else {
-            for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
-                const uint32_t i = 2 * e;
-                T* g = amps + base + rowoff[i >> l] + (i & rmask);
-                const T x0 = s[swz(i)], x1 = s[swz(i + 1)];
-                if (sizeof(R) == 4) {
-                    *reinterpret_cast<float4*>(g) = make_float4((float)x0.x, (float)x0.y, (float)x1.x, (float)x1.y);
-                } else {
-                    g[0] = x0;
-                    g[1] = x1;
-                }
-            }
-        }
+        if (fa.encode) tile::store_tile<T, R, true>(s, amps, rt, td, base, fa, cw);
+        else tile::store_tile<T, R, false>(s, amps, rt, td, base, fa, cw);
     }
 }
 

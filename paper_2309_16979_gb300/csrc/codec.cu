@@ -23,6 +23,7 @@
 //     8*w words to its final offset.
 #include <algorithm>
 
+#include "sv_internal.h"
 #include "codec_dev.cuh"
 
 namespace sv {

@@ -8,7 +8,7 @@
 // precision (no FP64 on the complex64 path).
 #pragma once
 
-#include "sv_internal.h"
+#include "sv_dev_types.h"
 
 namespace sv {
 namespace codec {

@@ -20,6 +20,7 @@
 #include <thread>
 
 #include "engine.h"
+#include "jit.h"
 
 namespace sv {
 
@@ -225,7 +226,43 @@ struct DevPass {
     std::vector<CtaCtrl> ctl;
     std::vector<R> d2m;
     size_t ops_at = 0, phases_at = 0, pops_at = 0, ctl_at = 0, d2m_at = 0;  // byte offsets in the uploaded blob
+    // sub-pass kernels generated for this pass's gate sequences (jit.cpp), with
+    // the matrix values each reads; a null kernel runs the table-driven one
+    std::vector<const JitFn*> jfn;
+    std::vector<std::vector<R>> jpar;
 };
+
+// Generate and compile (one parallel batch, cached per process) the
+// specialised kernels of every register-phase sub-pass of `dps`.
+template <typename R>
+static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
+{
+    if (!s->cfg.jit) return SV_OK;
+    std::vector<std::string> src;
+    std::vector<std::pair<DevPass<R>*, size_t>> where;
+    for (DevPass<R>* dp : dps) {
+        if (!dp->use_phases) continue;
+        const size_t ns = dp->td.size();
+        dp->jfn.assign(ns, nullptr);
+        dp->jpar.assign(ns, std::vector<R>());
+        for (size_t i = 0; i < ns; i++) {
+            const bool dec = i == 0 && dp->fuse_decode, enc = i + 1 == ns && dp->fuse_encode;
+            src.push_back(jit_source<R>(dp->phases.data() + dp->ph_off[i], dp->ph_cnt[i], dp->pops.data(),
+                                        dp->ctl.data(), dp->d2m.data(), dec, enc, dp->jpar[i]));
+            where.push_back({dp, i});
+        }
+    }
+    if (src.empty()) return SV_OK;
+    std::vector<const JitFn*> fns;
+    std::string err;
+    JitReport rep;
+    if (!jit_compile(src, s->cfg.device, fns, err, &rep))
+        return fail(s, SV_ERR_CUDA, "run-time kernel compilation failed: " + err);
+    for (size_t k = 0; k < src.size(); k++) where[k].first->jfn[where[k].second] = fns[k];
+    s->st.jit_kernels_compiled += rep.compiled;
+    s->st.t_jit_compile_s += rep.seconds;
+    return SV_OK;
+}
 
 template <typename R>
 static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t, int l, bool fuse_decode = false,
@@ -275,6 +312,10 @@ static cudaError_t launch_subpass(sv_state* s, const DevPass<R>& dp, size_t i, v
 {
     const uint8_t* base = static_cast<const uint8_t*>(s->d_ops);
     static const FuseArgs none{};
+    if (dp.use_phases && i < dp.jfn.size() && dp.jfn[i]) {
+        s->st.jit_launches++;
+        return jit_launch<R>(dp.jfn[i], amps, dp.td[i], gbase, fa ? *fa : none, dp.jpar[i], s->s_comp);
+    }
     if (dp.use_phases) {
         const int p0 = dp.ph_off[i], pn = dp.ph_cnt[i];
         const int op0 = pn ? dp.phases[p0].op_begin : 0;
@@ -312,8 +353,10 @@ static inline uint64_t deposit(uint64_t v, const std::vector<int>& pos)
 }
 
 // --------------------------------------------------- compressed streaming
+// Plan one pass for the device: its tile sub-passes, whether the codec
+// fuses into the first / last of them, and their device form.
 template <typename R>
-int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp)
+static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp, DevPass<R>& dp)
 {
     const int c = s->c, g = (int)pp.S.size();
     const int L = c + g;
@@ -334,7 +377,16 @@ int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const Pass
         }
         fenc = (subs.back().T & 0xffull) == 0xffull;
     }
-    DevPass<R> dp = build_dev_pass<R>(subs, L, t, l, fdec, fenc);
+    dp = build_dev_pass<R>(subs, L, t, l, fdec, fenc);
+    return SV_OK;
+}
+
+// Stream every chunk group of the state through one prepared pass.
+template <typename R>
+static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
+{
+    const int c = s->c, g = (int)pp.S.size();
+    const int L = c + g;
     int r = upload_pass<R>(s, dp);
     if (r) return r;
 
@@ -483,6 +535,16 @@ int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const Pass
     return SV_OK;
 }
 
+template <typename R>
+int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp)
+{
+    DevPass<R> dp;
+    int r = prepare_pass_compressed<R>(s, gates, pp, dp);
+    if (!r) r = jit_prepare<R>(s, {&dp});
+    if (!r) r = run_pass_compressed<R>(s, pp, dp);
+    return r;
+}
+
 // ------------------------------------------------------------ uncompressed
 template <typename R>
 int run_pass_uncompressed(sv_state* s, void* state, const std::vector<PGate>& gates, const std::vector<int>& ids)
@@ -495,8 +557,9 @@ int run_pass_uncompressed(sv_state* s, void* state, const std::vector<PGate>& ga
     const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
     if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
     DevPass<R> dp = build_dev_pass<R>(subs, L, t, l);
-    int r = upload_pass<R>(s, dp);
+    int r = jit_prepare<R>(s, {&dp});
     if (r) return r;
+    if ((r = upload_pass<R>(s, dp))) return r;
     const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
     for (size_t i = 0; i < dp.td.size(); i++) {
         const int pi = prof_begin(s);
@@ -522,9 +585,52 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
         return run_pass_uncompressed<R>(s, s->d_state, gates, ids);
     }
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
-    for (const PassPlan& pp : passes) {
-        int r = run_pass_compressed<R>(s, gates, pp);
+    // plan every pass first, so that their kernels compile in one parallel batch
+    std::vector<DevPass<R>> dps(passes.size());
+    std::vector<DevPass<R>*> ptrs;
+    for (size_t i = 0; i < passes.size(); i++) {
+        int r = prepare_pass_compressed<R>(s, gates, passes[i], dps[i]);
         if (r) return r;
+        ptrs.push_back(&dps[i]);
+    }
+    int r = jit_prepare<R>(s, ptrs);
+    if (r) return r;
+    for (size_t i = 0; i < passes.size(); i++) {
+        if ((r = run_pass_compressed<R>(s, passes[i], dps[i]))) return r;
+        dps[i] = DevPass<R>();
+    }
+    return SV_OK;
+}
+
+template <typename R>
+int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out)
+{
+    std::vector<DevPass<R>> dps;
+    if (s->mode == SV_UNCOMPRESSED) {
+        int t, l;
+        tile_shape(s->n, s->tq, s->lq, t, l);
+        std::vector<int> ids(gates.size());
+        for (size_t i = 0; i < gates.size(); i++) ids[i] = (int)i;
+        const std::vector<HOp> hops = local_ops(gates, ids, s->n, std::vector<int>(), false);
+        const std::vector<SubPlan> subs = plan_subpasses(hops, s->n, t, l, true);
+        if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+        dps.push_back(build_dev_pass<R>(subs, s->n, t, l));
+    } else {
+        const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
+        dps.resize(passes.size());
+        for (size_t i = 0; i < passes.size(); i++) {
+            int r = prepare_pass_compressed<R>(s, gates, passes[i], dps[i]);
+            if (r) return r;
+        }
+    }
+    for (DevPass<R>& dp : dps) {
+        if (!dp.use_phases) continue;
+        for (size_t i = 0; i < dp.td.size(); i++) {
+            std::vector<R> par;
+            out.push_back(jit_source<R>(dp.phases.data() + dp.ph_off[i], dp.ph_cnt[i], dp.pops.data(), dp.ctl.data(),
+                                        dp.d2m.data(), i == 0 && dp.fuse_decode,
+                                        i + 1 == dp.td.size() && dp.fuse_encode, par));
+        }
     }
     return SV_OK;
 }
@@ -1255,6 +1361,8 @@ template int grad_compressed<double>(sv_state*, const std::vector<PGate>&, size_
                                      double*, double*);
 template int apply_circuit<float>(sv_state*, const std::vector<PGate>&);
 template int apply_circuit<double>(sv_state*, const std::vector<PGate>&);
+template int jit_sources<float>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&);
+template int jit_sources<double>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&);
 template int init_state<float>(sv_state*);
 template int init_state<double>(sv_state*);
 template int amplitudes<float>(sv_state*, const uint64_t*, size_t, double*);

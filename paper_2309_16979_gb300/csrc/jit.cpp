@@ -1,0 +1,662 @@
+// jit.cpp -- sub-pass kernels specialised to their gate sequence (MEMQSim
+// Sec. 2, "Online stage" step (3): the kernel that applies a pass's fused
+// gates to the staged chunk group), generated at run time and compiled with
+// NVRTC for the device in use.
+//
+// The table-driven phase kernel (apply_phase.cu) spends most of its issue
+// slots interpreting its op stream: fetching each op's record, dispatching on
+// its form, reconciling registers between forms. Here each sub-pass becomes a
+// kernel of its own, written out as straight-line code: per phase, the
+// sixteen register loads at the phase's swizzled offsets, then every gate as
+// exactly the multiply-adds its matrix needs, then the stores.
+//
+// What is baked into the code is the sub-pass's structure: the phases'
+// register and thread bits, each gate's target bits and controls, and which
+// matrix entries are exactly 0, +-1 or +-i (a zero drops a term, +-1 and +-i
+// turn a product into a move or a negation; an X, or any 0/1 permutation
+// whose controls are all register bits, only renames the registers holding
+// the pair). Every other entry is read from the kernel's by-value parameter
+// block (the constant bank), so circuits that differ only in their rotation
+// angles share kernels. Kernels are cached per process by their source text.
+#include "jit.h"
+
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <thread>
+#include <unordered_map>
+
+#include "jit_embed.inc"  // kJitHeaderNames / kJitHeaders / kJitHeaderCount: device headers the kernels include
+
+namespace sv {
+
+struct JitFn {
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+};
+
+namespace {
+
+constexpr size_t kMaxParamBytes = 24576;  // by-value parameter block cap (CUDA allows 32764 bytes in all)
+constexpr int kJitThreads = 256;
+
+// ------------------------------------------------------------ generation
+// A complex coefficient as the generated code sees it.
+enum Cls { C_ZERO, C_ONE, C_MONE, C_I, C_MI, C_REAL, C_IMAG, C_GEN };
+
+struct Coef {
+    int cls = C_ZERO;
+    std::string re, im;  // expressions of the parts a REAL / IMAG / GEN coefficient reads
+};
+
+std::string pref(size_t i) { return "p.m[" + std::to_string(i) + "]"; }
+
+template <typename R>
+Coef fixed_coef(R re, R im, size_t pidx)
+{
+    Coef c;
+    if (re == 0 && im == 0) c.cls = C_ZERO;
+    else if (re == 1 && im == 0) c.cls = C_ONE;
+    else if (re == -1 && im == 0) c.cls = C_MONE;
+    else if (re == 0 && im == 1) c.cls = C_I;
+    else if (re == 0 && im == -1) c.cls = C_MI;
+    else if (im == 0) c.cls = C_REAL;
+    else if (re == 0) c.cls = C_IMAG;
+    else c.cls = C_GEN;
+    c.re = pref(pidx);
+    c.im = pref(pidx + 1);
+    return c;
+}
+
+// A real sum of signed products, written so that the compiler contracts it
+// into multiply-adds.
+struct Sum {
+    struct Term {
+        int sign;
+        std::string coef;  // empty: 1
+        std::string var;
+    };
+    std::vector<Term> t;
+    void add(int sg, const std::string& c, const std::string& v) { t.push_back({sg, c, v}); }
+    std::string str() const
+    {
+        if (t.empty()) return "(R)0";
+        std::string s;
+        for (size_t k = 0; k < t.size(); k++) {
+            const std::string prod = t[k].coef.empty() ? t[k].var : t[k].coef + " * " + t[k].var;
+            if (k == 0) s += (t[k].sign < 0 ? "-" : "") + prod;
+            else s += (t[k].sign < 0 ? " - " : " + ") + prod;
+        }
+        return s;
+    }
+};
+
+// (re, im) += e * (vr + i vi)
+void cmac(Sum& re, Sum& im, const Coef& e, const std::string& vr, const std::string& vi)
+{
+    switch (e.cls) {
+        case C_ZERO: break;
+        case C_ONE: re.add(1, "", vr); im.add(1, "", vi); break;
+        case C_MONE: re.add(-1, "", vr); im.add(-1, "", vi); break;
+        case C_I: re.add(-1, "", vi); im.add(1, "", vr); break;
+        case C_MI: re.add(1, "", vi); im.add(-1, "", vr); break;
+        case C_REAL: re.add(1, e.re, vr); im.add(1, e.re, vi); break;
+        case C_IMAG: re.add(-1, e.im, vi); im.add(1, e.im, vr); break;
+        default:
+            re.add(1, e.re, vr);
+            re.add(-1, e.im, vi);
+            im.add(1, e.re, vi);
+            im.add(1, e.im, vr);
+            break;
+    }
+}
+
+std::string hex(uint64_t v)
+{
+    char b[32];
+    std::snprintf(b, sizeof b, "0x%llx", (unsigned long long)v);
+    return b;
+}
+
+template <typename R>
+struct Gen {
+    std::ostringstream o;
+    std::vector<R>& par;
+    int thr_of_tile[16];  // tile bit -> thread index bit of the current phase (-1: register bit)
+    int slot[16];         // register index -> variable holding it
+    int tmp = 0;
+    bool ok = true;
+    explicit Gen(std::vector<R>& p) : par(p) {}
+    std::string rv(int m) const { return "r" + std::to_string(slot[m]); }
+    std::string iv(int m) const { return "q" + std::to_string(slot[m]); }
+    size_t push(const R* v, int n)
+    {
+        const size_t at = par.size();
+        for (int i = 0; i < n; i++) par.push_back(v[i]);
+        return at;
+    }
+};
+
+// Coefficient chosen at run time by `sel` (0..n-1) among candidates whose
+// parts sit at params[pidx[k]], params[pidx[k] + 1].
+template <typename R>
+Coef select_coef(Gen<R>& g, const std::string& sel, const std::vector<size_t>& pidx)
+{
+    const size_t n = pidx.size();
+    bool same = true, real = true, imag = true;
+    for (size_t k = 0; k < n; k++) {
+        const R re = g.par[pidx[k]], im = g.par[pidx[k] + 1];
+        if (re != g.par[pidx[0]] || im != g.par[pidx[0] + 1]) same = false;
+        if (im != 0) real = false;
+        if (re != 0) imag = false;
+    }
+    if (same) return fixed_coef<R>(g.par[pidx[0]], g.par[pidx[0] + 1], pidx[0]);
+    Coef c;
+    c.cls = real ? C_REAL : imag ? C_IMAG : C_GEN;
+    auto pick = [&](int part) {
+        if (n == 2) return "(" + sel + " ? " + pref(pidx[1] + part) + " : " + pref(pidx[0] + part) + ")";
+        return "((" + sel + ") & 2u ? ((" + sel + ") & 1u ? " + pref(pidx[3] + part) + " : " + pref(pidx[2] + part) +
+               ") : ((" + sel + ") & 1u ? " + pref(pidx[1] + part) + " : " + pref(pidx[0] + part) + "))";
+    };
+    const std::string name = "e" + std::to_string(g.tmp++);
+    if (c.cls != C_IMAG) {
+        g.o << "const R " << name << "r = " << pick(0) << ";\n";
+        c.re = name + "r";
+    }
+    if (c.cls != C_REAL) {
+        g.o << "const R " << name << "i = " << pick(1) << ";\n";
+        c.im = name + "i";
+    }
+    return c;
+}
+
+// expression of a constant entry-index bit (see kSrcNone); empty for none
+template <typename R>
+std::string const_bit(Gen<R>& g, uint8_t s)
+{
+    if (s == kSrcNone) return "";
+    if (s < 0x40) {
+        const int j = s < 16 ? g.thr_of_tile[s] : -1;
+        if (j < 0) {
+            g.ok = false;
+            return "0u";
+        }
+        return "((threadIdx.x >> " + std::to_string(j) + ") & 1u)";
+    }
+    if (s < 0x80) return "(uint32_t)((base >> " + std::to_string(s - 0x40) + ") & 1ull)";
+    return "(uint32_t)((gbase >> " + std::to_string(s - 0x80) + ") & 1ull)";
+}
+
+// controls that are not register bits: thread bits and bits outside the tile
+template <typename R>
+std::string op_cond(Gen<R>& g, const PhaseOp<R>& op, const CtaCtrl* ctl)
+{
+    std::vector<std::string> parts;
+    if (op.tmask) {
+        uint32_t tm = 0;
+        for (int b = 0; b < 16; b++) {
+            if (!((op.tmask >> b) & 1u)) continue;
+            const int j = g.thr_of_tile[b];
+            if (j < 0) g.ok = false;
+            else tm |= 1u << j;
+        }
+        parts.push_back("(threadIdx.x & " + hex(tm) + "u) == " + hex(tm) + "u");
+    }
+    if (op.flags & 1u) {
+        const CtaCtrl cc = ctl[op.aux];
+        if (cc.cl) parts.push_back("(base & " + hex(cc.cl) + "ull) == " + hex(cc.cl) + "ull");
+        if (cc.cg) parts.push_back("(gbase & " + hex(cc.cg) + "ull) == " + hex(cc.cg) + "ull");
+    }
+    std::string s;
+    for (size_t k = 0; k < parts.size(); k++) s += (k ? " && (" : "(") + parts[k] + ")";
+    return s;
+}
+
+// register m *= e
+template <typename R>
+void mul_reg(Gen<R>& g, int m, const Coef& e)
+{
+    if (e.cls == C_ONE) return;
+    Sum re, im;
+    cmac(re, im, e, "xr", "xi");
+    g.o << "{ const R xr = " << g.rv(m) << ", xi = " << g.iv(m) << "; " << g.rv(m) << " = " << re.str() << "; "
+        << g.iv(m) << " = " << im.str() << "; }\n";
+}
+
+template <typename R>
+void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, int b, const std::string& cond)
+{
+    const R* m = op.m;
+    const bool ident = m[0] == 1 && m[1] == 0 && m[2] == 0 && m[3] == 0 && m[4] == 0 && m[5] == 0 && m[6] == 1 &&
+                       m[7] == 0;
+    if (ident) return;
+    const bool xperm = m[0] == 0 && m[1] == 0 && m[2] == 1 && m[3] == 0 && m[4] == 1 && m[5] == 0 && m[6] == 0 &&
+                       m[7] == 0;
+    if (xperm && cond.empty()) {
+        for (int i = 0; i < 16; i++)
+            if ((op.amask >> i) & 1u) std::swap(g.slot[i], g.slot[i | (1 << b)]);
+        return;
+    }
+    const size_t pb = g.push(m, 8);
+    Coef e[4];
+    for (int k = 0; k < 4; k++) e[k] = fixed_coef<R>(m[2 * k], m[2 * k + 1], pb + 2 * k);
+    if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    for (int i = 0; i < 16; i++) {
+        if (!((op.amask >> i) & 1u)) continue;
+        const int j = i | (1 << b);
+        Sum xr, xi, yr, yi;
+        cmac(xr, xi, e[0], "xr", "xi");
+        cmac(xr, xi, e[1], "yr", "yi");
+        cmac(yr, yi, e[2], "xr", "xi");
+        cmac(yr, yi, e[3], "yr", "yi");
+        g.o << "{ const R xr = " << g.rv(i) << ", xi = " << g.iv(i) << ", yr = " << g.rv(j) << ", yi = " << g.iv(j)
+            << "; " << g.rv(i) << " = " << xr.str() << "; " << g.iv(i) << " = " << xi.str() << "; " << g.rv(j)
+            << " = " << yr.str() << "; " << g.iv(j) << " = " << yi.str() << "; }\n";
+    }
+    if (!cond.empty()) g.o << "}\n";
+}
+
+template <typename R>
+void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, int b0, int b1, const std::string& cond)
+{
+    const size_t pb = g.push(op.m, 8);
+    Coef e[4];
+    bool all_one = true;
+    for (int v = 0; v < 4; v++) {
+        e[v] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
+        if (e[v].cls != C_ONE) all_one = false;
+    }
+    if (all_one) return;
+    if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    for (int i = 0; i < 16; i++) {
+        if (!((op.amask >> i) & 1u)) continue;
+        mul_reg(g, i, e[((i >> b0) & 1) | (((i >> b1) & 1) << 1)]);
+    }
+    if (!cond.empty()) g.o << "}\n";
+}
+
+template <typename R>
+void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, int b0, const std::string& cond)
+{
+    const size_t pb = g.push(op.m, 8);
+    const std::string cb = const_bit(g, op.csrc);
+    auto entry = [&](int rb, int c) { return op.rsel ? (c | (rb << 1)) : (rb | (c << 1)); };
+    if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    Coef e[2];
+    for (int rb = 0; rb < 2; rb++) {
+        if (cb.empty()) {
+            const int v = entry(rb, 0);
+            e[rb] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
+        } else {
+            e[rb] = select_coef(g, cb, {pb + 2 * (size_t)entry(rb, 0), pb + 2 * (size_t)entry(rb, 1)});
+        }
+    }
+    for (int i = 0; i < 16; i++) {
+        if (!((op.amask >> i) & 1u)) continue;
+        mul_reg(g, i, e[(i >> b0) & 1]);
+    }
+    if (!cond.empty()) g.o << "}\n";
+}
+
+template <typename R>
+void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, const std::string& cond)
+{
+    const size_t pb = g.push(op.m, 8);
+    const std::string c0 = const_bit(g, op.csrc), c1 = const_bit(g, op.csrc1);
+    if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    Coef e;
+    if (c0.empty() && c1.empty()) e = fixed_coef<R>(op.m[0], op.m[1], pb);
+    else if (c1.empty()) e = select_coef(g, c0, {pb, pb + 2});
+    else if (c0.empty()) e = select_coef(g, c1, {pb, pb + 4});
+    else e = select_coef(g, "(" + c0 + " | (" + c1 + " << 1))", {pb, pb + 2, pb + 4, pb + 6});
+    for (int i = 0; i < 16; i++)
+        if ((op.amask >> i) & 1u) mul_reg(g, i, e);
+    if (!cond.empty()) g.o << "}\n";
+}
+
+template <typename R>
+void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, const R* d2m, const std::string& cond)
+{
+    const int b0 = op.pad & 3, b1 = (op.pad >> 2) & 3;
+    const size_t pb = g.push(d2m + 32ull * op.aux, 32);
+    Coef e[16];
+    for (int k = 0; k < 16; k++) e[k] = fixed_coef<R>(g.par[pb + 2 * k], g.par[pb + 2 * k + 1], pb + 2 * k);
+    if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    for (int i = 0; i < 16; i++) {
+        if (!((op.amask >> i) & 1u)) continue;
+        int idx[4];
+        for (int k = 0; k < 4; k++) idx[k] = i | ((k & 1) << b0) | (((k >> 1) & 1) << b1);
+        g.o << "{ ";
+        for (int k = 0; k < 4; k++)
+            g.o << "const R v" << k << "r = " << g.rv(idx[k]) << ", v" << k << "i = " << g.iv(idx[k]) << "; ";
+        for (int r = 0; r < 4; r++) {
+            Sum re, im;
+            for (int k = 0; k < 4; k++)
+                cmac(re, im, e[4 * r + k], "v" + std::to_string(k) + "r", "v" + std::to_string(k) + "i");
+            g.o << g.rv(idx[r]) << " = " << re.str() << "; " << g.iv(idx[r]) << " = " << im.str() << "; ";
+        }
+        g.o << "}\n";
+    }
+    if (!cond.empty()) g.o << "}\n";
+}
+
+template <typename R> struct RName;
+template <> struct RName<float> { static constexpr const char* r = "float"; static constexpr const char* t = "float2"; static constexpr int minb = 3; };
+template <> struct RName<double> { static constexpr const char* r = "double"; static constexpr const char* t = "double2"; static constexpr int minb = 2; };
+
+// ------------------------------------------------------------ NVRTC / driver
+struct Nvrtc {
+    bool ok = false;
+    std::string why;
+    nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*) = nullptr;
+    nvrtcResult (*compile)(nvrtcProgram, int, const char* const*) = nullptr;
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t*) = nullptr;
+    nvrtcResult (*cubin)(nvrtcProgram, char*) = nullptr;
+    nvrtcResult (*log_size)(nvrtcProgram, size_t*) = nullptr;
+    nvrtcResult (*log)(nvrtcProgram, char*) = nullptr;
+    nvrtcResult (*destroy)(nvrtcProgram*) = nullptr;
+};
+
+Nvrtc load_nvrtc()
+{
+    Nvrtc n;
+    std::vector<std::string> names = {"libnvrtc.so.13", "libnvrtc.so"};
+    if (const char* h = std::getenv("CUDA_HOME")) names.push_back(std::string(h) + "/lib64/libnvrtc.so.13");
+    names.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+    void* lib = nullptr;
+    for (const std::string& nm : names)
+        if ((lib = dlopen(nm.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+    if (!lib) {
+        n.why = "libnvrtc.so.13 not found";
+        return n;
+    }
+    bool ok = true;
+    auto sym = [&](const char* s) {
+        void* p = dlsym(lib, s);
+        if (!p) ok = false;
+        return p;
+    };
+    n.create = reinterpret_cast<decltype(n.create)>(sym("nvrtcCreateProgram"));
+    n.compile = reinterpret_cast<decltype(n.compile)>(sym("nvrtcCompileProgram"));
+    n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(sym("nvrtcGetCUBINSize"));
+    n.cubin = reinterpret_cast<decltype(n.cubin)>(sym("nvrtcGetCUBIN"));
+    n.log_size = reinterpret_cast<decltype(n.log_size)>(sym("nvrtcGetProgramLogSize"));
+    n.log = reinterpret_cast<decltype(n.log)>(sym("nvrtcGetProgramLog"));
+    n.destroy = reinterpret_cast<decltype(n.destroy)>(sym("nvrtcDestroyProgram"));
+    n.ok = ok;
+    if (!ok) n.why = "libnvrtc lacks an expected entry point";
+    return n;
+}
+
+Nvrtc& nvrtc()
+{
+    static Nvrtc n = load_nvrtc();
+    return n;
+}
+
+struct Drv {
+    bool ok = false;
+    std::string why;
+    CUresult (*load)(CUmodule*, const void*) = nullptr;
+    CUresult (*getfn)(CUfunction*, CUmodule, const char*) = nullptr;
+    CUresult (*setattr)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                       void**, void**) = nullptr;
+};
+
+Drv load_drv()
+{
+    Drv d;
+    bool ok = true;
+    auto sym = [&](const char* s) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion(s, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            ok = false;
+        return p;
+    };
+    d.load = reinterpret_cast<decltype(d.load)>(sym("cuModuleLoadData"));
+    d.getfn = reinterpret_cast<decltype(d.getfn)>(sym("cuModuleGetFunction"));
+    d.setattr = reinterpret_cast<decltype(d.setattr)>(sym("cuFuncSetAttribute"));
+    d.launch = reinterpret_cast<decltype(d.launch)>(sym("cuLaunchKernel"));
+    d.ok = ok;
+    if (!ok) d.why = "CUDA driver entry points unavailable";
+    return d;
+}
+
+Drv& drv()
+{
+    static Drv d = load_drv();
+    return d;
+}
+
+std::mutex g_mu;
+std::unordered_map<std::string, std::unique_ptr<JitFn>> g_cache;  // key: device, arch, source
+
+struct Job {
+    const std::string* src;
+    std::string key;
+    std::string cubin;
+    std::string log;
+    bool ok = false;
+};
+
+void compile_one(Job& j, const std::string& arch_opt)
+{
+    Nvrtc& n = nvrtc();
+    nvrtcProgram prog;
+    if (n.create(&prog, j.src->c_str(), "sv_subpass.cu", kJitHeaderCount, kJitHeaders, kJitHeaderNames) !=
+        NVRTC_SUCCESS) {
+        j.log = "nvrtcCreateProgram failed";
+        return;
+    }
+    const char* opts[] = {arch_opt.c_str(), "--std=c++17"};
+    const nvrtcResult r = n.compile(prog, 2, opts);
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    if (ls > 1) {
+        j.log.resize(ls);
+        n.log(prog, &j.log[0]);
+    }
+    if (r == NVRTC_SUCCESS) {
+        size_t cs = 0;
+        n.cubin_size(prog, &cs);
+        j.cubin.resize(cs);
+        if (cs && n.cubin(prog, &j.cubin[0]) == NVRTC_SUCCESS) j.ok = true;
+    }
+    n.destroy(&prog);
+}
+
+}  // namespace
+
+template <typename R>
+std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
+                       bool enc, std::vector<R>& params)
+{
+    params.clear();
+    Gen<R> g(params);
+    std::ostringstream body;
+    for (int pi = 0; pi < nph; pi++) {
+        const Phase& P = ph[pi];
+        for (int b = 0; b < 16; b++) g.thr_of_tile[b] = -1;
+        std::string tb;
+        for (int j = 0; j < kPhaseTileQubits - kPhaseRegBits; j++) {
+            g.thr_of_tile[P.tpos[j]] = j;
+            tb += (j ? " | " : "") + std::string("(((threadIdx.x >> ") + std::to_string(j) + ") & 1u) << " +
+                  std::to_string(P.tpos[j]) + ")";
+        }
+        for (int m = 0; m < 16; m++) g.slot[m] = m;
+        g.o.str("");
+        g.o << "{\nconst uint32_t stb = tile::swz(" << tb << ");\nR ";
+        for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << "r" << m << ", q" << m;
+        g.o << ";\n";
+        for (int m = 0; m < 16; m++)
+            g.o << "{ const T v = s[stb ^ " << P.sroff[m] << "u]; r" << m << " = v.x; q" << m << " = v.y; }\n";
+        for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
+            const PhaseOp<R>& op = ops[oi];
+            const std::string cond = op_cond(g, op, ctl);
+            const uint32_t code = op.code;
+            if (code < kCodeDiag2) {
+                const uint32_t kind = code / 8, b0 = code & 3;
+                if (kind == PK_DIAG1) emit_diag1(g, op, (int)b0, cond);
+                else emit_dense1(g, op, (int)b0, cond);
+            } else if (code < kCodeDiagT) {
+                const uint32_t x = (code - kCodeDiag2) & 15;
+                emit_diag2(g, op, (int)(x & 3), (int)(x >> 2), cond);
+            } else if (code < kCodeDense2) {
+                emit_diagt(g, op, cond);
+            } else if (code == kCodeDense2) {
+                emit_dense2(g, op, d2m, cond);
+            } else {
+                g.ok = false;
+            }
+        }
+        for (int m = 0; m < 16; m++)
+            g.o << "s[stb ^ " << P.sroff[m] << "u] = tile::mk2<T, R>(" << g.rv(m) << ", " << g.iv(m) << ");\n";
+        g.o << "__syncthreads();\n}\n";
+        body << g.o.str();
+    }
+    if (!g.ok || params.size() * sizeof(R) > kMaxParamBytes) {
+        params.clear();
+        return std::string();
+    }
+    std::ostringstream src;
+    src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
+        << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
+        << "struct P { R m[" << std::max<size_t>(1, params.size()) << "]; };\n"
+        << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << RName<R>::minb << ")\n"
+        << "svj(T* __restrict__ amps, const TileDesc td, const uint64_t gbase, const uint64_t ntiles, "
+           "const FuseArgs fa, const P p)\n{\n"
+        << "extern __shared__ __align__(16) unsigned char smem[];\n"
+        << "T* s = reinterpret_cast<T*>(smem);\n"
+        << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + (sizeof(T) << tile::kT));\n"
+        << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n"
+        << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
+        << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
+        << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
+        << "__syncthreads();\n"
+        << body.str()
+        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
+        << "}\n}\n";
+    if (params.empty()) params.push_back((R)0);
+    return src.str();
+}
+
+bool jit_compile(const std::vector<std::string>& sources, int device, std::vector<const JitFn*>& fns,
+                 std::string& err, JitReport* rep)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    fns.assign(sources.size(), nullptr);
+    std::lock_guard<std::mutex> lk(g_mu);
+    Nvrtc& n = nvrtc();
+    Drv& d = drv();
+    if (!d.ok) {
+        err = d.why;
+        return false;
+    }
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess) {
+        err = "cannot query the device's compute capability";
+        return false;
+    }
+    const std::string arch = "sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
+    const std::string prefix = std::to_string(device) + "/" + arch + "\n";
+    std::vector<Job> jobs;
+    std::unordered_map<std::string, size_t> job_of;
+    for (const std::string& s : sources) {
+        if (s.empty()) continue;
+        std::string key = prefix + s;
+        if (g_cache.count(key) || job_of.count(key)) continue;
+        job_of[key] = jobs.size();
+        Job j;
+        j.src = &s;
+        j.key = std::move(key);
+        jobs.push_back(std::move(j));
+    }
+    if (!jobs.empty()) {
+        if (!n.ok) {
+            err = n.why;
+            return false;
+        }
+        const std::string arch_opt = "--gpu-architecture=" + arch;
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const size_t nthr = std::min<size_t>(jobs.size(), hw);
+        std::vector<std::thread> pool;
+        std::atomic_size_t next{0};
+        for (size_t t = 0; t < nthr; t++)
+            pool.emplace_back([&]() {
+                for (size_t k; (k = next.fetch_add(1)) < jobs.size();) compile_one(jobs[k], arch_opt);
+            });
+        for (std::thread& th : pool) th.join();
+        if (cudaSetDevice(device) != cudaSuccess || cudaFree(nullptr) != cudaSuccess) {
+            err = "cannot make the device current";
+            return false;
+        }
+        const size_t tile_bytes = sizeof(double) * 2 << kPhaseTileQubits;
+        const int smem_max = (int)(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32));
+        for (Job& j : jobs) {
+            if (!j.ok) {
+                err = "NVRTC compilation failed: " + j.log.substr(0, 2000);
+                return false;
+            }
+            auto fn = std::make_unique<JitFn>();
+            CUresult r = d.load(&fn->mod, j.cubin.data());
+            if (r == CUDA_SUCCESS) r = d.getfn(&fn->fn, fn->mod, "svj");
+            if (r == CUDA_SUCCESS) r = d.setattr(fn->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem_max);
+            if (r != CUDA_SUCCESS) {
+                err = "loading a compiled kernel failed (CUresult " + std::to_string((int)r) + ")";
+                return false;
+            }
+            g_cache[j.key] = std::move(fn);
+        }
+    }
+    for (size_t i = 0; i < sources.size(); i++) {
+        if (sources[i].empty()) continue;
+        fns[i] = g_cache[prefix + sources[i]].get();
+    }
+    if (rep) {
+        rep->compiled += jobs.size();
+        rep->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return true;
+}
+
+template <typename R>
+cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t gbase, const FuseArgs& fa,
+                       const std::vector<R>& params, cudaStream_t st)
+{
+    if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
+    const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
+    const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, 152ull * 32);
+    const size_t smem = ((sizeof(R) * 2) << kPhaseTileQubits) +
+                        ((fa.decode || fa.encode) ? sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32) : 0);
+    void* a = amps;
+    TileDesc t = td;
+    uint64_t gb = gbase, nt = ntiles;
+    FuseArgs f = fa;
+    void* args[] = {&a, &t, &gb, &nt, &f, const_cast<R*>(params.data())};
+    const CUresult r = drv().launch(fn->fn, grid, 1, 1, kJitThreads, 1, 1, (unsigned)smem, (CUstream)st, args, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
+                                       bool, std::vector<float>&);
+template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,
+                                        bool, bool, std::vector<double>&);
+template cudaError_t jit_launch<float>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
+                                       const std::vector<float>&, cudaStream_t);
+template cudaError_t jit_launch<double>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
+                                        const std::vector<double>&, cudaStream_t);
+
+}  // namespace sv

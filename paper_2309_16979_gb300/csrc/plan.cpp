@@ -329,7 +329,6 @@ void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, 
 // --------------------------------------------------------- register phases
 static int classify_2x2(const cd* m)
 {
-    if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) return PK_SWAP;
     bool real = true, rx = true;
     for (int i = 0; i < 4; i++)
         if (m[i].imag() != 0) real = false;

@@ -15,41 +15,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "sv_dev_types.h"
+
 namespace sv {
-
-// ------------------------------------------------------------------ codec
-constexpr uint32_t kMagic = 0x31435653u;  // "SVC1"
-constexpr int kBlock = 256;               // values per codec block
-
-struct CodecLayout {
-    uint32_t nb;      // blocks, both planes
-    uint32_t bpc;     // block pairs (256 amplitudes each) per chunk
-    size_t w_off, a_off, o_off, p_off;
-    size_t max_bytes; // metadata + worst-case payload (32 bits per value)
-};
-
-__host__ __device__ inline size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
-
-__host__ __device__ inline CodecLayout codec_layout(int c)
-{
-    CodecLayout L;
-    L.nb = (uint32_t)((2ull << c) >> 8);
-    L.bpc = L.nb / 2;
-    L.w_off = 32;
-    L.a_off = L.w_off + pad16(L.nb);
-    L.o_off = L.a_off + pad16(4ull * L.nb);
-    L.p_off = L.o_off + pad16(4ull * (L.nb + 1));
-    L.max_bytes = L.p_off + (size_t)L.nb * 1024;
-    return L;
-}
-
-// device -> host record of one encoded chunk
-struct ChunkOut {
-    uint64_t bytes;   // stream length
-    uint64_t sumsq;   // sum of q^2 over the chunk (exact; norm^2 = sumsq * Delta^2)
-};
-
-enum : int { kErrCorrupt = 1, kErrRange = 2 };
 
 // --------------------------------------------------------------- gate ops
 enum OpType : int32_t { OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG = 2 };
@@ -71,13 +39,6 @@ struct DevOp {
     R m[32];               // dense1: 2x2, dense2: 4x4, diag: 4 entries; (re, im) pairs
 };
 
-// Register-phase form of a sub-pass (tiles of exactly kPhaseTileQubits
-// qubits, 256 threads, 16 amplitudes per thread): a phase keeps 4 tile
-// qubits in registers and applies every op whose mixing qubits are among
-// them; phases exchange amplitudes through shared memory.
-constexpr int kPhaseTileQubits = 12;
-constexpr int kPhaseRegBits = 4;
-
 // Op kinds of a phase. A phase op's `code` is dense, so one jump-table
 // dispatch selects code specialised at compile time:
 //   kinds PK_GENERIC..PK_DIAG1 (one register bit b0): code = kind * 8 + ctrl * 4 + b0
@@ -89,7 +50,7 @@ enum PhaseOpKind : uint32_t {
     PK_GENERIC = 0,  // 2x2 complex matrix on register bit b0
     PK_REAL = 1,     // 2x2 real matrix
     PK_RX = 2,       // [[p, i q], [i r, s]] with real p, q, r, s
-    PK_SWAP = 3,     // X: exchange the pair
+    PK_UNUSED3 = 3,  // (free: an exchange form for X measured slower than X as a real matrix)
     PK_DIAG1 = 4,    // diagonal whose entry index has one register bit b0
     PK_DIAG2 = 5,    // diagonal whose entry index bits are register bits (b0, b1)
     PK_DIAGT = 6,    // diagonal whose entry index is constant per thread
@@ -129,25 +90,6 @@ struct Phase {
 };
 static_assert(sizeof(Phase) == 64, "phase records are 64 bytes");
 
-constexpr int kMaxTileQubits = 13;
-constexpr int kMaxLocalQubits = 48;
-
-struct TileDesc {
-    int32_t t;                  // tile qubits
-    int32_t l;                  // low local bits 0..l-1 always in the tile (rows are 2^l contiguous)
-    int32_t L;                  // local qubits of the buffer (c + g, or n when uncompressed)
-    int32_t nout;               // L - t
-    int8_t hpos[kMaxTileQubits];          // local positions of tile bits l..t-1
-    int8_t opos[kMaxLocalQubits];         // local positions outside the tile (ascending)
-};
-
-// per-group staging parameters for decode
-constexpr int kMaxGroupChunks = 256;
-
-struct GroupIn {
-    uint32_t bytes[kMaxGroupChunks];      // stream length of each staged chunk
-};
-
 // ------------------------------------------------------------ launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
@@ -163,26 +105,6 @@ cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks
 template <typename R>
 cudaError_t launch_apply(void* amps, const TileDesc& td, const DevOp<R>* ops, int nops,
                          uint64_t gbase, cudaStream_t st);
-
-// Optional fusion of the chunk codec into a tile sub-pass (tiles whose rows
-// are whole 256-amplitude block pairs, i.e. l = 8): decode the group's chunk
-// streams straight into shared memory instead of reading amplitudes, and/or
-// encode the tile's block pairs (widths, anchors, packed staging, sum q^2)
-// instead of writing amplitudes; launch_encode_finish then completes the
-// streams (offset scan, header, compaction).
-struct FuseArgs {
-    int32_t decode = 0, encode = 0;
-    int32_t c = 0, dtype = 0, k = 0;
-    double scale = 1.0;
-    const uint8_t* in = nullptr;
-    size_t in_stride = 0;
-    GroupIn gin{};
-    uint8_t* out = nullptr;
-    size_t out_stride = 0;
-    uint32_t* sparse = nullptr;
-    unsigned long long* blocksq = nullptr;
-    int* err = nullptr;
-};
 
 // Capacity of the constant-memory phase / op tables (one pass at a time).
 constexpr int kConstPhases = 128;

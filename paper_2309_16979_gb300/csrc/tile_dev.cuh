@@ -1,0 +1,169 @@
+// tile_dev.cuh -- tile staging shared by the register-phase kernel
+// (apply_phase.cu) and the sub-pass kernels generated at run time (jit.cpp):
+// the shared-memory swizzle, the per-CTA row table, HBM <-> shared copies of
+// one 2^12-amplitude tile, and the fused codec steps that replace them.
+//
+// Shared memory is XOR-swizzled: amplitude i sits at swz(i) = i ^ (((i >> 4)
+// ^ (i >> 8)) & 15), so the 16 lanes of a half-warp, whose four low thread
+// bits map to tile bits of four different residues mod 4, hit 16 different
+// bank pairs whatever the register qubits are. swz is linear over XOR.
+#pragma once
+
+#include "codec_dev.cuh"
+
+namespace sv {
+namespace tile {
+
+constexpr int kThreads = 256;
+constexpr int kT = kPhaseTileQubits;  // 12
+constexpr int kN = 1 << kT;           // 4096 amplitudes per tile
+constexpr int kLowBits = 5;           // rows of at least 32 contiguous amplitudes
+constexpr int kCodecWords = 2 * 264;  // per-warp codec staging (decode payload / encode packing)
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
+
+template <typename T, typename R>
+__device__ __forceinline__ T mk2(R x, R y)
+{
+    T v;
+    v.x = x;
+    v.y = y;
+    return v;
+}
+
+// Per-CTA tables: local offset of each tile row, and the bit of each local
+// position outside the tile (tile index bit i -> local bit opos[i]).
+struct Rows {
+    uint64_t rowoff[1 << (kT - kLowBits)];
+    uint64_t opos[kMaxLocalQubits];
+};
+
+__device__ __forceinline__ void setup_rows(Rows& rt, const TileDesc& td)
+{
+    const uint32_t nrows = 1u << (kT - td.l);
+    for (uint32_t rw = threadIdx.x; rw < nrows; rw += blockDim.x) {
+        uint64_t off = 0;
+        for (int i = 0; i < kT - td.l; i++)
+            if ((rw >> i) & 1u) off |= 1ull << td.hpos[i];
+        rt.rowoff[rw] = off;
+    }
+    for (int i = threadIdx.x; i < td.nout; i += blockDim.x) rt.opos[i] = 1ull << td.opos[i];
+}
+
+__device__ __forceinline__ uint64_t tile_base(const Rows& rt, const TileDesc& td, uint64_t tile)
+{
+    uint64_t base = 0;
+    for (int i = 0; i < td.nout; i++)
+        if ((tile >> i) & 1ull) base |= rt.opos[i];
+    return base;
+}
+
+// Fused codec steps, out of line: they run once per row, not per gate.
+template <typename T, typename R>
+__device__ __noinline__ void decode_row(T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw, int lane)
+{
+    const uint64_t cmask = (1ull << fa.c) - 1;
+    const uint32_t r = (uint32_t)(li >> fa.c);
+    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
+    R x[2][8];
+    if (!codec::decode_pair<R>(fa.in + (size_t)r * fa.in_stride, fa.gin.bytes[r], fa.in_stride, fa.c, fa.dtype, bp,
+                               reinterpret_cast<uint32_t(*)[264]>(cw), (R)fa.scale, x, lane)) {
+        if (lane == 0) atomicOr(fa.err, kErrCorrupt);
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[0][m] = x[1][m] = (R)0;
+    }
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        T v;
+        v.x = x[0][m];
+        v.y = x[1][m];
+        s[swz(rw * 256u + 8u * lane + m)] = v;
+    }
+}
+
+template <typename T, typename R>
+__device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw,
+                                        int lane)
+{
+    const CodecLayout CL = codec_layout(fa.c);
+    const uint64_t cmask = (1ull << fa.c) - 1;
+    const uint32_t r = (uint32_t)(li >> fa.c);
+    const uint32_t bp = (uint32_t)((li & cmask) >> 8);
+    R x[2][8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const T v = s[swz(rw * 256u + 8u * lane + m)];
+        x[0][m] = v.x;
+        x[1][m] = v.y;
+    }
+    codec::encode_pair<R>(x, fa.c, fa.k, bp, fa.out + (size_t)r * fa.out_stride,
+                          fa.sparse + (uint64_t)r * CL.nb * 256ull, fa.blocksq + (uint64_t)r * CL.bpc + bp,
+                          reinterpret_cast<uint32_t(*)[260]>(cw), fa.err, lane);
+}
+
+// HBM (or the compressed streams) -> shared memory for the tile at `base`.
+// DEC: decode the group's chunk streams, one warp per 256-amplitude block
+// pair (rows are block pairs, td.l = 8); otherwise 16-byte vector loads along
+// the rows.
+template <typename T, typename R, bool DEC>
+__device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
+                                          uint64_t base, const FuseArgs& fa, uint32_t* cw)
+{
+    const int l = td.l;
+    if (DEC) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const uint32_t nrows = 1u << (kT - l);
+        for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
+            decode_row<T, R>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
+    } else {
+        const uint32_t rmask = (1u << l) - 1u;
+        for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
+            const uint32_t i = 2 * e;
+            const T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
+            T x0, x1;
+            if (sizeof(R) == 4) {
+                const float4 v = *reinterpret_cast<const float4*>(g);
+                x0.x = v.x; x0.y = v.y; x1.x = v.z; x1.y = v.w;
+            } else {
+                x0 = g[0];
+                x1 = g[1];
+            }
+            s[swz(i)] = x0;
+            s[swz(i + 1)] = x1;
+        }
+    }
+}
+
+// shared memory -> HBM (or the codec staging when ENC) for the tile at `base`
+template <typename T, typename R, bool ENC>
+__device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
+                                           uint64_t base, const FuseArgs& fa, uint32_t* cw)
+{
+    const int l = td.l;
+    if (ENC) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const uint32_t nrows = 1u << (kT - l);
+        for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
+            encode_row<T, R>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
+    } else {
+        const uint32_t rmask = (1u << l) - 1u;
+        for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
+            const uint32_t i = 2 * e;
+            T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
+            const T x0 = s[swz(i)], x1 = s[swz(i + 1)];
+            if (sizeof(R) == 4) {
+                *reinterpret_cast<float4*>(g) = make_float4((float)x0.x, (float)x0.y, (float)x1.x, (float)x1.y);
+            } else {
+                g[0] = x0;
+                g[1] = x1;
+            }
+        }
+    }
+}
+
+}  // namespace tile
+}  // namespace sv
