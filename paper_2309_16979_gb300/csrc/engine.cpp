@@ -238,7 +238,7 @@ template <typename R>
 static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
 {
     if (!s->cfg.jit) return SV_OK;
-    std::vector<std::string> src;
+    std::vector<std::string> keys;
     std::vector<std::pair<DevPass<R>*, size_t>> where;
     for (DevPass<R>* dp : dps) {
         if (!dp->use_phases) continue;
@@ -247,18 +247,28 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
         dp->jpar.assign(ns, std::vector<R>());
         for (size_t i = 0; i < ns; i++) {
             const bool dec = i == 0 && dp->fuse_decode, enc = i + 1 == ns && dp->fuse_encode;
-            src.push_back(jit_source<R>(dp->phases.data() + dp->ph_off[i], dp->ph_cnt[i], dp->pops.data(),
-                                        dp->ctl.data(), dp->d2m.data(), dec, enc, dp->jpar[i]));
+            const Phase* ph = dp->phases.data() + dp->ph_off[i];
+            jit_params<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->d2m.data(), dp->jpar[i]);
+            std::string key;
+            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->d2m.data(), dec, enc, key);
+            keys.push_back(std::move(key));
             where.push_back({dp, i});
         }
     }
-    if (src.empty()) return SV_OK;
+    if (keys.empty()) return SV_OK;
+    auto source_of = [&](size_t k) {
+        DevPass<R>* dp = where[k].first;
+        const size_t i = where[k].second;
+        return jit_source<R>(dp->phases.data() + dp->ph_off[i], dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(),
+                             dp->d2m.data(), i == 0 && dp->fuse_decode, i + 1 == dp->td.size() && dp->fuse_encode,
+                             dp->jpar[i]);
+    };
     std::vector<const JitFn*> fns;
     std::string err;
     JitReport rep;
-    if (!jit_compile(src, s->cfg.device, fns, err, &rep))
+    if (!jit_compile(keys, source_of, s->cfg.device, fns, err, &rep))
         return fail(s, SV_ERR_CUDA, "run-time kernel compilation failed: " + err);
-    for (size_t k = 0; k < src.size(); k++) where[k].first->jfn[where[k].second] = fns[k];
+    for (size_t k = 0; k < keys.size(); k++) where[k].first->jfn[where[k].second] = fns[k];
     s->st.jit_kernels_compiled += rep.compiled;
     s->st.t_jit_compile_s += rep.seconds;
     return SV_OK;
@@ -627,9 +637,10 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
         if (!dp.use_phases) continue;
         for (size_t i = 0; i < dp.td.size(); i++) {
             std::vector<R> par;
-            out.push_back(jit_source<R>(dp.phases.data() + dp.ph_off[i], dp.ph_cnt[i], dp.pops.data(), dp.ctl.data(),
-                                        dp.d2m.data(), i == 0 && dp.fuse_decode,
-                                        i + 1 == dp.td.size() && dp.fuse_encode, par));
+            const Phase* ph = dp.phases.data() + dp.ph_off[i];
+            jit_params<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.d2m.data(), par);
+            out.push_back(jit_source<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.ctl.data(), dp.d2m.data(),
+                                        i == 0 && dp.fuse_decode, i + 1 == dp.td.size() && dp.fuse_encode, par));
         }
     }
     return SV_OK;

@@ -29,6 +29,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -49,6 +50,10 @@ namespace {
 constexpr size_t kMaxParamBytes = 24576;  // by-value parameter block cap (CUDA allows 32764 bytes in all)
 constexpr int kJitThreads = 256;
 
+// Complex64 sub-passes that read amplitudes from HBM double-buffer the tile:
+// the next tile's copy is in flight while the current one is processed.
+bool prefetches(bool dec, size_t rsize) { return rsize == 4 && !dec; }
+
 // ------------------------------------------------------------ generation
 // A complex coefficient as the generated code sees it.
 enum Cls { C_ZERO, C_ONE, C_MONE, C_I, C_MI, C_REAL, C_IMAG, C_GEN };
@@ -61,17 +66,23 @@ struct Coef {
 std::string pref(size_t i) { return "p.m[" + std::to_string(i) + "]"; }
 
 template <typename R>
+int entry_class(R re, R im)
+{
+    if (re == 0 && im == 0) return C_ZERO;
+    if (re == 1 && im == 0) return C_ONE;
+    if (re == -1 && im == 0) return C_MONE;
+    if (re == 0 && im == 1) return C_I;
+    if (re == 0 && im == -1) return C_MI;
+    if (im == 0) return C_REAL;
+    if (re == 0) return C_IMAG;
+    return C_GEN;
+}
+
+template <typename R>
 Coef fixed_coef(R re, R im, size_t pidx)
 {
     Coef c;
-    if (re == 0 && im == 0) c.cls = C_ZERO;
-    else if (re == 1 && im == 0) c.cls = C_ONE;
-    else if (re == -1 && im == 0) c.cls = C_MONE;
-    else if (re == 0 && im == 1) c.cls = C_I;
-    else if (re == 0 && im == -1) c.cls = C_MI;
-    else if (im == 0) c.cls = C_REAL;
-    else if (re == 0) c.cls = C_IMAG;
-    else c.cls = C_GEN;
+    c.cls = entry_class(re, im);
     c.re = pref(pidx);
     c.im = pref(pidx + 1);
     return c;
@@ -130,20 +141,22 @@ std::string hex(uint64_t v)
 template <typename R>
 struct Gen {
     std::ostringstream o;
-    std::vector<R>& par;
+    const std::vector<R>& par;  // the kernel's parameter block (jit_params)
     int thr_of_tile[16];  // tile bit -> thread index bit of the current phase (-1: register bit)
     int slot[16];         // register index -> variable holding it
     int tmp = 0;
     bool ok = true;
-    explicit Gen(std::vector<R>& p) : par(p) {}
+    // Conditional exchanges on a register bit (an X whose controls are thread
+    // or CTA bits) not yet applied to the registers: each is folded into the
+    // phase's store addresses unless a later op of the phase depends on its bit.
+    struct Pend {
+        std::string cond;
+        int b;
+    };
+    std::vector<Pend> pend;
+    explicit Gen(const std::vector<R>& p) : par(p) {}
     std::string rv(int m) const { return "r" + std::to_string(slot[m]); }
     std::string iv(int m) const { return "q" + std::to_string(slot[m]); }
-    size_t push(const R* v, int n)
-    {
-        const size_t at = par.size();
-        for (int i = 0; i < n; i++) par.push_back(v[i]);
-        return at;
-    }
 };
 
 // Coefficient chosen at run time by `sel` (0..n-1) among candidates whose
@@ -221,6 +234,55 @@ std::string op_cond(Gen<R>& g, const PhaseOp<R>& op, const CtaCtrl* ctl)
     return s;
 }
 
+// register bits an op acts on as target or diagonal index
+template <typename R>
+uint32_t op_bits(const PhaseOp<R>& op)
+{
+    const uint32_t code = op.code;
+    if (code < kCodeDiag2) return 1u << (code & 3);
+    if (code < kCodeDiagT) {
+        const uint32_t x = (code - kCodeDiag2) & 15;
+        return (1u << (x & 3)) | (1u << (x >> 2));
+    }
+    if (code < kCodeDense2) return 0;
+    return (1u << (op.pad & 3)) | (1u << ((op.pad >> 2) & 3));
+}
+
+// does the op commute with exchanging the registers that differ in bit x?
+template <typename R>
+bool symmetric(const PhaseOp<R>& op, int x)
+{
+    if (op_bits(op) & (1u << x)) return false;
+    for (int i = 0; i < 16; i++)
+        if (((op.amask >> i) & 1u) != ((op.amask >> (i ^ (1 << x))) & 1u)) return false;
+    return true;
+}
+
+template <typename R>
+void emit_exchange(Gen<R>& g, const std::string& cond, int b)
+{
+    g.o << "if (" << cond << ") {\n";
+    for (int i = 0; i < 16; i++) {
+        if (i & (1 << b)) continue;
+        const int j = i | (1 << b);
+        g.o << "{ const R tr = " << g.rv(i) << ", ti = " << g.iv(i) << "; " << g.rv(i) << " = " << g.rv(j) << "; "
+            << g.iv(i) << " = " << g.iv(j) << "; " << g.rv(j) << " = tr; " << g.iv(j) << " = ti; }\n";
+    }
+    g.o << "}\n";
+}
+
+// apply the pending exchanges the op does not commute with
+template <typename R>
+void settle(Gen<R>& g, const PhaseOp<R>& op)
+{
+    std::vector<typename Gen<R>::Pend> keep;
+    for (const auto& pd : g.pend) {
+        if (symmetric(op, pd.b)) keep.push_back(pd);
+        else emit_exchange(g, pd.cond, pd.b);
+    }
+    g.pend.swap(keep);
+}
+
 // register m *= e
 template <typename R>
 void mul_reg(Gen<R>& g, int m, const Coef& e)
@@ -233,7 +295,7 @@ void mul_reg(Gen<R>& g, int m, const Coef& e)
 }
 
 template <typename R>
-void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, int b, const std::string& cond)
+void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::string& cond)
 {
     const R* m = op.m;
     const bool ident = m[0] == 1 && m[1] == 0 && m[2] == 0 && m[3] == 0 && m[4] == 0 && m[5] == 0 && m[6] == 1 &&
@@ -246,7 +308,13 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, int b, const std::string& cond
             if ((op.amask >> i) & 1u) std::swap(g.slot[i], g.slot[i | (1 << b)]);
         return;
     }
-    const size_t pb = g.push(m, 8);
+    uint32_t leaders = 0;  // every pair of bit b: an exchange of all of them can wait for the stores
+    for (int i = 0; i < 16; i++)
+        if (!(i & (1 << b))) leaders |= 1u << i;
+    if (xperm && op.amask == leaders) {
+        g.pend.push_back({cond, b});
+        return;
+    }
     Coef e[4];
     for (int k = 0; k < 4; k++) e[k] = fixed_coef<R>(m[2 * k], m[2 * k + 1], pb + 2 * k);
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
@@ -266,9 +334,8 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, int b, const std::string& cond
 }
 
 template <typename R>
-void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, int b0, int b1, const std::string& cond)
+void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, const std::string& cond)
 {
-    const size_t pb = g.push(op.m, 8);
     Coef e[4];
     bool all_one = true;
     for (int v = 0; v < 4; v++) {
@@ -285,9 +352,8 @@ void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, int b0, int b1, const std::stri
 }
 
 template <typename R>
-void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, int b0, const std::string& cond)
+void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, const std::string& cond)
 {
-    const size_t pb = g.push(op.m, 8);
     const std::string cb = const_bit(g, op.csrc);
     auto entry = [&](int rb, int c) { return op.rsel ? (c | (rb << 1)) : (rb | (c << 1)); };
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
@@ -308,9 +374,8 @@ void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, int b0, const std::string& cond
 }
 
 template <typename R>
-void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, const std::string& cond)
+void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& cond)
 {
-    const size_t pb = g.push(op.m, 8);
     const std::string c0 = const_bit(g, op.csrc), c1 = const_bit(g, op.csrc1);
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
     Coef e;
@@ -324,10 +389,9 @@ void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, const std::string& cond)
 }
 
 template <typename R>
-void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, const R* d2m, const std::string& cond)
+void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& cond)
 {
     const int b0 = op.pad & 3, b1 = (op.pad >> 2) & 3;
-    const size_t pb = g.push(d2m + 32ull * op.aux, 32);
     Coef e[16];
     for (int k = 0; k < 16; k++) e[k] = fixed_coef<R>(g.par[pb + 2 * k], g.par[pb + 2 * k + 1], pb + 2 * k);
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
@@ -444,7 +508,8 @@ std::mutex g_mu;
 std::unordered_map<std::string, std::unique_ptr<JitFn>> g_cache;  // key: device, arch, source
 
 struct Job {
-    const std::string* src;
+    size_t index = 0;
+    const std::string* src = nullptr;
     std::string key;
     std::string cubin;
     std::string log;
@@ -480,12 +545,68 @@ void compile_one(Job& j, const std::string& arch_opt)
 }  // namespace
 
 template <typename R>
-std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, std::vector<R>& params)
+void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params)
 {
     params.clear();
+    for (int pi = 0; pi < nph; pi++)
+        for (int oi = ph[pi].op_begin; oi < ph[pi].op_begin + ph[pi].op_count; oi++) {
+            const PhaseOp<R>& op = ops[oi];
+            if (op.code == kCodeDense2) params.insert(params.end(), d2m + 32ull * op.aux, d2m + 32ull * op.aux + 32);
+            else params.insert(params.end(), op.m, op.m + 8);
+        }
+    if (params.empty()) params.push_back((R)0);
+}
+
+template <typename R>
+void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec, bool enc,
+             std::string& key)
+{
+    key.clear();
+    auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
+    const uint8_t hdr[4] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, 1};
+    put(hdr, 4);
+    for (int pi = 0; pi < nph; pi++) {
+        const Phase& P = ph[pi];
+        put(P.tpos, sizeof P.tpos);
+        put(P.sroff, sizeof P.sroff);
+        put(&P.op_count, sizeof P.op_count);
+        for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
+            const PhaseOp<R>& op = ops[oi];
+            put(&op.code, 2);
+            put(&op.amask, 2);
+            put(&op.tmask, 2);
+            put(&op.flags, 1);
+            put(&op.csrc, 1);
+            put(&op.csrc1, 1);
+            put(&op.rsel, 1);
+            put(&op.pad, 2);
+            if (op.flags & 1u) put(&ctl[op.aux], sizeof(CtaCtrl));
+            // the value-dependent choices of the generator: each entry's class
+            // and, for 2x2 / diagonal ops, which entries are equal
+            const bool d2 = op.code == kCodeDense2;
+            const R* v = d2 ? d2m + 32ull * op.aux : op.m;
+            const int ne = d2 ? 16 : 4;
+            for (int k = 0; k < ne; k++) key.push_back((char)entry_class(v[2 * k], v[2 * k + 1]));
+            if (!d2) {
+                uint8_t eq = 0;
+                int bit = 0;
+                for (int a = 0; a < 4; a++)
+                    for (int b = a + 1; b < 4; b++, bit++)
+                        if (v[2 * a] == v[2 * b] && v[2 * a + 1] == v[2 * b + 1]) eq |= (uint8_t)(1u << bit);
+                key.push_back((char)eq);
+            }
+        }
+    }
+}
+
+template <typename R>
+std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
+                       bool enc, const std::vector<R>& params)
+{
+    (void)d2m;
     Gen<R> g(params);
     std::ostringstream body;
+    size_t pb = 0;  // parameter slot of the current op (8 values, 32 for a 4x4)
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
         for (int b = 0; b < 16; b++) g.thr_of_tile[b] = -1;
@@ -497,7 +618,7 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
         }
         for (int m = 0; m < 16; m++) g.slot[m] = m;
         g.o.str("");
-        g.o << "{\nconst uint32_t stb = tile::swz(" << tb << ");\nR ";
+        g.o << "{\nconst uint32_t stb = tile::swz(" << tb << ") ^ bo;\nR ";
         for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << "r" << m << ", q" << m;
         g.o << ";\n";
         for (int m = 0; m < 16; m++)
@@ -506,30 +627,40 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             const PhaseOp<R>& op = ops[oi];
             const std::string cond = op_cond(g, op, ctl);
             const uint32_t code = op.code;
+            settle(g, op);
             if (code < kCodeDiag2) {
                 const uint32_t kind = code / 8, b0 = code & 3;
-                if (kind == PK_DIAG1) emit_diag1(g, op, (int)b0, cond);
-                else emit_dense1(g, op, (int)b0, cond);
+                if (kind == PK_DIAG1) emit_diag1(g, op, pb, (int)b0, cond);
+                else emit_dense1(g, op, pb, (int)b0, cond);
             } else if (code < kCodeDiagT) {
                 const uint32_t x = (code - kCodeDiag2) & 15;
-                emit_diag2(g, op, (int)(x & 3), (int)(x >> 2), cond);
+                emit_diag2(g, op, pb, (int)(x & 3), (int)(x >> 2), cond);
             } else if (code < kCodeDense2) {
-                emit_diagt(g, op, cond);
+                emit_diagt(g, op, pb, cond);
             } else if (code == kCodeDense2) {
-                emit_dense2(g, op, d2m, cond);
+                emit_dense2(g, op, pb, cond);
             } else {
                 g.ok = false;
             }
+            pb += code == kCodeDense2 ? 32 : 8;
+        }
+        // a pending exchange on bit b sends register m to m ^ (1 << b): the
+        // swizzled offsets are linear over XOR, so it XORs the thread's base
+        std::string sst = "stb";
+        if (!g.pend.empty()) {
+            g.o << "uint32_t sst = stb;\n";
+            for (const auto& pd : g.pend) g.o << "if (" << pd.cond << ") sst ^= " << P.sroff[1 << pd.b] << "u;\n";
+            g.pend.clear();
+            sst = "sst";
         }
         for (int m = 0; m < 16; m++)
-            g.o << "s[stb ^ " << P.sroff[m] << "u] = tile::mk2<T, R>(" << g.rv(m) << ", " << g.iv(m) << ");\n";
+            g.o << "s[" << sst << " ^ " << P.sroff[m] << "u] = tile::mk2<T, R>(" << g.rv(m) << ", " << g.iv(m)
+                << ");\n";
         g.o << "__syncthreads();\n}\n";
         body << g.o.str();
     }
-    if (!g.ok || params.size() * sizeof(R) > kMaxParamBytes) {
-        params.clear();
-        return std::string();
-    }
+    if (!g.ok || params.size() * sizeof(R) > kMaxParamBytes) return std::string();
+    const bool pf = prefetches(dec, sizeof(R));
     std::ostringstream src;
     src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
         << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
@@ -539,26 +670,38 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
            "const FuseArgs fa, const P p)\n{\n"
         << "extern __shared__ __align__(16) unsigned char smem[];\n"
         << "T* s = reinterpret_cast<T*>(smem);\n"
-        << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + (sizeof(T) << tile::kT));\n"
-        << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n"
-        << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
-        << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
-        << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
-        << "__syncthreads();\n"
-        << body.str()
-        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
+        << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + (sizeof(T) << tile::kT) * " << (pf ? 2 : 1) << ");\n"
+        << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n";
+    if (pf) {
+        // tile buffer bo (element offset 0 or 4096) is processed while the
+        // other one fills; bo is folded into every phase's base offset
+        src << "__syncthreads();\n"
+            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T>(s, amps, rt, td, tile::tile_base(rt, td, blockIdx.x));\n"
+            << "uint32_t bo = 0;\n"
+            << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo ^= tile::kN) {\n"
+            << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
+            << "tile::cp_async_wait_all();\n__syncthreads();\n"
+            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T>(s + (bo ^ tile::kN), amps, rt, td, "
+               "tile::tile_base(rt, td, tl + gridDim.x));\n";
+    } else {
+        src << "const uint32_t bo = 0;\n"
+            << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
+            << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
+            << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
+            << "__syncthreads();\n";
+    }
+    src << body.str()
+        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ">(s + bo, amps, rt, td, base, fa, cw);\n"
         << "}\n}\n";
-    if (params.empty()) params.push_back((R)0);
     return src.str();
 }
 
-bool jit_compile(const std::vector<std::string>& sources, int device, std::vector<const JitFn*>& fns,
-                 std::string& err, JitReport* rep)
+bool jit_compile(const std::vector<std::string>& keys, const std::function<std::string(size_t)>& source_of,
+                 int device, std::vector<const JitFn*>& fns, std::string& err, JitReport* rep)
 {
     const auto t0 = std::chrono::steady_clock::now();
-    fns.assign(sources.size(), nullptr);
+    fns.assign(keys.size(), nullptr);
     std::lock_guard<std::mutex> lk(g_mu);
-    Nvrtc& n = nvrtc();
     Drv& d = drv();
     if (!d.ok) {
         err = d.why;
@@ -571,46 +714,59 @@ bool jit_compile(const std::vector<std::string>& sources, int device, std::vecto
         return false;
     }
     const std::string arch = "sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
-    const std::string prefix = std::to_string(device) + "/" + arch + "\n";
+    const std::string prefix = std::to_string(device) + "/" + arch + "/";
     std::vector<Job> jobs;
+    std::vector<std::string> srcs;
     std::unordered_map<std::string, size_t> job_of;
-    for (const std::string& s : sources) {
-        if (s.empty()) continue;
-        std::string key = prefix + s;
+    for (size_t i = 0; i < keys.size(); i++) {
+        if (keys[i].empty()) continue;
+        std::string key = prefix + keys[i];
         if (g_cache.count(key) || job_of.count(key)) continue;
         job_of[key] = jobs.size();
         Job j;
-        j.src = &s;
+        j.index = i;
         j.key = std::move(key);
         jobs.push_back(std::move(j));
     }
-    if (!jobs.empty()) {
+    // sources of the kernels not compiled yet (an empty source: the sub-pass
+    // cannot be specialised and stays on the table-driven kernel)
+    srcs.resize(jobs.size());
+    std::vector<Job*> todo;
+    for (size_t k = 0; k < jobs.size(); k++) {
+        srcs[k] = source_of(jobs[k].index);
+        jobs[k].src = &srcs[k];
+        if (!srcs[k].empty()) todo.push_back(&jobs[k]);
+    }
+    if (!todo.empty()) {
+        Nvrtc& n = nvrtc();
         if (!n.ok) {
             err = n.why;
             return false;
         }
         const std::string arch_opt = "--gpu-architecture=" + arch;
         const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-        const size_t nthr = std::min<size_t>(jobs.size(), hw);
+        const size_t nthr = std::min<size_t>(todo.size(), hw);
         std::vector<std::thread> pool;
         std::atomic_size_t next{0};
         for (size_t t = 0; t < nthr; t++)
             pool.emplace_back([&]() {
-                for (size_t k; (k = next.fetch_add(1)) < jobs.size();) compile_one(jobs[k], arch_opt);
+                for (size_t k; (k = next.fetch_add(1)) < todo.size();) compile_one(*todo[k], arch_opt);
             });
         for (std::thread& th : pool) th.join();
         if (cudaSetDevice(device) != cudaSuccess || cudaFree(nullptr) != cudaSuccess) {
             err = "cannot make the device current";
             return false;
         }
-        const size_t tile_bytes = sizeof(double) * 2 << kPhaseTileQubits;
-        const int smem_max = (int)(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32));
-        for (Job& j : jobs) {
+    }
+    const size_t tile_bytes = sizeof(double) * 2 << kPhaseTileQubits;
+    const int smem_max = (int)(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32));
+    for (Job& j : jobs) {
+        auto fn = std::make_unique<JitFn>();
+        if (!j.src->empty()) {
             if (!j.ok) {
                 err = "NVRTC compilation failed: " + j.log.substr(0, 2000);
                 return false;
             }
-            auto fn = std::make_unique<JitFn>();
             CUresult r = d.load(&fn->mod, j.cubin.data());
             if (r == CUDA_SUCCESS) r = d.getfn(&fn->fn, fn->mod, "svj");
             if (r == CUDA_SUCCESS) r = d.setattr(fn->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem_max);
@@ -618,17 +774,16 @@ bool jit_compile(const std::vector<std::string>& sources, int device, std::vecto
                 err = "loading a compiled kernel failed (CUresult " + std::to_string((int)r) + ")";
                 return false;
             }
-            g_cache[j.key] = std::move(fn);
+            if (rep) rep->compiled++;
         }
+        g_cache[j.key] = std::move(fn);
     }
-    for (size_t i = 0; i < sources.size(); i++) {
-        if (sources[i].empty()) continue;
-        fns[i] = g_cache[prefix + sources[i]].get();
+    for (size_t i = 0; i < keys.size(); i++) {
+        if (keys[i].empty()) continue;
+        const JitFn* f = g_cache[prefix + keys[i]].get();
+        fns[i] = f->fn ? f : nullptr;
     }
-    if (rep) {
-        rep->compiled += jobs.size();
-        rep->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
+    if (rep) rep->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return true;
 }
 
@@ -639,7 +794,7 @@ cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t
     if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, 152ull * 32);
-    const size_t smem = ((sizeof(R) * 2) << kPhaseTileQubits) +
+    const size_t smem = (((sizeof(R) * 2) << kPhaseTileQubits) * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +
                         ((fa.decode || fa.encode) ? sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32) : 0);
     void* a = amps;
     TileDesc t = td;
@@ -650,10 +805,16 @@ cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
+template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const float*, std::vector<float>&);
+template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&);
+template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool, bool,
+                             std::string&);
+template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*, bool, bool,
+                              std::string&);
 template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
-                                       bool, std::vector<float>&);
+                                       bool, const std::vector<float>&);
 template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,
-                                        bool, bool, std::vector<double>&);
+                                        bool, bool, const std::vector<double>&);
 template cudaError_t jit_launch<float>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
                                        const std::vector<float>&, cudaStream_t);
 template cudaError_t jit_launch<double>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,

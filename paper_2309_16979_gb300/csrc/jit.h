@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -14,27 +15,38 @@ namespace sv {
 
 struct JitFn;  // a loaded kernel (owned by the process-wide cache)
 
-// CUDA C++ source of the kernel for one register-phase sub-pass: its phases
-// and ops (as dev_phases lays them out), whether it decodes the chunk streams
-// (dec) and/or encodes the block pairs (enc). The matrix values the kernel
-// reads are appended to `params` (the kernel's by-value parameter block); the
-// source depends only on the sub-pass's structure, not on those values.
-// Returns an empty string when the sub-pass cannot be specialised (it then
-// runs on the table-driven kernel).
+// The kernel for one register-phase sub-pass is described by its phases and
+// ops as dev_phases lays them out, whether it decodes the chunk streams (dec)
+// and whether it encodes the block pairs (enc).
+//
+// jit_params: the kernel's by-value parameter block, the matrix values of its
+// ops in order, 8 per op (32 for a 4x4).
+template <typename R>
+void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params);
+
+// jit_key: a compact description of everything the generated code depends
+// on (the sub-pass's structure and which matrix entries are exactly 0, +-1,
+// +-i or equal to each other), not on the remaining matrix values.
+template <typename R>
+void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec, bool enc,
+             std::string& key);
+
+// jit_source: the CUDA C++ source of the kernel, reading `params`. Empty when
+// the sub-pass cannot be specialised (it then runs on the table-driven kernel).
 template <typename R>
 std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, std::vector<R>& params);
+                       bool enc, const std::vector<R>& params);
 
-// Compile (in parallel) and load the kernels of `sources` for `device`,
-// reusing kernels compiled before in this process; fns[i] receives the
-// kernel of sources[i] (nullptr for an empty source). On failure returns
-// false with the reason in `err`.
+// Look the kernels of `keys` up in the process-wide cache for `device`;
+// generate (source_of(i)), compile (in parallel) and load the ones missing.
+// fns[i] receives the kernel of keys[i], nullptr for an empty key or an
+// unspecialisable sub-pass. On failure returns false with the reason in `err`.
 struct JitReport {
     uint64_t compiled = 0;   // kernels compiled by this call
-    double seconds = 0;      // wall time spent compiling and loading
+    double seconds = 0;      // wall time spent looking up, generating, compiling and loading
 };
-bool jit_compile(const std::vector<std::string>& sources, int device, std::vector<const JitFn*>& fns,
-                 std::string& err, JitReport* rep);
+bool jit_compile(const std::vector<std::string>& keys, const std::function<std::string(size_t)>& source_of,
+                 int device, std::vector<const JitFn*>& fns, std::string& err, JitReport* rep);
 
 // Launch a generated kernel over the 2^(td.L - 12) tiles of `amps`.
 template <typename R>

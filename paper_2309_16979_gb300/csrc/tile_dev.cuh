@@ -138,6 +138,29 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
     }
 }
 
+// Asynchronous HBM -> shared copy of the tile at `base` (cp.async, one
+// amplitude per copy so that the swizzled destinations need no registers),
+// committed as one group; cp_async_wait_all() then __syncthreads() make it
+// visible. Used to fetch the next tile while the current one is processed.
+template <typename T>
+__device__ __forceinline__ void prefetch_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
+                                              uint64_t base)
+{
+    const int l = td.l;
+    const uint32_t rmask = (1u << l) - 1u;
+    for (uint32_t i = threadIdx.x; i < kN; i += kThreads) {
+        const T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(s + swz(i));
+        if (sizeof(T) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
+        else
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // shared memory -> HBM (or the codec staging when ENC) for the tile at `base`
 template <typename T, typename R, bool ENC>
 __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
