@@ -276,7 +276,8 @@ def roofline_from_stats(d):
 
 STAT_KEYS = ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d", "bytes_d2h", "t_decode_s", "t_apply_s",
              "t_encode_s", "n_decode", "n_apply", "n_encode", "alg_bytes_decode", "alg_bytes_apply",
-             "alg_bytes_encode", "jit_launches")
+             "alg_bytes_encode", "jit_launches", "t_h2d_s", "t_d2h_s", "t_encode_finish_s", "t_host_prepare_s",
+             "t_host_wait_s")
 
 
 # ------------------------------------------------------------ our arm
@@ -362,6 +363,12 @@ def run_apply(args, rank, world):
         "host_link": {"achieved_gbs": round(link_bytes / t_local / 1e9, 1), "peak_gbs": link,
                       "frac_of_bidir": round(link_bytes / t_local / 1e9 / link["bidir"], 3) if link else None,
                       "per_step": per_step},
+        # per step, ms: kernel and copy durations (CUDA events on their streams; copies
+        # overlap kernels) and host time planning / blocked on the GPU
+        "breakdown_ms_per_step": {k: round(d[v] / args.steps * 1e3, 2) for k, v in (
+            ("apply", "t_apply_s"), ("decode", "t_decode_s"), ("encode", "t_encode_s"),
+            ("encode_finish", "t_encode_finish_s"), ("h2d", "t_h2d_s"), ("d2h", "t_d2h_s"),
+            ("host_prepare", "t_host_prepare_s"), ("host_wait", "t_host_wait_s"))},
         "stored_state": {"compressed_bytes": st["compressed_bytes"], "raw_bytes": st["raw_bytes"],
                          "ratio": round(st["raw_bytes"] / max(1, st["compressed_bytes"]), 2),
                          "norm2": st["norm2"], "energy": energy, **quality},

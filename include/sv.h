@@ -134,6 +134,13 @@ typedef struct sv_stats_t {
        launches, and the wall time spent generating, compiling and loading them */
     uint64_t jit_kernels_compiled, jit_launches;
     double t_jit_compile_s;
+    /* with sv_config.profile: CUDA-event durations of the chunk-group copies
+       (host -> device, device -> host) and of the kernels that complete fused
+       encodes (offset scan, compaction) */
+    double t_h2d_s, t_d2h_s, t_encode_finish_s;
+    /* host wall time planning passes and looking up / compiling their kernels,
+       and blocked waiting for GPU work (always collected) */
+    double t_host_prepare_s, t_host_wait_s;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */

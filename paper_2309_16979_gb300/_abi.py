@@ -53,7 +53,9 @@ class SvStats(C.Structure):
                 ("alg_bytes_decode", C.c_uint64), ("alg_bytes_apply", C.c_uint64),
                 ("alg_bytes_encode", C.c_uint64),
                 ("jit_kernels_compiled", C.c_uint64), ("jit_launches", C.c_uint64),
-                ("t_jit_compile_s", C.c_double)]
+                ("t_jit_compile_s", C.c_double),
+                ("t_h2d_s", C.c_double), ("t_d2h_s", C.c_double), ("t_encode_finish_s", C.c_double),
+                ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double)]
 
 
 # every entry point declared in include/sv.h

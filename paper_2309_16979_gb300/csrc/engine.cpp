@@ -42,7 +42,10 @@ int wait_event(sv_state* s, cudaEvent_t ev)
     int spins = 0;
     for (;;) {
         const cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return SV_OK;
+        if (e == cudaSuccess) {
+            s->st.t_host_wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            return SV_OK;
+        }
         if (e != cudaErrorNotReady) return cuda_fail(s, e, "cudaEventQuery");
         if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
         const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -56,7 +59,10 @@ int wait_stream(sv_state* s, cudaStream_t st)
     int spins = 0;
     for (;;) {
         const cudaError_t e = cudaStreamQuery(st);
-        if (e == cudaSuccess) return SV_OK;
+        if (e == cudaSuccess) {
+            s->st.t_host_wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            return SV_OK;
+        }
         if (e != cudaErrorNotReady) return cuda_fail(s, e, "cudaStreamQuery");
         if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
         const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -128,11 +134,12 @@ void arena_free(Arena& a)
 // ------------------------------------------------------------- profiling
 // With sv_config.profile, kernel launches on the compute stream are bracketed
 // by CUDA events; durations are read once the pass has synchronised.
-enum { PROF_DECODE = 0, PROF_APPLY = 1, PROF_ENCODE = 2 };
+enum { PROF_DECODE = 0, PROF_APPLY = 1, PROF_ENCODE = 2, PROF_FINISH = 3, PROF_H2D = 4, PROF_D2H = 5 };
 
-static int prof_begin(sv_state* s)
+static int prof_begin(sv_state* s, cudaStream_t st = nullptr)
 {
     if (!s->cfg.profile) return -1;
+    if (!st) st = s->s_comp;
     const size_t i = s->prof_used;
     while (s->prof_ev.size() < 2 * (i + 1)) {
         cudaEvent_t ev;
@@ -140,15 +147,15 @@ static int prof_begin(sv_state* s)
         s->prof_ev.push_back(ev);
     }
     if (s->prof_rec.size() < i + 1) s->prof_rec.resize(i + 1);
-    cudaEventRecord(s->prof_ev[2 * i], s->s_comp);
+    cudaEventRecord(s->prof_ev[2 * i], st);
     s->prof_used++;
     return (int)i;
 }
 
-static void prof_end(sv_state* s, int i, int kind, uint64_t bytes)
+static void prof_end(sv_state* s, int i, int kind, uint64_t bytes, cudaStream_t st = nullptr)
 {
     if (i < 0) return;
-    cudaEventRecord(s->prof_ev[2 * i + 1], s->s_comp);
+    cudaEventRecord(s->prof_ev[2 * i + 1], st ? st : s->s_comp);
     s->prof_rec[i] = {kind, bytes};
 }
 
@@ -164,6 +171,9 @@ static void prof_collect(sv_state* s)
         if (r.kind == PROF_DECODE) { s->st.t_decode_s += ms * 1e-3; s->st.n_decode++; s->st.alg_bytes_decode += r.bytes; }
         if (r.kind == PROF_APPLY) { s->st.t_apply_s += ms * 1e-3; s->st.n_apply++; s->st.alg_bytes_apply += r.bytes; }
         if (r.kind == PROF_ENCODE) { s->st.t_encode_s += ms * 1e-3; s->st.n_encode++; s->st.alg_bytes_encode += r.bytes; }
+        if (r.kind == PROF_FINISH) s->st.t_encode_finish_s += ms * 1e-3;
+        if (r.kind == PROF_H2D) s->st.t_h2d_s += ms * 1e-3;
+        if (r.kind == PROF_D2H) s->st.t_d2h_s += ms * 1e-3;
     }
     s->prof_used = 0;
 }
@@ -426,6 +436,7 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
         if (s->slot_used[slot]) {
             if ((e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0))) return cuda_fail(s, e, "wait comp");
         }
+        const int ph2d = prof_begin(s, s->s_h2d);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = base | deposit((uint64_t)j, spos);
             ch[j] = k;
@@ -436,6 +447,7 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
             if (e) return cuda_fail(s, e, "H2D chunk");
             s->st.bytes_h2d += cr.bytes;
         }
+        prof_end(s, ph2d, PROF_H2D, 0, s->s_h2d);
         if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d))) return cuda_fail(s, e, "record h2d");
         if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0))) return cuda_fail(s, e, "wait h2d");
         if (s->slot_used[slot]) {
@@ -481,9 +493,11 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
         }
         int launches = 0;
         if (dp.fuse_encode) {
+            const int pf = prof_begin(s);
             if ((e = launch_encode_finish(c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse, s->d_blocksq,
                                           s->d_co[slot], s->s_comp, &launches)))
                 return cuda_fail(s, e, "encode");
+            prof_end(s, pf, PROF_FINISH, 0);
         } else {
             pi = prof_begin(s);
             slot_prof[slot] = pi;
@@ -508,6 +522,7 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
         int rr = wait_event(s, s->ev_comp[slot]);
         if (rr) return rr;
         cudaError_t e;
+        const int pd2h = prof_begin(s, s->s_d2h);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = slot_chunks[slot][j];
             const ChunkOut co = s->h_co[slot][j];
@@ -522,6 +537,7 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
             if (slot_prof[slot] >= 0) s->prof_rec[slot_prof[slot]].bytes += co.bytes;
             norm2 += (double)co.sumsq * delta2;
         }
+        prof_end(s, pd2h, PROF_D2H, 0, s->s_d2h);
         if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h))) return cuda_fail(s, e, "record d2h");
         return SV_OK;
     };
@@ -594,6 +610,7 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
         for (size_t i = 0; i < gates.size(); i++) ids[i] = (int)i;
         return run_pass_uncompressed<R>(s, s->d_state, gates, ids);
     }
+    const auto t0 = std::chrono::steady_clock::now();
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
     // plan every pass first, so that their kernels compile in one parallel batch
     std::vector<DevPass<R>> dps(passes.size());
@@ -605,6 +622,7 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
     }
     int r = jit_prepare<R>(s, ptrs);
     if (r) return r;
+    s->st.t_host_prepare_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (size_t i = 0; i < passes.size(); i++) {
         if ((r = run_pass_compressed<R>(s, passes[i], dps[i]))) return r;
         dps[i] = DevPass<R>();
@@ -1204,6 +1222,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
         cudaError_t e;
         if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0)))
             return cuda_fail(s, e, "wait comp");
+        const int ph2d = prof_begin(s, s->s_h2d);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = base | deposit((uint64_t)j, spos);
             ch[j] = k;
@@ -1216,6 +1235,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
                 return cuda_fail(s, e, "H2D chunk");
             s->st.bytes_h2d += s->cur[k].bytes + s->lcur[k].bytes;
         }
+        prof_end(s, ph2d, PROF_H2D, 0, s->s_h2d);
         if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0)))
             return cuda_fail(s, e, "record h2d");
         if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0)))
@@ -1259,6 +1279,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
         int rr = wait_event(s, s->ev_comp[slot]);
         if (rr) return rr;
         cudaError_t e;
+        const int pd2h = prof_begin(s, s->s_d2h);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = slot_chunks[slot][j];
             const ChunkOut cp = s->h_co[slot][j], cl = s->h_co2[slot][j];
@@ -1276,6 +1297,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
             s->lnxt[k] = {dl, cl.bytes};
             s->st.bytes_d2h += cp.bytes + cl.bytes;
         }
+        prof_end(s, pd2h, PROF_D2H, 0, s->s_d2h);
         if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h))) return cuda_fail(s, e, "record d2h");
         return SV_OK;
     };
