@@ -5,7 +5,8 @@ Default workload (the configuration the headline metric is quoted on):
 n = 30 qubits, complex64, chunks of 2^22 amplitudes held compressed in pinned
 host memory (error bound 1e-6), a depth-40 random layered circuit (H / RX / RZ
 on every qubit, then a CNOT on a seeded random pairing per layer; 1800
-gates), streamed through the GPU in groups of 2^4 chunks. One step = one
+gates), streamed through the GPU in groups of 2^g chunks (g chosen by the
+library from the free device memory: 6 here, four groups per pass). One step = one
 sv_apply_circuit of that circuit: every pass streams all chunks host -> GPU,
 decodes, applies the fused gates in on-chip tiles, re-encodes (with the FP64
 norm) and streams them back.
@@ -43,16 +44,16 @@ METRIC = "amp-gate updates/s"
 
 # name -> (n, chunk qubits, eb, dtype, group qubits, circuit, extra)
 WORKLOADS = {
-    "c1-layers": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="layers", depth=40),
-    "c1-ghz": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="ghz"),
-    "c1-qft": dict(n=30, c=22, eb=1e-6, dtype="c64", group=4, circuit="qft"),
-    "c0-qft": dict(n=16, c=10, eb=1e-6, dtype="c128", group=4, circuit="qft"),
-    "c0-layers": dict(n=16, c=10, eb=1e-6, dtype="c128", group=4, circuit="layers", depth=20),
-    "c2-ghz": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="ghz"),
-    "c2-qft": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="qft"),
-    "c2-clifford": dict(n=36, c=26, eb=1e-5, dtype="c64", group=4, circuit="clifford", depth=30),
-    "c3-grad": dict(n=24, c=24, eb=0.0, dtype="c64", group=4, circuit="hea", layers=10, mode="uncompressed"),
-    "c4-grad": dict(n=32, c=24, eb=1e-6, dtype="c64", group=4, circuit="hea", layers=8, sets=16),
+    "c1-layers": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40),
+    "c1-ghz": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="ghz"),
+    "c1-qft": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="qft"),
+    "c0-qft": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="qft"),
+    "c0-layers": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="layers", depth=20),
+    "c2-ghz": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="ghz"),
+    "c2-qft": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft"),
+    "c2-clifford": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30),
+    "c3-grad": dict(n=24, c=24, eb=0.0, dtype="c64", group=0, circuit="hea", layers=10, mode="uncompressed"),
+    "c4-grad": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16),
 }
 
 
@@ -97,7 +98,7 @@ def make_circuit(w, seed=1):
     raise ValueError(w["circuit"])
 
 
-def describe(w, ngates):
+def describe(w, ngates, group=None):
     if w["circuit"] == "hea":
         return (f"adjoint gradient, hardware-efficient ansatz n={w['n']}, {w['layers']} layers, 1-D Ising, "
                 f"{w['dtype']}, " + ("uncompressed in HBM" if w.get("mode") == "uncompressed" else
@@ -105,7 +106,7 @@ def describe(w, ngates):
     name = {"layers": f"random layered circuit depth {w.get('depth')}", "ghz": "GHZ", "qft": "QFT on a seeded basis state",
             "clifford": f"random Clifford+RZ depth {w.get('depth')} (40% of slots on the 10 high qubits)"}[w["circuit"]]
     return (f"{name}, n={w['n']} ({ngates} gates), {w['dtype']}, chunk=2^{w['c']}, eb={w['eb']}, compressed chunks "
-            f"in pinned host DRAM, streamed in groups of 2^{w['group']} chunks")
+            f"in pinned host DRAM, streamed in groups of 2^{group if group is not None else w['group']} chunks")
 
 
 # ------------------------------------------------------------ distributed
@@ -297,6 +298,7 @@ def run_apply(args, rank, world):
 
     sim = StateVector(n, c, w["eb"], dtype=w["dtype"], init_index=init, max_group_qubits=w["group"], profile=True,
                       device=dev, jit=bool(args.jit))
+    group = sim.stats()["group_qubits"]  # resolved (0 = chosen from the free device memory)
     for _ in range(args.warmup):
         sim.apply(gates)
     s0 = sim.stats()
@@ -349,8 +351,8 @@ def run_apply(args, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": f"{w['dtype']} (FP32 gate arithmetic for c64, FP64 reductions)"
         if w["dtype"] == "c64" else "c128 (FP64)", "data": "synthetic",
-        "config": {"workload": describe(w, len(gates)), "n_qubits": n, "chunk_qubits": c, "abs_error_bound": w["eb"],
-                   "group_qubits": w["group"], "gates": len(gates),
+        "config": {"workload": describe(w, len(gates), group), "n_qubits": n, "chunk_qubits": c,
+                   "abs_error_bound": w["eb"], "group_qubits": group, "gates": len(gates),
                    "l2": "inputs larger than L2: every pass streams the whole state; groups of 2^(c+g) amplitudes",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": gpu_launches,

@@ -88,8 +88,11 @@ typedef struct sv_config {
     int32_t dtype;                /* SV_C64 (default) or SV_C128 */
     int32_t mode;                 /* SV_COMPRESSED (default) or SV_UNCOMPRESSED */
     uint64_t init_index;          /* initial basis state |init_index> (default 0) */
-    int32_t max_group_qubits;     /* high qubits staged together per pass, g_max >= 2
-                                     (default 4, capped at n - chunk_qubits) */
+    int32_t max_group_qubits;     /* high qubits staged together per pass, g_max: 2..8, or 0
+                                     (default) = automatic: the largest g <= 8 that leaves at
+                                     least 4 chunk groups per pass (when n - chunk_qubits >= 4)
+                                     and whose staging buffers fit in 40% of the free device
+                                     memory; capped at n - chunk_qubits */
     int32_t tile_qubits;          /* qubits of one on-chip tile (0 = default for dtype) */
     int32_t pipeline_slots;       /* chunk-group buffers in flight, 2..4 (default 3) */
     int32_t renormalize;          /* 1: scale by 1/||psi|| at the next decode (default 0) */
@@ -228,8 +231,9 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
  * exposes the library's own code generator for inspection and testing.
  *   n, chunk_qubits: as in sv_create (chunk_qubits ignored when cfg->mode is
  *                    SV_UNCOMPRESSED).
- *   cfg:             NULL for defaults; dtype, mode, max_group_qubits,
- *                    tile_qubits and fuse_codec are used.
+ *   cfg:             NULL for defaults; dtype, mode, max_group_qubits (0 is
+ *                    taken as 4 here: no device is queried), tile_qubits and
+ *                    fuse_codec are used.
  *   gates, ngates:   host gate list, validated as in sv_apply_circuit.
  *   buf, cap:        host buffer receiving the sources, each terminated by a
  *                    NUL byte, in launch order; NULL to query the size only.

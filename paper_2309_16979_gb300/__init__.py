@@ -34,7 +34,7 @@ class StateVector:
     (mode="compressed") or whole in HBM (mode="uncompressed")."""
 
     def __init__(self, n: int, chunk_qubits: int = 0, eb: float = 1e-6, dtype: str = "c64",
-                 mode: str = "compressed", init_index: int = 0, max_group_qubits: int = 4,
+                 mode: str = "compressed", init_index: int = 0, max_group_qubits: int = 0,
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,

@@ -147,6 +147,35 @@ void release(sv_state* s)
     delete s;
 }
 
+// Device bytes of the streaming buffers for groups of 2^g chunks (create_impl).
+static size_t group_footprint(int c, int g, int dtype, int nslots)
+{
+    const CodecLayout L = codec_layout(c);
+    const size_t stride = (L.max_bytes + 255) & ~size_t(255);
+    const size_t amp = dtype == SV_C128 ? 16 : 8;
+    const size_t per_chunk = (amp << c) + (size_t)L.nb * 1024 + 8ull * L.bpc +
+                             (size_t)nslots * (2 * stride + sizeof(ChunkOut));
+    return per_chunk << g;
+}
+
+// Automatic g_max: the largest group (at most 2^8 chunks) that keeps at least
+// four groups per pass for the copy / compute pipeline when the state has
+// enough chunks, and whose buffers take at most 40% of the free device memory
+// (an adjoint gradient allocates a second set of the same size).
+static int auto_group_qubits(int n, int c, const sv_config& cfg)
+{
+    const int nh = n - c;
+    if (cfg.mode != SV_COMPRESSED || nh <= 2) return 2;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 4;
+    }
+    int g = std::max(2, std::min(8, nh >= 4 ? nh - 2 : nh));
+    while (g > 2 && group_footprint(c, g, cfg.dtype, cfg.pipeline_slots) > (size_t)(0.4 * (double)free_b)) g--;
+    return g;
+}
+
 template <typename R>
 int create_impl(sv_state* s)
 {
@@ -204,7 +233,7 @@ void sv_config_default(sv_config* cfg)
     cfg->dtype = SV_C64;
     cfg->mode = SV_COMPRESSED;
     cfg->init_index = 0;
-    cfg->max_group_qubits = 4;
+    cfg->max_group_qubits = 0;
     cfg->tile_qubits = 0;
     cfg->pipeline_slots = 3;
     cfg->renormalize = 0;
@@ -231,7 +260,8 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     if (cfg.dtype != SV_C64 && cfg.dtype != SV_C128) return reject(SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
     if (cfg.mode != SV_COMPRESSED && cfg.mode != SV_UNCOMPRESSED) return reject(SV_ERR_ARG, "bad mode");
     if (cfg.init_index >> n) return reject(SV_ERR_ARG, "init_index out of range");
-    if (cfg.max_group_qubits < 2 || cfg.max_group_qubits > 8) return reject(SV_ERR_ARG, "max_group_qubits must be 2..8");
+    if (cfg.max_group_qubits != 0 && (cfg.max_group_qubits < 2 || cfg.max_group_qubits > 8))
+        return reject(SV_ERR_ARG, "max_group_qubits must be 0 (automatic) or 2..8");
     if (cfg.pipeline_slots < 2 || cfg.pipeline_slots > 4) return reject(SV_ERR_ARG, "pipeline_slots must be 2..4");
     if (cfg.tile_qubits && (cfg.tile_qubits < 2 || cfg.tile_qubits > kMaxTileQubits))
         return reject(SV_ERR_ARG, "tile_qubits must be 2..13");
@@ -264,7 +294,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     s->nh = n - s->c;
     s->eb = abs_error_bound;
     s->k = k;
-    s->gmax = cfg.max_group_qubits;
+    s->gmax = cfg.max_group_qubits ? cfg.max_group_qubits : auto_group_qubits(n, chunk_qubits, cfg);
     s->nslots = cfg.pipeline_slots;
     s->tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
     s->lq = 5;
@@ -436,7 +466,7 @@ int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, 
     tmp.mode = cfg.mode;
     tmp.dtype = cfg.dtype;
     tmp.cfg = cfg;
-    tmp.gmax = cfg.max_group_qubits;
+    tmp.gmax = cfg.max_group_qubits ? cfg.max_group_qubits : 4;
     tmp.tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
     tmp.lq = 5;
     tmp.perm.resize(n);

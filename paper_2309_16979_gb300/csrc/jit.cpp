@@ -50,6 +50,11 @@ namespace {
 constexpr size_t kMaxParamBytes = 24576;  // by-value parameter block cap (CUDA allows 32764 bytes in all)
 constexpr int kJitThreads = 256;
 
+// slot of tile offset x in the padded shared-memory layout (tile::PadLayout)
+uint32_t pad_slot(uint32_t x) { return x + (x >> 4) + (x >> 8); }
+// slots of one padded tile buffer (tile::kPadElems)
+size_t tile_pad_elems() { return (pad_slot((1u << kPhaseTileQubits) - 1) + 1 + 15) & ~size_t(15); }
+
 // Complex64 sub-passes that read amplitudes from HBM double-buffer the tile:
 // the next tile's copy is in flight while the current one is processed.
 bool prefetches(bool dec, size_t rsize) { return rsize == 4 && !dec; }
@@ -271,16 +276,38 @@ void emit_exchange(Gen<R>& g, const std::string& cond, int b)
     g.o << "}\n";
 }
 
-// apply the pending exchanges the op does not commute with
+// Before an op: a pending exchange on bit b stays pending if the op commutes
+// with it, or if the op acts on b as its target or diagonal index (a 2x2 or
+// diagonal op whose controls do not involve b): the op is then applied
+// conjugated by the exchange, X U X, whose entries are U's with the b index
+// flipped, chosen per thread (returned); otherwise it is applied now.
 template <typename R>
-void settle(Gen<R>& g, const PhaseOp<R>& op)
+std::vector<typename Gen<R>::Pend> settle(Gen<R>& g, const PhaseOp<R>& op)
 {
-    std::vector<typename Gen<R>::Pend> keep;
+    std::vector<typename Gen<R>::Pend> keep, conj;
+    const bool conjugable = op.code < kCodeDiagT;  // 2x2, one- or two-register diagonal
     for (const auto& pd : g.pend) {
-        if (symmetric(op, pd.b)) keep.push_back(pd);
-        else emit_exchange(g, pd.cond, pd.b);
+        if (symmetric(op, pd.b)) {
+            keep.push_back(pd);
+        } else if (conjugable && ((op_bits(op) >> pd.b) & 1u)) {
+            keep.push_back(pd);
+            conj.push_back(pd);
+        } else {
+            emit_exchange(g, pd.cond, pd.b);
+        }
     }
     g.pend.swap(keep);
+    return conj;
+}
+
+// selector expression over pending exchanges: bit j set when conj[j] holds
+template <typename R>
+std::string flip_sel(const std::vector<typename Gen<R>::Pend>& conj)
+{
+    std::string s;
+    for (size_t j = 0; j < conj.size(); j++)
+        s += (j ? " | " : "") + std::string("((") + conj[j].cond + ") ? " + std::to_string(1u << j) + "u : 0u)";
+    return "(" + s + ")";
 }
 
 // register m *= e
@@ -295,7 +322,8 @@ void mul_reg(Gen<R>& g, int m, const Coef& e)
 }
 
 template <typename R>
-void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::string& cond)
+void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::string& cond,
+                 const std::vector<typename Gen<R>::Pend>& conj)
 {
     const R* m = op.m;
     const bool ident = m[0] == 1 && m[1] == 0 && m[2] == 0 && m[3] == 0 && m[4] == 0 && m[5] == 0 && m[6] == 1 &&
@@ -312,11 +340,27 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
     for (int i = 0; i < 16; i++)
         if (!(i & (1 << b))) leaders |= 1u << i;
     if (xperm && op.amask == leaders) {
+        // at most three pending, on distinct bits (their store bases are the
+        // eight sign combinations); apply the oldest otherwise
+        for (size_t k = 0; k < g.pend.size();) {
+            if (g.pend[k].b == b || g.pend.size() >= 3) {
+                emit_exchange(g, g.pend[k].cond, g.pend[k].b);
+                g.pend.erase(g.pend.begin() + (long)k);
+            } else {
+                k++;
+            }
+        }
         g.pend.push_back({cond, b});
         return;
     }
     Coef e[4];
-    for (int k = 0; k < 4; k++) e[k] = fixed_coef<R>(m[2 * k], m[2 * k + 1], pb + 2 * k);
+    if (conj.empty()) {
+        for (int k = 0; k < 4; k++) e[k] = fixed_coef<R>(m[2 * k], m[2 * k + 1], pb + 2 * k);
+    } else {
+        // X U X: row and column index flipped (entry k -> k ^ 3)
+        const std::string sel = flip_sel<R>(conj);
+        for (int k = 0; k < 4; k++) e[k] = select_coef(g, sel, {pb + 2 * (size_t)k, pb + 2 * (size_t)(k ^ 3)});
+    }
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
@@ -334,15 +378,30 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
 }
 
 template <typename R>
-void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, const std::string& cond)
+void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, const std::string& cond,
+                const std::vector<typename Gen<R>::Pend>& conj)
 {
     Coef e[4];
     bool all_one = true;
-    for (int v = 0; v < 4; v++) {
-        e[v] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
-        if (e[v].cls != C_ONE) all_one = false;
-    }
+    for (int v = 0; v < 4; v++)
+        if (entry_class(op.m[2 * v], op.m[2 * v + 1]) != C_ONE) all_one = false;
     if (all_one) return;
+    const std::string sel = conj.empty() ? std::string() : flip_sel<R>(conj);
+    for (int v = 0; v < 4; v++) {
+        if (conj.empty()) {
+            e[v] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
+            continue;
+        }
+        // a pending exchange on b0 (b1) flips entry-index bit 0 (1)
+        std::vector<size_t> cand;
+        for (uint32_t c = 0; c < (1u << conj.size()); c++) {
+            int w = v;
+            for (size_t j = 0; j < conj.size(); j++)
+                if ((c >> j) & 1u) w ^= conj[j].b == b0 ? 1 : 2;
+            cand.push_back(pb + 2 * (size_t)w);
+        }
+        e[v] = select_coef(g, sel, cand);
+    }
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
@@ -352,18 +411,26 @@ void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, cons
 }
 
 template <typename R>
-void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, const std::string& cond)
+void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, const std::string& cond,
+                const std::vector<typename Gen<R>::Pend>& conj)
 {
     const std::string cb = const_bit(g, op.csrc);
     auto entry = [&](int rb, int c) { return op.rsel ? (c | (rb << 1)) : (rb | (c << 1)); };
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
     Coef e[2];
+    const std::string fs = conj.empty() ? std::string() : "(" + conj[0].cond + ")";  // flips the register bit
     for (int rb = 0; rb < 2; rb++) {
-        if (cb.empty()) {
+        if (cb.empty() && fs.empty()) {
             const int v = entry(rb, 0);
             e[rb] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
-        } else {
+        } else if (fs.empty()) {
             e[rb] = select_coef(g, cb, {pb + 2 * (size_t)entry(rb, 0), pb + 2 * (size_t)entry(rb, 1)});
+        } else if (cb.empty()) {
+            e[rb] = select_coef(g, fs, {pb + 2 * (size_t)entry(rb, 0), pb + 2 * (size_t)entry(rb ^ 1, 0)});
+        } else {
+            e[rb] = select_coef(g, "(" + cb + " | (" + fs + " ? 2u : 0u))",
+                                {pb + 2 * (size_t)entry(rb, 0), pb + 2 * (size_t)entry(rb, 1),
+                                 pb + 2 * (size_t)entry(rb ^ 1, 0), pb + 2 * (size_t)entry(rb ^ 1, 1)});
         }
     }
     for (int i = 0; i < 16; i++) {
@@ -617,24 +684,32 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
                   std::to_string(P.tpos[j]) + ")";
         }
         for (int m = 0; m < 16; m++) g.slot[m] = m;
+        // padded slot of register index m relative to the thread's base
+        uint32_t K[16];
+        for (int m = 0; m < 16; m++) {
+            uint32_t o = 0;
+            for (int q = 0; q < kPhaseRegBits; q++)
+                if ((m >> q) & 1) o |= 1u << P.rpos[q];
+            K[m] = pad_slot(o);
+        }
         g.o.str("");
-        g.o << "{\nconst uint32_t stb = tile::swz(" << tb << ") ^ bo;\nR ";
+        g.o << "{\nconst uint32_t tb = " << tb << ";\nconst uint32_t sb = tb + (tb >> 4) + (tb >> 8) + bo;\nR ";
         for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << "r" << m << ", q" << m;
         g.o << ";\n";
         for (int m = 0; m < 16; m++)
-            g.o << "{ const T v = s[stb ^ " << P.sroff[m] << "u]; r" << m << " = v.x; q" << m << " = v.y; }\n";
+            g.o << "{ const T v = s[sb + " << K[m] << "u]; r" << m << " = v.x; q" << m << " = v.y; }\n";
         for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
             const PhaseOp<R>& op = ops[oi];
             const std::string cond = op_cond(g, op, ctl);
             const uint32_t code = op.code;
-            settle(g, op);
+            const auto conj = settle(g, op);
             if (code < kCodeDiag2) {
                 const uint32_t kind = code / 8, b0 = code & 3;
-                if (kind == PK_DIAG1) emit_diag1(g, op, pb, (int)b0, cond);
-                else emit_dense1(g, op, pb, (int)b0, cond);
+                if (kind == PK_DIAG1) emit_diag1(g, op, pb, (int)b0, cond, conj);
+                else emit_dense1(g, op, pb, (int)b0, cond, conj);
             } else if (code < kCodeDiagT) {
                 const uint32_t x = (code - kCodeDiag2) & 15;
-                emit_diag2(g, op, pb, (int)(x & 3), (int)(x >> 2), cond);
+                emit_diag2(g, op, pb, (int)(x & 3), (int)(x >> 2), cond, conj);
             } else if (code < kCodeDense2) {
                 emit_diagt(g, op, pb, cond);
             } else if (code == kCodeDense2) {
@@ -644,18 +719,25 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             }
             pb += code == kCodeDense2 ? 32 : 8;
         }
-        // a pending exchange on bit b sends register m to m ^ (1 << b): the
-        // swizzled offsets are linear over XOR, so it XORs the thread's base
-        std::string sst = "stb";
-        if (!g.pend.empty()) {
-            g.o << "uint32_t sst = stb;\n";
-            for (const auto& pd : g.pend) g.o << "if (" << pd.cond << ") sst ^= " << P.sroff[1 << pd.b] << "u;\n";
-            g.pend.clear();
-            sst = "sst";
+        // a pending exchange on register bit b sends register m to the slot of
+        // m ^ (1 << b), i.e. K[m] +- pad_slot(1 << rpos[b]) (the layout is
+        // additive over disjoint bits): one base per sign combination
+        const size_t np = g.pend.size();
+        for (size_t j = 0; j < np; j++)
+            g.o << "const uint32_t d" << j << " = (" << g.pend[j].cond << ") ? "
+                << pad_slot(1u << P.rpos[g.pend[j].b]) << "u : 0u;\n";
+        for (uint32_t c = 0; np && c < (1u << np); c++) {
+            g.o << "const uint32_t sb" << c << " = sb";
+            for (size_t j = 0; j < np; j++) g.o << (((c >> j) & 1) ? " - d" : " + d") << j;
+            g.o << ";\n";
         }
-        for (int m = 0; m < 16; m++)
-            g.o << "s[" << sst << " ^ " << P.sroff[m] << "u] = tile::mk2<T, R>(" << g.rv(m) << ", " << g.iv(m)
-                << ");\n";
+        for (int m = 0; m < 16; m++) {
+            uint32_t c = 0;
+            for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
+            g.o << "s[" << (np ? "sb" + std::to_string(c) : std::string("sb")) << " + " << K[m] << "u] = tile::mk2<T, R>("
+                << g.rv(m) << ", " << g.iv(m) << ");\n";
+        }
+        g.pend.clear();
         g.o << "__syncthreads();\n}\n";
         body << g.o.str();
     }
@@ -670,28 +752,30 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
            "const FuseArgs fa, const P p)\n{\n"
         << "extern __shared__ __align__(16) unsigned char smem[];\n"
         << "T* s = reinterpret_cast<T*>(smem);\n"
-        << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + (sizeof(T) << tile::kT) * " << (pf ? 2 : 1) << ");\n"
+        << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + sizeof(T) * tile::kPadElems * " << (pf ? 2 : 1) << ");\n"
         << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n";
     if (pf) {
         // tile buffer bo (element offset 0 or 4096) is processed while the
         // other one fills; bo is folded into every phase's base offset
         src << "__syncthreads();\n"
-            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T>(s, amps, rt, td, tile::tile_base(rt, td, blockIdx.x));\n"
+            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout>(s, amps, rt, td, "
+               "tile::tile_base(rt, td, blockIdx.x));\n"
             << "uint32_t bo = 0;\n"
-            << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo ^= tile::kN) {\n"
+            << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo = tile::kPadElems - bo) {\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
             << "tile::cp_async_wait_all();\n__syncthreads();\n"
-            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T>(s + (bo ^ tile::kN), amps, rt, td, "
-               "tile::tile_base(rt, td, tl + gridDim.x));\n";
+            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T, tile::PadLayout>(s + (tile::kPadElems - bo), amps, "
+               "rt, td, tile::tile_base(rt, td, tl + gridDim.x));\n";
     } else {
         src << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
-            << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ">(s, amps, rt, td, base, fa, cw);\n"
+            << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ", tile::PadLayout>(s, amps, rt, td, base, fa, cw);\n"
             << "__syncthreads();\n";
     }
     src << body.str()
-        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ">(s + bo, amps, rt, td, base, fa, cw);\n"
+        << "tile::store_tile<T, R, " << (enc ? "true" : "false")
+        << ", tile::PadLayout>(s + bo, amps, rt, td, base, fa, cw);\n"
         << "}\n}\n";
     return src.str();
 }
@@ -758,7 +842,7 @@ bool jit_compile(const std::vector<std::string>& keys, const std::function<std::
             return false;
         }
     }
-    const size_t tile_bytes = sizeof(double) * 2 << kPhaseTileQubits;
+    const size_t tile_bytes = sizeof(double) * 2 * tile_pad_elems();
     const int smem_max = (int)(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32));
     for (Job& j : jobs) {
         auto fn = std::make_unique<JitFn>();
@@ -794,7 +878,7 @@ cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t
     if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, 152ull * 32);
-    const size_t smem = (((sizeof(R) * 2) << kPhaseTileQubits) * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +
+    const size_t smem = (sizeof(R) * 2 * tile_pad_elems() * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +
                         ((fa.decode || fa.encode) ? sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32) : 0);
     void* a = amps;
     TileDesc t = td;

@@ -3,10 +3,17 @@
 // the shared-memory swizzle, the per-CTA row table, HBM <-> shared copies of
 // one 2^12-amplitude tile, and the fused codec steps that replace them.
 //
-// Shared memory is XOR-swizzled: amplitude i sits at swz(i) = i ^ (((i >> 4)
-// ^ (i >> 8)) & 15), so the 16 lanes of a half-warp, whose four low thread
-// bits map to tile bits of four different residues mod 4, hit 16 different
-// bank pairs whatever the register qubits are. swz is linear over XOR.
+// Two shared-memory layouts of a tile keep the 16 lanes of a half-warp, whose
+// four low thread bits map to tile bits of four different residues mod 4, on
+// 16 different bank pairs whatever the register qubits are:
+//  - SwzLayout: amplitude i at swz(i) = i ^ (((i >> 4) ^ (i >> 8)) & 15),
+//    linear over XOR (a register's address is the thread's base XOR a
+//    constant);
+//  - PadLayout: amplitude i at i + (i >> 4) + (i >> 8) (a spare slot after
+//    every 16 and every 256 amplitudes), additive over disjoint bit sets (a
+//    register's address is the thread's base plus a constant, folded into
+//    the load's immediate offset). Tile bit b moves the slot by 2^(b mod 4)
+//    modulo 16 in both.
 #pragma once
 
 #include "codec_dev.cuh"
@@ -34,6 +41,21 @@ __device__ __forceinline__ T mk2(R x, R y)
     v.y = y;
     return v;
 }
+
+// at(a | b) = join(at(a), at(b)) for offsets a, b with disjoint bits
+struct SwzLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t i) { return swz(i); }
+    static __device__ __forceinline__ uint32_t join(uint32_t a, uint32_t b) { return a ^ b; }
+};
+
+struct PadLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t i) { return i + (i >> 4) + (i >> 8); }
+    static __device__ __forceinline__ uint32_t join(uint32_t a, uint32_t b) { return a + b; }
+};
+// slots of one padded tile buffer: the last slot + 1, rounded up to 16 (a
+// second buffer stays 16-byte aligned); jit.cpp sizes shared memory the same way
+constexpr uint32_t kPadElems = ((kN - 1) + (kN - 1) / 16 + (kN - 1) / 256 + 1 + 15) & ~15u;
+static_assert(kPadElems == 4368, "padded tile buffer");
 
 // Per-CTA tables: local offset of each tile row, and the bit of each local
 // position outside the tile (tile index bit i -> local bit opos[i]).
@@ -63,7 +85,7 @@ __device__ __forceinline__ uint64_t tile_base(const Rows& rt, const TileDesc& td
 }
 
 // Fused codec steps, out of line: they run once per row, not per gate.
-template <typename T, typename R>
+template <typename T, typename R, typename Lay = SwzLayout>
 __device__ __noinline__ void decode_row(T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw, int lane)
 {
     const uint64_t cmask = (1ull << fa.c) - 1;
@@ -81,11 +103,11 @@ __device__ __noinline__ void decode_row(T* s, uint32_t rw, const FuseArgs& fa, u
         T v;
         v.x = x[0][m];
         v.y = x[1][m];
-        s[swz(rw * 256u + 8u * lane + m)] = v;
+        s[Lay::at(rw * 256u + 8u * lane + m)] = v;
     }
 }
 
-template <typename T, typename R>
+template <typename T, typename R, typename Lay = SwzLayout>
 __device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs& fa, uint64_t li, uint32_t* cw,
                                         int lane)
 {
@@ -96,7 +118,7 @@ __device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs&
     R x[2][8];
 #pragma unroll
     for (int m = 0; m < 8; m++) {
-        const T v = s[swz(rw * 256u + 8u * lane + m)];
+        const T v = s[Lay::at(rw * 256u + 8u * lane + m)];
         x[0][m] = v.x;
         x[1][m] = v.y;
     }
@@ -109,7 +131,7 @@ __device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs&
 // DEC: decode the group's chunk streams, one warp per 256-amplitude block
 // pair (rows are block pairs, td.l = 8); otherwise 16-byte vector loads along
 // the rows.
-template <typename T, typename R, bool DEC>
+template <typename T, typename R, bool DEC, typename Lay = SwzLayout>
 __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                           uint64_t base, const FuseArgs& fa, uint32_t* cw)
 {
@@ -118,12 +140,17 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         const uint32_t nrows = 1u << (kT - l);
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
-            decode_row<T, R>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
+            decode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        const uint32_t rmask = (1u << l) - 1u;
-        for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
-            const uint32_t i = 2 * e;
-            const T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
+        // amplitudes 2t + 512k and 2t + 512k + 1 (t = thread): the row and the
+        // slot split into a per-thread part and a compile-time part (l <= 8)
+        const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
+        const T* g0 = amps + base + (t2 & rmask);
+        const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
+#pragma unroll
+        for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
+            const T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
+            const uint32_t ak = Lay::at(512u * k);
             T x0, x1;
             if (sizeof(R) == 4) {
                 const float4 v = *reinterpret_cast<const float4*>(g);
@@ -132,8 +159,8 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
                 x0 = g[0];
                 x1 = g[1];
             }
-            s[swz(i)] = x0;
-            s[swz(i + 1)] = x1;
+            s[Lay::join(a0, ak)] = x0;
+            s[Lay::join(a1, ak)] = x1;
         }
     }
 }
@@ -142,15 +169,19 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
 // amplitude per copy so that the swizzled destinations need no registers),
 // committed as one group; cp_async_wait_all() then __syncthreads() make it
 // visible. Used to fetch the next tile while the current one is processed.
-template <typename T>
+template <typename T, typename Lay = SwzLayout>
 __device__ __forceinline__ void prefetch_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                               uint64_t base)
 {
     const int l = td.l;
-    const uint32_t rmask = (1u << l) - 1u;
-    for (uint32_t i = threadIdx.x; i < kN; i += kThreads) {
-        const T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(s + swz(i));
+    // amplitude t + 256k (t = thread): row and slot split as in load_tile
+    const uint32_t t = threadIdx.x, rmask = (1u << l) - 1u;
+    const T* g0 = amps + base + (t & rmask);
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(s), a0 = Lay::at(t);
+#pragma unroll
+    for (uint32_t k = 0; k < kN / kThreads; k++) {
+        const T* g = g0 + rt.rowoff[(t >> l) + ((256u * k) >> l)];
+        const uint32_t d = d0 + (uint32_t)sizeof(T) * Lay::join(a0, Lay::at(256u * k));
         if (sizeof(T) == 8)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
         else
@@ -162,7 +193,7 @@ __device__ __forceinline__ void prefetch_tile(T* s, const T* __restrict__ amps, 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // shared memory -> HBM (or the codec staging when ENC) for the tile at `base`
-template <typename T, typename R, bool ENC>
+template <typename T, typename R, bool ENC, typename Lay = SwzLayout>
 __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                            uint64_t base, const FuseArgs& fa, uint32_t* cw)
 {
@@ -171,13 +202,16 @@ __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, con
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         const uint32_t nrows = 1u << (kT - l);
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
-            encode_row<T, R>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
+            encode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        const uint32_t rmask = (1u << l) - 1u;
-        for (uint32_t e = threadIdx.x; e < kN / 2; e += kThreads) {
-            const uint32_t i = 2 * e;
-            T* g = amps + base + rt.rowoff[i >> l] + (i & rmask);
-            const T x0 = s[swz(i)], x1 = s[swz(i + 1)];
+        const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
+        T* g0 = amps + base + (t2 & rmask);
+        const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
+#pragma unroll
+        for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
+            T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
+            const uint32_t ak = Lay::at(512u * k);
+            const T x0 = s[Lay::join(a0, ak)], x1 = s[Lay::join(a1, ak)];
             if (sizeof(R) == 4) {
                 *reinterpret_cast<float4*>(g) = make_float4((float)x0.x, (float)x0.y, (float)x1.x, (float)x1.y);
             } else {

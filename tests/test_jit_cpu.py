@@ -84,7 +84,7 @@ def test_conditional_exchange_folds_into_store_addresses(jit_sources):
     # store base instead of register moves
     gates = [W.Gate("H", (q,)) for q in range(12)] + [W.Gate("CNOT", (1,), (7,)), W.Gate("CNOT", (2,), (9,))]
     srcs = [s for s in jit_sources(12, 12, gates, mode="uncompressed") if s]
-    assert any("sst ^=" in s for s in srcs)
+    assert any("const uint32_t sb0 = sb" in s for s in srcs)
 
 
 def test_x_gates_cost_no_arithmetic(jit_sources):
