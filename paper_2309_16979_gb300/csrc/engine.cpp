@@ -260,7 +260,7 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
             const Phase* ph = dp->phases.data() + dp->ph_off[i];
             jit_params<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->d2m.data(), dp->jpar[i]);
             std::string key;
-            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->d2m.data(), dec, enc, key);
+            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->jpar[i], dec, enc, key);
             keys.push_back(std::move(key));
             where.push_back({dp, i});
         }

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <functional>
@@ -325,7 +326,7 @@ template <typename R>
 void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::string& cond,
                  const std::vector<typename Gen<R>::Pend>& conj)
 {
-    const R* m = op.m;
+    const R* m = g.par.data() + pb;  // the op's entries as the kernel reads them
     const bool ident = m[0] == 1 && m[1] == 0 && m[2] == 0 && m[3] == 0 && m[4] == 0 && m[5] == 0 && m[6] == 1 &&
                        m[7] == 0;
     if (ident) return;
@@ -384,12 +385,12 @@ void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, cons
     Coef e[4];
     bool all_one = true;
     for (int v = 0; v < 4; v++)
-        if (entry_class(op.m[2 * v], op.m[2 * v + 1]) != C_ONE) all_one = false;
+        if (entry_class(g.par[pb + 2 * v], g.par[pb + 2 * v + 1]) != C_ONE) all_one = false;
     if (all_one) return;
     const std::string sel = conj.empty() ? std::string() : flip_sel<R>(conj);
     for (int v = 0; v < 4; v++) {
         if (conj.empty()) {
-            e[v] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
+            e[v] = fixed_coef<R>(g.par[pb + 2 * v], g.par[pb + 2 * v + 1], pb + 2 * v);
             continue;
         }
         // a pending exchange on b0 (b1) flips entry-index bit 0 (1)
@@ -422,7 +423,7 @@ void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, const std::s
     for (int rb = 0; rb < 2; rb++) {
         if (cb.empty() && fs.empty()) {
             const int v = entry(rb, 0);
-            e[rb] = fixed_coef<R>(op.m[2 * v], op.m[2 * v + 1], pb + 2 * v);
+            e[rb] = fixed_coef<R>(g.par[pb + 2 * v], g.par[pb + 2 * v + 1], pb + 2 * v);
         } else if (fs.empty()) {
             e[rb] = select_coef(g, cb, {pb + 2 * (size_t)entry(rb, 0), pb + 2 * (size_t)entry(rb, 1)});
         } else if (cb.empty()) {
@@ -446,7 +447,7 @@ void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& c
     const std::string c0 = const_bit(g, op.csrc), c1 = const_bit(g, op.csrc1);
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
     Coef e;
-    if (c0.empty() && c1.empty()) e = fixed_coef<R>(op.m[0], op.m[1], pb);
+    if (c0.empty() && c1.empty()) e = fixed_coef<R>(g.par[pb], g.par[pb + 1], pb);
     else if (c1.empty()) e = select_coef(g, c0, {pb, pb + 2});
     else if (c0.empty()) e = select_coef(g, c1, {pb, pb + 4});
     else e = select_coef(g, "(" + c0 + " | (" + c1 + " << 1))", {pb, pb + 2, pb + 4, pb + 6});
@@ -611,23 +612,93 @@ void compile_one(Job& j, const std::string& arch_opt)
 
 }  // namespace
 
+// An op applied to every amplitude of the tile: no controls outside its
+// registers' pair structure and none among them.
+template <typename R>
+bool uncontrolled(const PhaseOp<R>& op)
+{
+    if (op.flags || op.tmask) return false;
+    uint32_t all = 0xffffu;
+    if (op.code < kCodeDiag2 && op.code / 8 != PK_DIAG1) {
+        all = 0;  // 2x2: the pair leaders of the target bit
+        for (int i = 0; i < 16; i++)
+            if (!(i & (1 << (op.code & 3)))) all |= 1u << i;
+    } else if (op.code == kCodeDense2) {
+        all = 0;
+        const int b0 = op.pad & 3, b1 = (op.pad >> 2) & 3;
+        for (int i = 0; i < 16; i++)
+            if (!(i & ((1 << b0) | (1 << b1)))) all |= 1u << i;
+    }
+    return op.amask == all;
+}
+
 template <typename R>
 void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params)
 {
+    using C = std::complex<double>;
     params.clear();
+    // each op's entries in order; an uncontrolled op U is stored as U / a,
+    // with a its first entry (so that the entry becomes exactly 1 and the
+    // generated code skips its multiplies) unless that entry is under a
+    // quarter of the largest, then the largest; the product of those factors
+    // is multiplied into the last such op instead. The choice of entry changes
+    // only for rotations near pi. With |a| >= |largest| / 4, U / a scales
+    // amplitudes by at most 4 x (entries per row): 2^3 for a 2x2, 2^2 for a
+    // diagonal, 2^4 for a 4x4; ops are factored while the sum of those bounds
+    // stays within 2^120 (inside the FP32 range; a bound on the structure, so
+    // small changes of the angles do not change which ops are factored).
+    struct Norm {
+        size_t at;
+        int n;
+        C a;
+    };
+    std::vector<Norm> norm;
+    int growth = 0;  // log2 of the bound on the amplitudes' growth so far
     for (int pi = 0; pi < nph; pi++)
         for (int oi = ph[pi].op_begin; oi < ph[pi].op_begin + ph[pi].op_count; oi++) {
             const PhaseOp<R>& op = ops[oi];
+            const size_t at = params.size();
+            const int n = op.code == kCodeDense2 ? 16 : 4;
             if (op.code == kCodeDense2) params.insert(params.end(), d2m + 32ull * op.aux, d2m + 32ull * op.aux + 32);
             else params.insert(params.end(), op.m, op.m + 8);
+            if (!uncontrolled(op)) continue;
+            C big(0, 0);
+            for (int k = 0; k < n; k++) {
+                const C e((double)params[at + 2 * k], (double)params[at + 2 * k + 1]);
+                if (std::abs(e) > std::abs(big)) big = e;
+            }
+            const C first((double)params[at], (double)params[at + 1]);
+            const C a = std::abs(first) >= 0.25 * std::abs(big) ? first : big;
+            if (std::abs(a) == 0 || a == C(1, 0)) continue;
+            const int g = n == 16 ? 4 : (op.code < kCodeDiag2 && op.code / 8 != PK_DIAG1) ? 3 : 2;
+            if (growth + g > 120) continue;
+            growth += g;
+            norm.push_back({at, n, a});
         }
+    if (!norm.empty()) {
+        C rest(1, 0);
+        for (size_t j = 0; j + 1 < norm.size(); j++) rest *= norm[j].a;
+        for (size_t j = 0; j < norm.size(); j++) {
+            const C f = j + 1 < norm.size() ? C(1, 0) / norm[j].a : rest;
+            for (int k = 0; k < norm[j].n; k++) {
+                R* e = &params[norm[j].at + 2 * k];
+                const C x((double)e[0], (double)e[1]);
+                // an entry equal to the factor becomes exactly 1 (complex
+                // division would leave a rounding residue in its imaginary part)
+                const C v = (j + 1 < norm.size() && x == norm[j].a) ? C(1, 0) : x * f;
+                e[0] = (R)v.real();
+                e[1] = (R)v.imag();
+            }
+        }
+    }
     if (params.empty()) params.push_back((R)0);
 }
 
 template <typename R>
-void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec, bool enc,
-             std::string& key)
+void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
+             bool dec, bool enc, std::string& key)
 {
+    size_t pb = 0;
     key.clear();
     auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
     const uint8_t hdr[4] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, 1};
@@ -651,7 +722,8 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
             // the value-dependent choices of the generator: each entry's class
             // and, for 2x2 / diagonal ops, which entries are equal
             const bool d2 = op.code == kCodeDense2;
-            const R* v = d2 ? d2m + 32ull * op.aux : op.m;
+            const R* v = params.data() + pb;
+            pb += d2 ? 32 : 8;
             const int ne = d2 ? 16 : 4;
             for (int k = 0; k < ne; k++) key.push_back((char)entry_class(v[2 * k], v[2 * k + 1]));
             if (!d2) {
@@ -891,10 +963,10 @@ cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t
 
 template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const float*, std::vector<float>&);
 template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&);
-template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool, bool,
-                             std::string&);
-template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*, bool, bool,
-                              std::string&);
+template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const std::vector<float>&,
+                             bool, bool, std::string&);
+template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const std::vector<double>&,
+                              bool, bool, std::string&);
 template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
                                        bool, const std::vector<float>&);
 template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,

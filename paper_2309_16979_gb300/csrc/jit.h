@@ -20,16 +20,19 @@ struct JitFn;  // a loaded kernel (owned by the process-wide cache)
 // and whether it encodes the block pairs (enc).
 //
 // jit_params: the kernel's by-value parameter block, the matrix values of its
-// ops in order, 8 per op (32 for a 4x4).
+// ops in order, 8 per op (32 for a 4x4). Ops that act on every amplitude are
+// stored divided by their largest-magnitude entry, and the product of those
+// scalars is multiplied into the last of them, so the sub-pass's result is
+// unchanged while most gates carry an exact 1.
 template <typename R>
 void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params);
 
 // jit_key: a compact description of everything the generated code depends
-// on (the sub-pass's structure and which matrix entries are exactly 0, +-1,
-// +-i or equal to each other), not on the remaining matrix values.
+// on (the sub-pass's structure and which entries of `params` are exactly 0,
+// +-1, +-i or equal to each other), not on the remaining values.
 template <typename R>
-void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec, bool enc,
-             std::string& key);
+void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
+             bool dec, bool enc, std::string& key);
 
 // jit_source: the CUDA C++ source of the kernel, reading `params`. Empty when
 // the sub-pass cannot be specialised (it then runs on the table-driven kernel).

@@ -80,12 +80,18 @@ def test_compressed_generated_kernels_with_fused_codec(SV):
 
 
 def test_kernels_reused_when_only_angles_change(SV):
+    """Kernels are keyed by structure: new angles that keep every rotation on
+    the same side of the factoring threshold (away from pi) compile nothing."""
     n, c = 16, 10
     g1 = W.random_layers(n, 5, seed=31)
+    rng = W.SplitMix64(77)
+    for x in g1:
+        if x.kind in ("RX", "RY", "RZ"):
+            x.theta = 2.0 * rng.uniform() - 1.0
     g2 = copy.deepcopy(g1)
     for x in g2:
         if x.kind in ("RX", "RY", "RZ"):
-            x.theta = 0.7 * x.theta + 0.05
+            x.theta = 0.9 * x.theta + 0.05
     with SV(n, c, 1e-6, max_group_qubits=3, init_index=9) as s:
         s.apply(g1)
         k1 = s.stats()["jit_kernels_compiled"]
