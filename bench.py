@@ -250,13 +250,17 @@ def host_link_peak():
     return out
 
 
-def load_traffic(kind):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+def load_traffic(kind, alg_bytes_per_launch):
+    """DRAM bytes per launch of the dominant kernel: the committed ncu capture's
+    measured / algorithmic byte ratio (taken on a smaller launch of the same
+    kernel; traffic grows with the amplitudes processed) applied to this run's
+    algorithmic bytes per launch; None without a capture."""
     path = os.path.join(ROOT, "profiles", f"traffic_k_{kind}.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
-        return json.load(f).get("bytes_per_launch")
+        t = json.load(f)
+    return int(alg_bytes_per_launch * t["bytes_per_amplitude"] / t["algorithmic_bytes_per_amplitude"])
 
 
 def roofline_from_stats(d):
@@ -271,7 +275,8 @@ def roofline_from_stats(d):
     bytes_per_launch = d[bk] / max(1, d[nk])
     achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": load_traffic(top), "kernel": f"k_{top}",
+            "frac": round(achieved / hbm_peak, 4), "traffic": load_traffic(top, bytes_per_launch),
+            "kernel": f"k_{top}",
             "peak_source": f"{peak_kind} (copy)", "launches": int(d[nk]),
             "avg_launch_ms": round(avg_s * 1e3, 4), "alg_bytes_per_launch": int(bytes_per_launch),
             "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, total), 3) for k, v in kinds.items()}}
