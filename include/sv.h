@@ -234,7 +234,11 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
  *   cfg:             NULL for defaults; dtype, mode, max_group_qubits (0 is
  *                    taken as 4 here: no device is queried), tile_qubits and
  *                    fuse_codec are used.
- *   gates, ngates:   host gate list, validated as in sv_apply_circuit.
+ *   gates, ngates:   host gate list, validated as in sv_apply_circuit
+ *                    (sv_grad when adjoint is set).
+ *   adjoint:         0: the kernels of sv_apply_circuit; 1: those of the
+ *                    reverse sweep of sv_grad (psi and lambda together, with
+ *                    the gradient partials).
  *   buf, cap:        host buffer receiving the sources, each terminated by a
  *                    NUL byte, in launch order; NULL to query the size only.
  *   needed:          receives the bytes required; nkernels the number of
@@ -242,8 +246,8 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
  *                    empty source and runs the table-driven kernel).
  * Errors: SV_ERR_ARG for invalid sizes or gates, or cap < *needed.
  */
-int sv_jit_sources(int n, int chunk_qubits, const sv_config* cfg, const sv_gate* gates, size_t ngates, char* buf,
-                   size_t cap, size_t* needed, size_t* nkernels);
+int sv_jit_sources(int n, int chunk_qubits, const sv_config* cfg, const sv_gate* gates, size_t ngates, int adjoint,
+                   char* buf, size_t cap, size_t* needed, size_t* nkernels);
 
 /*
  * The chunk passes sv_apply_circuit would run, computed on the host only (no

@@ -150,9 +150,11 @@ def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, 
 
 
 def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", mode: str = "compressed",
-                max_group_qubits: int = 4, tile_qubits: int = 0, fuse_codec: bool = True) -> list:
+                max_group_qubits: int = 4, tile_qubits: int = 0, fuse_codec: bool = True,
+                adjoint: bool = False) -> list:
     """Host-only: the CUDA C++ sources of the sub-pass kernels sv_apply_circuit
-    would generate for this circuit (sv_jit_sources), in launch order."""
+    (or, with adjoint, the reverse sweep of sv_grad) would generate for this
+    circuit (sv_jit_sources), in launch order."""
     L = load()
     cfg = _abi.SvConfig()
     L.sv_config_default(C.byref(cfg))
@@ -163,10 +165,11 @@ def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", 
     cfg.fuse_codec = int(fuse_codec)
     arr = _abi.gates_to_c(gates)
     need, nk = C.c_size_t(0), C.c_size_t(0)
-    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), None, 0, C.byref(need),
-                            C.byref(nk)), "sv_jit_sources", None)
+    adj = int(adjoint)
+    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), adj, None, 0,
+                            C.byref(need), C.byref(nk)), "sv_jit_sources", None)
     buf = C.create_string_buffer(max(1, need.value))
-    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), buf, need.value,
+    _check(L.sv_jit_sources(n, chunk_qubits, C.byref(cfg), C.addressof(arr), len(gates), adj, buf, need.value,
                             C.byref(need), C.byref(nk)), "sv_jit_sources", None)
     parts = buf.raw[:need.value].split(b"\0")[:nk.value]
     return [x.decode() for x in parts]

@@ -117,8 +117,8 @@ def load() -> C.CDLL:
     L.sv_codec_encode_noalloc.restype = C.c_int
     L.sv_chunk_stream.argtypes = [P, C.c_uint64, P, SZ, C.POINTER(SZ)]
     L.sv_chunk_stream.restype = C.c_int
-    L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_char_p, SZ, C.POINTER(SZ),
-                                 C.POINTER(SZ)]
+    L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_int, C.c_char_p, SZ,
+                                 C.POINTER(SZ), C.POINTER(SZ)]
     L.sv_jit_sources.restype = C.c_int
     _lib = L
     return L

@@ -451,8 +451,8 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
     return SV_OK;
 }
 
-int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, size_t ngates, char* buf, size_t cap,
-                   size_t* needed, size_t* nkernels)
+int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, size_t ngates, int adjoint, char* buf,
+                   size_t cap, size_t* needed, size_t* nkernels)
 {
     sv_config cfg;
     sv_config_default(&cfg);
@@ -472,9 +472,14 @@ int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, 
     tmp.perm.resize(n);
     for (int q = 0; q < n; q++) tmp.perm[q] = q;
     std::vector<PGate> pg;
-    int r = lower(&tmp, gates, ngates, nullptr, 0, false, pg);
+    size_t nparams = 0;
+    for (size_t i = 0; adjoint && i < ngates; i++)
+        if (gates[i].param_index >= 0) nparams = std::max(nparams, (size_t)gates[i].param_index + 1);
+    int r = lower(&tmp, gates, ngates, nullptr, nparams, adjoint != 0, pg);
     std::vector<std::string> src;
-    if (!r) r = cfg.dtype == SV_C128 ? jit_sources<double>(&tmp, pg, src) : jit_sources<float>(&tmp, pg, src);
+    if (!r)
+        r = cfg.dtype == SV_C128 ? jit_sources<double>(&tmp, pg, src, adjoint != 0)
+                                 : jit_sources<float>(&tmp, pg, src, adjoint != 0);
     if (r) {
         g_create_error = tmp.err;
         return r;

@@ -325,6 +325,64 @@ static int upload_pass(sv_state* s, DevPass<R>& dp)
     return SV_OK;
 }
 
+// Adjoint sub-passes as generated two-vector kernels (jit.cpp): psi and
+// lambda in registers, the gradient partials inline. `ok` stays false (the
+// k_adjoint path runs) when generation is off or a sub-pass cannot be
+// specialised; the sub-passes' gradient slots are then left to that path.
+template <typename R>
+struct AdjPlan {
+    bool ok = false;
+    std::vector<TileDesc> td;
+    std::vector<std::vector<R>> par;
+    std::vector<const JitFn*> fn;
+    std::vector<int> nsl, gslot;  // gradient slots of each sub-pass, index of its first one in slot_params
+};
+
+template <typename R>
+static int jit_adjoint_plan(sv_state* s, const std::vector<SubPlan>& subs, int L, int t, int l,
+                            std::vector<int>& slot_params, AdjPlan<R>& ap)
+{
+    ap = AdjPlan<R>();
+    if (!s->cfg.jit || t != kPhaseTileQubits || l != 5 || subs.empty()) return SV_OK;
+    struct Sub {
+        std::vector<Phase> ph;
+        std::vector<PhaseOp<R>> ops;
+        std::vector<CtaCtrl> ctl;
+        std::vector<R> d2m;
+        std::vector<int32_t> grad;
+    };
+    std::vector<Sub> sv(subs.size());
+    std::vector<int> sp_local;
+    std::vector<std::string> keys(subs.size());
+    for (size_t i = 0; i < subs.size(); i++) {
+        const TileDesc td = tile_desc(subs[i].T, L, t, l);
+        ap.td.push_back(td);
+        ap.gslot.push_back((int)(slot_params.size() + sp_local.size()));
+        const size_t before = sp_local.size();
+        dev_phases<R>(subs[i], td, sv[i].ph, sv[i].ops, sv[i].ctl, sv[i].d2m, &sv[i].grad, &sp_local);
+        ap.nsl.push_back((int)(sp_local.size() - before));
+        ap.par.emplace_back();
+        jit_params<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].d2m.data(), ap.par.back(), false);
+        jit_key<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].ctl.data(), ap.par.back(), false,
+                   false, keys[i], sv[i].grad.data());
+    }
+    auto source_of = [&](size_t k) {
+        return jit_source<R>(sv[k].ph.data(), (int)sv[k].ph.size(), sv[k].ops.data(), sv[k].ctl.data(),
+                             sv[k].d2m.data(), false, false, ap.par[k], sv[k].grad.data());
+    };
+    std::string err;
+    JitReport rep;
+    if (!jit_compile(keys, source_of, s->cfg.device, ap.fn, err, &rep))
+        return fail(s, SV_ERR_CUDA, "run-time kernel compilation failed: " + err);
+    s->st.jit_kernels_compiled += rep.compiled;
+    s->st.t_jit_compile_s += rep.seconds;
+    for (const JitFn* f : ap.fn)
+        if (!f) return SV_OK;
+    slot_params.insert(slot_params.end(), sp_local.begin(), sp_local.end());
+    ap.ok = true;
+    return SV_OK;
+}
+
 // launch sub-pass i of an uploaded pass on a buffer of 2^L local amplitudes
 template <typename R>
 static cudaError_t launch_subpass(sv_state* s, const DevPass<R>& dp, size_t i, void* amps, uint64_t gbase,
@@ -631,8 +689,50 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
 }
 
 template <typename R>
-int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out)
+int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out, bool adjoint)
 {
+    if (adjoint) {
+        // the reverse sweep of sv_grad: every pass in reverse order, daggered gates
+        std::vector<PGate> inv(gates.size());
+        for (size_t i = 0; i < gates.size(); i++) {
+            inv[i] = gates[i];
+            const int K = 1 << gates[i].nt;
+            for (int a = 0; a < K; a++)
+                for (int b = 0; b < K; b++) inv[i].m[a * K + b] = std::conj(gates[i].m[b * K + a]);
+        }
+        std::vector<PassPlan> passes;
+        if (s->mode == SV_UNCOMPRESSED) {
+            PassPlan pp;
+            for (size_t i = 0; i < gates.size(); i++) pp.gates.push_back((int)i);
+            passes.push_back(pp);
+        } else {
+            passes = plan_passes(gates, s->n, s->c, s->gmax);
+        }
+        for (size_t p = passes.size(); p-- > 0;) {
+            const PassPlan& pp = passes[p];
+            const int c = s->mode == SV_UNCOMPRESSED ? s->n : s->c;
+            const int L = c + (int)pp.S.size();
+            int t, l;
+            tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
+            if (t != kPhaseTileQubits || l != 5) continue;
+            std::vector<int> rids(pp.gates.rbegin(), pp.gates.rend());
+            const std::vector<SubPlan> subs = plan_subpasses(local_ops(inv, rids, c, pp.S, true), L, t, l, true);
+            for (const SubPlan& sp : subs) {
+                const TileDesc td = tile_desc(sp.T, L, t, l);
+                std::vector<Phase> ph;
+                std::vector<PhaseOp<R>> ops;
+                std::vector<CtaCtrl> ctl;
+                std::vector<R> d2m, par;
+                std::vector<int32_t> grad;
+                std::vector<int> slots;
+                dev_phases<R>(sp, td, ph, ops, ctl, d2m, &grad, &slots);
+                jit_params<R>(ph.data(), (int)ph.size(), ops.data(), d2m.data(), par, false);
+                out.push_back(jit_source<R>(ph.data(), (int)ph.size(), ops.data(), ctl.data(), d2m.data(), false,
+                                            false, par, grad.data()));
+            }
+        }
+        return SV_OK;
+    }
     std::vector<DevPass<R>> dps;
     if (s->mode == SV_UNCOMPRESSED) {
         int t, l;
@@ -1002,15 +1102,23 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
     std::vector<DevOp<R>> ops;
     std::vector<int> slot_base;
     int max_slots = 0;
-    for (const SubPlan& sp : subs) {
-        TileDesc td = tile_desc(sp.T, L, t, l);
-        tds.push_back(td);
-        offs.push_back((int)ops.size());
-        slot_base.push_back((int)slot_params.size());
-        int base = 0;
-        dev_ops<R>(sp, td, ops, &base, &slot_params);
-        max_slots = std::max(max_slots, base);
-        cnts.push_back((int)ops.size() - offs.back());
+    AdjPlan<R> ap;
+    if ((r = jit_adjoint_plan<R>(s, subs, L, t, l, slot_params, ap))) return r;
+    if (ap.ok) {
+        tds = ap.td;
+        slot_base = ap.gslot;
+        for (int v : ap.nsl) max_slots = std::max(max_slots, v);
+    } else {
+        for (const SubPlan& sp : subs) {
+            TileDesc td = tile_desc(sp.T, L, t, l);
+            tds.push_back(td);
+            offs.push_back((int)ops.size());
+            slot_base.push_back((int)slot_params.size());
+            int base = 0;
+            dev_ops<R>(sp, td, ops, &base, &slot_params);
+            max_slots = std::max(max_slots, base);
+            cnts.push_back((int)ops.size() - offs.back());
+        }
     }
     const uint64_t ntiles = 1ull << (L - t);
     const size_t nslots_total = slot_params.size();
@@ -1038,18 +1146,26 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
             break;
         }
         s->st.kernel_launches += 3;
-        if ((r = upload_ops<R>(s, ops))) break;
+        if (!ap.ok && (r = upload_ops<R>(s, ops))) break;
         const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
         for (size_t i = 0; i < tds.size(); i++) {
-            if ((e = launch_adjoint<R>(s->d_state, s->d_lam, tds[i], d_ops + offs[i], cnts[i], 0, d_gpart, ntiles,
-                                       s->s_comp))) {
+            unsigned parts = (unsigned)ntiles;  // gradient partials per slot
+            if (ap.ok) {
+                e = jit_launch_adjoint<R>(ap.fn[i], s->d_state, s->d_lam, tds[i], 0, d_gpart, ap.par[i], s->s_comp,
+                                          &parts);
+                s->st.jit_launches++;
+            } else {
+                e = launch_adjoint<R>(s->d_state, s->d_lam, tds[i], d_ops + offs[i], cnts[i], 0, d_gpart, ntiles,
+                                      s->s_comp);
+            }
+            if (e) {
                 r = cuda_fail(s, e, "adjoint");
                 break;
             }
             s->st.kernel_launches++;
             const int nsl = (i + 1 < tds.size() ? slot_base[i + 1] : (int)nslots_total) - slot_base[i];
             if (nsl > 0) {
-                if ((e = launch_sum_partials(d_gpart, nsl, (int)ntiles, d_acc + 1 + slot_base[i], s->s_comp))) {
+                if ((e = launch_sum_partials(d_gpart, nsl, (int)parts, d_acc + 1 + slot_base[i], s->s_comp))) {
                     r = cuda_fail(s, e, "grad reduce");
                     break;
                 }
@@ -1179,24 +1295,32 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
     const std::vector<HOp> hops = local_ops(inv, rids, c, pp.S, true);
     const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
     if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+    AdjPlan<R> ap;
+    int r = jit_adjoint_plan<R>(s, subs, L, t, l, slot_params, ap);
+    if (r) return r;
     std::vector<TileDesc> tds;
     std::vector<int> offs, cnts, gslot, nsl;
     std::vector<DevOp<R>> ops;
-    for (const SubPlan& sp : subs) {
-        TileDesc td = tile_desc(sp.T, L, t, l);
-        tds.push_back(td);
-        offs.push_back((int)ops.size());
-        gslot.push_back((int)slot_params.size());
-        int base = 0;
-        dev_ops<R>(sp, td, ops, &base, &slot_params);
-        nsl.push_back(base);
-        cnts.push_back((int)ops.size() - offs.back());
+    if (ap.ok) {
+        tds = ap.td;
+        gslot = ap.gslot;
+        nsl = ap.nsl;
+    } else {
+        for (const SubPlan& sp : subs) {
+            TileDesc td = tile_desc(sp.T, L, t, l);
+            tds.push_back(td);
+            offs.push_back((int)ops.size());
+            gslot.push_back((int)slot_params.size());
+            int base = 0;
+            dev_ops<R>(sp, td, ops, &base, &slot_params);
+            nsl.push_back(base);
+            cnts.push_back((int)ops.size() - offs.back());
+        }
     }
     const uint64_t ntiles = 1ull << (L - t);
     for (int v : nsl)
         if ((uint64_t)v * ntiles > gpart_cap) return fail(s, SV_ERR_ARG, "gradient partial buffer too small");
-    int r = upload_ops<R>(s, ops);
-    if (r) return r;
+    if (!ap.ok && (r = upload_ops<R>(s, ops))) return r;
     const DevOp<R>* d_ops = static_cast<const DevOp<R>*>(s->d_ops);
 
     std::vector<int> spos, fpos;
@@ -1240,34 +1364,49 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
             return cuda_fail(s, e, "record h2d");
         if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0)))
             return cuda_fail(s, e, "wait d2h");
+        const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
+        int pi = prof_begin(s);
         if ((e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gp, s->d_amps, 1.0, s->d_err, s->s_comp)) ||
             (e = launch_decode<R>(s->d_in2[slot], s->stride, c, s->dtype, gch, gl, s->d_amps2, 1.0, s->d_err,
                                   s->s_comp)))
             return cuda_fail(s, e, "decode");
+        prof_end(s, pi, PROF_DECODE, 2 * amp_bytes);
         s->st.kernel_launches += 2;
         const uint64_t gbase = base << c;
         for (size_t i = 0; i < tds.size(); i++) {
-            if ((e = launch_adjoint<R>(s->d_amps, s->d_amps2, tds[i], d_ops + offs[i], cnts[i], gbase, d_gpart, ntiles,
-                                       s->s_comp)))
-                return cuda_fail(s, e, "adjoint");
+            pi = prof_begin(s);
+            unsigned parts = (unsigned)ntiles;  // gradient partials per slot
+            if (ap.ok) {
+                e = jit_launch_adjoint<R>(ap.fn[i], s->d_amps, s->d_amps2, tds[i], gbase, d_gpart, ap.par[i], s->s_comp,
+                                          &parts);
+                s->st.jit_launches++;
+            } else {
+                e = launch_adjoint<R>(s->d_amps, s->d_amps2, tds[i], d_ops + offs[i], cnts[i], gbase, d_gpart, ntiles,
+                                      s->s_comp);
+            }
+            if (e) return cuda_fail(s, e, "adjoint");
+            prof_end(s, pi, PROF_APPLY, 4 * amp_bytes);
             s->st.kernel_launches++;
             if (nsl[i] > 0) {
-                if ((e = launch_sum_partials(d_gpart, nsl[i], (int)ntiles, d_acc + 1 + gslot[i], s->s_comp)))
+                if ((e = launch_sum_partials(d_gpart, nsl[i], (int)parts, d_acc + 1 + gslot[i], s->s_comp)))
                     return cuda_fail(s, e, "grad reduce");
                 s->st.kernel_launches++;
             }
         }
         int launches = 0;
+        pi = prof_begin(s);
         if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
                                   s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)) ||
             (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, gch, s->d_out2[slot], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches)) ||
-            (e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
+                                  s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches)))
+            return cuda_fail(s, e, "encode");
+        prof_end(s, pi, PROF_ENCODE, 2 * amp_bytes);
+        if ((e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
                                  s->s_comp)) ||
             (e = cudaMemcpyAsync(s->h_co2[slot], s->d_co2[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
                                  s->s_comp)) ||
             (e = cudaEventRecord(s->ev_comp[slot], s->s_comp)))
-            return cuda_fail(s, e, "encode");
+            return cuda_fail(s, e, "encode sizes");
         s->st.kernel_launches += launches;
         s->slot_used[slot] = true;
         s->st.groups++;
@@ -1306,6 +1445,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
         if (gi >= 1 && (r = finish(gi - 1))) return r;
     }
     if ((r = sync_all(s))) return r;
+    prof_collect(s);
     if ((r = check_device_error(s))) return r;
     s->cur.swap(s->nxt);
     s->lcur.swap(s->lnxt);
@@ -1394,8 +1534,8 @@ template int grad_compressed<double>(sv_state*, const std::vector<PGate>&, size_
                                      double*, double*);
 template int apply_circuit<float>(sv_state*, const std::vector<PGate>&);
 template int apply_circuit<double>(sv_state*, const std::vector<PGate>&);
-template int jit_sources<float>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&);
-template int jit_sources<double>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&);
+template int jit_sources<float>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&, bool);
+template int jit_sources<double>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&, bool);
 template int init_state<float>(sv_state*);
 template int init_state<double>(sv_state*);
 template int amplitudes<float>(sv_state*, const uint64_t*, size_t, double*);

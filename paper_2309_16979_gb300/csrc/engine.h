@@ -19,7 +19,8 @@ void tile_shape(int L, int tq, int lq, int& t, int& l);
 template <typename R> int init_state(sv_state* s);
 template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& gates);
 // host only: the sources of the kernels apply_circuit would generate
-template <typename R> int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out);
+template <typename R>
+int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out, bool adjoint);
 template <typename R> int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out);
 template <typename R> int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
 template <typename R>

@@ -160,9 +160,10 @@ struct Gen {
         int b;
     };
     std::vector<Pend> pend;
+    int nvec = 1;  // 2 in an adjoint sub-pass: psi in r/q, lambda in u/w, same ops on both
     explicit Gen(const std::vector<R>& p) : par(p) {}
-    std::string rv(int m) const { return "r" + std::to_string(slot[m]); }
-    std::string iv(int m) const { return "q" + std::to_string(slot[m]); }
+    std::string rv(int m, int v = 0) const { return (v ? "u" : "r") + std::to_string(slot[m]); }
+    std::string iv(int m, int v = 0) const { return (v ? "w" : "q") + std::to_string(slot[m]); }
 };
 
 // Coefficient chosen at run time by `sel` (0..n-1) among candidates whose
@@ -268,12 +269,14 @@ template <typename R>
 void emit_exchange(Gen<R>& g, const std::string& cond, int b)
 {
     g.o << "if (" << cond << ") {\n";
-    for (int i = 0; i < 16; i++) {
-        if (i & (1 << b)) continue;
-        const int j = i | (1 << b);
-        g.o << "{ const R tr = " << g.rv(i) << ", ti = " << g.iv(i) << "; " << g.rv(i) << " = " << g.rv(j) << "; "
-            << g.iv(i) << " = " << g.iv(j) << "; " << g.rv(j) << " = tr; " << g.iv(j) << " = ti; }\n";
-    }
+    for (int v = 0; v < g.nvec; v++)
+        for (int i = 0; i < 16; i++) {
+            if (i & (1 << b)) continue;
+            const int j = i | (1 << b);
+            g.o << "{ const R tr = " << g.rv(i, v) << ", ti = " << g.iv(i, v) << "; " << g.rv(i, v) << " = "
+                << g.rv(j, v) << "; " << g.iv(i, v) << " = " << g.iv(j, v) << "; " << g.rv(j, v) << " = tr; "
+                << g.iv(j, v) << " = ti; }\n";
+        }
     g.o << "}\n";
 }
 
@@ -318,8 +321,9 @@ void mul_reg(Gen<R>& g, int m, const Coef& e)
     if (e.cls == C_ONE) return;
     Sum re, im;
     cmac(re, im, e, "xr", "xi");
-    g.o << "{ const R xr = " << g.rv(m) << ", xi = " << g.iv(m) << "; " << g.rv(m) << " = " << re.str() << "; "
-        << g.iv(m) << " = " << im.str() << "; }\n";
+    for (int v = 0; v < g.nvec; v++)
+        g.o << "{ const R xr = " << g.rv(m, v) << ", xi = " << g.iv(m, v) << "; " << g.rv(m, v) << " = " << re.str()
+            << "; " << g.iv(m, v) << " = " << im.str() << "; }\n";
 }
 
 template <typename R>
@@ -371,9 +375,11 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
         cmac(xr, xi, e[1], "yr", "yi");
         cmac(yr, yi, e[2], "xr", "xi");
         cmac(yr, yi, e[3], "yr", "yi");
-        g.o << "{ const R xr = " << g.rv(i) << ", xi = " << g.iv(i) << ", yr = " << g.rv(j) << ", yi = " << g.iv(j)
-            << "; " << g.rv(i) << " = " << xr.str() << "; " << g.iv(i) << " = " << xi.str() << "; " << g.rv(j)
-            << " = " << yr.str() << "; " << g.iv(j) << " = " << yi.str() << "; }\n";
+        for (int v = 0; v < g.nvec; v++)
+            g.o << "{ const R xr = " << g.rv(i, v) << ", xi = " << g.iv(i, v) << ", yr = " << g.rv(j, v)
+                << ", yi = " << g.iv(j, v) << "; " << g.rv(i, v) << " = " << xr.str() << "; " << g.iv(i, v) << " = "
+                << xi.str() << "; " << g.rv(j, v) << " = " << yr.str() << "; " << g.iv(j, v) << " = " << yi.str()
+                << "; }\n";
     }
     if (!cond.empty()) g.o << "}\n";
 }
@@ -467,23 +473,66 @@ void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& 
         if (!((op.amask >> i) & 1u)) continue;
         int idx[4];
         for (int k = 0; k < 4; k++) idx[k] = i | ((k & 1) << b0) | (((k >> 1) & 1) << b1);
-        g.o << "{ ";
-        for (int k = 0; k < 4; k++)
-            g.o << "const R v" << k << "r = " << g.rv(idx[k]) << ", v" << k << "i = " << g.iv(idx[k]) << "; ";
-        for (int r = 0; r < 4; r++) {
-            Sum re, im;
+        for (int vv = 0; vv < g.nvec; vv++) {
+            g.o << "{ ";
             for (int k = 0; k < 4; k++)
-                cmac(re, im, e[4 * r + k], "v" + std::to_string(k) + "r", "v" + std::to_string(k) + "i");
-            g.o << g.rv(idx[r]) << " = " << re.str() << "; " << g.iv(idx[r]) << " = " << im.str() << "; ";
+                g.o << "const R v" << k << "r = " << g.rv(idx[k], vv) << ", v" << k << "i = " << g.iv(idx[k], vv)
+                    << "; ";
+            for (int r = 0; r < 4; r++) {
+                Sum re, im;
+                for (int k = 0; k < 4; k++)
+                    cmac(re, im, e[4 * r + k], "v" + std::to_string(k) + "r", "v" + std::to_string(k) + "i");
+                g.o << g.rv(idx[r], vv) << " = " << re.str() << "; " << g.iv(idx[r], vv) << " = " << im.str() << "; ";
+            }
+            g.o << "}\n";
         }
-        g.o << "}\n";
     }
     if (!cond.empty()) g.o << "}\n";
 }
 
+// Adjoint: this thread's part of Im<lambda| G |psi> for the generator G (1 X,
+// 2 Y, 3 Z) on register bit b, taken before the op is applied: summed over
+// the thread's pairs in R, over the warp by shuffles, then added in FP64 to
+// the CTA's slot. A pending exchange on b (registers hold X psi, X lambda on
+// the threads where it holds) flips the sign for Y and Z (X Y X = -Y, X Z X = -Z).
+template <typename R>
+void emit_grad(Gen<R>& g, int b, int gen, int slot, const std::vector<typename Gen<R>::Pend>& conj)
+{
+    g.o << "{ R gp = (R)0;\n";
+    for (int i = 0; i < 16; i++) {
+        if (i & (1 << b)) continue;
+        const int j = i | (1 << b);
+        const std::string p0r = g.rv(i, 0), p0i = g.iv(i, 0), p1r = g.rv(j, 0), p1i = g.iv(j, 0);
+        const std::string l0r = g.rv(i, 1), l0i = g.iv(i, 1), l1r = g.rv(j, 1), l1i = g.iv(j, 1);
+        if (gen == 1)  // conj(l0) p1 + conj(l1) p0
+            g.o << "gp += " << l0r << " * " << p1i << " - " << l0i << " * " << p1r << " + " << l1r << " * " << p0i
+                << " - " << l1i << " * " << p0r << ";\n";
+        else if (gen == 2)  // conj(l0)(-i p1) + conj(l1)(i p0): Im = -Re(conj(l0) p1) + Re(conj(l1) p0)
+            g.o << "gp += " << l1r << " * " << p0r << " + " << l1i << " * " << p0i << " - " << l0r << " * " << p1r
+                << " - " << l0i << " * " << p1i << ";\n";
+        else  // conj(l0) p0 - conj(l1) p1
+            g.o << "gp += " << l0r << " * " << p0i << " - " << l0i << " * " << p0r << " - " << l1r << " * " << p1i
+                << " + " << l1i << " * " << p1r << ";\n";
+    }
+    for (const auto& pd : conj)
+        if (pd.b == b && gen != 1) g.o << "if (" << pd.cond << ") gp = -gp;\n";
+    g.o << "gp += __shfl_xor_sync(0xffffffffu, gp, 16); gp += __shfl_xor_sync(0xffffffffu, gp, 8); "
+           "gp += __shfl_xor_sync(0xffffffffu, gp, 4); gp += __shfl_xor_sync(0xffffffffu, gp, 2); "
+           "gp += __shfl_xor_sync(0xffffffffu, gp, 1);\n"
+        << "if ((threadIdx.x & 31u) == 0u) atomicAdd(&gacc[" << slot << "], (double)gp); }\n";
+}
+
 template <typename R> struct RName;
-template <> struct RName<float> { static constexpr const char* r = "float"; static constexpr const char* t = "float2"; static constexpr int minb = 3; };
-template <> struct RName<double> { static constexpr const char* r = "double"; static constexpr const char* t = "double2"; static constexpr int minb = 2; };
+template <> struct RName<float> {
+    static constexpr const char* r = "float";
+    static constexpr const char* t = "float2";
+    static constexpr int minb = 3, minb_adj = 2;
+};
+template <> struct RName<double> {
+    static constexpr const char* r = "double";
+    static constexpr const char* t = "double2";
+    static constexpr int minb = 2, minb_adj = 1;
+};
 
 // ------------------------------------------------------------ NVRTC / driver
 struct Nvrtc {
@@ -633,7 +682,7 @@ bool uncontrolled(const PhaseOp<R>& op)
 }
 
 template <typename R>
-void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params)
+void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, std::vector<R>& params, bool factor)
 {
     using C = std::complex<double>;
     params.clear();
@@ -661,7 +710,7 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
             const int n = op.code == kCodeDense2 ? 16 : 4;
             if (op.code == kCodeDense2) params.insert(params.end(), d2m + 32ull * op.aux, d2m + 32ull * op.aux + 32);
             else params.insert(params.end(), op.m, op.m + 8);
-            if (!uncontrolled(op)) continue;
+            if (!factor || !uncontrolled(op)) continue;
             C big(0, 0);
             for (int k = 0; k < n; k++) {
                 const C e((double)params[at + 2 * k], (double)params[at + 2 * k + 1]);
@@ -696,12 +745,12 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
 
 template <typename R>
 void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
-             bool dec, bool enc, std::string& key)
+             bool dec, bool enc, std::string& key, const int32_t* grad)
 {
     size_t pb = 0;
     key.clear();
     auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
-    const uint8_t hdr[4] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, 1};
+    const uint8_t hdr[4] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, (uint8_t)(grad ? 2 : 1)};
     put(hdr, 4);
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
@@ -718,6 +767,7 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
             put(&op.csrc1, 1);
             put(&op.rsel, 1);
             put(&op.pad, 2);
+            if (grad) put(&grad[oi], sizeof(int32_t));
             if (op.flags & 1u) put(&ctl[op.aux], sizeof(CtaCtrl));
             // the value-dependent choices of the generator: each entry's class
             // and, for 2x2 / diagonal ops, which entries are equal
@@ -740,10 +790,13 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
 
 template <typename R>
 std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, const std::vector<R>& params)
+                       bool enc, const std::vector<R>& params, const int32_t* grad)
 {
     (void)d2m;
     Gen<R> g(params);
+    const bool adj = grad != nullptr;
+    g.nvec = adj ? 2 : 1;
+    int nslot = 0;
     std::ostringstream body;
     size_t pb = 0;  // parameter slot of the current op (8 values, 32 for a 4x4)
     for (int pi = 0; pi < nph; pi++) {
@@ -765,16 +818,26 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             K[m] = pad_slot(o);
         }
         g.o.str("");
-        g.o << "{\nconst uint32_t tb = " << tb << ";\nconst uint32_t sb = tb + (tb >> 4) + (tb >> 8) + bo;\nR ";
-        for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << "r" << m << ", q" << m;
-        g.o << ";\n";
-        for (int m = 0; m < 16; m++)
-            g.o << "{ const T v = s[sb + " << K[m] << "u]; r" << m << " = v.x; q" << m << " = v.y; }\n";
+        g.o << "{\nconst uint32_t tb = " << tb << ";\nconst uint32_t sb = tb + (tb >> 4) + (tb >> 8) + bo;\n";
+        for (int v = 0; v < g.nvec; v++) {
+            g.o << "R ";
+            for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << g.rv(m, v) << ", " << g.iv(m, v);
+            g.o << ";\n";
+            for (int m = 0; m < 16; m++)
+                g.o << "{ const T v = " << (v ? "sl" : "s") << "[sb + " << K[m] << "u]; " << g.rv(m, v)
+                    << " = v.x; " << g.iv(m, v) << " = v.y; }\n";
+        }
         for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
             const PhaseOp<R>& op = ops[oi];
             const std::string cond = op_cond(g, op, ctl);
             const uint32_t code = op.code;
             const auto conj = settle(g, op);
+            if (adj && grad[oi] >= 0) {
+                // a parameterised RX / RY (2x2) or RZ (one-register diagonal) on register bit code & 3
+                if (code >= kCodeDiag2) g.ok = false;
+                emit_grad(g, (int)(code & 3), grad[oi] & 3, grad[oi] >> 2, conj);
+                nslot = std::max(nslot, (grad[oi] >> 2) + 1);
+            }
             if (code < kCodeDiag2) {
                 const uint32_t kind = code / 8, b0 = code & 3;
                 if (kind == PK_DIAG1) emit_diag1(g, op, pb, (int)b0, cond, conj);
@@ -803,17 +866,48 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             for (size_t j = 0; j < np; j++) g.o << (((c >> j) & 1) ? " - d" : " + d") << j;
             g.o << ";\n";
         }
-        for (int m = 0; m < 16; m++) {
-            uint32_t c = 0;
-            for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
-            g.o << "s[" << (np ? "sb" + std::to_string(c) : std::string("sb")) << " + " << K[m] << "u] = tile::mk2<T, R>("
-                << g.rv(m) << ", " << g.iv(m) << ");\n";
-        }
+        for (int v = 0; v < g.nvec; v++)
+            for (int m = 0; m < 16; m++) {
+                uint32_t c = 0;
+                for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
+                g.o << (v ? "sl[" : "s[") << (np ? "sb" + std::to_string(c) : std::string("sb")) << " + " << K[m]
+                    << "u] = tile::mk2<T, R>(" << g.rv(m, v) << ", " << g.iv(m, v) << ");\n";
+            }
         g.pend.clear();
         g.o << "__syncthreads();\n}\n";
         body << g.o.str();
     }
     if (!g.ok || params.size() * sizeof(R) > kMaxParamBytes) return std::string();
+    if (adj) {
+        // psi and lambda tiles side by side in shared memory, plain loads and
+        // stores; gradient partials in FP64 per CTA, written at the end
+        std::ostringstream src;
+        src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
+            << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
+            << "struct P { R m[" << std::max<size_t>(1, params.size()) << "]; };\n"
+            << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << RName<R>::minb_adj << ")\n"
+            << "svj(T* __restrict__ amps, T* __restrict__ lam, const TileDesc td, const uint64_t gbase, "
+               "const uint64_t ntiles, double* __restrict__ gpart, const P p)\n{\n"
+            << "extern __shared__ __align__(16) unsigned char smem[];\n"
+            << "T* s = reinterpret_cast<T*>(smem);\nT* sl = s + tile::kPadElems;\n"
+            << "__shared__ tile::Rows rt;\n__shared__ double gacc[" << std::max(1, nslot) << "];\n"
+            << "tile::setup_rows(rt, td);\n"
+            << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gacc[k] = 0.0;\n"
+            << "const uint32_t bo = 0;\n"
+            << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
+            << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
+            << "tile::load_plain<T, R, tile::PadLayout>(s, amps, rt, td, base);\n"
+            << "tile::load_plain<T, R, tile::PadLayout>(sl, lam, rt, td, base);\n"
+            << "__syncthreads();\n"
+            << body.str()
+            << "tile::store_plain<T, R, tile::PadLayout>(s, amps, rt, td, base);\n"
+            << "tile::store_plain<T, R, tile::PadLayout>(sl, lam, rt, td, base);\n"
+            << "}\n__syncthreads();\n"
+            << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gpart[(uint64_t)k * gridDim.x + "
+               "blockIdx.x] = gacc[k];\n"
+            << "}\n";
+        return src.str();
+    }
     const bool pf = prefetches(dec, sizeof(R));
     std::ostringstream src;
     src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
@@ -915,7 +1009,7 @@ bool jit_compile(const std::vector<std::string>& keys, const std::function<std::
         }
     }
     const size_t tile_bytes = sizeof(double) * 2 * tile_pad_elems();
-    const int smem_max = (int)(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32));
+    const int smem_max = (int)std::max(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32), 2 * tile_bytes);
     for (Job& j : jobs) {
         auto fn = std::make_unique<JitFn>();
         if (!j.src->empty()) {
@@ -943,13 +1037,34 @@ bool jit_compile(const std::vector<std::string>& keys, const std::function<std::
     return true;
 }
 
+unsigned jit_grid(uint64_t ntiles) { return (unsigned)std::min<uint64_t>(ntiles, 152ull * 32); }
+
+template <typename R>
+cudaError_t jit_launch_adjoint(const JitFn* fn, void* psi, void* lam, const TileDesc& td, uint64_t gbase,
+                               double* gpart, const std::vector<R>& params, cudaStream_t st, unsigned* grid_out)
+{
+    if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
+    const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
+    const unsigned grid = jit_grid(ntiles);
+    if (grid_out) *grid_out = grid;
+    const size_t smem = sizeof(R) * 2 * tile_pad_elems() * 2;
+    void* a = psi;
+    void* b = lam;
+    TileDesc t = td;
+    uint64_t gb = gbase, nt = ntiles;
+    double* gp = gpart;
+    void* args[] = {&a, &b, &t, &gb, &nt, &gp, const_cast<R*>(params.data())};
+    const CUresult r = drv().launch(fn->fn, grid, 1, 1, kJitThreads, 1, 1, (unsigned)smem, (CUstream)st, args, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
 template <typename R>
 cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t gbase, const FuseArgs& fa,
                        const std::vector<R>& params, cudaStream_t st)
 {
     if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
-    const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, 152ull * 32);
+    const unsigned grid = jit_grid(ntiles);
     const size_t smem = (sizeof(R) * 2 * tile_pad_elems() * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +
                         ((fa.decode || fa.encode) ? sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32) : 0);
     void* a = amps;
@@ -961,18 +1076,23 @@ cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
-template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const float*, std::vector<float>&);
-template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&);
+template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const float*, std::vector<float>&, bool);
+template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&,
+                                 bool);
 template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const std::vector<float>&,
-                             bool, bool, std::string&);
+                             bool, bool, std::string&, const int32_t*);
 template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const std::vector<double>&,
-                              bool, bool, std::string&);
+                              bool, bool, std::string&, const int32_t*);
 template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
-                                       bool, const std::vector<float>&);
+                                       bool, const std::vector<float>&, const int32_t*);
 template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,
-                                        bool, bool, const std::vector<double>&);
+                                        bool, bool, const std::vector<double>&, const int32_t*);
 template cudaError_t jit_launch<float>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
                                        const std::vector<float>&, cudaStream_t);
+template cudaError_t jit_launch_adjoint<float>(const JitFn*, void*, void*, const TileDesc&, uint64_t, double*,
+                                               const std::vector<float>&, cudaStream_t, unsigned*);
+template cudaError_t jit_launch_adjoint<double>(const JitFn*, void*, void*, const TileDesc&, uint64_t, double*,
+                                                const std::vector<double>&, cudaStream_t, unsigned*);
 template cudaError_t jit_launch<double>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
                                         const std::vector<double>&, cudaStream_t);
 

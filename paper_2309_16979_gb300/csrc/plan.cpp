@@ -73,16 +73,52 @@ static uint64_t mixing_mask(const PGate& g)
     return m;
 }
 
+// Gates one pass staging the high qubits S would apply, scanning the remaining
+// gates in order; a gate that cannot run blocks its qubits for later ones.
+static int count_pass(const std::vector<PGate>& g, const std::vector<int>& remaining, uint64_t S, uint64_t high,
+                      uint64_t all)
+{
+    uint64_t blocked = 0;
+    int k = 0;
+    for (int gi : remaining) {
+        const uint64_t qm = qubit_mask(g[gi]);
+        if ((qm & blocked) || (mixing_mask(g[gi]) & high & ~S)) {
+            blocked |= qm;
+            if ((blocked & all) == all) break;
+            continue;
+        }
+        k++;
+    }
+    return k;
+}
+
 std::vector<PassPlan> plan_passes(const std::vector<PGate>& g, int n, int c, int gmax)
 {
     std::vector<PassPlan> passes;
-    const uint64_t high = (n > c) ? (((n >= 64) ? ~0ull : ((1ull << n) - 1)) & ~((1ull << c) - 1)) : 0;
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t high = (n > c) ? (all & ~((1ull << c) - 1)) : 0;
     const int nh = n - c;
     const int gsz = std::min(gmax, nh);
     std::vector<int> remaining(g.size());
     for (size_t i = 0; i < g.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
         uint64_t S = 0, blocked = 0;
+        // Stage one high qubit at a time, the one that lets the pass apply the
+        // most gates; when none adds any, the scan below stages first-come.
+        for (int cur = count_pass(g, remaining, S, high, all); popc(S) < gsz;) {
+            int best = -1, bestn = cur;
+            for (int q = c; q < n; q++) {
+                if ((S >> q) & 1) continue;
+                const int k = count_pass(g, remaining, S | (1ull << q), high, all);
+                if (k > bestn) {
+                    bestn = k;
+                    best = q;
+                }
+            }
+            if (best < 0) break;
+            S |= 1ull << best;
+            cur = bestn;
+        }
         PassPlan pp;
         std::vector<int> deferred;
         for (int gi : remaining) {
@@ -217,16 +253,74 @@ static bool try_fuse(HOp& a, const HOp& b)
     return true;
 }
 
+// Ops one sweep with tile set T would apply (no growth of T), scanning the
+// remaining ops in order; an op that cannot run blocks its qubits for later
+// ones. The scan stops once every local qubit is blocked.
+static int count_fit(const std::vector<HOp>& ops, const std::vector<int>& remaining, uint64_t T, uint64_t allL)
+{
+    uint64_t bL = 0, bG = 0;
+    int n = 0;
+    for (int oi : remaining) {
+        const HOp& o = ops[oi];
+        if ((o.qL & bL) || (o.qG & bG) || (o.mixL & ~T)) {
+            bL |= o.qL;
+            bG |= o.qG;
+            if ((bL & allL) == allL) break;
+            continue;
+        }
+        n++;
+    }
+    return n;
+}
+
 std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
 {
     std::vector<SubPlan> subs;
     const uint64_t low = (l >= 64) ? ~0ull : ((1ull << l) - 1);
     const int fl = first_l > 0 ? std::min(first_l, t) : l;
     const uint64_t first_low = (fl >= 64) ? ~0ull : ((1ull << fl) - 1);
+    const uint64_t allL = (L >= 64) ? ~0ull : ((1ull << L) - 1);
     std::vector<int> remaining(ops.size());
     for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
         uint64_t T = subs.empty() ? first_low : low, bL = 0, bG = 0;
+        // Grow the tile one qubit at a time by the qubit that lets the sweep
+        // apply the most ops; when no single qubit adds any (ops that need two
+        // new qubits), the scan below grows it first-come in circuit order.
+        for (int cur = count_fit(ops, remaining, T, allL); popc(T) < t;) {
+            int best = -1, bestn = cur;
+            for (int p = 0; p < L; p++) {
+                if ((T >> p) & 1) continue;
+                const int k = count_fit(ops, remaining, T | (1ull << p), allL);
+                if (k > bestn) {
+                    bestn = k;
+                    best = p;
+                }
+            }
+            if (best >= 0) {
+                T |= 1ull << best;
+                cur = bestn;
+                continue;
+            }
+            // no single qubit helps: the pair that helps most (two-qubit ops
+            // with both qubits outside the tile)
+            int b0 = -1, b1 = -1;
+            for (int p = 0; p < L && popc(T) + 2 <= t; p++) {
+                if ((T >> p) & 1) continue;
+                for (int q = p + 1; q < L; q++) {
+                    if ((T >> q) & 1) continue;
+                    const int k = count_fit(ops, remaining, T | (1ull << p) | (1ull << q), allL);
+                    if (k > bestn) {
+                        bestn = k;
+                        b0 = p;
+                        b1 = q;
+                    }
+                }
+            }
+            if (b0 < 0) break;
+            T |= (1ull << b0) | (1ull << b1);
+            cur = bestn;
+        }
         SubPlan sp;
         std::vector<int> deferred;
         for (int oi : remaining) {
@@ -340,8 +434,10 @@ static int classify_2x2(const cd* m)
 
 template <typename R>
 void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out,
-                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m)
+                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m, std::vector<int32_t>* grad,
+                std::vector<int>* slot_params)
 {
+    int nslot = 0;
     int tbit[64];  // local position -> tile bit (-1 outside the tile)
     for (int p = 0; p < 64; p++) tbit[p] = -1;
     for (int p = 0; p < td.l; p++) tbit[p] = p;
@@ -463,6 +559,14 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
                 d.pad = (uint16_t)(b1 * 4 + b0);
             }
             out.push_back(d);
+            if (grad) {
+                if (o.param >= 0) {
+                    grad->push_back((nslot++ << 2) | o.gen);
+                    if (slot_params) slot_params->push_back(o.param);
+                } else {
+                    grad->push_back(-1);
+                }
+            }
         }
         // swizzled shared-memory offset of each register index (the swizzle is
         // linear over XOR, so the device adds the thread's part with one XOR)
@@ -479,9 +583,10 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
 }
 
 template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&,
-                                std::vector<CtaCtrl>&, std::vector<float>&);
+                                std::vector<CtaCtrl>&, std::vector<float>&, std::vector<int32_t>*, std::vector<int>*);
 template void dev_phases<double>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<double>>&,
-                                 std::vector<CtaCtrl>&, std::vector<double>&);
+                                 std::vector<CtaCtrl>&, std::vector<double>&, std::vector<int32_t>*,
+                                 std::vector<int>*);
 
 template void dev_ops<float>(const SubPlan&, const TileDesc&, std::vector<DevOp<float>>&, int*, std::vector<int>*);
 template void dev_ops<double>(const SubPlan&, const TileDesc&, std::vector<DevOp<double>>&, int*,

@@ -77,10 +77,14 @@ template <typename R>
 void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, int* grad_slot_base,
              std::vector<int>* slot_params);
 
-// Register phases of one sub-pass on a 2^12 tile (apply_phase.cu).
+// Register phases of one sub-pass on a 2^12 tile (apply_phase.cu, jit.cpp).
+// With `grad` (adjoint sub-passes): one entry per op appended to `out`, -1 or
+// (gradient slot << 2) | generator (1 X, 2 Y, 3 Z), slots numbered from 0 in
+// the order the ops are placed; slot_params receives each slot's parameter.
 template <typename R>
 void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out,
-                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m);
+                std::vector<CtaCtrl>& ctl, std::vector<R>& d2m, std::vector<int32_t>* grad = nullptr,
+                std::vector<int>* slot_params = nullptr);
 
 // ------------------------------------------------------------- the store
 struct Segment {

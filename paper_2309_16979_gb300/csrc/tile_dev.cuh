@@ -127,6 +127,54 @@ __device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs&
                           reinterpret_cast<uint32_t(*)[260]>(cw), fa.err, lane);
 }
 
+// Plain copies of one tile between HBM and shared memory (no codec).
+template <typename T, typename R, typename Lay>
+__device__ __forceinline__ void load_plain(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
+                                           uint64_t base)
+{
+    const int l = td.l;
+    const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
+    const T* g0 = amps + base + (t2 & rmask);
+    const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
+#pragma unroll
+    for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
+        const T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
+        const uint32_t ak = Lay::at(512u * k);
+        T x0, x1;
+        if (sizeof(R) == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(g);
+            x0.x = v.x; x0.y = v.y; x1.x = v.z; x1.y = v.w;
+        } else {
+            x0 = g[0];
+            x1 = g[1];
+        }
+        s[Lay::join(a0, ak)] = x0;
+        s[Lay::join(a1, ak)] = x1;
+    }
+}
+
+template <typename T, typename R, typename Lay>
+__device__ __forceinline__ void store_plain(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
+                                            uint64_t base)
+{
+    const int l = td.l;
+    const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
+    T* g0 = amps + base + (t2 & rmask);
+    const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
+#pragma unroll
+    for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
+        T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
+        const uint32_t ak = Lay::at(512u * k);
+        const T x0 = s[Lay::join(a0, ak)], x1 = s[Lay::join(a1, ak)];
+        if (sizeof(R) == 4) {
+            *reinterpret_cast<float4*>(g) = make_float4((float)x0.x, (float)x0.y, (float)x1.x, (float)x1.y);
+        } else {
+            g[0] = x0;
+            g[1] = x1;
+        }
+    }
+}
+
 // HBM (or the compressed streams) -> shared memory for the tile at `base`.
 // DEC: decode the group's chunk streams, one warp per 256-amplitude block
 // pair (rows are block pairs, td.l = 8); otherwise 16-byte vector loads along
@@ -142,26 +190,7 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
             decode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        // amplitudes 2t + 512k and 2t + 512k + 1 (t = thread): the row and the
-        // slot split into a per-thread part and a compile-time part (l <= 8)
-        const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
-        const T* g0 = amps + base + (t2 & rmask);
-        const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
-#pragma unroll
-        for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
-            const T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
-            const uint32_t ak = Lay::at(512u * k);
-            T x0, x1;
-            if (sizeof(R) == 4) {
-                const float4 v = *reinterpret_cast<const float4*>(g);
-                x0.x = v.x; x0.y = v.y; x1.x = v.z; x1.y = v.w;
-            } else {
-                x0 = g[0];
-                x1 = g[1];
-            }
-            s[Lay::join(a0, ak)] = x0;
-            s[Lay::join(a1, ak)] = x1;
-        }
+        load_plain<T, R, Lay>(s, amps, rt, td, base);
     }
 }
 
@@ -204,21 +233,7 @@ __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, con
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
             encode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
-        T* g0 = amps + base + (t2 & rmask);
-        const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
-#pragma unroll
-        for (uint32_t k = 0; k < kN / (2 * kThreads); k++) {
-            T* g = g0 + rt.rowoff[(t2 >> l) + ((512u * k) >> l)];
-            const uint32_t ak = Lay::at(512u * k);
-            const T x0 = s[Lay::join(a0, ak)], x1 = s[Lay::join(a1, ak)];
-            if (sizeof(R) == 4) {
-                *reinterpret_cast<float4*>(g) = make_float4((float)x0.x, (float)x0.y, (float)x1.x, (float)x1.y);
-            } else {
-                g[0] = x0;
-                g[1] = x1;
-            }
-        }
+        store_plain<T, R, Lay>(s, amps, rt, td, base);
     }
 }
 
