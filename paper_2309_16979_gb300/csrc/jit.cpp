@@ -797,7 +797,7 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     const bool adj = grad != nullptr;
     g.nvec = adj ? 2 : 1;
     int nslot = 0;
-    std::ostringstream body;
+    std::ostringstream body, hoist;
     size_t pb = 0;  // parameter slot of the current op (8 values, 32 for a 4x4)
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
@@ -818,7 +818,11 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             K[m] = pad_slot(o);
         }
         g.o.str("");
-        g.o << "{\nconst uint32_t tb = " << tb << ";\nconst uint32_t sb = tb + (tb >> 4) + (tb >> 8) + bo;\n";
+        // the thread's slot base of this phase does not depend on the tile:
+        // computed once per kernel (hoisted), offset by the buffer per tile
+        hoist << "const uint32_t tb" << pi << " = " << tb << ";\nconst uint32_t sbb" << pi << " = tb" << pi
+              << " + (tb" << pi << " >> 4) + (tb" << pi << " >> 8);\n";
+        g.o << "{\nconst uint32_t sb = sbb" << pi << " + bo;\n";
         for (int v = 0; v < g.nvec; v++) {
             g.o << "R ";
             for (int m = 0; m < 16; m++) g.o << (m ? ", " : "") << g.rv(m, v) << ", " << g.iv(m, v);
@@ -891,17 +895,17 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << "extern __shared__ __align__(16) unsigned char smem[];\n"
             << "T* s = reinterpret_cast<T*>(smem);\nT* sl = s + tile::kPadElems;\n"
             << "__shared__ tile::Rows rt;\n__shared__ double gacc[" << std::max(1, nslot) << "];\n"
-            << "tile::setup_rows(rt, td);\n"
+            << "tile::setup_rows(rt, td);\n" << hoist.str()
             << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gacc[k] = 0.0;\n"
             << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
-            << "tile::load_plain<T, R, tile::PadLayout>(s, amps, rt, td, base);\n"
-            << "tile::load_plain<T, R, tile::PadLayout>(sl, lam, rt, td, base);\n"
+            << "tile::load_plain<T, R, tile::PadLayout, 5>(s, amps, rt, td, base);\n"
+            << "tile::load_plain<T, R, tile::PadLayout, 5>(sl, lam, rt, td, base);\n"
             << "__syncthreads();\n"
             << body.str()
-            << "tile::store_plain<T, R, tile::PadLayout>(s, amps, rt, td, base);\n"
-            << "tile::store_plain<T, R, tile::PadLayout>(sl, lam, rt, td, base);\n"
+            << "tile::store_plain<T, R, tile::PadLayout, 5>(s, amps, rt, td, base);\n"
+            << "tile::store_plain<T, R, tile::PadLayout, 5>(sl, lam, rt, td, base);\n"
             << "}\n__syncthreads();\n"
             << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gpart[(uint64_t)k * gridDim.x + "
                "blockIdx.x] = gacc[k];\n"
@@ -909,6 +913,9 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
         return src.str();
     }
     const bool pf = prefetches(dec, sizeof(R));
+    // rows of the tile: whole codec block pairs (8 low bits) in a sub-pass that
+    // decodes or encodes, 32 amplitudes (5) otherwise
+    const std::string lb = (dec || enc) ? "8" : "5";
     std::ostringstream src;
     src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
         << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
@@ -919,29 +926,30 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
         << "extern __shared__ __align__(16) unsigned char smem[];\n"
         << "T* s = reinterpret_cast<T*>(smem);\n"
         << "uint32_t* cw = reinterpret_cast<uint32_t*>(smem + sizeof(T) * tile::kPadElems * " << (pf ? 2 : 1) << ");\n"
-        << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n";
+        << "__shared__ tile::Rows rt;\ntile::setup_rows(rt, td);\n" << hoist.str();
     if (pf) {
         // tile buffer bo (element offset 0 or 4096) is processed while the
         // other one fills; bo is folded into every phase's base offset
         src << "__syncthreads();\n"
-            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout>(s, amps, rt, td, "
+            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s, amps, rt, td, "
                "tile::tile_base(rt, td, blockIdx.x));\n"
             << "uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo = tile::kPadElems - bo) {\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
             << "tile::cp_async_wait_all();\n__syncthreads();\n"
-            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T, tile::PadLayout>(s + (tile::kPadElems - bo), amps, "
-               "rt, td, tile::tile_base(rt, td, tl + gridDim.x));\n";
+            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb
+            << ">(s + (tile::kPadElems - bo), amps, rt, td, tile::tile_base(rt, td, tl + gridDim.x));\n";
     } else {
         src << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
-            << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ", tile::PadLayout>(s, amps, rt, td, base, fa, cw);\n"
+            << "tile::load_tile<T, R, " << (dec ? "true" : "false") << ", tile::PadLayout, " << lb
+            << ">(s, amps, rt, td, base, fa, cw);\n"
             << "__syncthreads();\n";
     }
     src << body.str()
-        << "tile::store_tile<T, R, " << (enc ? "true" : "false")
-        << ", tile::PadLayout>(s + bo, amps, rt, td, base, fa, cw);\n"
+        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ", tile::PadLayout, " << lb
+        << ">(s + bo, amps, rt, td, base, fa, cw);\n"
         << "}\n}\n";
     return src.str();
 }
@@ -1043,7 +1051,7 @@ template <typename R>
 cudaError_t jit_launch_adjoint(const JitFn* fn, void* psi, void* lam, const TileDesc& td, uint64_t gbase,
                                double* gpart, const std::vector<R>& params, cudaStream_t st, unsigned* grid_out)
 {
-    if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
+    if (!fn || td.t != kPhaseTileQubits || td.l != 5 || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = jit_grid(ntiles);
     if (grid_out) *grid_out = grid;
@@ -1062,7 +1070,9 @@ template <typename R>
 cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t gbase, const FuseArgs& fa,
                        const std::vector<R>& params, cudaStream_t st)
 {
-    if (!fn || td.t != kPhaseTileQubits || params.empty()) return cudaErrorInvalidValue;
+    // the kernel was generated for rows of 8 low bits when it decodes or encodes, 5 otherwise
+    if (!fn || td.t != kPhaseTileQubits || td.l != ((fa.decode || fa.encode) ? 8 : 5) || params.empty())
+        return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = jit_grid(ntiles);
     const size_t smem = (sizeof(R) * 2 * tile_pad_elems() * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +

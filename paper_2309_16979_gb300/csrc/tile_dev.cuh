@@ -128,11 +128,12 @@ __device__ __noinline__ void encode_row(const T* s, uint32_t rw, const FuseArgs&
 }
 
 // Plain copies of one tile between HBM and shared memory (no codec).
-template <typename T, typename R, typename Lay>
+// LB >= 0: the tile's low bits l known at compile time (td.l otherwise).
+template <typename T, typename R, typename Lay, int LB = -1>
 __device__ __forceinline__ void load_plain(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                            uint64_t base)
 {
-    const int l = td.l;
+    const int l = LB >= 0 ? LB : td.l;
     const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
     const T* g0 = amps + base + (t2 & rmask);
     const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
@@ -153,11 +154,11 @@ __device__ __forceinline__ void load_plain(T* s, const T* __restrict__ amps, con
     }
 }
 
-template <typename T, typename R, typename Lay>
+template <typename T, typename R, typename Lay, int LB = -1>
 __device__ __forceinline__ void store_plain(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                             uint64_t base)
 {
-    const int l = td.l;
+    const int l = LB >= 0 ? LB : td.l;
     const uint32_t t2 = 2 * threadIdx.x, rmask = (1u << l) - 1u;
     T* g0 = amps + base + (t2 & rmask);
     const uint32_t a0 = Lay::at(t2), a1 = Lay::at(t2 + 1);
@@ -179,7 +180,7 @@ __device__ __forceinline__ void store_plain(const T* s, T* __restrict__ amps, co
 // DEC: decode the group's chunk streams, one warp per 256-amplitude block
 // pair (rows are block pairs, td.l = 8); otherwise 16-byte vector loads along
 // the rows.
-template <typename T, typename R, bool DEC, typename Lay = SwzLayout>
+template <typename T, typename R, bool DEC, typename Lay = SwzLayout, int LB = -1>
 __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                           uint64_t base, const FuseArgs& fa, uint32_t* cw)
 {
@@ -190,7 +191,7 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
             decode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        load_plain<T, R, Lay>(s, amps, rt, td, base);
+        load_plain<T, R, Lay, LB>(s, amps, rt, td, base);
     }
 }
 
@@ -198,11 +199,11 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ amps, cons
 // amplitude per copy so that the swizzled destinations need no registers),
 // committed as one group; cp_async_wait_all() then __syncthreads() make it
 // visible. Used to fetch the next tile while the current one is processed.
-template <typename T, typename Lay = SwzLayout>
+template <typename T, typename Lay = SwzLayout, int LB = -1>
 __device__ __forceinline__ void prefetch_tile(T* s, const T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                               uint64_t base)
 {
-    const int l = td.l;
+    const int l = LB >= 0 ? LB : td.l;
     // amplitude t + 256k (t = thread): row and slot split as in load_tile
     const uint32_t t = threadIdx.x, rmask = (1u << l) - 1u;
     const T* g0 = amps + base + (t & rmask);
@@ -222,7 +223,7 @@ __device__ __forceinline__ void prefetch_tile(T* s, const T* __restrict__ amps, 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // shared memory -> HBM (or the codec staging when ENC) for the tile at `base`
-template <typename T, typename R, bool ENC, typename Lay = SwzLayout>
+template <typename T, typename R, bool ENC, typename Lay = SwzLayout, int LB = -1>
 __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, const Rows& rt, const TileDesc& td,
                                            uint64_t base, const FuseArgs& fa, uint32_t* cw)
 {
@@ -233,7 +234,7 @@ __device__ __forceinline__ void store_tile(const T* s, T* __restrict__ amps, con
         for (uint32_t rw = wid; rw < nrows; rw += kThreads / 32)
             encode_row<T, R, Lay>(s, rw, fa, base + rt.rowoff[rw], cw + wid * kCodecWords, lane);
     } else {
-        store_plain<T, R, Lay>(s, amps, rt, td, base);
+        store_plain<T, R, Lay, LB>(s, amps, rt, td, base);
     }
 }
 

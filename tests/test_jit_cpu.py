@@ -93,3 +93,16 @@ def test_x_gates_cost_no_arithmetic(jit_sources):
     gates = [W.Gate("X", (q,)) for q in range(12)]
     srcs = [s for s in jit_sources(12, 12, gates, mode="uncompressed") if s]
     assert srcs and all("p.m[" not in s for s in srcs)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_generated_adjoint_kernels_compile(jit_sources, dtype):
+    """Reverse-sweep kernels of sv_grad: psi and lambda together, one
+    gradient accumulation per parameterised gate."""
+    lib = _nvrtc()
+    gates, nparams = W.hea(14, 2)
+    srcs = [s for s in jit_sources(14, 9, gates, dtype=dtype, max_group_qubits=3, adjoint=True) if s]
+    assert srcs
+    assert sum(s.count("atomicAdd(&gacc") for s in srcs) == nparams
+    rc, log = _compile(lib, srcs[0])
+    assert rc == 0, log
