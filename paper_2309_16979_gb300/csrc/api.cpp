@@ -128,6 +128,8 @@ void release(sv_state* s)
         if (s->ev_comp[i]) cudaEventDestroy(s->ev_comp[i]);
         if (s->ev_d2h[i]) cudaEventDestroy(s->ev_d2h[i]);
     }
+    cudaFree(s->d_carry);
+    if (s->ev_prev_d2h) cudaEventDestroy(s->ev_prev_d2h);
     cudaFree(s->d_amps);
     cudaFree(s->d_sparse);
     cudaFree(s->d_blocksq);
@@ -154,7 +156,7 @@ static size_t group_footprint(int c, int g, int dtype, int nslots)
     const size_t stride = (L.max_bytes + 255) & ~size_t(255);
     const size_t amp = dtype == SV_C128 ? 16 : 8;
     const size_t per_chunk = (amp << c) + (size_t)L.nb * 1024 + 8ull * L.bpc +
-                             (size_t)nslots * (2 * stride + sizeof(ChunkOut));
+                             (size_t)nslots * (2 * stride + sizeof(ChunkOut)) + stride;  // + the carry buffer
     return per_chunk << g;
 }
 
@@ -212,7 +214,13 @@ int create_impl(sv_state* s)
             (e = cudaEventCreateWithFlags(&s->ev_d2h[i], cudaEventDisableTiming)))
             return cuda_fail(s, e, "cudaEventCreate");
     }
+    if ((e = cudaMalloc(&s->d_carry, s->stride * gch))) {
+        cudaGetLastError();
+        return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the carry buffer failed");
+    }
+    if ((e = cudaEventCreateWithFlags(&s->ev_prev_d2h, cudaEventDisableTiming))) return cuda_fail(s, e, "cudaEventCreate");
     const uint64_t nchunks = 1ull << s->nh;
+    s->carry_at.assign(nchunks, -1);
     s->cur.assign(nchunks, ChunkRef{});
     s->nxt.assign(nchunks, ChunkRef{});
     const size_t seg = std::max<size_t>((size_t)1 << 30, 4 * s->stride);

@@ -311,6 +311,12 @@ static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t,
 template <typename R>
 static int upload_pass(sv_state* s, DevPass<R>& dp)
 {
+    // generated kernels take their matrices by value: nothing to upload (the
+    // copy from pageable host memory would wait for the compute stream)
+    bool all_generated = dp.use_phases && !dp.jfn.empty();
+    for (const JitFn* f : dp.jfn)
+        if (!f) all_generated = false;
+    if (all_generated) return SV_OK;
     std::vector<uint8_t> blob;
     dp.ops_at = append_section(blob, dp.ops);
     dp.phases_at = append_section(blob, dp.phases);
@@ -459,9 +465,13 @@ static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates,
     return SV_OK;
 }
 
-// Stream every chunk group of the state through one prepared pass.
+// Stream every chunk group of the state through one prepared pass. With
+// `carry` (another pass of the same circuit follows) the pass ends without
+// draining the GPU: its last group's streams go device to device into
+// d_carry, where the next pass reads them, and that pass's other host copies
+// wait only for the device -> host copies of this pass's earlier groups.
 template <typename R>
-static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
+static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, bool carry = false)
 {
     const int c = s->c, g = (int)pp.S.size();
     const int L = c + g;
@@ -483,6 +493,17 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
     out_arena.reset();
     double norm2 = 0;
     const double delta2 = std::ldexp(1.0, 2 * s->k);
+    std::vector<std::pair<uint64_t, int>> carry_next;  // chunks this pass leaves in d_carry
+    bool carried_in = false;
+    for (int32_t v : s->carry_at)
+        if (v >= 0) {
+            carried_in = true;
+            break;
+        }
+    if (carried_in) {
+        cudaError_t e = cudaStreamWaitEvent(s->s_h2d, s->ev_prev_d2h, 0);
+        if (e) return cuda_fail(s, e, "wait previous pass");
+    }
 
     auto issue = [&](uint64_t gi) -> int {
         const int slot = (int)(gi % NS);
@@ -500,10 +521,17 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
             ch[j] = k;
             const ChunkRef& cr = s->cur[k];
             gin.bytes[j] = (uint32_t)cr.bytes;
-            e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
-                                s->s_h2d);
+            if (s->carry_at[k] >= 0) {
+                // newest stream still on the device (last group of the previous pass)
+                e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride,
+                                    s->d_carry + (size_t)s->carry_at[k] * s->stride, cr.bytes,
+                                    cudaMemcpyDeviceToDevice, s->s_h2d);
+            } else {
+                e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                    s->s_h2d);
+                s->st.bytes_h2d += cr.bytes;
+            }
             if (e) return cuda_fail(s, e, "H2D chunk");
-            s->st.bytes_h2d += cr.bytes;
         }
         prof_end(s, ph2d, PROF_H2D, 0, s->s_h2d);
         if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d))) return cuda_fail(s, e, "record h2d");
@@ -580,6 +608,20 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
         int rr = wait_event(s, s->ev_comp[slot]);
         if (rr) return rr;
         cudaError_t e;
+        const bool last = gi + 1 == ngroups;
+        if (carry && last) {
+            // host copies of every earlier group are what the next pass reads
+            // from the host; this group's streams it reads from d_carry
+            if ((e = cudaEventRecord(s->ev_prev_d2h, s->s_d2h))) return cuda_fail(s, e, "record d2h");
+            if ((e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0))) return cuda_fail(s, e, "wait comp");
+            for (int j = 0; j < gch; j++) {
+                const uint64_t k = slot_chunks[slot][j];
+                if ((e = cudaMemcpyAsync(s->d_carry + (size_t)j * s->stride, s->d_out[slot] + (size_t)j * s->stride,
+                                         s->h_co[slot][j].bytes, cudaMemcpyDeviceToDevice, s->s_h2d)))
+                    return cuda_fail(s, e, "carry copy");
+                carry_next.push_back({k, j});
+            }
+        }
         const int pd2h = prof_begin(s, s->s_d2h);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = slot_chunks[slot][j];
@@ -604,9 +646,14 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp)
         if (gi < ngroups && (r = issue(gi))) return r;
         if (gi >= 1 && (r = finish(gi - 1))) return r;
     }
-    if ((r = sync_all(s))) return r;
-    prof_collect(s);
-    if ((r = check_device_error(s))) return r;
+    // the streams carried in were read by this pass's copies (all enqueued)
+    for (int32_t& v : s->carry_at) v = -1;
+    for (const auto& kj : carry_next) s->carry_at[kj.first] = kj.second;
+    if (!carry) {
+        if ((r = sync_all(s))) return r;
+        prof_collect(s);
+        if ((r = check_device_error(s))) return r;
+    }
     s->cur.swap(s->nxt);
     s->cur_arena = 1 - s->cur_arena;
     uint64_t total = 0;
@@ -682,10 +729,15 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
     if (r) return r;
     s->st.t_host_prepare_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (size_t i = 0; i < passes.size(); i++) {
-        if ((r = run_pass_compressed<R>(s, passes[i], dps[i]))) return r;
+        if ((r = run_pass_compressed<R>(s, passes[i], dps[i], i + 1 < passes.size()))) break;
         dps[i] = DevPass<R>();
     }
-    return SV_OK;
+    if (r) {
+        // a failed pass may leave copies in flight and streams carried
+        sync_all(s);
+        for (int32_t& v : s->carry_at) v = -1;
+    }
+    return r;
 }
 
 template <typename R>

@@ -128,6 +128,14 @@ struct sv_state {
     sv::ChunkOut* h_co[4] = {};
     cudaEvent_t ev_h2d[4] = {}, ev_comp[4] = {}, ev_d2h[4] = {};
     bool slot_used[4] = {};
+    // Cross-pass pipelining inside one sv_apply_circuit: the streams of the last
+    // group of a pass are copied device to device into d_carry (chunk k at
+    // carry_at[k] * stride, -1 when not carried) so the next pass starts
+    // without their host round trip; ev_prev_d2h marks the host copies of the
+    // pass's other groups complete.
+    uint8_t* d_carry = nullptr;
+    std::vector<int32_t> carry_at;
+    cudaEvent_t ev_prev_d2h = nullptr;
     void* d_amps = nullptr;
     uint32_t* d_sparse = nullptr;
     unsigned long long* d_blocksq = nullptr;
