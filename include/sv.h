@@ -148,6 +148,15 @@ typedef struct sv_stats_t {
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
 
+/*
+ * Turn the per-launch CUDA-event timing of sv_config.profile on (1) or off (0)
+ * for the following calls (the paper has no counterpart: measurement). The
+ * events add a little time to every launch, so throughput is best measured
+ * with it off and the breakdown taken on a separate call with it on.
+ * Errors: SV_ERR_ARG for a NULL handle.
+ */
+int sv_set_profile(sv_state* s, int on);
+
 /* Fill *cfg with the defaults listed above. */
 void sv_config_default(sv_config* cfg);
 

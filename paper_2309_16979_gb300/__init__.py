@@ -108,6 +108,10 @@ class StateVector:
         _check(L.sv_chunk_stream(self._h, k, buf, nb.value, C.byref(nb)), "sv_chunk_stream", self._h)
         return bytes(buf)[:nb.value]
 
+    def set_profile(self, on: bool) -> None:
+        """Per-launch CUDA-event timing on or off for the following calls."""
+        _check(load().sv_set_profile(self._h, int(on)), "sv_set_profile", self._h)
+
     def stats(self) -> dict:
         st = _abi.SvStats()
         _check(load().sv_stats(self._h, C.byref(st)), "sv_stats", self._h)

@@ -62,7 +62,7 @@ class SvStats(C.Structure):
 EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "sv_amplitudes",
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
-           "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources")
+           "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile")
 
 _lib = None
 
@@ -120,6 +120,8 @@ def load() -> C.CDLL:
     L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_int, C.c_char_p, SZ,
                                  C.POINTER(SZ), C.POINTER(SZ)]
     L.sv_jit_sources.restype = C.c_int
+    L.sv_set_profile.argtypes = [P, C.c_int]
+    L.sv_set_profile.restype = C.c_int
     _lib = L
     return L
 

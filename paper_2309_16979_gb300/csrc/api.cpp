@@ -129,6 +129,7 @@ void release(sv_state* s)
         if (s->ev_d2h[i]) cudaEventDestroy(s->ev_d2h[i]);
     }
     cudaFree(s->d_carry);
+    cudaFree(s->d_carry_bytes);
     if (s->ev_prev_d2h) cudaEventDestroy(s->ev_prev_d2h);
     cudaFree(s->d_amps);
     cudaFree(s->d_sparse);
@@ -214,7 +215,7 @@ int create_impl(sv_state* s)
             (e = cudaEventCreateWithFlags(&s->ev_d2h[i], cudaEventDisableTiming)))
             return cuda_fail(s, e, "cudaEventCreate");
     }
-    if ((e = cudaMalloc(&s->d_carry, s->stride * gch))) {
+    if ((e = cudaMalloc(&s->d_carry, s->stride * gch)) || (e = cudaMalloc(&s->d_carry_bytes, sizeof(uint64_t) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the carry buffer failed");
     }
@@ -512,6 +513,13 @@ int sv_chunk_stream(const sv_state* s, uint64_t k, void* h_buf, size_t cap, size
     *h_nbytes = cr.bytes;
     if (!h_buf || cap < cr.bytes) return SV_ERR_ARG;
     std::memcpy(h_buf, cr.ptr, cr.bytes);
+    return SV_OK;
+}
+
+int sv_set_profile(sv_state* s, int on)
+{
+    if (!s) return SV_ERR_ARG;
+    s->cfg.profile = on ? 1 : 0;
     return SV_OK;
 }
 

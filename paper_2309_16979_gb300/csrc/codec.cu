@@ -247,6 +247,54 @@ cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* 
     return cudaGetLastError();
 }
 
+namespace {
+
+// copy `nb` bytes between 16-byte aligned stream slots, blocks of one stream
+__device__ __forceinline__ void copy_stream(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint64_t nb)
+{
+    const uint64_t nv = nb / 16, step = (uint64_t)gridDim.x * blockDim.x;
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += step) d[i] = s[i];
+    for (uint64_t i = nv * 16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += step) dst[i] = src[i];
+}
+
+__global__ void k_copy_streams(const uint8_t* __restrict__ src, const ChunkOut* __restrict__ co,
+                               uint8_t* __restrict__ dst, uint64_t* __restrict__ bytes, size_t stride)
+{
+    const int j = blockIdx.y;
+    const uint64_t nb = co[j].bytes < stride ? co[j].bytes : stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bytes[j] = nb;
+    copy_stream(src + (size_t)j * stride, dst + (size_t)j * stride, nb);
+}
+
+__global__ void k_gather_streams(const uint8_t* __restrict__ src, const uint64_t* __restrict__ bytes,
+                                 uint8_t* __restrict__ dst, size_t stride, StreamMoves mv)
+{
+    const int i = blockIdx.y;
+    const uint64_t nb = bytes[mv.src[i]] < stride ? bytes[mv.src[i]] : stride;
+    copy_stream(src + (size_t)mv.src[i] * stride, dst + (size_t)mv.dst[i] * stride, nb);
+}
+
+}  // namespace
+
+cudaError_t launch_copy_streams(const uint8_t* src, const ChunkOut* co, uint8_t* dst, uint64_t* bytes, size_t stride,
+                                int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_copy_streams<<<dim3(64, n), 256, 0, st>>>(src, co, dst, bytes, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, uint8_t* dst, size_t stride,
+                                  const StreamMoves& mv, cudaStream_t st)
+{
+    if (mv.n <= 0) return cudaSuccess;
+    if (mv.n > kMaxGroupChunks) return cudaErrorInvalidValue;
+    k_gather_streams<<<dim3(64, mv.n), 256, 0, st>>>(src, bytes, dst, stride, mv);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st)
 {

@@ -465,83 +465,111 @@ static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates,
     return SV_OK;
 }
 
-// Stream every chunk group of the state through one prepared pass. With
-// `carry` (another pass of the same circuit follows) the pass ends without
-// draining the GPU: its last group's streams go device to device into
-// d_carry, where the next pass reads them, and that pass's other host copies
-// wait only for the device -> host copies of this pass's earlier groups.
+// Stream every chunk group of the passes through the GPU (Sec. 2, "Online
+// stage" steps (1)-(6)): per group, host -> device copies of its chunk
+// streams, decode, the pass's tile sub-passes, encode, device -> host copies.
+// Group issues run one ahead of their completions, across pass boundaries
+// too: the next pass's first copies overlap the previous pass's last group,
+// whose streams the next pass takes from the device (copied into d_carry by a
+// kernel right after their encode) instead of through the host.
 template <typename R>
-static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, bool carry = false)
+static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::vector<DevPass<R>>& dps)
 {
-    const int c = s->c, g = (int)pp.S.size();
-    const int L = c + g;
-    int r = upload_pass<R>(s, dp);
-    if (r) return r;
-
-    // chunk-index bit positions of staged and fixed high qubits
-    std::vector<int> spos, fpos;
-    for (int q = c; q < s->n; q++) {
-        if (std::find(pp.S.begin(), pp.S.end(), q) != pp.S.end()) spos.push_back(q - c);
-        else fpos.push_back(q - c);
+    const int c = s->c, NS = s->nslots;
+    struct PassInfo {
+        std::vector<int> spos, fpos;  // chunk-index bit positions of staged and fixed high qubits
+        uint64_t ngroups = 0, done = 0;
+        int g = 0, gch = 0, L = 0, arena = 0;
+        double norm2 = 0;
+    };
+    std::vector<PassInfo> pinfo(passes.size());
+    std::vector<std::pair<int, uint64_t>> items;  // (pass, group) in issue order
+    for (size_t p = 0; p < passes.size(); p++) {
+        PassInfo& P = pinfo[p];
+        for (int q = c; q < s->n; q++) {
+            if (std::find(passes[p].S.begin(), passes[p].S.end(), q) != passes[p].S.end()) P.spos.push_back(q - c);
+            else P.fpos.push_back(q - c);
+        }
+        P.g = (int)passes[p].S.size();
+        P.gch = 1 << P.g;
+        P.L = c + P.g;
+        P.ngroups = 1ull << P.fpos.size();
+        P.arena = (s->cur_arena + 1 + (int)p) & 1;  // the arena pass p writes
+        for (uint64_t gi = 0; gi < P.ngroups; gi++) items.push_back({(int)p, gi});
     }
-    const uint64_t ngroups = 1ull << fpos.size();
-    const int gch = 1 << g;
-    const int NS = s->nslots;
+    // renormalisation feeds a pass's norm into the next pass's decode: no
+    // lookahead across passes then
+    const bool cross = !s->cfg.renormalize;
+    const double delta2 = std::ldexp(1.0, 2 * s->k);
     std::vector<std::vector<uint64_t>> slot_chunks(NS);
     std::vector<int> slot_prof(NS, -1);
-    Arena& out_arena = s->arena[1 - s->cur_arena];
-    out_arena.reset();
-    double norm2 = 0;
-    const double delta2 = std::ldexp(1.0, 2 * s->k);
-    std::vector<std::pair<uint64_t, int>> carry_next;  // chunks this pass leaves in d_carry
-    bool carried_in = false;
-    for (int32_t v : s->carry_at)
-        if (v >= 0) {
-            carried_in = true;
-            break;
-        }
-    if (carried_in) {
-        cudaError_t e = cudaStreamWaitEvent(s->s_h2d, s->ev_prev_d2h, 0);
-        if (e) return cuda_fail(s, e, "wait previous pass");
-    }
+    std::vector<std::pair<uint64_t, int>> carry_next;  // chunks the current pass leaves in d_carry
+    std::vector<uint64_t> unsized;                      // carried chunks of the group being issued, length unknown
+    std::vector<std::pair<int, std::vector<uint64_t>>> unsized_prof;  // profiled launches reading them
+    for (int32_t& v : s->carry_at) v = -1;
 
-    auto issue = [&](uint64_t gi) -> int {
-        const int slot = (int)(gi % NS);
-        const uint64_t base = deposit(gi, fpos);
+    auto issue = [&](size_t idx) -> int {
+        const int p = items[idx].first;
+        const uint64_t gi = items[idx].second;
+        PassInfo& P = pinfo[p];
+        DevPass<R>& dp = dps[p];
+        const int slot = (int)(idx % NS), gch = P.gch, L = P.L;
+        cudaError_t e;
+        int r;
+        if (gi == 0) {
+            // this pass reads the previous pass's last group from d_carry and
+            // its other groups from the host once their copies are complete
+            for (int32_t& v : s->carry_at) v = -1;
+            for (const auto& kj : carry_next) s->carry_at[kj.first] = kj.second;
+            carry_next.clear();
+            if (p > 0 && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_prev_d2h, 0))) return cuda_fail(s, e, "wait d2h");
+            if ((r = upload_pass<R>(s, dp))) return r;
+        }
+        const uint64_t base = deposit(gi, P.fpos);
         auto& ch = slot_chunks[slot];
         ch.resize(gch);
         GroupIn gin{};
-        cudaError_t e;
-        if (s->slot_used[slot]) {
-            if ((e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0))) return cuda_fail(s, e, "wait comp");
-        }
+        StreamMoves mv;
+        if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0)))
+            return cuda_fail(s, e, "wait comp");
         const int ph2d = prof_begin(s, s->s_h2d);
         for (int j = 0; j < gch; j++) {
-            const uint64_t k = base | deposit((uint64_t)j, spos);
+            const uint64_t k = base | deposit((uint64_t)j, P.spos);
             ch[j] = k;
+            if (s->carry_at[k] >= 0) {
+                // on the device: gathered into the slot by a kernel below. Before
+                // the previous pass's last group completes on the host its length
+                // is known on the device only: decode then bounds it by the slot
+                mv.src[mv.n] = (uint16_t)s->carry_at[k];
+                mv.dst[mv.n] = (uint16_t)j;
+                mv.n++;
+                if (p > 0 && pinfo[p - 1].done == pinfo[p - 1].ngroups) {
+                    gin.bytes[j] = (uint32_t)s->cur[k].bytes;
+                } else {
+                    gin.bytes[j] = (uint32_t)s->stride;
+                    unsized.push_back(k);
+                }
+                continue;
+            }
             const ChunkRef& cr = s->cur[k];
             gin.bytes[j] = (uint32_t)cr.bytes;
-            if (s->carry_at[k] >= 0) {
-                // newest stream still on the device (last group of the previous pass)
-                e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride,
-                                    s->d_carry + (size_t)s->carry_at[k] * s->stride, cr.bytes,
-                                    cudaMemcpyDeviceToDevice, s->s_h2d);
-            } else {
-                e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
-                                    s->s_h2d);
-                s->st.bytes_h2d += cr.bytes;
-            }
-            if (e) return cuda_fail(s, e, "H2D chunk");
+            if ((e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                     s->s_h2d)))
+                return cuda_fail(s, e, "H2D chunk");
+            s->st.bytes_h2d += cr.bytes;
         }
         prof_end(s, ph2d, PROF_H2D, 0, s->s_h2d);
         if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d))) return cuda_fail(s, e, "record h2d");
         if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0))) return cuda_fail(s, e, "wait h2d");
-        if (s->slot_used[slot]) {
-            if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0))) return cuda_fail(s, e, "wait d2h");
-        }
+        if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0)))
+            return cuda_fail(s, e, "wait d2h");
+        if (mv.n && (e = launch_gather_streams(s->d_carry, s->d_carry_bytes, s->d_in[slot], s->stride, mv, s->s_comp)))
+            return cuda_fail(s, e, "gather streams");
+        if (mv.n) s->st.kernel_launches++;
         const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
         uint64_t in_bytes = 0;
         for (int j = 0; j < gch; j++) in_bytes += gin.bytes[j];
+        in_bytes -= (uint64_t)unsized.size() * s->stride;  // their lengths are added once known
         int pi = -1;
         if (!dp.fuse_decode) {
             pi = prof_begin(s);
@@ -549,6 +577,7 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, 
                                       s->s_comp)))
                 return cuda_fail(s, e, "decode");
             prof_end(s, pi, PROF_DECODE, in_bytes + amp_bytes);
+            if (!unsized.empty()) unsized_prof.push_back({pi, unsized});
             s->st.kernel_launches++;
         }
         const uint64_t gbase = base << c;
@@ -574,9 +603,11 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, 
             // algorithmic bytes: what the launch reads (stream or amplitudes) and writes
             // (amplitudes; a fused encode's stream bytes are added once known)
             prof_end(s, pi, PROF_APPLY, (fa.decode ? in_bytes : amp_bytes) + (fa.encode ? 0 : amp_bytes));
+            if (fa.decode && !unsized.empty()) unsized_prof.push_back({pi, unsized});
             if (fa.encode) slot_prof[slot] = pi;
             s->st.kernel_launches++;
         }
+        unsized.clear();
         int launches = 0;
         if (dp.fuse_encode) {
             const int pf = prof_begin(s);
@@ -593,6 +624,14 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, 
             prof_end(s, pi, PROF_ENCODE, amp_bytes);
         }
         s->st.kernel_launches += launches;
+        if (cross && gi + 1 == P.ngroups && (size_t)p + 1 < passes.size()) {
+            // the last group of a pass: its streams stay on the device for the next pass
+            if ((e = launch_copy_streams(s->d_out[slot], s->d_co[slot], s->d_carry, s->d_carry_bytes, s->stride, gch,
+                                         s->s_comp)))
+                return cuda_fail(s, e, "carry streams");
+            s->st.kernel_launches++;
+            for (int j = 0; j < gch; j++) carry_next.push_back({ch[j], j});
+        }
         if ((e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,
                                  s->s_comp)))
             return cuda_fail(s, e, "D2H sizes");
@@ -603,25 +642,17 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, 
         return SV_OK;
     };
 
-    auto finish = [&](uint64_t gi) -> int {
-        const int slot = (int)(gi % NS);
+    auto finish = [&](size_t idx) -> int {
+        const int p = items[idx].first;
+        PassInfo& P = pinfo[p];
+        const int slot = (int)(idx % NS), gch = P.gch;
         int rr = wait_event(s, s->ev_comp[slot]);
         if (rr) return rr;
         cudaError_t e;
-        const bool last = gi + 1 == ngroups;
-        if (carry && last) {
-            // host copies of every earlier group are what the next pass reads
-            // from the host; this group's streams it reads from d_carry
-            if ((e = cudaEventRecord(s->ev_prev_d2h, s->s_d2h))) return cuda_fail(s, e, "record d2h");
-            if ((e = cudaStreamWaitEvent(s->s_h2d, s->ev_comp[slot], 0))) return cuda_fail(s, e, "wait comp");
-            for (int j = 0; j < gch; j++) {
-                const uint64_t k = slot_chunks[slot][j];
-                if ((e = cudaMemcpyAsync(s->d_carry + (size_t)j * s->stride, s->d_out[slot] + (size_t)j * s->stride,
-                                         s->h_co[slot][j].bytes, cudaMemcpyDeviceToDevice, s->s_h2d)))
-                    return cuda_fail(s, e, "carry copy");
-                carry_next.push_back({k, j});
-            }
-        }
+        Arena& out_arena = s->arena[P.arena];
+        // the arena this pass writes held the data of two passes before, whose
+        // copies to the device all precede this group's (stream order)
+        if (P.done == 0) out_arena.reset();
         const int pd2h = prof_begin(s, s->s_d2h);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = slot_chunks[slot][j];
@@ -629,50 +660,60 @@ static int run_pass_compressed(sv_state* s, const PassPlan& pp, DevPass<R>& dp, 
             if (co.bytes > s->stride) return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
             uint8_t* dst = arena_alloc(s, out_arena, co.bytes);
             if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
-            e = cudaMemcpyAsync(dst, s->d_out[slot] + (size_t)j * s->stride, co.bytes, cudaMemcpyDeviceToHost,
-                                s->s_d2h);
-            if (e) return cuda_fail(s, e, "D2H chunk");
-            s->nxt[k] = {dst, co.bytes};
+            if ((e = cudaMemcpyAsync(dst, s->d_out[slot] + (size_t)j * s->stride, co.bytes, cudaMemcpyDeviceToHost,
+                                     s->s_d2h)))
+                return cuda_fail(s, e, "D2H chunk");
+            // the pass read chunk k's previous stream before writing it: update in place
+            s->cur[k] = {dst, co.bytes};
             s->st.bytes_d2h += co.bytes;
             if (slot_prof[slot] >= 0) s->prof_rec[slot_prof[slot]].bytes += co.bytes;
-            norm2 += (double)co.sumsq * delta2;
+            P.norm2 += (double)co.sumsq * delta2;
         }
         prof_end(s, pd2h, PROF_D2H, 0, s->s_d2h);
-        if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h))) return cuda_fail(s, e, "record d2h");
+        if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h)) || (e = cudaEventRecord(s->ev_prev_d2h, s->s_d2h)))
+            return cuda_fail(s, e, "record d2h");
+        if (++P.done == P.ngroups) {
+            // the streams this pass left on the device now have their lengths
+            for (const auto& u : unsized_prof)
+                if (u.first >= 0)
+                    for (uint64_t k : u.second) s->prof_rec[u.first].bytes += s->cur[k].bytes;
+            unsized_prof.clear();
+            s->st.passes++;
+            s->st.norm2 = P.norm2;
+            if (P.norm2 < 1e-300) return fail(s, SV_ERR_NORM_COLLAPSE, "norm of the stored state collapsed to zero");
+            s->scale = s->cfg.renormalize ? 1.0 / std::sqrt(P.norm2) : 1.0;
+        }
         return SV_OK;
     };
 
-    for (uint64_t gi = 0; gi <= ngroups; gi++) {
-        if (gi < ngroups && (r = issue(gi))) return r;
-        if (gi >= 1 && (r = finish(gi - 1))) return r;
+    int r = SV_OK;
+    for (size_t idx = 0; idx <= items.size() && !r; idx++) {
+        // without lookahead across passes, a pass's last group completes before the next pass starts
+        const bool boundary = idx < items.size() && idx >= 1 && items[idx].first != items[idx - 1].first;
+        if (!cross && boundary && (r = finish(idx - 1))) break;
+        if (idx < items.size() && (r = issue(idx))) break;
+        if (idx >= 1 && !(!cross && boundary) && (r = finish(idx - 1))) break;
     }
-    // the streams carried in were read by this pass's copies (all enqueued)
+    const int rs = sync_all(s);
     for (int32_t& v : s->carry_at) v = -1;
-    for (const auto& kj : carry_next) s->carry_at[kj.first] = kj.second;
-    if (!carry) {
-        if ((r = sync_all(s))) return r;
-        prof_collect(s);
-        if ((r = check_device_error(s))) return r;
-    }
-    s->cur.swap(s->nxt);
-    s->cur_arena = 1 - s->cur_arena;
+    if (r) return r;
+    if (rs) return rs;
+    prof_collect(s);
+    if ((r = check_device_error(s))) return r;
+    if (!passes.empty()) s->cur_arena = pinfo.back().arena;
     uint64_t total = 0;
     for (const ChunkRef& cr : s->cur) total += cr.bytes;
     s->st.compressed_bytes = total;
-    s->st.norm2 = norm2;
-    s->st.passes++;
-    if (norm2 < 1e-300) return fail(s, SV_ERR_NORM_COLLAPSE, "norm of the stored state collapsed to zero");
-    s->scale = s->cfg.renormalize ? 1.0 / std::sqrt(norm2) : 1.0;
     return SV_OK;
 }
 
 template <typename R>
 int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp)
 {
-    DevPass<R> dp;
-    int r = prepare_pass_compressed<R>(s, gates, pp, dp);
-    if (!r) r = jit_prepare<R>(s, {&dp});
-    if (!r) r = run_pass_compressed<R>(s, pp, dp);
+    std::vector<DevPass<R>> dps(1);
+    int r = prepare_pass_compressed<R>(s, gates, pp, dps[0]);
+    if (!r) r = jit_prepare<R>(s, {&dps[0]});
+    if (!r) r = stream_passes<R>(s, {pp}, dps);
     return r;
 }
 
@@ -728,16 +769,7 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
     int r = jit_prepare<R>(s, ptrs);
     if (r) return r;
     s->st.t_host_prepare_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    for (size_t i = 0; i < passes.size(); i++) {
-        if ((r = run_pass_compressed<R>(s, passes[i], dps[i], i + 1 < passes.size()))) break;
-        dps[i] = DevPass<R>();
-    }
-    if (r) {
-        // a failed pass may leave copies in flight and streams carried
-        sync_all(s);
-        for (int32_t& v : s->carry_at) v = -1;
-    }
-    return r;
+    return stream_passes<R>(s, passes, dps);
 }
 
 template <typename R>
@@ -1515,8 +1547,7 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     if (r) return r;
     if ((r = init_state<R>(s))) return r;
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
-    for (const PassPlan& pp : passes)
-        if ((r = run_pass_compressed<R>(s, gates, pp))) return r;
+    if ((r = apply_circuit<R>(s, gates))) return r;  // the forward sweep (the same plan)
     std::vector<sv_pauli_term> phys(nterms);
     for (size_t i = 0; i < nterms; i++) {
         phys[i] = H[i];

@@ -129,11 +129,12 @@ struct sv_state {
     cudaEvent_t ev_h2d[4] = {}, ev_comp[4] = {}, ev_d2h[4] = {};
     bool slot_used[4] = {};
     // Cross-pass pipelining inside one sv_apply_circuit: the streams of the last
-    // group of a pass are copied device to device into d_carry (chunk k at
+    // group of a pass are copied on the device into d_carry (chunk k at
     // carry_at[k] * stride, -1 when not carried) so the next pass starts
-    // without their host round trip; ev_prev_d2h marks the host copies of the
-    // pass's other groups complete.
+    // without their host round trip; ev_prev_d2h is recorded after the latest
+    // device -> host copies.
     uint8_t* d_carry = nullptr;
+    uint64_t* d_carry_bytes = nullptr;  // lengths of the streams in d_carry
     std::vector<int32_t> carry_at;
     cudaEvent_t ev_prev_d2h = nullptr;
     void* d_amps = nullptr;

@@ -131,6 +131,20 @@ cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* 
 template <typename R>
 cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st);
 
+// Stream copies between the device slots of consecutive passes: the first
+// co[j].bytes bytes of stream j (at j * stride in src) to the same place in
+// dst, its length to bytes[j]; and streams mv.src[i] of src (lengths from
+// bytes) to slots mv.dst[i] of dst.
+struct StreamMoves {
+    uint16_t src[kMaxGroupChunks];
+    uint16_t dst[kMaxGroupChunks];
+    int32_t n = 0;
+};
+cudaError_t launch_copy_streams(const uint8_t* src, const ChunkOut* co, uint8_t* dst, uint64_t* bytes, size_t stride,
+                                int n, cudaStream_t st);
+cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, uint8_t* dst, size_t stride,
+                                  const StreamMoves& mv, cudaStream_t st);
+
 // sum_t coeff_t <A| P_t |B> pieces; see reduce.cu
 struct PauliDev {
     double coeff;
