@@ -492,8 +492,10 @@ void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& 
 
 // Adjoint: this thread's part of Im<lambda| G |psi> for the generator G (1 X,
 // 2 Y, 3 Z) on register bit b, taken before the op is applied: summed over
-// the thread's pairs in R, over the warp by shuffles, then added in FP64 to
-// the CTA's slot. A pending exchange on b (registers hold X psi, X lambda on
+// the thread's pairs and over the warp by shuffles in R, added to the warp's
+// own entry of the slot (shared memory, in R, over the CTA's tiles); the
+// kernel sums a slot's warp entries in FP64 at its end (GB300's FP64 pipe is
+// narrow: nothing FP64 runs per tile). A pending exchange on b (registers hold X psi, X lambda on
 // the threads where it holds) flips the sign for Y and Z (X Y X = -Y, X Z X = -Z).
 template <typename R>
 void emit_grad(Gen<R>& g, int b, int gen, int slot, const std::vector<typename Gen<R>::Pend>& conj)
@@ -519,7 +521,7 @@ void emit_grad(Gen<R>& g, int b, int gen, int slot, const std::vector<typename G
     g.o << "gp += __shfl_xor_sync(0xffffffffu, gp, 16); gp += __shfl_xor_sync(0xffffffffu, gp, 8); "
            "gp += __shfl_xor_sync(0xffffffffu, gp, 4); gp += __shfl_xor_sync(0xffffffffu, gp, 2); "
            "gp += __shfl_xor_sync(0xffffffffu, gp, 1);\n"
-        << "if ((threadIdx.x & 31u) == 0u) atomicAdd(&gacc[" << slot << "], (double)gp); }\n";
+        << "if ((threadIdx.x & 31u) == 0u) gw[" << slot << " * 8 + (threadIdx.x >> 5)] += gp; }\n";
 }
 
 template <typename R> struct RName;
@@ -890,13 +892,13 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
             << "struct P { R m[" << std::max<size_t>(1, params.size()) << "]; };\n"
             << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << RName<R>::minb_adj << ")\n"
-            << "svj(T* __restrict__ amps, T* __restrict__ lam, const TileDesc td, const uint64_t gbase, "
+            << "svja(T* __restrict__ amps, T* __restrict__ lam, const TileDesc td, const uint64_t gbase, "
                "const uint64_t ntiles, double* __restrict__ gpart, const P p)\n{\n"
             << "extern __shared__ __align__(16) unsigned char smem[];\n"
             << "T* s = reinterpret_cast<T*>(smem);\nT* sl = s + tile::kPadElems;\n"
-            << "__shared__ tile::Rows rt;\n__shared__ double gacc[" << std::max(1, nslot) << "];\n"
+            << "__shared__ tile::Rows rt;\n__shared__ R gw[" << std::max(1, nslot) * 8 << "];  // [slot][warp]\n"
             << "tile::setup_rows(rt, td);\n" << hoist.str()
-            << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gacc[k] = 0.0;\n"
+            << "for (int k = threadIdx.x; k < " << nslot * 8 << "; k += blockDim.x) gw[k] = (R)0;\n"
             << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
@@ -907,8 +909,9 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << "tile::store_plain<T, R, tile::PadLayout, 5>(s, amps, rt, td, base);\n"
             << "tile::store_plain<T, R, tile::PadLayout, 5>(sl, lam, rt, td, base);\n"
             << "}\n__syncthreads();\n"
-            << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) gpart[(uint64_t)k * gridDim.x + "
-               "blockIdx.x] = gacc[k];\n"
+            << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) {\n"
+            << "double v = 0.0;\nfor (int w = 0; w < 8; w++) v += (double)gw[k * 8 + w];\n"
+            << "gpart[(uint64_t)k * gridDim.x + blockIdx.x] = v;\n}\n"
             << "}\n";
         return src.str();
     }
@@ -1026,7 +1029,10 @@ bool jit_compile(const std::vector<std::string>& keys, const std::function<std::
                 return false;
             }
             CUresult r = d.load(&fn->mod, j.cubin.data());
-            if (r == CUDA_SUCCESS) r = d.getfn(&fn->fn, fn->mod, "svj");
+            if (r == CUDA_SUCCESS) {
+                // svj: a sub-pass kernel; svja: an adjoint (two-vector) one
+                r = d.getfn(&fn->fn, fn->mod, j.src->find("\nsvja(") != std::string::npos ? "svja" : "svj");
+            }
             if (r == CUDA_SUCCESS) r = d.setattr(fn->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem_max);
             if (r != CUDA_SUCCESS) {
                 err = "loading a compiled kernel failed (CUresult " + std::to_string((int)r) + ")";
