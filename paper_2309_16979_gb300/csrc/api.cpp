@@ -306,7 +306,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     s->gmax = cfg.max_group_qubits ? cfg.max_group_qubits : auto_group_qubits(n, chunk_qubits, cfg);
     s->nslots = cfg.pipeline_slots;
     s->tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
-    s->lq = 5;
+    s->lq = kTileLowQubits;
     s->perm.resize(n);
     for (int q = 0; q < n; q++) s->perm[q] = q;
     s->st.chunk_qubits = s->c;
@@ -448,7 +448,7 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
         }
         const int L = c + (int)passes[p].S.size();
         int t, l;
-        tile_shape(L, tq, 5, t, l);
+        tile_shape(L, tq, kTileLowQubits, t, l);
         const std::vector<HOp> hops = local_ops(pg, passes[p].gates, c, passes[p].S, false);
         const std::vector<SubPlan> sp = plan_subpasses(hops, L, t, l, true);
         if (sp.empty() && !hops.empty()) return SV_ERR_ARG;
@@ -477,7 +477,7 @@ int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, 
     tmp.cfg = cfg;
     tmp.gmax = cfg.max_group_qubits ? cfg.max_group_qubits : 4;
     tmp.tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
-    tmp.lq = 5;
+    tmp.lq = kTileLowQubits;
     tmp.perm.resize(n);
     for (int q = 0; q < n; q++) tmp.perm[q] = q;
     std::vector<PGate> pg;

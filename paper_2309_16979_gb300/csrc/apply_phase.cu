@@ -401,7 +401,7 @@ cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* pha
                                 const PhaseOp<R>* ops, int op0, int nops, const CtaCtrl* ctl, const R* dense2,
                                 uint64_t gbase, const FuseArgs& fa, cudaStream_t st, int ph_base)
 {
-    if (td.l != 5 && td.l != 8) return cudaErrorInvalidValue;
+    if (td.l < tile::kMinLowBits || td.l > 8) return cudaErrorInvalidValue;
     if ((fa.decode || fa.encode) && td.l != 8) return cudaErrorInvalidValue;
     if (ph_base >= 0)
         return launch_impl<R, true>(amps, td, phases, nphases, ops, op0, nops, ctl, dense2, gbase, fa, st, ph_base);

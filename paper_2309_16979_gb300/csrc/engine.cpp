@@ -260,7 +260,7 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
             const Phase* ph = dp->phases.data() + dp->ph_off[i];
             jit_params<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->d2m.data(), dp->jpar[i]);
             std::string key;
-            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->jpar[i], dec, enc, key);
+            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->jpar[i], dec, enc, dp->td[i].l, key);
             keys.push_back(std::move(key));
             where.push_back({dp, i});
         }
@@ -271,7 +271,7 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
         const size_t i = where[k].second;
         return jit_source<R>(dp->phases.data() + dp->ph_off[i], dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(),
                              dp->d2m.data(), i == 0 && dp->fuse_decode, i + 1 == dp->td.size() && dp->fuse_encode,
-                             dp->jpar[i]);
+                             dp->td[i].l, dp->jpar[i]);
     };
     std::vector<const JitFn*> fns;
     std::string err;
@@ -289,7 +289,7 @@ static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t,
                                  bool fuse_encode = false)
 {
     DevPass<R> dp;
-    dp.use_phases = (t == kPhaseTileQubits && l == 5);
+    dp.use_phases = (t == kPhaseTileQubits && l >= 4 && l <= 5);
     dp.fuse_decode = dp.use_phases && fuse_decode;
     dp.fuse_encode = dp.use_phases && fuse_encode;
     for (size_t si = 0; si < subs.size(); si++) {
@@ -349,7 +349,7 @@ static int jit_adjoint_plan(sv_state* s, const std::vector<SubPlan>& subs, int L
                             std::vector<int>& slot_params, AdjPlan<R>& ap)
 {
     ap = AdjPlan<R>();
-    if (!s->cfg.jit || t != kPhaseTileQubits || l != 5 || subs.empty()) return SV_OK;
+    if (!s->cfg.jit || t != kPhaseTileQubits || l < 4 || l > 5 || subs.empty()) return SV_OK;
     struct Sub {
         std::vector<Phase> ph;
         std::vector<PhaseOp<R>> ops;
@@ -370,11 +370,11 @@ static int jit_adjoint_plan(sv_state* s, const std::vector<SubPlan>& subs, int L
         ap.par.emplace_back();
         jit_params<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].d2m.data(), ap.par.back(), false);
         jit_key<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].ctl.data(), ap.par.back(), false,
-                   false, keys[i], sv[i].grad.data());
+                   false, td.l, keys[i], sv[i].grad.data());
     }
     auto source_of = [&](size_t k) {
         return jit_source<R>(sv[k].ph.data(), (int)sv[k].ph.size(), sv[k].ops.data(), sv[k].ctl.data(),
-                             sv[k].d2m.data(), false, false, ap.par[k], sv[k].grad.data());
+                             sv[k].d2m.data(), false, false, ap.td[k].l, ap.par[k], sv[k].grad.data());
     };
     std::string err;
     JitReport rep;
@@ -453,13 +453,13 @@ static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates,
     // holds whole block pairs (local bits 0..7) needs no extra sub-pass, and
     // the encode into the last sub-pass when its tile holds them.
     bool fdec = false, fenc = false;
-    if (t == kPhaseTileQubits && l == 5 && c >= 8 && !subs.empty() && s->cfg.fuse_codec) {
+    if (t == kPhaseTileQubits && l >= 4 && l <= 5 && c >= 8 && !subs.empty() && s->cfg.fuse_codec) {
         std::vector<SubPlan> alt = plan_subpasses(hops, L, t, l, true, 8);
         if (!alt.empty() && alt.size() <= subs.size()) {
             subs.swap(alt);
             fdec = true;
         }
-        fenc = (subs.back().T & 0xffull) == 0xffull;
+        fenc = replan_tail(subs, L, t, l, 8, fdec);
     }
     dp = build_dev_pass<R>(subs, L, t, l, fdec, fenc);
     return SV_OK;
@@ -798,7 +798,7 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
             const int L = c + (int)pp.S.size();
             int t, l;
             tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
-            if (t != kPhaseTileQubits || l != 5) continue;
+            if (t != kPhaseTileQubits || l < 4 || l > 5) continue;
             std::vector<int> rids(pp.gates.rbegin(), pp.gates.rend());
             const std::vector<SubPlan> subs = plan_subpasses(local_ops(inv, rids, c, pp.S, true), L, t, l, true);
             for (const SubPlan& sp : subs) {
@@ -812,7 +812,7 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
                 dev_phases<R>(sp, td, ph, ops, ctl, d2m, &grad, &slots);
                 jit_params<R>(ph.data(), (int)ph.size(), ops.data(), d2m.data(), par, false);
                 out.push_back(jit_source<R>(ph.data(), (int)ph.size(), ops.data(), ctl.data(), d2m.data(), false,
-                                            false, par, grad.data()));
+                                            false, td.l, par, grad.data()));
             }
         }
         return SV_OK;
@@ -842,7 +842,8 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
             const Phase* ph = dp.phases.data() + dp.ph_off[i];
             jit_params<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.d2m.data(), par);
             out.push_back(jit_source<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.ctl.data(), dp.d2m.data(),
-                                        i == 0 && dp.fuse_decode, i + 1 == dp.td.size() && dp.fuse_encode, par));
+                                        i == 0 && dp.fuse_decode, i + 1 == dp.td.size() && dp.fuse_encode,
+                                        dp.td[i].l, par));
         }
     }
     return SV_OK;

@@ -44,12 +44,14 @@ namespace sv {
 struct JitFn {
     CUmodule mod = nullptr;
     CUfunction fn = nullptr;
+    int lrow = 0;  // low bits of the tile rows the kernel was generated for
 };
 
 namespace {
 
 constexpr size_t kMaxParamBytes = 24576;  // by-value parameter block cap (CUDA allows 32764 bytes in all)
 constexpr int kJitThreads = 256;
+constexpr size_t kKeyHeader = 5;  // key bytes: sizeof(R), dec, enc, mode, row bits
 
 // slot of tile offset x in the padded shared-memory layout (tile::PadLayout)
 uint32_t pad_slot(uint32_t x) { return x + (x >> 4) + (x >> 8); }
@@ -747,13 +749,14 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
 
 template <typename R>
 void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
-             bool dec, bool enc, std::string& key, const int32_t* grad)
+             bool dec, bool enc, int lrow, std::string& key, const int32_t* grad)
 {
     size_t pb = 0;
     key.clear();
     auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
-    const uint8_t hdr[4] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, (uint8_t)(grad ? 2 : 1)};
-    put(hdr, 4);
+    const uint8_t hdr[kKeyHeader] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, (uint8_t)(grad ? 2 : 1),
+                                     (uint8_t)lrow};
+    put(hdr, kKeyHeader);
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
         put(P.tpos, sizeof P.tpos);
@@ -792,7 +795,7 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
 
 template <typename R>
 std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, const std::vector<R>& params, const int32_t* grad)
+                       bool enc, int lrow, const std::vector<R>& params, const int32_t* grad)
 {
     (void)d2m;
     Gen<R> g(params);
@@ -902,12 +905,12 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
             << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
-            << "tile::load_plain<T, R, tile::PadLayout, 5>(s, amps, rt, td, base);\n"
-            << "tile::load_plain<T, R, tile::PadLayout, 5>(sl, lam, rt, td, base);\n"
+            << "tile::load_plain<T, R, tile::PadLayout, " << lrow << ">(s, amps, rt, td, base);\n"
+            << "tile::load_plain<T, R, tile::PadLayout, " << lrow << ">(sl, lam, rt, td, base);\n"
             << "__syncthreads();\n"
             << body.str()
-            << "tile::store_plain<T, R, tile::PadLayout, 5>(s, amps, rt, td, base);\n"
-            << "tile::store_plain<T, R, tile::PadLayout, 5>(sl, lam, rt, td, base);\n"
+            << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(s, amps, rt, td, base);\n"
+            << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(sl, lam, rt, td, base);\n"
             << "}\n__syncthreads();\n"
             << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) {\n"
             << "double v = 0.0;\nfor (int w = 0; w < 8; w++) v += (double)gw[k * 8 + w];\n"
@@ -918,7 +921,7 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     const bool pf = prefetches(dec, sizeof(R));
     // rows of the tile: whole codec block pairs (8 low bits) in a sub-pass that
     // decodes or encodes, 32 amplitudes (5) otherwise
-    const std::string lb = (dec || enc) ? "8" : "5";
+    const std::string lb = std::to_string(lrow);
     std::ostringstream src;
     src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
         << "typedef " << RName<R>::r << " R;\ntypedef " << RName<R>::t << " T;\n"
@@ -1023,6 +1026,7 @@ bool jit_compile(const std::vector<std::string>& keys, const std::function<std::
     const int smem_max = (int)std::max(tile_bytes + sizeof(uint32_t) * 2 * 264 * (kJitThreads / 32), 2 * tile_bytes);
     for (Job& j : jobs) {
         auto fn = std::make_unique<JitFn>();
+        fn->lrow = (uint8_t)j.key[prefix.size() + kKeyHeader - 1];
         if (!j.src->empty()) {
             if (!j.ok) {
                 err = "NVRTC compilation failed: " + j.log.substr(0, 2000);
@@ -1057,7 +1061,7 @@ template <typename R>
 cudaError_t jit_launch_adjoint(const JitFn* fn, void* psi, void* lam, const TileDesc& td, uint64_t gbase,
                                double* gpart, const std::vector<R>& params, cudaStream_t st, unsigned* grid_out)
 {
-    if (!fn || td.t != kPhaseTileQubits || td.l != 5 || params.empty()) return cudaErrorInvalidValue;
+    if (!fn || td.t != kPhaseTileQubits || td.l != fn->lrow || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = jit_grid(ntiles);
     if (grid_out) *grid_out = grid;
@@ -1076,9 +1080,8 @@ template <typename R>
 cudaError_t jit_launch(const JitFn* fn, void* amps, const TileDesc& td, uint64_t gbase, const FuseArgs& fa,
                        const std::vector<R>& params, cudaStream_t st)
 {
-    // the kernel was generated for rows of 8 low bits when it decodes or encodes, 5 otherwise
-    if (!fn || td.t != kPhaseTileQubits || td.l != ((fa.decode || fa.encode) ? 8 : 5) || params.empty())
-        return cudaErrorInvalidValue;
+    // the kernel was generated for the tile rows of its sub-pass (8 low bits when it decodes or encodes)
+    if (!fn || td.t != kPhaseTileQubits || td.l != fn->lrow || params.empty()) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (td.L - kPhaseTileQubits);
     const unsigned grid = jit_grid(ntiles);
     const size_t smem = (sizeof(R) * 2 * tile_pad_elems() * (prefetches(fa.decode != 0, sizeof(R)) ? 2 : 1)) +
@@ -1096,13 +1099,13 @@ template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const 
 template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&,
                                  bool);
 template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const std::vector<float>&,
-                             bool, bool, std::string&, const int32_t*);
+                             bool, bool, int, std::string&, const int32_t*);
 template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const std::vector<double>&,
-                              bool, bool, std::string&, const int32_t*);
+                              bool, bool, int, std::string&, const int32_t*);
 template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
-                                       bool, const std::vector<float>&, const int32_t*);
+                                       bool, int, const std::vector<float>&, const int32_t*);
 template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,
-                                        bool, bool, const std::vector<double>&, const int32_t*);
+                                        bool, bool, int, const std::vector<double>&, const int32_t*);
 template cudaError_t jit_launch<float>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
                                        const std::vector<float>&, cudaStream_t);
 template cudaError_t jit_launch_adjoint<float>(const JitFn*, void*, void*, const TileDesc&, uint64_t, double*,

@@ -355,6 +355,34 @@ std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, i
     return subs;
 }
 
+bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bool keep_first)
+{
+    const uint64_t want = (last_l >= 64) ? ~0ull : ((1ull << last_l) - 1);
+    if (subs.empty() || (subs.back().T & want) == want) return !subs.empty();
+    const size_t kmax = std::min<size_t>(3, subs.size() - (keep_first ? 1 : 0));
+    for (size_t k = 1; k <= kmax; k++) {
+        // the last k sub-passes' ops, in the planned order, backwards
+        std::vector<HOp> rev;
+        for (size_t i = subs.size() - k; i < subs.size(); i++)
+            for (const HOp& o : subs[i].ops) rev.push_back(o);
+        std::reverse(rev.begin(), rev.end());
+        std::vector<SubPlan> alt = plan_subpasses(rev, L, t, l, false, last_l);
+        if (alt.empty() || alt.size() > k) continue;
+        std::reverse(alt.begin(), alt.end());
+        for (SubPlan& sp : alt) {
+            std::reverse(sp.ops.begin(), sp.ops.end());
+            std::vector<HOp> fused;
+            for (const HOp& o : sp.ops)
+                if (fused.empty() || !try_fuse(fused.back(), o)) fused.push_back(o);
+            sp.ops.swap(fused);
+        }
+        subs.resize(subs.size() - k);
+        for (SubPlan& sp : alt) subs.push_back(std::move(sp));
+        return true;
+    }
+    return false;
+}
+
 TileDesc tile_desc(uint64_t T, int L, int t, int l)
 {
     TileDesc td{};

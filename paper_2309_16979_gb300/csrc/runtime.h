@@ -71,6 +71,14 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
 // first_l > 0: the first sub-pass's tile must contain local bits 0..first_l-1.
 std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l = 0);
 
+// Make the last tile contain local bits 0..last_l-1 without adding a
+// sub-pass: the ops of the last k <= 3 sub-passes (a suffix of the planned
+// order) are planned again backwards, the first tile of that backward plan
+// required to hold the bits (reversing a sequence keeps which ops commute),
+// and put back in forward order. keep_first: leave subs[0] unchanged.
+// Returns whether the last tile holds the bits.
+bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bool keep_first);
+
 // Tile descriptor and device ops of one sub-pass.
 TileDesc tile_desc(uint64_t T, int L, int t, int l);
 template <typename R>

@@ -60,6 +60,11 @@ enum : int { kErrCorrupt = 1, kErrRange = 2 };
 // them; phases exchange amplitudes through shared memory.
 constexpr int kPhaseTileQubits = 12;
 constexpr int kPhaseRegBits = 4;
+// Local qubits 0..3 are in every tile: a tile is 256 rows of 16 contiguous
+// amplitudes (128 B of complex64, one full line per row), which leaves 8 of
+// the 12 tile qubits to the planner. Sub-passes that fuse the codec take
+// rows of 256 (whole block pairs).
+constexpr int kTileLowQubits = 4;
 
 constexpr int kMaxTileQubits = 13;
 constexpr int kMaxLocalQubits = 48;

@@ -24,7 +24,7 @@ namespace tile {
 constexpr int kThreads = 256;
 constexpr int kT = kPhaseTileQubits;  // 12
 constexpr int kN = 1 << kT;           // 4096 amplitudes per tile
-constexpr int kLowBits = 5;           // rows of at least 32 contiguous amplitudes
+constexpr int kMinLowBits = kTileLowQubits;  // rows of at least 16 contiguous amplitudes
 constexpr int kCodecWords = 2 * 264;  // per-warp codec staging (decode payload / encode packing)
 
 template <typename R> struct V2;
@@ -60,7 +60,7 @@ static_assert(kPadElems == 4368, "padded tile buffer");
 // Per-CTA tables: local offset of each tile row, and the bit of each local
 // position outside the tile (tile index bit i -> local bit opos[i]).
 struct Rows {
-    uint64_t rowoff[1 << (kT - kLowBits)];
+    uint64_t rowoff[1 << (kT - kMinLowBits)];
     uint64_t opos[kMaxLocalQubits];
 };
 
