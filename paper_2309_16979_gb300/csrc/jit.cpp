@@ -25,6 +25,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <map>
 #include <atomic>
 #include <chrono>
 #include <complex>
@@ -163,10 +164,137 @@ struct Gen {
     };
     std::vector<Pend> pend;
     int nvec = 1;  // 2 in an adjoint sub-pass: psi in r/q, lambda in u/w, same ops on both
+    // Complex64: two register updates with the same coefficients run as one
+    // packed FP32x2 instruction each (half the issue slots); pk_order: the
+    // register bits to pair amplitudes along, least used by the phase first
+    // (when one vector is packed).
+    bool pack = false;
+    int pk_order[4] = {0, 1, 2, 3};
     explicit Gen(const std::vector<R>& p) : par(p) {}
     std::string rv(int m, int v = 0) const { return (v ? "u" : "r") + std::to_string(slot[m]); }
     std::string iv(int m, int v = 0) const { return (v ? "w" : "q") + std::to_string(slot[m]); }
 };
+
+// One register update as the generated code writes it: local copies of its
+// inputs, then each output variable as a sum over those copies.
+struct Blk {
+    int i = 0, v = 0;  // register index (the op's loop index) and vector
+    std::vector<std::pair<std::string, std::string>> in;  // local name, variable
+    std::vector<std::pair<std::string, Sum>> out;         // variable, value
+    std::string sig() const
+    {
+        std::string k;
+        for (const auto& x : in) k += x.first + ",";
+        for (const auto& x : out) k += x.second.str() + ";";
+        return k;
+    }
+};
+
+// Packed form of a sum: the first plain positive term (else a product) starts
+// it, the others follow as packed multiply-adds / adds; kp collects the
+// coefficient pairs (the same value in both halves) it needs.
+std::string packed_sum(const Sum& s, std::map<std::string, std::string>& kp, int& tmp)
+{
+    auto K = [&](int sg, const std::string& c) {
+        const std::string e = c.empty() ? (sg < 0 ? "-1.0f" : "1.0f") : (sg < 0 ? "-" + c : c);
+        auto it = kp.find(e);
+        if (it != kp.end()) return it->second;
+        const std::string name = "k" + std::to_string(tmp++);
+        kp[e] = name;
+        return name;
+    };
+    if (s.t.empty()) return "make_float2(0.0f, 0.0f)";
+    std::vector<Sum::Term> t = s.t;
+    for (size_t k = 0; k < t.size(); k++)
+        if (t[k].coef.empty() && t[k].sign > 0) {
+            std::rotate(t.begin(), t.begin() + (long)k, t.begin() + (long)k + 1);
+            break;
+        }
+    std::string acc = (t[0].coef.empty() && t[0].sign > 0) ? t[0].var
+                                                            : "__fmul2_rn(" + K(t[0].sign, t[0].coef) + ", " + t[0].var + ")";
+    for (size_t k = 1; k < t.size(); k++) {
+        if (t[k].coef.empty() && t[k].sign > 0) acc = "__fadd2_rn(" + acc + ", " + t[k].var + ")";
+        else acc = "__ffma2_rn(" + K(t[k].sign, t[k].coef) + ", " + t[k].var + ", " + acc + ")";
+    }
+    return acc;
+}
+
+// Print an op's register updates: in pairs of identical updates as packed
+// instructions where the generator packs (psi with lambda in an adjoint
+// sub-pass, else registers that differ in one bit the op does not touch),
+// the rest one by one.
+template <typename R>
+void flush(Gen<R>& g, std::vector<Blk>& bl)
+{
+    std::vector<int> mate(bl.size(), -1);
+    if (g.pack) {
+        std::vector<std::string> sg(bl.size());
+        for (size_t a = 0; a < bl.size(); a++) sg[a] = bl[a].sig();
+        auto find = [&](int i, int v, const std::string& k) {
+            for (size_t c = 0; c < bl.size(); c++)
+                if (bl[c].i == i && bl[c].v == v && sg[c] == k) return (int)c;
+            return -1;
+        };
+        if (g.nvec == 2) {
+            for (size_t a = 0; a < bl.size(); a++)
+                if (bl[a].v == 0 && mate[a] < 0) {
+                    const int c = find(bl[a].i, 1, sg[a]);
+                    if (c >= 0 && mate[c] < 0) {
+                        mate[a] = c;
+                        mate[c] = (int)a;
+                    }
+                }
+        } else {
+            int best = -1, bestn = 0;
+            for (int q = 0; q < 4; q++) {
+                const int b = g.pk_order[q];
+                int n = 0;
+                for (size_t a = 0; a < bl.size(); a++)
+                    if (find(bl[a].i ^ (1 << b), bl[a].v, sg[a]) >= 0) n++;
+                if (n > bestn) {
+                    bestn = n;
+                    best = b;
+                }
+            }
+            for (size_t a = 0; best >= 0 && a < bl.size(); a++) {
+                if (mate[a] >= 0 || (bl[a].i >> best) & 1) continue;
+                const int c = find(bl[a].i ^ (1 << best), bl[a].v, sg[a]);
+                if (c >= 0 && mate[c] < 0) {
+                    mate[a] = c;
+                    mate[c] = (int)a;
+                }
+            }
+        }
+    }
+    std::map<std::string, std::string> kp;
+    std::ostringstream body;
+    for (size_t a = 0; a < bl.size(); a++) {
+        const Blk& A = bl[a];
+        if (mate[a] < 0) {
+            body << "{ const R ";
+            for (size_t k = 0; k < A.in.size(); k++) body << (k ? ", " : "") << A.in[k].first << " = " << A.in[k].second;
+            body << "; ";
+            for (const auto& x : A.out) body << x.first << " = " << x.second.str() << "; ";
+            body << "}\n";
+            continue;
+        }
+        if (mate[a] < (int)a) continue;
+        const Blk& B = bl[mate[a]];
+        body << "{ const float2 ";
+        for (size_t k = 0; k < A.in.size(); k++)
+            body << (k ? ", " : "") << A.in[k].first << " = make_float2(" << A.in[k].second << ", " << B.in[k].second
+                 << ")";
+        body << "; ";
+        for (size_t k = 0; k < A.out.size(); k++)
+            body << "const float2 o" << k << " = " << packed_sum(A.out[k].second, kp, g.tmp) << "; ";
+        for (size_t k = 0; k < A.out.size(); k++)
+            body << A.out[k].first << " = o" << k << ".x; " << B.out[k].first << " = o" << k << ".y; ";
+        body << "}\n";
+    }
+    for (const auto& x : kp) g.o << "const float2 " << x.second << " = make_float2(" << x.first << ", " << x.first << ");\n";
+    g.o << body.str();
+    bl.clear();
+}
 
 // Coefficient chosen at run time by `sel` (0..n-1) among candidates whose
 // parts sit at params[pidx[k]], params[pidx[k] + 1].
@@ -318,14 +446,19 @@ std::string flip_sel(const std::vector<typename Gen<R>::Pend>& conj)
 
 // register m *= e
 template <typename R>
-void mul_reg(Gen<R>& g, int m, const Coef& e)
+void mul_reg(Gen<R>& g, std::vector<Blk>& bl, int m, const Coef& e)
 {
     if (e.cls == C_ONE) return;
     Sum re, im;
     cmac(re, im, e, "xr", "xi");
-    for (int v = 0; v < g.nvec; v++)
-        g.o << "{ const R xr = " << g.rv(m, v) << ", xi = " << g.iv(m, v) << "; " << g.rv(m, v) << " = " << re.str()
-            << "; " << g.iv(m, v) << " = " << im.str() << "; }\n";
+    for (int v = 0; v < g.nvec; v++) {
+        Blk b;
+        b.i = m;
+        b.v = v;
+        b.in = {{"xr", g.rv(m, v)}, {"xi", g.iv(m, v)}};
+        b.out = {{g.rv(m, v), re}, {g.iv(m, v), im}};
+        bl.push_back(std::move(b));
+    }
 }
 
 template <typename R>
@@ -369,6 +502,7 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
         for (int k = 0; k < 4; k++) e[k] = select_coef(g, sel, {pb + 2 * (size_t)k, pb + 2 * (size_t)(k ^ 3)});
     }
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    std::vector<Blk> bl;
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
         const int j = i | (1 << b);
@@ -377,12 +511,16 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
         cmac(xr, xi, e[1], "yr", "yi");
         cmac(yr, yi, e[2], "xr", "xi");
         cmac(yr, yi, e[3], "yr", "yi");
-        for (int v = 0; v < g.nvec; v++)
-            g.o << "{ const R xr = " << g.rv(i, v) << ", xi = " << g.iv(i, v) << ", yr = " << g.rv(j, v)
-                << ", yi = " << g.iv(j, v) << "; " << g.rv(i, v) << " = " << xr.str() << "; " << g.iv(i, v) << " = "
-                << xi.str() << "; " << g.rv(j, v) << " = " << yr.str() << "; " << g.iv(j, v) << " = " << yi.str()
-                << "; }\n";
+        for (int v = 0; v < g.nvec; v++) {
+            Blk k;
+            k.i = i;
+            k.v = v;
+            k.in = {{"xr", g.rv(i, v)}, {"xi", g.iv(i, v)}, {"yr", g.rv(j, v)}, {"yi", g.iv(j, v)}};
+            k.out = {{g.rv(i, v), xr}, {g.iv(i, v), xi}, {g.rv(j, v), yr}, {g.iv(j, v), yi}};
+            bl.push_back(std::move(k));
+        }
     }
+    flush(g, bl);
     if (!cond.empty()) g.o << "}\n";
 }
 
@@ -412,10 +550,12 @@ void emit_diag2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, int b1, cons
         e[v] = select_coef(g, sel, cand);
     }
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    std::vector<Blk> bl;
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
-        mul_reg(g, i, e[((i >> b0) & 1) | (((i >> b1) & 1) << 1)]);
+        mul_reg(g, bl, i, e[((i >> b0) & 1) | (((i >> b1) & 1) << 1)]);
     }
+    flush(g, bl);
     if (!cond.empty()) g.o << "}\n";
 }
 
@@ -442,10 +582,12 @@ void emit_diag1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b0, const std::s
                                  pb + 2 * (size_t)entry(rb ^ 1, 0), pb + 2 * (size_t)entry(rb ^ 1, 1)});
         }
     }
+    std::vector<Blk> bl;
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
-        mul_reg(g, i, e[(i >> b0) & 1]);
+        mul_reg(g, bl, i, e[(i >> b0) & 1]);
     }
+    flush(g, bl);
     if (!cond.empty()) g.o << "}\n";
 }
 
@@ -459,8 +601,10 @@ void emit_diagt(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& c
     else if (c1.empty()) e = select_coef(g, c0, {pb, pb + 2});
     else if (c0.empty()) e = select_coef(g, c1, {pb, pb + 4});
     else e = select_coef(g, "(" + c0 + " | (" + c1 + " << 1))", {pb, pb + 2, pb + 4, pb + 6});
+    std::vector<Blk> bl;
     for (int i = 0; i < 16; i++)
-        if ((op.amask >> i) & 1u) mul_reg(g, i, e);
+        if ((op.amask >> i) & 1u) mul_reg(g, bl, i, e);
+    flush(g, bl);
     if (!cond.empty()) g.o << "}\n";
 }
 
@@ -471,24 +615,30 @@ void emit_dense2(Gen<R>& g, const PhaseOp<R>& op, size_t pb, const std::string& 
     Coef e[16];
     for (int k = 0; k < 16; k++) e[k] = fixed_coef<R>(g.par[pb + 2 * k], g.par[pb + 2 * k + 1], pb + 2 * k);
     if (!cond.empty()) g.o << "if (" << cond << ") {\n";
+    std::vector<Blk> bl;
     for (int i = 0; i < 16; i++) {
         if (!((op.amask >> i) & 1u)) continue;
         int idx[4];
         for (int k = 0; k < 4; k++) idx[k] = i | ((k & 1) << b0) | (((k >> 1) & 1) << b1);
         for (int vv = 0; vv < g.nvec; vv++) {
-            g.o << "{ ";
-            for (int k = 0; k < 4; k++)
-                g.o << "const R v" << k << "r = " << g.rv(idx[k], vv) << ", v" << k << "i = " << g.iv(idx[k], vv)
-                    << "; ";
+            Blk bk;
+            bk.i = i;
+            bk.v = vv;
+            for (int k = 0; k < 4; k++) {
+                bk.in.push_back({"v" + std::to_string(k) + "r", g.rv(idx[k], vv)});
+                bk.in.push_back({"v" + std::to_string(k) + "i", g.iv(idx[k], vv)});
+            }
             for (int r = 0; r < 4; r++) {
                 Sum re, im;
                 for (int k = 0; k < 4; k++)
                     cmac(re, im, e[4 * r + k], "v" + std::to_string(k) + "r", "v" + std::to_string(k) + "i");
-                g.o << g.rv(idx[r], vv) << " = " << re.str() << "; " << g.iv(idx[r], vv) << " = " << im.str() << "; ";
+                bk.out.push_back({g.rv(idx[r], vv), re});
+                bk.out.push_back({g.iv(idx[r], vv), im});
             }
-            g.o << "}\n";
+            bl.push_back(std::move(bk));
         }
     }
+    flush(g, bl);
     if (!cond.empty()) g.o << "}\n";
 }
 
@@ -814,6 +964,19 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
                   std::to_string(P.tpos[j]) + ")";
         }
         for (int m = 0; m < 16; m++) g.slot[m] = m;
+        // packing pays in adjoint sub-passes (psi and lambda updates pair up
+        // as they are); pairing registers of one vector costs as many register
+        // moves and split shared loads as it saves multiply-adds
+        g.pack = sizeof(R) == 4 && adj;
+        {
+            // pair registers along the bits the phase's ops touch least
+            int use[4] = {0, 0, 0, 0};
+            for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++)
+                for (int b = 0; b < 4; b++)
+                    if (!symmetric(ops[oi], b)) use[b]++;
+            for (int q = 0; q < 4; q++) g.pk_order[q] = q;
+            std::stable_sort(g.pk_order, g.pk_order + 4, [&](int a, int b) { return use[a] < use[b]; });
+        }
         // padded slot of register index m relative to the thread's base
         uint32_t K[16];
         for (int m = 0; m < 16; m++) {

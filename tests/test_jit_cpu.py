@@ -3,6 +3,7 @@ generator's sources compile with NVRTC for sm_103a, depend on the circuit's
 structure and not on its rotation angles, and fold thread-conditional
 exchanges into the phase's store addresses. No GPU is used."""
 import ctypes
+import dataclasses
 import os
 
 import pytest
@@ -101,8 +102,15 @@ def test_generated_adjoint_kernels_compile(jit_sources, dtype):
     gradient accumulation per parameterised gate."""
     lib = _nvrtc()
     gates, nparams = W.hea(14, 2)
+    theta = W.normal_params(nparams)
+    gates = [dataclasses.replace(g, theta=theta[g.param]) if g.param >= 0 else g for g in gates]
     srcs = [s for s in jit_sources(14, 9, gates, dtype=dtype, max_group_qubits=3, adjoint=True) if s]
     assert srcs
     assert sum(s.count("gw[") for s in srcs) - 3 * len(srcs) == nparams
-    rc, log = _compile(lib, srcs[0])
-    assert rc == 0, log
+    # complex64: psi's and lambda's updates share coefficients and run as
+    # packed FP32x2 instructions; complex128 has no packed form
+    packed = sum(s.count("__ffma2_rn(") + s.count("__fadd2_rn(") for s in srcs)
+    assert (packed > 0) == (dtype == "c64")
+    for s in srcs:
+        rc, log = _compile(lib, s)
+        assert rc == 0, log
