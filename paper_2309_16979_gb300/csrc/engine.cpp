@@ -260,7 +260,7 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
             const Phase* ph = dp->phases.data() + dp->ph_off[i];
             jit_params<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->d2m.data(), dp->jpar[i]);
             std::string key;
-            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->jpar[i], dec, enc, dp->td[i].l, key);
+            jit_key<R>(ph, dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(), dp->jpar[i], dec, enc, dp->td[i], key);
             keys.push_back(std::move(key));
             where.push_back({dp, i});
         }
@@ -271,7 +271,7 @@ static int jit_prepare(sv_state* s, const std::vector<DevPass<R>*>& dps)
         const size_t i = where[k].second;
         return jit_source<R>(dp->phases.data() + dp->ph_off[i], dp->ph_cnt[i], dp->pops.data(), dp->ctl.data(),
                              dp->d2m.data(), i == 0 && dp->fuse_decode, i + 1 == dp->td.size() && dp->fuse_encode,
-                             dp->td[i].l, dp->jpar[i]);
+                             dp->td[i], dp->jpar[i]);
     };
     std::vector<const JitFn*> fns;
     std::string err;
@@ -370,11 +370,11 @@ static int jit_adjoint_plan(sv_state* s, const std::vector<SubPlan>& subs, int L
         ap.par.emplace_back();
         jit_params<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].d2m.data(), ap.par.back(), false);
         jit_key<R>(sv[i].ph.data(), (int)sv[i].ph.size(), sv[i].ops.data(), sv[i].ctl.data(), ap.par.back(), false,
-                   false, td.l, keys[i], sv[i].grad.data());
+                   false, td, keys[i], sv[i].grad.data());
     }
     auto source_of = [&](size_t k) {
         return jit_source<R>(sv[k].ph.data(), (int)sv[k].ph.size(), sv[k].ops.data(), sv[k].ctl.data(),
-                             sv[k].d2m.data(), false, false, ap.td[k].l, ap.par[k], sv[k].grad.data());
+                             sv[k].d2m.data(), false, false, ap.td[k], ap.par[k], sv[k].grad.data());
     };
     std::string err;
     JitReport rep;
@@ -812,7 +812,7 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
                 dev_phases<R>(sp, td, ph, ops, ctl, d2m, &grad, &slots);
                 jit_params<R>(ph.data(), (int)ph.size(), ops.data(), d2m.data(), par, false);
                 out.push_back(jit_source<R>(ph.data(), (int)ph.size(), ops.data(), ctl.data(), d2m.data(), false,
-                                            false, td.l, par, grad.data()));
+                                            false, td, par, grad.data()));
             }
         }
         return SV_OK;
@@ -843,7 +843,7 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
             jit_params<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.d2m.data(), par);
             out.push_back(jit_source<R>(ph, dp.ph_cnt[i], dp.pops.data(), dp.ctl.data(), dp.d2m.data(),
                                         i == 0 && dp.fuse_decode, i + 1 == dp.td.size() && dp.fuse_encode,
-                                        dp.td[i].l, par));
+                                        dp.td[i], par));
         }
     }
     return SV_OK;

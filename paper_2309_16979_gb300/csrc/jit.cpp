@@ -897,16 +897,27 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
     if (params.empty()) params.push_back((R)0);
 }
 
+// The last phase of a forward sub-pass that does not encode stores its
+// registers straight to HBM (no shared-memory round trip) when its thread
+// bits 0 and 1 are tile bits 0 and 1: four consecutive lanes then write one
+// whole 32-byte sector (complex64).
+bool direct_store(const Phase* ph, int nph, bool enc, bool adj)
+{
+    return !enc && !adj && nph > 0 && ph[nph - 1].tpos[0] == 0 && ph[nph - 1].tpos[1] == 1;
+}
+
 template <typename R>
 void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
-             bool dec, bool enc, int lrow, std::string& key, const int32_t* grad)
+             bool dec, bool enc, const TileDesc& td, std::string& key, const int32_t* grad)
 {
     size_t pb = 0;
     key.clear();
     auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
     const uint8_t hdr[kKeyHeader] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, (uint8_t)(grad ? 2 : 1),
-                                     (uint8_t)lrow};
+                                     (uint8_t)td.l};
     put(hdr, kKeyHeader);
+    // the direct stores' offsets are compiled in
+    if (direct_store(ph, nph, enc, grad != nullptr)) put(td.hpos, (size_t)(td.t - td.l));
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
         put(P.tpos, sizeof P.tpos);
@@ -945,11 +956,13 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
 
 template <typename R>
 std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, int lrow, const std::vector<R>& params, const int32_t* grad)
+                       bool enc, const TileDesc& td, const std::vector<R>& params, const int32_t* grad)
 {
+    const int lrow = td.l;
     (void)d2m;
     Gen<R> g(params);
     const bool adj = grad != nullptr;
+    const bool ds = direct_store(ph, nph, enc, adj);
     g.nvec = adj ? 2 : 1;
     int nslot = 0;
     std::ostringstream body, hoist;
@@ -1026,10 +1039,43 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             }
             pb += code == kCodeDense2 ? 32 : 8;
         }
+        const size_t np = g.pend.size();
+        if (ds && pi + 1 == nph) {
+            // straight to HBM: tile bit b is local bit b below the rows' width,
+            // hpos[b - l] above; offsets are additive over disjoint bits like
+            // the padded layout, so a pending exchange moves the thread's base
+            auto sh = [&](int b) { return b < lrow ? b : (int)td.hpos[b - lrow]; };
+            std::string gt;
+            for (int j = 0; j < kPhaseTileQubits - kPhaseRegBits; j++)
+                gt += (j ? " | " : "") + std::string("((uint64_t)((threadIdx.x >> ") + std::to_string(j) +
+                      ") & 1u) << " + std::to_string(sh(P.tpos[j])) + ")";
+            hoist << "const uint64_t gth = " << gt << ";\n";
+            g.o << "T* const gq = amps + base + gth;\n";
+            for (size_t j = 0; j < np; j++)
+                g.o << "const int64_t e" << j << " = (" << g.pend[j].cond << ") ? (int64_t)" << hex(1ull << sh(P.rpos[g.pend[j].b]))
+                    << "ll : 0ll;\n";
+            for (uint32_t c = 0; np && c < (1u << np); c++) {
+                g.o << "T* const gq" << c << " = gq";
+                for (size_t j = 0; j < np; j++) g.o << (((c >> j) & 1) ? " - e" : " + e") << j;
+                g.o << ";\n";
+            }
+            for (int m = 0; m < 16; m++) {
+                uint64_t off = 0;
+                uint32_t c = 0;
+                for (int q = 0; q < kPhaseRegBits; q++)
+                    if ((m >> q) & 1) off |= 1ull << sh(P.rpos[q]);
+                for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
+                g.o << (np ? "gq" + std::to_string(c) : std::string("gq")) << "[" << hex(off)
+                    << "ull] = tile::mk2<T, R>(" << g.rv(m, 0) << ", " << g.iv(m, 0) << ");\n";
+            }
+            g.pend.clear();
+            g.o << "}\n";
+            body << g.o.str();
+            continue;
+        }
         // a pending exchange on register bit b sends register m to the slot of
         // m ^ (1 << b), i.e. K[m] +- pad_slot(1 << rpos[b]) (the layout is
         // additive over disjoint bits): one base per sign combination
-        const size_t np = g.pend.size();
         for (size_t j = 0; j < np; j++)
             g.o << "const uint32_t d" << j << " = (" << g.pend[j].cond << ") ? "
                 << pad_slot(1u << P.rpos[g.pend[j].b]) << "u : 0u;\n";
@@ -1116,10 +1162,11 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << ">(s, amps, rt, td, base, fa, cw);\n"
             << "__syncthreads();\n";
     }
-    src << body.str()
-        << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ", tile::PadLayout, " << lb
-        << ">(s + bo, amps, rt, td, base, fa, cw);\n"
-        << "}\n}\n";
+    src << body.str();
+    if (!ds)
+        src << "tile::store_tile<T, R, " << (enc ? "true" : "false") << ", tile::PadLayout, " << lb
+            << ">(s + bo, amps, rt, td, base, fa, cw);\n";
+    src << "}\n}\n";
     return src.str();
 }
 
@@ -1262,13 +1309,13 @@ template void jit_params<float>(const Phase*, int, const PhaseOp<float>*, const 
 template void jit_params<double>(const Phase*, int, const PhaseOp<double>*, const double*, std::vector<double>&,
                                  bool);
 template void jit_key<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const std::vector<float>&,
-                             bool, bool, int, std::string&, const int32_t*);
+                             bool, bool, const TileDesc&, std::string&, const int32_t*);
 template void jit_key<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const std::vector<double>&,
-                              bool, bool, int, std::string&, const int32_t*);
+                              bool, bool, const TileDesc&, std::string&, const int32_t*);
 template std::string jit_source<float>(const Phase*, int, const PhaseOp<float>*, const CtaCtrl*, const float*, bool,
-                                       bool, int, const std::vector<float>&, const int32_t*);
+                                       bool, const TileDesc&, const std::vector<float>&, const int32_t*);
 template std::string jit_source<double>(const Phase*, int, const PhaseOp<double>*, const CtaCtrl*, const double*,
-                                        bool, bool, int, const std::vector<double>&, const int32_t*);
+                                        bool, bool, const TileDesc&, const std::vector<double>&, const int32_t*);
 template cudaError_t jit_launch<float>(const JitFn*, void*, const TileDesc&, uint64_t, const FuseArgs&,
                                        const std::vector<float>&, cudaStream_t);
 template cudaError_t jit_launch_adjoint<float>(const JitFn*, void*, void*, const TileDesc&, uint64_t, double*,

@@ -17,8 +17,9 @@ struct JitFn;  // a loaded kernel (owned by the process-wide cache)
 
 // The kernel for one register-phase sub-pass is described by its phases and
 // ops as dev_phases lays them out, whether it decodes the chunk streams (dec),
-// whether it encodes the block pairs (enc), and the low bits of its tile
-// rows (lrow: TileDesc.l, 4 or 5, 8 with the codec).
+// whether it encodes the block pairs (enc), and its tile (td: the low bits
+// of its rows, td.l, 4, or 8 with the codec; where the last phase stores
+// straight to HBM, the positions of the tile's other bits, td.hpos).
 //
 // jit_params: the kernel's by-value parameter block, the matrix values of its
 // ops in order, 8 per op (32 for a 4x4). Ops that act on every amplitude are
@@ -34,7 +35,7 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
 // +-1, +-i or equal to each other), not on the remaining values.
 template <typename R>
 void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
-             bool dec, bool enc, int lrow, std::string& key, const int32_t* grad = nullptr);
+             bool dec, bool enc, const TileDesc& td, std::string& key, const int32_t* grad = nullptr);
 
 // jit_source: the CUDA C++ source of the kernel, reading `params`. Empty when
 // the sub-pass cannot be specialised (it then runs on the table-driven kernel).
@@ -47,7 +48,7 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
 // built with factor = false (a scalar factored out would scale the partials).
 template <typename R>
 std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const R* d2m, bool dec,
-                       bool enc, int lrow, const std::vector<R>& params, const int32_t* grad = nullptr);
+                       bool enc, const TileDesc& td, const std::vector<R>& params, const int32_t* grad = nullptr);
 
 // Look the kernels of `keys` up in the process-wide cache for `device`;
 // generate (source_of(i)), compile (in parallel) and load the ones missing.

@@ -500,7 +500,13 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
                 bG |= o.qG;
             }
         }
-        for (int b = 0; b < td.t && popc(Rm) < kPhaseRegBits; b++) Rm |= 1u << b;
+        // unused register bits: the lowest tile bits, except in the last phase,
+        // which leaves tile bits 0..3 to thread bits 0..3 (its stores can then
+        // go from registers straight to HBM in whole 32-byte sectors)
+        if (deferred.empty())
+            for (int b = td.t - 1; b >= 0 && popc(Rm) < kPhaseRegBits; b--) Rm |= 1u << b;
+        else
+            for (int b = 0; b < td.t && popc(Rm) < kPhaseRegBits; b++) Rm |= 1u << b;
         Phase ph{};
         int reg_of[32];
         for (int b = 0; b < 32; b++) reg_of[b] = -1;
