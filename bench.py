@@ -276,7 +276,8 @@ def roofline_from_stats(d):
     achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": load_traffic(top, bytes_per_launch),
-            "kernel": f"k_{top}",
+            "kernel": ("svj (generated sub-pass kernels)" if top == "apply" and d.get("jit_launches", 0) > 0
+                       else f"k_{top}"),
             "peak_source": f"{peak_kind} (copy)", "launches": int(d[nk]),
             "avg_launch_ms": round(avg_s * 1e3, 4), "alg_bytes_per_launch": int(bytes_per_launch),
             "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, total), 3) for k, v in kinds.items()}}
@@ -479,6 +480,7 @@ def run_grad(args, rank, world):
     barrier(world)
     clocks = ClockSampler(dev)
     clocks.start()
+    s0 = sim.stats()
     t0 = time.perf_counter()
     results = []
     for i in range(args.steps):
@@ -489,6 +491,7 @@ def run_grad(args, rank, world):
     barrier(world)
     t_max, _ = reduce_max_sum(world, t_local, 1.0, device="cuda")
     st = sim.stats()
+    launches = int(st["kernel_launches"] - s0["kernel_launches"])
     sim.close()
     errors = []
     if not args.no_extras and rank == 0:
@@ -505,7 +508,7 @@ def run_grad(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
             "config": {"workload": describe(w, len(gates)), "n_qubits": n, "params": npar, "gates": len(gates),
                        "parameter_sets": len(thetas), "parallelism": f"replicas x{world}"},
-            "gpu_launches": None, "clocks": clk, "passes_total": st["passes"],
+            "gpu_launches": launches, "clocks": clk, "passes_total": st["passes"],
             "errors_vs_fp64_gpu_adjoint": errors}
 
 
