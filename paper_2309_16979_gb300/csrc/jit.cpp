@@ -170,6 +170,9 @@ struct Gen {
     // (when one vector is packed).
     bool pack = false;
     int pk_order[4] = {0, 1, 2, 3};
+    // complex64 updates with real coefficients only: real and imaginary parts
+    // as one packed pair (decided per phase)
+    bool pack_parts = false;
     explicit Gen(const std::vector<R>& p) : par(p) {}
     std::string rv(int m, int v = 0) const { return (v ? "u" : "r") + std::to_string(slot[m]); }
     std::string iv(int m, int v = 0) const { return (v ? "w" : "q") + std::to_string(slot[m]); }
@@ -217,6 +220,32 @@ std::string packed_sum(const Sum& s, std::map<std::string, std::string>& kp, int
         else acc = "__ffma2_rn(" + K(t[k].sign, t[k].coef) + ", " + t[k].var + ", " + acc + ")";
     }
     return acc;
+}
+
+// Does every output pair (real part, imaginary part) of the update compute
+// the same sum, the real part over real inputs and the imaginary part over
+// the matching imaginary ones (real coefficients only)?
+bool parallel_parts(const Blk& b)
+{
+    if (b.in.size() % 2 || b.out.size() % 2) return false;
+    for (size_t k = 0; k < b.in.size(); k += 2) {
+        const std::string& a = b.in[k].first;
+        const std::string& c = b.in[k + 1].first;
+        if (a.empty() || a.back() != 'r' || c != a.substr(0, a.size() - 1) + "i") return false;
+    }
+    for (size_t k = 0; k < b.out.size(); k += 2) {
+        const Sum& re = b.out[k].second;
+        const Sum& im = b.out[k + 1].second;
+        if (re.t.size() != im.t.size() || re.t.empty()) return false;
+        for (size_t j = 0; j < re.t.size(); j++) {
+            const auto& x = re.t[j];
+            const auto& y = im.t[j];
+            if (x.sign != y.sign || x.coef != y.coef || x.var.empty() || x.var.back() != 'r' ||
+                y.var != x.var.substr(0, x.var.size() - 1) + "i")
+                return false;
+        }
+    }
+    return true;
 }
 
 // Print an op's register updates: in pairs of identical updates as packed
@@ -270,6 +299,25 @@ void flush(Gen<R>& g, std::vector<Blk>& bl)
     std::ostringstream body;
     for (size_t a = 0; a < bl.size(); a++) {
         const Blk& A = bl[a];
+        if (mate[a] < 0 && g.pack_parts && parallel_parts(A)) {
+            // real coefficients only: the real and imaginary parts of each
+            // amplitude see the same sums and run as one packed instruction on
+            // the register pair the shared-memory loads fill anyway
+            body << "{ const float2 ";
+            for (size_t k = 0; k < A.in.size(); k += 2)
+                body << (k ? ", " : "") << A.in[k].first.substr(0, A.in[k].first.size() - 1) << " = make_float2("
+                     << A.in[k].second << ", " << A.in[k + 1].second << ")";
+            body << "; ";
+            for (size_t k = 0; k < A.out.size(); k += 2) {
+                Sum m = A.out[k].second;
+                for (auto& t : m.t) t.var.pop_back();
+                body << "const float2 o" << k / 2 << " = " << packed_sum(m, kp, g.tmp) << "; ";
+            }
+            for (size_t k = 0; k < A.out.size(); k += 2)
+                body << A.out[k].first << " = o" << k / 2 << ".x; " << A.out[k + 1].first << " = o" << k / 2 << ".y; ";
+            body << "}\n";
+            continue;
+        }
         if (mate[a] < 0) {
             body << "{ const R ";
             for (size_t k = 0; k < A.in.size(); k++) body << (k ? ", " : "") << A.in[k].first << " = " << A.in[k].second;
@@ -897,13 +945,13 @@ void jit_params(const Phase* ph, int nph, const PhaseOp<R>* ops, const R* d2m, s
     if (params.empty()) params.push_back((R)0);
 }
 
-// The last phase of a forward sub-pass that does not encode stores its
-// registers straight to HBM (no shared-memory round trip) when its thread
-// bits 0 and 1 are tile bits 0 and 1: four consecutive lanes then write one
-// whole 32-byte sector (complex64).
-bool direct_store(const Phase* ph, int nph, bool enc, bool adj)
+// The last phase of a sub-pass that does not encode stores its registers
+// straight to HBM (no shared-memory round trip) when its thread bits 0 and 1
+// are tile bits 0 and 1: four consecutive lanes then write one whole 32-byte
+// sector (complex64). An adjoint sub-pass stores psi and lambda so.
+bool direct_store(const Phase* ph, int nph, bool enc)
 {
-    return !enc && !adj && nph > 0 && ph[nph - 1].tpos[0] == 0 && ph[nph - 1].tpos[1] == 1;
+    return !enc && nph > 0 && ph[nph - 1].tpos[0] == 0 && ph[nph - 1].tpos[1] == 1;
 }
 
 template <typename R>
@@ -917,7 +965,7 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
                                      (uint8_t)td.l};
     put(hdr, kKeyHeader);
     // the direct stores' offsets are compiled in
-    if (direct_store(ph, nph, enc, grad != nullptr)) put(td.hpos, (size_t)(td.t - td.l));
+    if (direct_store(ph, nph, enc)) put(td.hpos, (size_t)(td.t - td.l));
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
         put(P.tpos, sizeof P.tpos);
@@ -962,7 +1010,7 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     (void)d2m;
     Gen<R> g(params);
     const bool adj = grad != nullptr;
-    const bool ds = direct_store(ph, nph, enc, adj);
+    const bool ds = direct_store(ph, nph, enc);
     g.nvec = adj ? 2 : 1;
     int nslot = 0;
     std::ostringstream body, hoist;
@@ -989,6 +1037,19 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
                     if (!symmetric(ops[oi], b)) use[b]++;
             for (int q = 0; q < 4; q++) g.pk_order[q] = q;
             std::stable_sort(g.pk_order, g.pk_order + 4, [&](int a, int b) { return use[a] < use[b]; });
+        }
+        {
+            // pairing real and imaginary parts pays where real 2x2 gates (H,
+            // RY) outnumber complex diagonals in the phase; measured: -4 % on
+            // random layers, +8 % on QFT (mostly controlled phases) when
+            // always on
+            int nreal = 0, ndiag = 0;
+            for (int oi = P.op_begin; oi < P.op_begin + P.op_count; oi++) {
+                const uint32_t code = ops[oi].code;
+                if (code < kCodeDiag2 && code / 8 == PK_REAL) nreal++;
+                else if (code < kCodeDense2 && !(code < kCodeDiag2 && code / 8 != PK_DIAG1)) ndiag++;
+            }
+            g.pack_parts = sizeof(R) == 4 && nreal > 0 && nreal >= ndiag;
         }
         // padded slot of register index m relative to the thread's base
         uint32_t K[16];
@@ -1050,23 +1111,26 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
                 gt += (j ? " | " : "") + std::string("((uint64_t)((threadIdx.x >> ") + std::to_string(j) +
                       ") & 1u) << " + std::to_string(sh(P.tpos[j])) + ")";
             hoist << "const uint64_t gth = " << gt << ";\n";
-            g.o << "T* const gq = amps + base + gth;\n";
             for (size_t j = 0; j < np; j++)
                 g.o << "const int64_t e" << j << " = (" << g.pend[j].cond << ") ? (int64_t)" << hex(1ull << sh(P.rpos[g.pend[j].b]))
                     << "ll : 0ll;\n";
-            for (uint32_t c = 0; np && c < (1u << np); c++) {
-                g.o << "T* const gq" << c << " = gq";
-                for (size_t j = 0; j < np; j++) g.o << (((c >> j) & 1) ? " - e" : " + e") << j;
-                g.o << ";\n";
-            }
-            for (int m = 0; m < 16; m++) {
-                uint64_t off = 0;
-                uint32_t c = 0;
-                for (int q = 0; q < kPhaseRegBits; q++)
-                    if ((m >> q) & 1) off |= 1ull << sh(P.rpos[q]);
-                for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
-                g.o << (np ? "gq" + std::to_string(c) : std::string("gq")) << "[" << hex(off)
-                    << "ull] = tile::mk2<T, R>(" << g.rv(m, 0) << ", " << g.iv(m, 0) << ");\n";
+            for (int v = 0; v < g.nvec; v++) {
+                const std::string gp = v ? "gl" : "gq";
+                g.o << "T* const " << gp << " = " << (v ? "lam" : "amps") << " + base + gth;\n";
+                for (uint32_t c = 0; np && c < (1u << np); c++) {
+                    g.o << "T* const " << gp << c << " = " << gp;
+                    for (size_t j = 0; j < np; j++) g.o << (((c >> j) & 1) ? " - e" : " + e") << j;
+                    g.o << ";\n";
+                }
+                for (int m = 0; m < 16; m++) {
+                    uint64_t off = 0;
+                    uint32_t c = 0;
+                    for (int q = 0; q < kPhaseRegBits; q++)
+                        if ((m >> q) & 1) off |= 1ull << sh(P.rpos[q]);
+                    for (size_t j = 0; j < np; j++) c |= (uint32_t)((m >> g.pend[j].b) & 1) << j;
+                    g.o << (np ? gp + std::to_string(c) : gp) << "[" << hex(off) << "ull] = tile::mk2<T, R>("
+                        << g.rv(m, v) << ", " << g.iv(m, v) << ");\n";
+                }
             }
             g.pend.clear();
             g.o << "}\n";
@@ -1117,10 +1181,11 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
             << "tile::load_plain<T, R, tile::PadLayout, " << lrow << ">(s, amps, rt, td, base);\n"
             << "tile::load_plain<T, R, tile::PadLayout, " << lrow << ">(sl, lam, rt, td, base);\n"
             << "__syncthreads();\n"
-            << body.str()
-            << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(s, amps, rt, td, base);\n"
-            << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(sl, lam, rt, td, base);\n"
-            << "}\n__syncthreads();\n"
+            << body.str();
+        if (!ds)
+            src << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(s, amps, rt, td, base);\n"
+                << "tile::store_plain<T, R, tile::PadLayout, " << lrow << ">(sl, lam, rt, td, base);\n";
+        src << "}\n__syncthreads();\n"
             << "for (int k = threadIdx.x; k < " << nslot << "; k += blockDim.x) {\n"
             << "double v = 0.0;\nfor (int w = 0; w < 8; w++) v += (double)gw[k * 8 + w];\n"
             << "gpart[(uint64_t)k * gridDim.x + blockIdx.x] = v;\n}\n"
