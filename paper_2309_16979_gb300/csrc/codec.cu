@@ -176,25 +176,48 @@ k_encode_scan(uint8_t* __restrict__ out, size_t stride, int c, int dtype, int k,
     }
 }
 
-// One warp per block: move the block's 8*w packed words to payload + offset[b].
+// Move each block's 8*w packed words to payload + offset[b]. One warp per
+// kBlocksPerWarp consecutive blocks of a chunk (fewer when the chunk has
+// fewer): their widths and offsets are read at once and every payload load
+// is in flight before the first store (a warp per block left the copy
+// waiting on memory latency).
+constexpr int kBlocksPerWarp = 8;
+
 __global__ void __launch_bounds__(256)
-k_encode_compact(uint8_t* __restrict__ out, size_t stride, int c, uint64_t nwarps,
+k_encode_compact(uint8_t* __restrict__ out, size_t stride, int c, uint64_t nwarps, int lbw,
                  const uint32_t* __restrict__ sparse)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t gw = (uint64_t)blockIdx.x * 8 + wib;
     if (gw >= nwarps) return;
     const CodecLayout L = codec_layout(c);
-    const int sh = c - 7;
+    const int sh = c - 7 - lbw;  // log2 warps per chunk
+    const int nbw = 1 << lbw;    // blocks of this warp
     const uint32_t r = (uint32_t)(gw >> sh);
-    const uint32_t b = (uint32_t)(gw & ((1ull << sh) - 1));
+    const uint32_t b0 = (uint32_t)(gw & ((1ull << sh) - 1)) << lbw;
     uint8_t* so = out + (size_t)r * stride;
-    const uint32_t w = so[L.w_off + b];
-    if (w == 0) return;
-    const uint32_t off = *reinterpret_cast<const uint32_t*>(so + L.o_off + 4ull * b);
-    const uint4* src = reinterpret_cast<const uint4*>(sparse + ((uint64_t)r * L.nb + b) * 256ull);
-    uint4* dst = reinterpret_cast<uint4*>(so + L.p_off + 4ull * off);
-    for (uint32_t i = lane; i < 2 * w; i += 32) dst[i] = src[i];
+    uint32_t wl = 0, ol = 0;
+    if (lane < nbw) {
+        wl = so[L.w_off + b0 + lane];
+        ol = *reinterpret_cast<const uint32_t*>(so + L.o_off + 4ull * (b0 + lane));
+    }
+    const uint4* src0 = reinterpret_cast<const uint4*>(sparse + ((uint64_t)r * L.nb + b0) * 256ull);
+    uint4 v[kBlocksPerWarp][2];
+    uint32_t n[kBlocksPerWarp];  // 16-byte words of block k (2w <= 64)
+#pragma unroll
+    for (int k = 0; k < kBlocksPerWarp; k++) {
+        n[k] = 2u * __shfl_sync(FULL, wl, k);
+        const uint4* src = src0 + 64 * k;  // the staging slot of a block is 1 KiB
+        if (k < nbw && (uint32_t)lane < n[k]) v[k][0] = src[lane];
+        if (k < nbw && (uint32_t)lane + 32 < n[k]) v[k][1] = src[lane + 32];
+    }
+#pragma unroll
+    for (int k = 0; k < kBlocksPerWarp; k++) {
+        const uint32_t off = __shfl_sync(FULL, ol, k);
+        uint4* dst = reinterpret_cast<uint4*>(so + L.p_off + 4ull * off);
+        if (k < nbw && (uint32_t)lane < n[k]) dst[lane] = v[k][0];
+        if (k < nbw && (uint32_t)lane + 32 < n[k]) dst[lane + 32] = v[k][1];
+    }
 }
 
 template <typename R>
@@ -241,8 +264,10 @@ cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* 
                                  cudaStream_t st, int* launches)
 {
     k_encode_scan<<<nchunks, 1024, 0, st>>>(out, stride, c, dtype, k, blocksq, chunk_out);
-    const uint64_t nw2 = (uint64_t)nchunks << (c - 7);
-    k_encode_compact<<<blocks_for_warps(nw2), 256, 0, st>>>(out, stride, c, nw2, sparse);
+    // blocks per chunk: 2^(c-7); a warp takes up to kBlocksPerWarp of them
+    const int lbw = std::min(3, c - 7);
+    const uint64_t nw2 = (uint64_t)nchunks << (c - 7 - lbw);
+    k_encode_compact<<<blocks_for_warps(nw2), 256, 0, st>>>(out, stride, c, nw2, lbw, sparse);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }

@@ -50,31 +50,29 @@ __device__ __forceinline__ bool decode_pair(const uint8_t* __restrict__ s, uint6
                                             int lane)
 {
     const CodecLayout L = codec_layout(c);
-    bool ok = nbytes >= L.p_off && nbytes <= limit;
-    int k = 0;
-    uint32_t total = 0;
-    if (ok) {
-        const uint32_t h0 = ld32(s), h1 = ld32(s + 4), nbh = ld32(s + 12);
-        k = (int32_t)ld32(s + 8);
-        total = ld32(s + 16);
-        ok = h0 == kMagic && (h1 & 0xffffu) == 1u && ((h1 >> 16) & 0xffu) == (uint32_t)dtype &&
-             (h1 >> 24) == (uint32_t)c && k <= 0 && k >= -60 && nbh == L.nb && L.p_off + 4ull * total <= nbytes;
-    }
-    uint32_t w[2] = {0, 0}, off[2] = {0, 0};
-    int32_t anc[2] = {0, 0};
-    if (ok) {
+    if (!(nbytes >= L.p_off && nbytes <= limit)) return false;
+    // the header and this pair's metadata lie below p_off <= nbytes: all of
+    // them are loaded at once (one memory round trip), then validated
+    const uint32_t h0 = ld32(s), h1 = ld32(s + 4), nbh = ld32(s + 12);
+    const int k = (int32_t)ld32(s + 8);
+    const uint32_t total = ld32(s + 16);
+    uint32_t w[2], off[2], nxt[2];
+    int32_t anc[2];
 #pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const uint32_t b = p ? bp + L.bpc : bp;
-            w[p] = s[L.w_off + b];
-            off[p] = ld32(s + L.o_off + 4ull * b);
-            const uint32_t nxt = ld32(s + L.o_off + 4ull * (b + 1));
-            anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
-            ok = ok && w[p] <= 32u && nxt - off[p] == 8u * w[p] &&
-                 L.p_off + 4ull * ((uint64_t)off[p] + 8ull * w[p]) <= nbytes;
-        }
-        if (bp == 0) ok = ok && ld32(s + L.o_off) == 0u && ld32(s + L.o_off + 4ull * L.nb) == total;
+    for (int p = 0; p < 2; p++) {
+        const uint32_t b = p ? bp + L.bpc : bp;
+        w[p] = s[L.w_off + b];
+        off[p] = ld32(s + L.o_off + 4ull * b);
+        nxt[p] = ld32(s + L.o_off + 4ull * (b + 1));
+        anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
     }
+    bool ok = h0 == kMagic && (h1 & 0xffffu) == 1u && ((h1 >> 16) & 0xffu) == (uint32_t)dtype &&
+              (h1 >> 24) == (uint32_t)c && k <= 0 && k >= -60 && nbh == L.nb && L.p_off + 4ull * total <= nbytes;
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+        ok = ok && w[p] <= 32u && nxt[p] - off[p] == 8u * w[p] &&
+             L.p_off + 4ull * ((uint64_t)off[p] + 8ull * w[p]) <= nbytes;
+    if (bp == 0) ok = ok && ld32(s + L.o_off) == 0u && ld32(s + L.o_off + 4ull * L.nb) == total;
     if (!ok) return false;
     __syncwarp();
 #pragma unroll
