@@ -114,3 +114,16 @@ def test_generated_adjoint_kernels_compile(jit_sources, dtype):
     for s in srcs:
         rc, log = _compile(lib, s)
         assert rc == 0, log
+
+
+def test_exchange_circuits_reach_every_store_form(jit_sources):
+    """The circuits of the GPU parity tests for exchanges reach each way a
+    phase stores: shared memory with pending exchanges folded into its bases,
+    HBM directly (with and without pending exchanges), and real and
+    imaginary parts packed into FP32x2 pairs."""
+    from test_gpu_jit import _exchange_circuit
+    srcs = [s for s in jit_sources(14, 14, _exchange_circuit(14, 41), mode="uncompressed") if s]
+    assert any("const uint32_t sb0 = " in s for s in srcs)
+    assert any("T* const gq = " in s for s in srcs)
+    assert any("T* const gq0 = " in s for s in srcs)
+    assert any("{ const float2 " in s for s in srcs)
