@@ -210,11 +210,14 @@ int create_impl(sv_state* s)
         }
         if ((e = cudaHostAlloc(&s->h_co[i], sizeof(ChunkOut) * gch, cudaHostAllocDefault)))
             return fail(s, SV_ERR_HOST_OOM, "pinned allocation failed");
+    }
+    // all four of each (the lambda construction of the adjoint uses events
+    // 2 and 3 whatever the slot count)
+    for (int i = 0; i < 4; i++)
         if ((e = cudaEventCreateWithFlags(&s->ev_h2d[i], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&s->ev_comp[i], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&s->ev_d2h[i], cudaEventDisableTiming)))
             return cuda_fail(s, e, "cudaEventCreate");
-    }
     if ((e = cudaMalloc(&s->d_carry, s->stride * gch)) || (e = cudaMalloc(&s->d_carry_bytes, sizeof(uint64_t) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the carry buffer failed");

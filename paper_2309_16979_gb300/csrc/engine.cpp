@@ -1311,6 +1311,10 @@ static int ensure_lambda_store(sv_state* s)
 
 // lambda = H psi, one output chunk at a time from the staged source chunks
 // k ^ xh (one per distinct high x-mask); adds Re<psi_k|lambda_k> to *d_energy.
+// Two staging sets alternate: chunk k+1's sources cross the host link while
+// chunk k is decoded, multiplied and encoded, and chunk k's stream returns
+// to the host while chunk k+1 computes. d_terms holds every output chunk's
+// term table (2^(n-c) x phys.size() entries).
 template <typename R>
 static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, PauliDev* d_terms, double* d_part,
                         int nblocks, double* d_energy)
@@ -1324,46 +1328,90 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
     const size_t gcap = (size_t)1 << std::min(s->gmax, s->nh);
     if (X.size() > gcap)
         return fail(s, SV_ERR_ARG, "more distinct high x-masks than chunks in a staging group (raise max_group_qubits)");
+    const size_t m = X.size(), nt = phys.size();
+    const int nset = 2 * m <= gcap ? 2 : 1;
     Arena& la = s->larena[s->lcur_arena];
     la.reset();
     const uint64_t nch = 1ull << s->nh;
-    std::vector<PauliDev> hd(phys.size());
     cudaError_t e;
-    for (uint64_t k = 0; k < nch; k++) {
-        std::vector<uint64_t> ks;
-        for (uint64_t xh : X) ks.push_back(k ^ xh);
-        int r = stage_chunks<R>(s, ks);
-        if (r) return r;
-        for (size_t i = 0; i < phys.size(); i++) {
-            const uint64_t xh = phys[i].xmask >> c;
-            const size_t slot = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
-            const uint64_t src_chunk = k ^ xh;
-            const int hs = __builtin_popcountll(src_chunk & (phys[i].zmask >> c)) & 1;
-            hd[i] = pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, 0, hs ? -1.0 : 1.0);
-            hd[i].pad = (int32_t)slot;
-        }
-        if (!hd.empty() &&
-            (e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice, s->s_comp)))
+    if (nt) {
+        std::vector<PauliDev> hd(nch * nt);
+        for (uint64_t k = 0; k < nch; k++)
+            for (size_t i = 0; i < nt; i++) {
+                const uint64_t xh = phys[i].xmask >> c;
+                const size_t slot = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
+                const int hs = __builtin_popcountll((k ^ xh) & (phys[i].zmask >> c)) & 1;
+                PauliDev& d = hd[k * nt + i];
+                d = pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, 0, hs ? -1.0 : 1.0);
+                d.pad = (int32_t)slot;
+            }
+        if ((e = cudaMemcpy(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice)))
             return cuda_fail(s, e, "upload terms");
+    }
+    const size_t amp_bytes = sizeof(R) * 2;
+    auto issue = [&](uint64_t k) -> int {
+        const int sl = nset == 2 ? (int)(k & 1) : 0;
+        const size_t base = (size_t)sl * m;
+        uint8_t* in = s->d_in[0] + base * s->stride;
+        uint8_t* amps = static_cast<uint8_t*>(s->d_amps) + (base << c) * amp_bytes;
+        // the set's streams are overwritten once its previous decode is done
+        if (k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
+            return cuda_fail(s, e, "wait decode");
+        GroupIn gin{};
+        for (size_t j = 0; j < m; j++) {
+            const ChunkRef& cr = s->cur[k ^ X[j]];
+            gin.bytes[j] = (uint32_t)cr.bytes;
+            if ((e = cudaMemcpyAsync(in + j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
+                return cuda_fail(s, e, "H2D chunk");
+            s->st.bytes_h2d += cr.bytes;
+        }
+        if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)))
+            return cuda_fail(s, e, "record h2d");
+        if ((e = launch_decode<R>(in, s->stride, c, s->dtype, (int)m, gin, amps, s->scale, s->d_err, s->s_comp)) ||
+            (e = cudaEventRecord(s->ev_h2d[2 + sl], s->s_comp)))
+            return cuda_fail(s, e, "decode");
+        // the set's output stream is overwritten once its copy to the host is done
+        if (k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[sl], 0)))
+            return cuda_fail(s, e, "wait d2h");
         int launches = 0;
-        if ((e = launch_ham_chunk<R>(s->d_amps, s->d_amps2, c, d_terms, (int)hd.size(), s->s_comp)) ||
-            (e = launch_dot<R>(s->d_amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
+        if ((e = launch_ham_chunk<R>(amps, s->d_amps2, c, d_terms + k * nt, (int)nt, s->s_comp)) ||
+            (e = launch_dot<R>(amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
-            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, 1, s->d_out2[0], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co2[0], s->d_err, s->s_comp, &launches)) ||
-            (e = cudaMemcpyAsync(s->h_co2[0], s->d_co2[0], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)))
+            (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, 1, s->d_out2[sl], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co2[sl], s->d_err, s->s_comp, &launches)) ||
+            (e = cudaMemcpyAsync(s->h_co2[sl], s->d_co2[sl], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)) ||
+            (e = cudaEventRecord(s->ev_comp[sl], s->s_comp)))
             return cuda_fail(s, e, "lambda chunk");
-        s->st.kernel_launches += 3 + launches;
-        if ((r = wait_stream(s, s->s_comp))) return r;
-        const uint64_t bytes = s->h_co2[0][0].bytes;
+        s->st.kernel_launches += 4 + launches;
+        return SV_OK;
+    };
+    auto finish = [&](uint64_t k) -> int {
+        const int sl = nset == 2 ? (int)(k & 1) : 0;
+        int r = wait_event(s, s->ev_comp[sl]);
+        if (r) return r;
+        const uint64_t bytes = s->h_co2[sl][0].bytes;
+        if (bytes > s->stride) return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
         uint8_t* dst = arena_alloc(s, la, bytes);
         if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the lambda store failed");
-        if ((e = cudaMemcpyAsync(dst, s->d_out2[0], bytes, cudaMemcpyDeviceToHost, s->s_comp)))
+        if ((e = cudaMemcpyAsync(dst, s->d_out2[sl], bytes, cudaMemcpyDeviceToHost, s->s_d2h)) ||
+            (e = cudaEventRecord(s->ev_d2h[sl], s->s_d2h)))
             return cuda_fail(s, e, "D2H lambda chunk");
         s->st.bytes_d2h += bytes;
         s->lcur[k] = {dst, bytes};
+        return SV_OK;
+    };
+    int r = SV_OK;
+    for (uint64_t k = 0; k < nch && !r; k++) {
+        // one set: chunk k's sizes are read before chunk k+1 overwrites them
+        if (nset == 1) {
+            if (!(r = issue(k))) r = finish(k);
+            continue;
+        }
+        if (!(r = issue(k)) && k >= 1) r = finish(k - 1);
     }
-    return wait_stream(s, s->s_comp);
+    if (!r && nset == 2 && nch >= 1) r = finish(nch - 1);
+    const int rs = sync_all(s);
+    return r ? r : rs;
 }
 
 // One reverse pass over (psi, lambda): gradient partials and U^dagger on both.
@@ -1572,7 +1620,7 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr, *d_gpart = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms))) ||
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms) << s->nh)) ||
         (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
         (e = cudaMalloc(&d_acc, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)))) ||
         (e = cudaMalloc(&d_gpart, sizeof(double) * gpart_cap))) {
