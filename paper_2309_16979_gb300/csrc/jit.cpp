@@ -1210,15 +1210,16 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     if (pf) {
         // tile buffer bo (element offset 0 or 4096) is processed while the
         // other one fills; bo is folded into every phase's base offset
+        // the next tile's base, computed for its prefetch, is carried over
         src << "__syncthreads();\n"
-            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s, amps, rt, td, "
-               "tile::tile_base(rt, td, blockIdx.x));\n"
+            << "uint64_t base_n = blockIdx.x < ntiles ? tile::tile_base(rt, td, blockIdx.x) : 0ull;\n"
+            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s, amps, rt, td, base_n);\n"
             << "uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo = tile::kPadElems - bo) {\n"
-            << "const uint64_t base = tile::tile_base(rt, td, tl);\n"
+            << "const uint64_t base = base_n;\n"
             << "tile::cp_async_wait_all();\n__syncthreads();\n"
-            << "if (tl + gridDim.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb
-            << ">(s + (tile::kPadElems - bo), amps, rt, td, tile::tile_base(rt, td, tl + gridDim.x));\n";
+            << "if (tl + gridDim.x < ntiles) {\nbase_n = tile::tile_base(rt, td, tl + gridDim.x);\n"
+            << "tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s + (tile::kPadElems - bo), amps, rt, td, base_n);\n}\n";
     } else {
         src << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"

@@ -57,11 +57,13 @@ struct PadLayout {
 constexpr uint32_t kPadElems = ((kN - 1) + (kN - 1) / 16 + (kN - 1) / 256 + 1 + 15) & ~15u;
 static_assert(kPadElems == 4368, "padded tile buffer");
 
-// Per-CTA tables: local offset of each tile row, and the bit of each local
-// position outside the tile (tile index bit i -> local bit opos[i]).
+// Per-CTA tables: local offset of each tile row, and the local offset of
+// each 4-bit digit of a tile index (tile index bit i -> local bit opos[i];
+// digit k covers index bits 4k..4k+3).
+constexpr int kBaseDigits = (kMaxLocalQubits - kT + 3) / 4;
 struct Rows {
     uint64_t rowoff[1 << (kT - kMinLowBits)];
-    uint64_t opos[kMaxLocalQubits];
+    uint64_t digit[kBaseDigits][16];
 };
 
 __device__ __forceinline__ void setup_rows(Rows& rt, const TileDesc& td)
@@ -73,14 +75,20 @@ __device__ __forceinline__ void setup_rows(Rows& rt, const TileDesc& td)
             if ((rw >> i) & 1u) off |= 1ull << td.hpos[i];
         rt.rowoff[rw] = off;
     }
-    for (int i = threadIdx.x; i < td.nout; i += blockDim.x) rt.opos[i] = 1ull << td.opos[i];
+    for (int e = threadIdx.x; e < 16 * ((td.nout + 3) >> 2); e += blockDim.x) {
+        const int k = e >> 4;
+        uint64_t off = 0;
+        for (int b = 0; b < 4; b++)
+            if (((e >> b) & 1) && 4 * k + b < td.nout) off |= 1ull << td.opos[4 * k + b];
+        rt.digit[k][e & 15] = off;
+    }
 }
 
+// local offset of tile `tile`: the offsets of its 4-bit digits
 __device__ __forceinline__ uint64_t tile_base(const Rows& rt, const TileDesc& td, uint64_t tile)
 {
     uint64_t base = 0;
-    for (int i = 0; i < td.nout; i++)
-        if ((tile >> i) & 1ull) base |= rt.opos[i];
+    for (int k = 0; k < ((td.nout + 3) >> 2); k++) base |= rt.digit[k][(tile >> (4 * k)) & 15];
     return base;
 }
 
