@@ -161,6 +161,7 @@ struct Gen {
     struct Pend {
         std::string cond;
         int b;
+        uint32_t tm = 0;  // thread-index bits the condition requires (0: uniform over the CTA)
     };
     std::vector<Pend> pend;
     int nvec = 1;  // 2 in an adjoint sub-pass: psi in r/q, lambda in u/w, same ops on both
@@ -419,6 +420,16 @@ std::string op_cond(Gen<R>& g, const PhaseOp<R>& op, const CtaCtrl* ctl)
     return s;
 }
 
+// thread-index bits an op's controls require (its thread-bit controls)
+template <typename R>
+uint32_t thread_mask(const Gen<R>& g, const PhaseOp<R>& op)
+{
+    uint32_t tm = 0;
+    for (int b = 0; b < 16; b++)
+        if (((op.tmask >> b) & 1u) && g.thr_of_tile[b] >= 0) tm |= 1u << g.thr_of_tile[b];
+    return tm;
+}
+
 // register bits an op acts on as target or diagonal index
 template <typename R>
 uint32_t op_bits(const PhaseOp<R>& op)
@@ -538,7 +549,7 @@ void emit_dense1(Gen<R>& g, const PhaseOp<R>& op, size_t pb, int b, const std::s
                 k++;
             }
         }
-        g.pend.push_back({cond, b});
+        g.pend.push_back({cond, b, thread_mask(g, op)});
         return;
     }
     Coef e[4];
@@ -954,6 +965,61 @@ bool direct_store(const Phase* ph, int nph, bool enc)
     return !enc && nph > 0 && ph[nph - 1].tpos[0] == 0 && ph[nph - 1].tpos[1] == 1;
 }
 
+// Which pending exchanges to fold into a phase's store addresses (1) rather
+// than apply in registers (0): the choice with the least cost, counting an
+// exchange in registers as 64 issue cycles of a 256-thread tile (32 selects
+// per thread) and each extra shared-memory wavefront of the stores (bank
+// pairs shared within a half-warp, padded layout: slot mod 16) as one.
+template <typename R>
+std::vector<int> fold_plan(const Gen<R>& g, const Phase& P, const uint32_t* K)
+{
+    const size_t np = g.pend.size();
+    std::vector<int> best(np, 1);
+    bool lanes = false;  // any condition on lane bits 0..3?
+    for (const auto& pd : g.pend)
+        if (pd.tm & 15u) lanes = true;
+    if (!lanes) return best;
+    long best_cost = -1;
+    for (uint32_t f = 0; f < (1u << np); f++) {
+        long cost = 0;
+        for (size_t j = 0; j < np; j++)
+            if (!((f >> j) & 1)) cost += 64;
+        // extra wavefronts of the 16 stores over the CTA's 16 half-warps
+        for (int m = 0; m < 16; m++)
+            for (int hw = 0; hw < 16; hw++) {
+                int count[16] = {};
+                uint32_t seen[16][16];
+                int worst = 1;
+                for (int l = 0; l < 16; l++) {
+                    const uint32_t t = 16u * hw + l;
+                    uint32_t tb = 0;
+                    for (int j = 0; j < kPhaseTileQubits - kPhaseRegBits; j++)
+                        if ((t >> j) & 1u) tb |= 1u << P.tpos[j];
+                    int64_t slot = (int64_t)pad_slot(tb) + K[m];
+                    for (size_t j = 0; j < np; j++) {
+                        if (!((f >> j) & 1) || (t & g.pend[j].tm) != g.pend[j].tm) continue;
+                        const int64_t dlt = pad_slot(1u << P.rpos[g.pend[j].b]);
+                        slot += ((m >> g.pend[j].b) & 1) ? -dlt : dlt;
+                    }
+                    const uint32_t bank = (uint32_t)(slot & 15), sl = (uint32_t)slot;
+                    bool dup = false;
+                    for (int q = 0; q < count[bank]; q++)
+                        if (seen[bank][q] == sl) dup = true;
+                    if (!dup) {
+                        seen[bank][count[bank]++] = sl;
+                        worst = std::max(worst, count[bank]);
+                    }
+                }
+                cost += worst - 1;
+            }
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            for (size_t j = 0; j < np; j++) best[j] = (f >> j) & 1;
+        }
+    }
+    return best;
+}
+
 template <typename R>
 void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl, const std::vector<R>& params,
              bool dec, bool enc, const TileDesc& td, std::string& key, const int32_t* grad)
@@ -1099,6 +1165,18 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
                 g.ok = false;
             }
             pb += code == kCodeDense2 ? 32 : 8;
+        }
+        if (!(ds && pi + 1 == nph) && !g.pend.empty()) {
+            // a folded exchange conditional on lane bits shifts some lanes'
+            // store slots: where that makes two lanes of a half-warp share a
+            // bank pair, exchanging in registers (selects) is cheaper than the
+            // extra shared-memory wavefronts
+            const std::vector<int> how = fold_plan(g, P, K);
+            std::vector<typename Gen<R>::Pend> keep;
+            for (size_t j = 0; j < g.pend.size(); j++)
+                if (how[j]) keep.push_back(g.pend[j]);
+                else emit_exchange(g, g.pend[j].cond, g.pend[j].b);
+            g.pend.swap(keep);
         }
         const size_t np = g.pend.size();
         if (ds && pi + 1 == nph) {

@@ -616,6 +616,73 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
     }
 }
 
+// Number the tile's high bits so that no register phase holds a whole class
+// of tile bits with the same index mod 4. The padded shared-memory layout
+// moves tile bit b by 2^(b mod 4) slots mod 16, so a half-warp's 64-bit
+// accesses are free of bank conflicts only when its four thread bits cover
+// the four classes, and a phase whose register bits include a whole class
+// leaves its threads none of that class. Which local qubits a phase holds in
+// registers does not depend on the numbering; a deterministic search over
+// orders of the high bits keeps the first with the fewest such phases.
+template <typename R>
+void order_tile_bits(const SubPlan& sp, TileDesc& td)
+{
+    const int nh = td.t - td.l;
+    if (td.t != kPhaseTileQubits || nh < 2) return;
+    std::vector<Phase> ph;
+    std::vector<PhaseOp<R>> ops;
+    std::vector<CtaCtrl> ctl;
+    std::vector<R> d2m;
+    dev_phases<R>(sp, td, ph, ops, ctl, d2m);
+    // each phase's register qubits as local positions
+    std::vector<uint64_t> reg(ph.size(), 0);
+    for (size_t i = 0; i < ph.size(); i++)
+        for (int j = 0; j < kPhaseRegBits; j++) {
+            const int b = ph[i].rpos[j];
+            reg[i] |= 1ull << (b < td.l ? b : td.hpos[b - td.l]);
+        }
+    auto bad = [&](const int8_t* hp) {
+        int n = 0;
+        for (uint64_t rl : reg) {
+            uint32_t rt = 0;  // tile bits of the phase's registers under numbering hp
+            for (int b = 0; b < td.l; b++)
+                if ((rl >> b) & 1) rt |= 1u << b;
+            for (int i = 0; i < nh; i++)
+                if ((rl >> hp[i]) & 1) rt |= 1u << (td.l + i);
+            for (int r = 0; r < 4; r++) {
+                uint32_t cls = 0;
+                for (int b = r; b < td.t; b += 4) cls |= 1u << b;
+                if ((rt & cls) == cls) n++;
+            }
+        }
+        return n;
+    };
+    int best = bad(td.hpos);
+    if (best == 0) return;
+    int8_t cur[kMaxTileQubits], keep[kMaxTileQubits];
+    for (int i = 0; i < nh; i++) cur[i] = keep[i] = td.hpos[i];
+    uint64_t x = 0x9e3779b97f4a7c15ull;  // splitmix64 state: the search is deterministic
+    for (int trial = 0; trial < 256 && best > 0; trial++) {
+        for (int i = nh - 1; i > 0; i--) {
+            x += 0x9e3779b97f4a7c15ull;
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+            z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+            z ^= z >> 31;
+            std::swap(cur[i], cur[z % (uint64_t)(i + 1)]);
+        }
+        const int v = bad(cur);
+        if (v < best) {
+            best = v;
+            for (int i = 0; i < nh; i++) keep[i] = cur[i];
+        }
+    }
+    for (int i = 0; i < nh; i++) td.hpos[i] = keep[i];
+}
+
+template void order_tile_bits<float>(const SubPlan&, TileDesc&);
+template void order_tile_bits<double>(const SubPlan&, TileDesc&);
+
 template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&,
                                 std::vector<CtaCtrl>&, std::vector<float>&, std::vector<int32_t>*, std::vector<int>*);
 template void dev_phases<double>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<double>>&,
