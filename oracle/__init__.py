@@ -93,6 +93,13 @@ def lib():
         L.or_codec_encode.restype = C.c_int
         L.or_codec_decode.argtypes = [C.c_int, C.c_int, P, C.c_size_t, P]
         L.or_codec_decode.restype = C.c_int
+        L.or_codec_relative_exponent.argtypes = [C.c_double, C.c_double]
+        L.or_codec_relative_exponent.restype = C.c_int
+        L.or_codec_chunk_max.argtypes = [C.c_int, C.c_int, P]
+        L.or_codec_chunk_max.restype = C.c_double
+        L.or_codec_encode_relative.argtypes = [C.c_int, C.c_int, C.c_double, P, P, C.c_size_t,
+                                               C.POINTER(C.c_size_t)]
+        L.or_codec_encode_relative.restype = C.c_int
         _lib = L
     return _lib
 
@@ -241,8 +248,15 @@ def codec_max_bytes(c: int) -> int:
     return lib().or_codec_max_bytes(c)
 
 
-def codec_encode(amps: np.ndarray, eb: float) -> bytes:
-    """Encode one chunk of 2^c amplitudes (complex64 or complex128)."""
+def codec_relative_exponent(eb: float, m: float) -> int:
+    """Step exponent of the relative bound for a chunk whose largest component
+    magnitude is m."""
+    return lib().or_codec_relative_exponent(eb, m)
+
+
+def codec_encode(amps: np.ndarray, eb: float, relative: bool = False) -> bytes:
+    """Encode one chunk of 2^c amplitudes (complex64 or complex128); with
+    relative, the step follows the chunk's largest component (relative bound)."""
     amps = np.ascontiguousarray(amps)
     dtype = C64 if amps.dtype == np.complex64 else C128
     if amps.dtype not in (np.complex64, np.complex128):
@@ -253,8 +267,8 @@ def codec_encode(amps: np.ndarray, eb: float) -> bytes:
     cap = codec_max_bytes(c)
     out = np.zeros(cap, dtype=np.uint8)
     nb = C.c_size_t(0)
-    _check(lib().or_codec_encode(dtype, c, eb, _ptr(amps), _ptr(out), cap, C.byref(nb)),
-           "or_codec_encode")
+    fn = lib().or_codec_encode_relative if relative else lib().or_codec_encode
+    _check(fn(dtype, c, eb, _ptr(amps), _ptr(out), cap, C.byref(nb)), "or_codec_encode")
     return out[: nb.value].tobytes()
 
 

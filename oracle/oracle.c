@@ -46,6 +46,13 @@
  *      occupies bits [j*w, j*w + w) of the block's little-endian bit string
  *      of 8*w words; offset[b+1] = offset[b] + 8*w_b, offset[0] = 0.
  *      |q| must not exceed 2^24 - 1 (complex64) or 2^30 - 1 (complex128).
+ *
+ *      Relative bound (the paper fixes no bound; a reading that keeps spread
+ *      states from quantising to zero): a chunk whose largest component
+ *      magnitude is m > 0 takes k = floor(log2(2 * eb * m)) clamped to
+ *      [-60, 0] (k = 0 when m = 0), so |x - q*Delta| <= max(eb * m, 2^-61)
+ *      for every component. The stream format is the same; only k differs
+ *      between chunks.
  */
 #include <math.h>
 #include <stdint.h>
@@ -391,15 +398,54 @@ static double read_component(int dtype, const void *amps, size_t i, int plane)
     return ((const double *)amps)[2 * i + plane];
 }
 
+/* exponent k of the relative bound's step for a chunk whose largest
+ * component magnitude is m: floor(log2(2 eb m)) clamped to [-60, 0] */
+int or_codec_relative_exponent(double eb, double m)
+{
+    int e;
+    double f;
+    if (!(eb > 0) || !isfinite(eb) || !(m >= 0) || !isfinite(m)) return 1 << 30;
+    if (m == 0) return 0;
+    f = frexp((2.0 * eb) * m, &e); /* 2 eb m = f 2^e, f in [0.5, 1) */
+    (void)f;
+    e -= 1;
+    return e > 0 ? 0 : e < -60 ? -60 : e;
+}
+
+/* largest |re| or |im| of a chunk of 2^c amplitudes */
+double or_codec_chunk_max(int dtype, int c, const void *amps)
+{
+    size_t i, n = (size_t)2 << c;
+    double m = 0;
+    for (i = 0; i < n; i++) {
+        double x = dtype == 1 ? (double)((const float *)amps)[i] : ((const double *)amps)[i];
+        if (fabs(x) > m) m = fabs(x);
+    }
+    return m;
+}
+
+static int encode_with_step(int dtype, int c, int k, const void *amps, uint8_t *out, size_t cap, size_t *nbytes);
+
 int or_codec_encode(int dtype, int c, double eb, const void *amps, uint8_t *out, size_t cap, size_t *nbytes)
 {
+    if ((dtype != 1 && dtype != 2) || c < 8 || c > 30) return OR_ERR_ARG;
+    return encode_with_step(dtype, c, or_codec_step_exponent(eb), amps, out, cap, nbytes);
+}
+
+int or_codec_encode_relative(int dtype, int c, double eb, const void *amps, uint8_t *out, size_t cap,
+                             size_t *nbytes)
+{
+    if ((dtype != 1 && dtype != 2) || c < 8 || c > 30) return OR_ERR_ARG;
+    return encode_with_step(dtype, c, or_codec_relative_exponent(eb, or_codec_chunk_max(dtype, c, amps)), amps, out,
+                            cap, nbytes);
+}
+
+static int encode_with_step(int dtype, int c, int k, const void *amps, uint8_t *out, size_t cap, size_t *nbytes)
+{
     size_t nvals, nb, b, j, meta, w_off, a_off, o_off, p_off, total = 0;
-    int k;
     double qmax, inv;
     int32_t *q;
     uint32_t *z;
-    if ((dtype != 1 && dtype != 2) || c < 8 || c > 30) return OR_ERR_ARG;
-    k = or_codec_step_exponent(eb);
     if (k > 0 || k < -60) return OR_ERR_RANGE;
     qmax = dtype == 1 ? 16777215.0 : 1073741823.0;
     inv = ldexp(1.0, -k);

@@ -133,3 +133,60 @@ def test_planted_mistake_in_zigzag_is_caught():
     # a zigzag with z = -2r for r<0 (dropping the -1) would give z1 = 4, z3 = 6
     wrong_word0 = (0 | (4 << 4) | (8 << 8) | (6 << 12)).to_bytes(4, "little").hex()
     assert wrong_word0 not in want[160 * 2 // 2:]
+
+
+# ------------------------------------------------------- relative bound
+def test_relative_exponent_brackets_2_eb_m():
+    """k = floor(log2(2 eb m)), checked against the power of two it must sit
+    under, clamped to [-60, 0]; k = 0 for an all-zero chunk."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        eb = 10.0 ** rng.uniform(-7, -1)
+        m = 10.0 ** rng.uniform(-12, 0.5)
+        k = oracle.codec_relative_exponent(eb, m)
+        v = 2 * eb * m
+        if v >= 1.0:
+            assert k == 0
+        elif v < 2.0 ** -59:
+            assert k == -60
+        else:
+            assert 2.0 ** k <= v < 2.0 ** (k + 1)
+    assert oracle.codec_relative_exponent(1e-5, 0.0) == 0
+    assert oracle.codec_relative_exponent(1e-5, 2.0 ** -18) == -34  # 2e-5 * 2^-18 = 7.6e-11 -> 2^-34
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("scale", [1.0, 2.0 ** -9, 2.0 ** -18, 1e-12])
+def test_relative_bound_holds_pointwise(dtype, scale):
+    """|x - xhat| <= max(eb * m, 2^-61), m the chunk's largest component."""
+    rng = np.random.default_rng(11)
+    c, eb = 10, 1e-4
+    x = ((rng.standard_normal(1 << c) + 1j * rng.standard_normal(1 << c)) * scale).astype(dtype)
+    m = max(np.abs(x.real).max(), np.abs(x.imag).max())
+    d = oracle.codec_decode(oracle.codec_encode(x, eb, relative=True), c, dtype)
+    bound = max(eb * float(m), 2.0 ** -61)
+    assert np.abs(d.real.astype(np.float64) - x.real.astype(np.float64)).max() <= bound
+    assert np.abs(d.imag.astype(np.float64) - x.imag.astype(np.float64)).max() <= bound
+
+
+def test_relative_equals_absolute_when_the_chunk_peaks_at_one():
+    """A chunk whose largest component is exactly 1 gets the absolute step:
+    the two encodings are the same bytes."""
+    rng = np.random.default_rng(5)
+    x = ((rng.standard_normal(1024) + 1j * rng.standard_normal(1024)) * 0.2).astype(np.complex64)
+    x.real[17] = 1.0
+    x.real = np.clip(x.real, -1, 1)
+    x.imag = np.clip(x.imag, -1, 1)
+    for eb in (1e-3, 1e-5, 1e-6):
+        assert oracle.codec_encode(x, eb, relative=True) == oracle.codec_encode(x, eb)
+
+
+def test_relative_bound_keeps_a_spread_state():
+    """Amplitudes of 2^-8 under eb = 1e-2: the absolute step (2^-6) rounds
+    every component to zero, the relative one keeps them to 1 %."""
+    n = 16
+    x = np.full(1 << 10, 2.0 ** -(n / 2) * np.exp(0.3j), dtype=np.complex64)
+    da = oracle.codec_decode(oracle.codec_encode(x, 1e-2), 10)
+    dr = oracle.codec_decode(oracle.codec_encode(x, 1e-2, relative=True), 10)
+    assert not np.any(da)
+    assert np.abs(dr - x).max() <= 1e-2 * 2.0 ** -(n / 2) * 2 ** 0.5
