@@ -15,7 +15,9 @@ Metric: amplitude-gate updates per second = gates * 2^n / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload {c1-layers,c1-ghz,c1-qft,c0-qft,c0-layers,
-                              c2-ghz,c2-qft,c2-clifford,c3-grad,c4-grad}
+                              c2-ghz,c2-qft,c2-clifford,c3-grad,c4-grad,
+                              c2-qft-rel,c2-clifford-rel,c1-layers-rel}
+  (-rel: the relative error bound, each chunk's step from its largest component)
 
 With --gpus N under torchrun every rank runs an independent replica of the
 workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
@@ -52,6 +54,11 @@ WORKLOADS = {
     "c2-ghz": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="ghz"),
     "c2-qft": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft"),
     "c2-clifford": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30),
+    # the same with the relative error bound (step from each chunk's largest component)
+    "c2-qft-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft", relative=True),
+    "c2-clifford-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30,
+                            relative=True),
+    "c1-layers-rel": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40, relative=True),
     "c3-grad": dict(n=24, c=24, eb=0.0, dtype="c64", group=0, circuit="hea", layers=10, mode="uncompressed"),
     "c4-grad": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16),
 }
@@ -98,6 +105,19 @@ def make_circuit(w, seed=1):
     raise ValueError(w["circuit"])
 
 
+def host_budget():
+    """Pinned host memory the library may take: 70 % of the host's memory
+    (it then fails with SV_ERR_HOST_OOM instead of exhausting the host)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemTotal:"):
+                    return int(0.7 * int(line.split()[1]) * 1024)
+    except OSError:
+        pass
+    return 0
+
+
 def describe(w, ngates, group=None):
     if w["circuit"] == "hea":
         return (f"adjoint gradient, hardware-efficient ansatz n={w['n']}, {w['layers']} layers, 1-D Ising, "
@@ -105,7 +125,8 @@ def describe(w, ngates, group=None):
                                      f"compressed chunks 2^{w['c']}, eb={w['eb']}"))
     name = {"layers": f"random layered circuit depth {w.get('depth')}", "ghz": "GHZ", "qft": "QFT on a seeded basis state",
             "clifford": f"random Clifford+RZ depth {w.get('depth')} (40% of slots on the 10 high qubits)"}[w["circuit"]]
-    return (f"{name}, n={w['n']} ({ngates} gates), {w['dtype']}, chunk=2^{w['c']}, eb={w['eb']}, compressed chunks "
+    bound = "relative eb" if w.get("relative") else "eb"
+    return (f"{name}, n={w['n']} ({ngates} gates), {w['dtype']}, chunk=2^{w['c']}, {bound}={w['eb']}, compressed chunks "
             f"in pinned host DRAM, streamed in groups of "
             + (f"2^{group} chunks" if group is not None else
                (f"2^{w['group']} chunks" if w.get("group") else "chunks (group size chosen from the free HBM)")))
@@ -307,6 +328,7 @@ def run_apply(args, rank, world):
     # timed steps run without per-launch events; one extra profiled step after
     # them gives the kernel breakdown and the roofline
     sim = StateVector(n, c, w["eb"], dtype=w["dtype"], init_index=init, max_group_qubits=w["group"], profile=False,
+                      relative_bound=bool(w.get("relative", False)), host_budget_bytes=host_budget(),
                       device=dev, jit=bool(args.jit))
     group = sim.stats()["group_qubits"]  # resolved (0 = chosen from the free device memory)
     for _ in range(args.warmup):
@@ -473,7 +495,8 @@ def run_grad(args, rank, world):
     sets = w.get("sets", 1)
     thetas = [W.normal_params(npar, seed=(3 if sets == 1 else 100 + i)) for i in range(max(1, sets))]
     mode = w.get("mode", "compressed")
-    sim = StateVector(n, w["c"], w["eb"] or 1e-6, dtype=w["dtype"], mode=mode, max_group_qubits=w["group"], device=dev)
+    sim = StateVector(n, w["c"], w["eb"] or 1e-6, dtype=w["dtype"], mode=mode, max_group_qubits=w["group"], device=dev,
+                      host_budget_bytes=host_budget() if mode == "compressed" else 0)
     for i in range(args.warmup):
         sim.grad(gates, thetas[i % len(thetas)], terms)
     torch.cuda.synchronize()
@@ -557,19 +580,24 @@ def main():
         out = run_grad(args, rank, world) if args.w["circuit"] == "hea" else run_apply(args, rank, world)
     except Exception as exc:  # noqa: BLE001 -- reported, not hidden
         from paper_2309_16979_gb300._abi import SvError
-        if not (isinstance(exc, SvError) and exc.code == -6):
+        if not (isinstance(exc, SvError) and exc.code in (-6, -2)):
             raise
-        # an absolute error bound above the amplitudes' magnitude quantises the
-        # whole state to zero: a property of the bound, reported as such
         w = args.w
         out = {"metric": METRIC, "value": None, "unit": "amp-gate updates/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
                "config": {"workload": describe(w, len(make_circuit(w, seed=1))), "n_qubits": w["n"],
-                          "chunk_qubits": w["c"], "abs_error_bound": w["eb"]},
-               "norm_collapse": {"error": str(exc),
-                                 "reason": f"spread amplitudes (|a| ~ 2^-{w['n'] // 2}) fall below half the "
-                                           f"quantisation step of eb={w['eb']} and quantise to zero"}}
+                          "chunk_qubits": w["c"], "abs_error_bound": w["eb"]}}
+        if exc.code == -6:
+            # an absolute error bound above the amplitudes' magnitude quantises the
+            # whole state to zero: a property of the bound, reported as such
+            out["norm_collapse"] = {"error": str(exc),
+                                    "reason": f"spread amplitudes (|a| ~ 2^-{w['n'] // 2}) fall below half the "
+                                              f"quantisation step of eb={w['eb']} and quantise to zero"}
+        else:
+            # the compressed state outgrew the host memory the bench allows
+            out["host_oom"] = {"error": str(exc), "host_budget_bytes": host_budget(),
+                               "reason": "the stored state (two arenas) needs more pinned host memory"}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -107,6 +107,14 @@ typedef struct sv_config {
                                      NVRTC (cached per process, keyed by structure, not angles);
                                      0: the table-driven phase kernel. Compilation errors fail the
                                      call with SV_ERR_CUDA. */
+    int32_t relative_bound;       /* 0 (default): abs_error_bound bounds |x - xhat| for every stored
+                                     component; 1: relative bound, a chunk whose largest component
+                                     magnitude is m is stored with the step 2^k, k = floor(log2(2 eb m))
+                                     clamped to [-60, 0], so |x - xhat| <= max(eb m, 2^-61) (spread
+                                     states keep their amplitudes instead of quantising to zero).
+                                     Needs eb >= 2^-23 (complex64) / 2^-29 (complex128), else
+                                     SV_ERR_RANGE; the codec then runs in separate kernels (the
+                                     chunk maximum precedes the encode) */
     uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
@@ -364,6 +372,14 @@ int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, 
  * byte-identical to sv_codec_encode's.
  */
 #define SV_NOALLOC_MAX_CHUNK_QUBITS 20
+/* sv_codec_encode with the relative bound of sv_config.relative_bound: the
+ * chunk's step follows its largest component magnitude m (k in the stream
+ * header), |x - xhat| <= max(eb m, 2^-61). eb >= 2^-23 (complex64) / 2^-29
+ * (complex128), else SV_ERR_RANGE; otherwise as sv_codec_encode. The stream
+ * decodes with sv_codec_decode. */
+int sv_codec_encode_relative(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
+                             size_t cap, size_t* nbytes);
+
 int sv_codec_encode_noalloc(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
                             size_t cap, size_t* h_nbytes);
 

@@ -298,10 +298,10 @@ def codec_status_decode(stream: bytes, c: int, dtype=np.complex64) -> int:
     return lib().or_codec_decode(dt, c, _ptr(buf), buf.size, _ptr(out))
 
 
-def compress_roundtrip(psi: np.ndarray, c: int, eb: float) -> np.ndarray:
+def compress_roundtrip(psi: np.ndarray, c: int, eb: float, relative: bool = False) -> np.ndarray:
     """Quantise a whole state chunk by chunk through the reference codec."""
     out = np.empty_like(psi)
     for k in range(psi.size >> c):
         seg = psi[k << c:(k + 1) << c]
-        out[k << c:(k + 1) << c] = codec_decode(codec_encode(seg, eb), c, psi.dtype)
+        out[k << c:(k + 1) << c] = codec_decode(codec_encode(seg, eb, relative), c, psi.dtype)
     return out

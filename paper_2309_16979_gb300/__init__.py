@@ -38,7 +38,7 @@ class StateVector:
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,
-                 jit: bool = True):
+                 jit: bool = True, relative_bound: bool = False):
         L = load()
         cfg = _abi.SvConfig()
         L.sv_config_default(C.byref(cfg))
@@ -55,6 +55,7 @@ class StateVector:
         cfg.profile = int(profile)
         cfg.fuse_codec = int(fuse_codec)
         cfg.jit = int(jit)
+        cfg.relative_bound = int(relative_bound)
         h = C.c_void_p()
         _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
         self._h = h
@@ -185,9 +186,11 @@ def codec_max_bytes(chunk_qubits: int) -> int:
     return load().sv_codec_max_bytes(chunk_qubits)
 
 
-def codec_encode(d_amps, eb: float, d_stream=None):
+def codec_encode(d_amps, eb: float, d_stream=None, relative: bool = False):
     """Encode one chunk held in a CUDA tensor (complex64/complex128, 2^c
-    elements). Returns (stream tensor uint8 on the device, nbytes)."""
+    elements); relative: the step follows the chunk's largest component
+    (sv_codec_encode_relative). Returns (stream tensor uint8 on the device,
+    nbytes)."""
     import torch
     c = int(d_amps.numel()).bit_length() - 1
     dt = SV_C64 if d_amps.dtype == torch.complex64 else SV_C128
@@ -196,8 +199,8 @@ def codec_encode(d_amps, eb: float, d_stream=None):
         d_stream = torch.empty(cap, dtype=torch.uint8, device=d_amps.device)
     nb = C.c_size_t(0)
     torch.cuda.synchronize(d_amps.device)
-    code = load().sv_codec_encode(dt, c, eb, d_amps.data_ptr(), d_stream.data_ptr(), d_stream.numel(),
-                                  C.byref(nb))
+    fn = load().sv_codec_encode_relative if relative else load().sv_codec_encode
+    code = fn(dt, c, eb, d_amps.data_ptr(), d_stream.data_ptr(), d_stream.numel(), C.byref(nb))
     if code:
         raise SvError(code, "sv_codec_encode")
     return d_stream, nb.value

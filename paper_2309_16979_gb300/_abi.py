@@ -38,7 +38,7 @@ class SvConfig(C.Structure):
                 ("max_group_qubits", C.c_int32), ("tile_qubits", C.c_int32),
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
                 ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("jit", C.c_int32),
-                ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
+                ("relative_bound", C.c_int32), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 
 class SvStats(C.Structure):
@@ -62,7 +62,8 @@ class SvStats(C.Structure):
 EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "sv_amplitudes",
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
-           "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile")
+           "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile",
+           "sv_codec_encode_relative")
 
 _lib = None
 
@@ -115,6 +116,8 @@ def load() -> C.CDLL:
     L.sv_plan.restype = C.c_int
     L.sv_codec_encode_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
     L.sv_codec_encode_noalloc.restype = C.c_int
+    L.sv_codec_encode_relative.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
+    L.sv_codec_encode_relative.restype = C.c_int
     L.sv_chunk_stream.argtypes = [P, C.c_uint64, P, SZ, C.POINTER(SZ)]
     L.sv_chunk_stream.restype = C.c_int
     L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_int, C.c_char_p, SZ,

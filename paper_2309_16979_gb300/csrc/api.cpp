@@ -130,6 +130,8 @@ void release(sv_state* s)
     }
     cudaFree(s->d_carry);
     cudaFree(s->d_carry_bytes);
+    cudaFree(s->d_kc);
+    cudaFree(s->d_mbits);
     if (s->ev_prev_d2h) cudaEventDestroy(s->ev_prev_d2h);
     cudaFree(s->d_amps);
     cudaFree(s->d_sparse);
@@ -218,6 +220,10 @@ int create_impl(sv_state* s)
             (e = cudaEventCreateWithFlags(&s->ev_comp[i], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&s->ev_d2h[i], cudaEventDisableTiming)))
             return cuda_fail(s, e, "cudaEventCreate");
+    if ((e = cudaMalloc(&s->d_kc, sizeof(int32_t) * gch)) || (e = cudaMalloc(&s->d_mbits, sizeof(uint64_t) * gch))) {
+        cudaGetLastError();
+        return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the chunk step table failed");
+    }
     if ((e = cudaMalloc(&s->d_carry, s->stride * gch)) || (e = cudaMalloc(&s->d_carry_bytes, sizeof(uint64_t) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the carry buffer failed");
@@ -253,6 +259,7 @@ void sv_config_default(sv_config* cfg)
     cfg->host_budget_bytes = 0;
     cfg->fuse_codec = 1;
     cfg->jit = 1;
+    cfg->relative_bound = 0;
     cfg->timeout_s = 600.0;
 }
 
@@ -287,6 +294,9 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
         k = step_exponent(abs_error_bound);
         const int kmin = cfg.dtype == SV_C64 ? -23 : -29;  // |q| of an amplitude of magnitude 1 must fit
         if (k < kmin) return reject(SV_ERR_RANGE, "abs_error_bound too small for the quantiser's integer range");
+        // relative bound: |q| < 1/eb must fit the quantiser
+        if (cfg.relative_bound && abs_error_bound < std::ldexp(1.0, kmin))
+            return reject(SV_ERR_RANGE, "relative bound: eb below 2^-23 (complex64) / 2^-29 (complex128)");
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -306,6 +316,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     s->nh = n - s->c;
     s->eb = abs_error_bound;
     s->k = k;
+    s->rel = cfg.mode == SV_COMPRESSED && cfg.relative_bound != 0;
     s->gmax = cfg.max_group_qubits ? cfg.max_group_qubits : auto_group_qubits(n, chunk_qubits, cfg);
     s->nslots = cfg.pipeline_slots;
     s->tq = cfg.tile_qubits ? cfg.tile_qubits : kPhaseTileQubits;
@@ -548,13 +559,16 @@ size_t sv_codec_max_bytes(int chunk_qubits)
     return codec_layout(chunk_qubits).max_bytes;
 }
 
-int sv_codec_encode(int dtype, int c, double eb, const void* d_amps, void* d_stream, size_t cap, size_t* h_nbytes)
+static int codec_encode_impl(int dtype, int c, double eb, const void* d_amps, void* d_stream, size_t cap,
+                             size_t* h_nbytes, bool relative)
 {
     if ((dtype != SV_C64 && dtype != SV_C128) || c < 8 || c > 30 || !d_amps || !d_stream || !h_nbytes)
         return SV_ERR_ARG;
     if (!(eb > 0) || !std::isfinite(eb) || eb > 1.0) return SV_ERR_ARG;
     const int k = step_exponent(eb);
     if (k < -60) return SV_ERR_RANGE;
+    // relative bound: |q| < 1/eb must fit the quantiser (2^24 - 1 / 2^30 - 1)
+    if (relative && eb < std::ldexp(1.0, dtype == SV_C64 ? -23 : -29)) return SV_ERR_RANGE;
     const CodecLayout L = codec_layout(c);
     if (cap < L.p_off) return SV_ERR_ARG;
     uint32_t* d_sparse = nullptr;
@@ -562,13 +576,17 @@ int sv_codec_encode(int dtype, int c, double eb, const void* d_amps, void* d_str
     ChunkOut* d_co = nullptr;
     int* d_err = nullptr;
     uint8_t* d_tmp = nullptr;
+    unsigned long long* d_mbits = nullptr;
+    int32_t* d_kc = nullptr;
     cudaError_t e;
     int r = SV_OK;
     // the encoder writes a whole worst-case slot; use a temporary when cap is smaller
     const bool direct = cap >= L.max_bytes;
     if ((e = cudaMalloc(&d_sparse, (size_t)L.nb * 1024)) || (e = cudaMalloc(&d_bsq, 8ull * L.bpc)) ||
         (e = cudaMalloc(&d_co, sizeof(ChunkOut))) || (e = cudaMalloc(&d_err, sizeof(int))) ||
-        (!direct && (e = cudaMalloc(&d_tmp, L.max_bytes)))) {
+        (!direct && (e = cudaMalloc(&d_tmp, L.max_bytes))) ||
+        (relative && ((e = cudaMalloc(&d_mbits, sizeof(unsigned long long))) ||
+                      (e = cudaMalloc(&d_kc, sizeof(int32_t)))))) {
         cudaGetLastError();
         r = SV_ERR_DEVICE_OOM;
     } else {
@@ -576,10 +594,15 @@ int sv_codec_encode(int dtype, int c, double eb, const void* d_amps, void* d_str
         ChunkOut co{};
         int herr = 0;
         cudaMemset(d_err, 0, sizeof(int));
-        e = dtype == SV_C64
-                ? launch_encode<float>(d_amps, c, dtype, k, 1, dst, L.max_bytes, d_sparse, d_bsq, d_co, d_err, 0, nullptr)
-                : launch_encode<double>(d_amps, c, dtype, k, 1, dst, L.max_bytes, d_sparse, d_bsq, d_co, d_err, 0,
-                                        nullptr);
+        e = cudaSuccess;
+        if (relative)
+            e = dtype == SV_C64 ? launch_chunk_steps<float>(d_amps, c, 1, eb, d_mbits, d_kc, 0, nullptr)
+                                : launch_chunk_steps<double>(d_amps, c, 1, eb, d_mbits, d_kc, 0, nullptr);
+        if (!e)
+            e = dtype == SV_C64 ? launch_encode<float>(d_amps, c, dtype, k, 1, dst, L.max_bytes, d_sparse, d_bsq,
+                                                       d_co, d_err, 0, nullptr, d_kc)
+                                : launch_encode<double>(d_amps, c, dtype, k, 1, dst, L.max_bytes, d_sparse, d_bsq,
+                                                        d_co, d_err, 0, nullptr, d_kc);
         if (e || (e = cudaMemcpy(&co, d_co, sizeof(co), cudaMemcpyDeviceToHost)) ||
             (e = cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost))) {
             r = SV_ERR_CUDA;
@@ -597,7 +620,20 @@ int sv_codec_encode(int dtype, int c, double eb, const void* d_amps, void* d_str
     cudaFree(d_co);
     cudaFree(d_err);
     cudaFree(d_tmp);
+    cudaFree(d_mbits);
+    cudaFree(d_kc);
     return r;
+}
+
+int sv_codec_encode(int dtype, int c, double eb, const void* d_amps, void* d_stream, size_t cap, size_t* h_nbytes)
+{
+    return codec_encode_impl(dtype, c, eb, d_amps, d_stream, cap, h_nbytes, false);
+}
+
+int sv_codec_encode_relative(int dtype, int c, double eb, const void* d_amps, void* d_stream, size_t cap,
+                             size_t* h_nbytes)
+{
+    return codec_encode_impl(dtype, c, eb, d_amps, d_stream, cap, h_nbytes, true);
 }
 
 int sv_codec_decode(int dtype, int c, const void* d_stream, size_t nbytes, void* d_amps)

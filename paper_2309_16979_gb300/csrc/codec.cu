@@ -86,8 +86,8 @@ k_decode(const uint8_t* __restrict__ in, size_t stride, int c, int dtype, uint64
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_encode_blocks(const typename V2<R>::T* __restrict__ amps, int c, uint64_t nwarps, int k,
-                uint8_t* __restrict__ out, size_t stride, uint32_t* __restrict__ sparse,
-                unsigned long long* __restrict__ blocksq, int* err)
+                const int32_t* __restrict__ kc, uint8_t* __restrict__ out, size_t stride,
+                uint32_t* __restrict__ sparse, unsigned long long* __restrict__ blocksq, int* err)
 {
     __shared__ __align__(16) uint32_t pk[8][2][260];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -99,16 +99,17 @@ k_encode_blocks(const typename V2<R>::T* __restrict__ amps, int c, uint64_t nwar
     const uint32_t bp = (uint32_t)(gw & ((1ull << sh) - 1));
     R x[2][8];
     load8(amps + ((uint64_t)r << c) + 256ull * bp + 8ull * lane, x);
-    codec::encode_pair<R>(x, c, k, bp, out + (size_t)r * stride, sparse + (uint64_t)r * L.nb * 256ull,
+    codec::encode_pair<R>(x, c, kc ? kc[r] : k, bp, out + (size_t)r * stride, sparse + (uint64_t)r * L.nb * 256ull,
                           blocksq + (uint64_t)r * L.bpc + bp, pk[wib], err, lane);
 }
 
 // One CTA per chunk: widths -> offsets (exclusive scan of 8*w), header,
 // zeroed padding, and the chunk's record {bytes, sum q^2}.
 __global__ void __launch_bounds__(1024)
-k_encode_scan(uint8_t* __restrict__ out, size_t stride, int c, int dtype, int k,
+k_encode_scan(uint8_t* __restrict__ out, size_t stride, int c, int dtype, int k0, const int32_t* __restrict__ kc,
               const unsigned long long* __restrict__ blocksq, ChunkOut* __restrict__ co)
 {
+    const int k = kc ? kc[blockIdx.x] : k0;
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long qsum[32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -173,6 +174,8 @@ k_encode_scan(uint8_t* __restrict__ out, size_t stride, int c, int dtype, int k,
         for (size_t i = L.o_off + 4ull * (nb + 1); i < L.p_off; i++) so[i] = 0;
         co[r].bytes = L.p_off + 4ull * total;
         co[r].sumsq = tot2;
+        co[r].k = k;
+        co[r].pad = 0;
     }
 }
 
@@ -220,6 +223,49 @@ k_encode_compact(uint8_t* __restrict__ out, size_t stride, int c, uint64_t nwarp
     }
 }
 
+// Relative bound: the largest |re| or |im| of each chunk, as the bits of a
+// non-negative float / double (their order is the values' order), merged by
+// atomicMax per CTA; grid.y = chunk.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_chunk_max(const R* __restrict__ comps, int c, unsigned long long* __restrict__ mbits)
+{
+    const uint64_t n = 2ull << c, r = blockIdx.y;
+    const R* x = comps + r * n;
+    unsigned long long m = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        // fabs clears the sign bit (a -0.0 would otherwise order above every value)
+        const unsigned long long b = sizeof(R) == 4
+                                         ? (unsigned long long)__float_as_uint(fabsf((float)x[i]))
+                                         : (unsigned long long)__double_as_longlong(fabs((double)x[i]));
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&mbits[r], m);
+}
+
+// step exponent of each chunk: floor(log2(2 eb m)) clamped to [-60, 0], 0 for
+// an all-zero chunk (2 eb exact, one rounded FP64 product, exact exponent)
+template <typename R>
+__global__ void k_chunk_steps(const unsigned long long* __restrict__ mbits, double two_eb, int nchunks,
+                              int32_t* __restrict__ kc)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nchunks) return;
+    const double m = sizeof(R) == 4 ? (double)__uint_as_float((unsigned)mbits[r])
+                                    : __longlong_as_double((long long)mbits[r]);
+    int k = 0;
+    if (m > 0) {
+        const double v = __dmul_rn(two_eb, m);
+        k = v >= 1.0 ? 0 : max(-60, ilogb(v));
+    }
+    kc[r] = k;
+}
+
 template <typename R>
 __global__ void k_fill_basis(typename V2<R>::T* amps, uint64_t count, int64_t one_at)
 {
@@ -248,22 +294,35 @@ cudaError_t launch_decode(const uint8_t* in, size_t stride, int c, int dtype, in
 }
 
 template <typename R>
+cudaError_t launch_chunk_steps(const void* amps, int c, int nchunks, double eb, unsigned long long* mbits,
+                               int32_t* kc, cudaStream_t st, int* launches)
+{
+    cudaError_t e = cudaMemsetAsync(mbits, 0, sizeof(unsigned long long) * nchunks, st);
+    if (e) return e;
+    const unsigned bx = (unsigned)std::min<uint64_t>((2ull << c) / 256 / 8 + 1, 4096);
+    k_chunk_max<R><<<dim3(bx, (unsigned)nchunks), 256, 0, st>>>(static_cast<const R*>(amps), c, mbits);
+    k_chunk_steps<R><<<(nchunks + 255) / 256, 256, 0, st>>>(mbits, 2.0 * eb, nchunks, kc);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks, uint8_t* out,
                           size_t stride, uint32_t* sparse, unsigned long long* blocksq,
-                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches)
+                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches, const int32_t* kc)
 {
     const uint64_t nw = (uint64_t)nchunks << (c - 8);
     k_encode_blocks<R><<<blocks_for_warps(nw), 256, 0, st>>>(
-        static_cast<const typename V2<R>::T*>(amps), c, nw, k, out, stride, sparse, blocksq, err);
+        static_cast<const typename V2<R>::T*>(amps), c, nw, k, kc, out, stride, sparse, blocksq, err);
     if (launches) *launches += 1;
-    return launch_encode_finish(c, dtype, k, nchunks, out, stride, sparse, blocksq, chunk_out, st, launches);
+    return launch_encode_finish(c, dtype, k, nchunks, out, stride, sparse, blocksq, chunk_out, st, launches, kc);
 }
 
 cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* out, size_t stride,
                                  const uint32_t* sparse, const unsigned long long* blocksq, ChunkOut* chunk_out,
-                                 cudaStream_t st, int* launches)
+                                 cudaStream_t st, int* launches, const int32_t* kc)
 {
-    k_encode_scan<<<nchunks, 1024, 0, st>>>(out, stride, c, dtype, k, blocksq, chunk_out);
+    k_encode_scan<<<nchunks, 1024, 0, st>>>(out, stride, c, dtype, k, kc, blocksq, chunk_out);
     // blocks per chunk: 2^(c-7); a warp takes up to kBlocksPerWarp of them
     const int lbw = std::min(3, c - 7);
     const uint64_t nw2 = (uint64_t)nchunks << (c - 7 - lbw);
@@ -333,9 +392,14 @@ template cudaError_t launch_decode<float>(const uint8_t*, size_t, int, int, int,
 template cudaError_t launch_decode<double>(const uint8_t*, size_t, int, int, int, const GroupIn&, void*,
                                            double, int*, cudaStream_t);
 template cudaError_t launch_encode<float>(const void*, int, int, int, int, uint8_t*, size_t, uint32_t*,
-                                          unsigned long long*, ChunkOut*, int*, cudaStream_t, int*);
+                                          unsigned long long*, ChunkOut*, int*, cudaStream_t, int*, const int32_t*);
 template cudaError_t launch_encode<double>(const void*, int, int, int, int, uint8_t*, size_t, uint32_t*,
-                                           unsigned long long*, ChunkOut*, int*, cudaStream_t, int*);
+                                           unsigned long long*, ChunkOut*, int*, cudaStream_t, int*,
+                                           const int32_t*);
+template cudaError_t launch_chunk_steps<float>(const void*, int, int, double, unsigned long long*, int32_t*,
+                                               cudaStream_t, int*);
+template cudaError_t launch_chunk_steps<double>(const void*, int, int, double, unsigned long long*, int32_t*,
+                                                cudaStream_t, int*);
 template cudaError_t launch_fill_basis<float>(void*, uint64_t, int64_t, cudaStream_t);
 template cudaError_t launch_fill_basis<double>(void*, uint64_t, int64_t, cudaStream_t);
 

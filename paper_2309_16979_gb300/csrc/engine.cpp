@@ -455,7 +455,8 @@ static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates,
     // holds whole block pairs (local bits 0..7) needs no extra sub-pass, and
     // the encode into the last sub-pass when its tile holds them.
     bool fdec = false, fenc = false;
-    if (t == kPhaseTileQubits && l >= 4 && l <= 5 && c >= 8 && !subs.empty() && s->cfg.fuse_codec) {
+    // (the relative bound's step needs the chunk maximum before any block is encoded)
+    if (t == kPhaseTileQubits && l >= 4 && l <= 5 && c >= 8 && !subs.empty() && s->cfg.fuse_codec && !s->rel) {
         std::vector<SubPlan> alt = plan_subpasses(hops, L, t, l, true, 8);
         if (!alt.empty() && alt.size() <= subs.size()) {
             subs.swap(alt);
@@ -502,7 +503,6 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
     // renormalisation feeds a pass's norm into the next pass's decode: no
     // lookahead across passes then
     const bool cross = !s->cfg.renormalize;
-    const double delta2 = std::ldexp(1.0, 2 * s->k);
     std::vector<std::vector<uint64_t>> slot_chunks(NS);
     std::vector<int> slot_prof(NS, -1);
     std::vector<std::pair<uint64_t, int>> carry_next;  // chunks the current pass leaves in d_carry
@@ -620,8 +620,12 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
         } else {
             pi = prof_begin(s);
             slot_prof[slot] = pi;
+            if (s->rel && (e = launch_chunk_steps<R>(s->d_amps, c, gch, s->eb, s->d_mbits, s->d_kc, s->s_comp,
+                                                     &launches)))
+                return cuda_fail(s, e, "chunk steps");
             if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
-                                      s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)))
+                                      s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches,
+                                      s->rel ? s->d_kc : nullptr)))
                 return cuda_fail(s, e, "encode");
             prof_end(s, pi, PROF_ENCODE, amp_bytes);
         }
@@ -669,7 +673,7 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
             s->cur[k] = {dst, co.bytes};
             s->st.bytes_d2h += co.bytes;
             if (slot_prof[slot] >= 0) s->prof_rec[slot_prof[slot]].bytes += co.bytes;
-            P.norm2 += (double)co.sumsq * delta2;
+            P.norm2 += (double)co.sumsq * std::ldexp(1.0, 2 * co.k);
         }
         prof_end(s, pd2h, PROF_D2H, 0, s->s_d2h);
         if ((e = cudaEventRecord(s->ev_d2h[slot], s->s_d2h)) || (e = cudaEventRecord(s->ev_prev_d2h, s->s_d2h)))
@@ -874,8 +878,10 @@ int init_state(sv_state* s)
                                   s->s_comp)))
         return cuda_fail(s, e, "fill");
     int launches = 1;
+    if (s->rel && (e = launch_chunk_steps<R>(s->d_amps, c, nenc, s->eb, s->d_mbits, s->d_kc, s->s_comp, &launches)))
+        return cuda_fail(s, e, "chunk steps");
     if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, nenc, s->d_out[0], s->stride, s->d_sparse,
-                              s->d_blocksq, s->d_co[0], s->d_err, s->s_comp, &launches)))
+                              s->d_blocksq, s->d_co[0], s->d_err, s->s_comp, &launches, s->rel ? s->d_kc : nullptr)))
         return cuda_fail(s, e, "encode");
     s->st.kernel_launches += launches;
     if ((e = cudaMemcpyAsync(s->h_co[0], s->d_co[0], sizeof(ChunkOut) * nenc, cudaMemcpyDeviceToHost, s->s_comp)))
@@ -1380,8 +1386,11 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         if ((e = launch_ham_chunk<R>(amps, s->d_amps2, c, d_terms + k * nt, (int)nt, s->s_comp)) ||
             (e = launch_dot<R>(amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
+            (s->rel && (e = launch_chunk_steps<R>(s->d_amps2, c, 1, s->eb, s->d_mbits, s->d_kc, s->s_comp,
+                                                  &launches))) ||
             (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, 1, s->d_out2[sl], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co2[sl], s->d_err, s->s_comp, &launches)) ||
+                                  s->d_blocksq, s->d_co2[sl], s->d_err, s->s_comp, &launches,
+                                  s->rel ? s->d_kc : nullptr)) ||
             (e = cudaMemcpyAsync(s->h_co2[sl], s->d_co2[sl], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)) ||
             (e = cudaEventRecord(s->ev_comp[sl], s->s_comp)))
             return cuda_fail(s, e, "lambda chunk");
@@ -1531,10 +1540,15 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
         }
         int launches = 0;
         pi = prof_begin(s);
-        if ((e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches)) ||
+        int32_t* kc = s->rel ? s->d_kc : nullptr;
+        if ((s->rel && (e = launch_chunk_steps<R>(s->d_amps, c, gch, s->eb, s->d_mbits, s->d_kc, s->s_comp,
+                                                  &launches))) ||
+            (e = launch_encode<R>(s->d_amps, c, s->dtype, s->k, gch, s->d_out[slot], s->stride, s->d_sparse,
+                                  s->d_blocksq, s->d_co[slot], s->d_err, s->s_comp, &launches, kc)) ||
+            (s->rel && (e = launch_chunk_steps<R>(s->d_amps2, c, gch, s->eb, s->d_mbits, s->d_kc, s->s_comp,
+                                                  &launches))) ||
             (e = launch_encode<R>(s->d_amps2, c, s->dtype, s->kl, gch, s->d_out2[slot], s->stride, s->d_sparse,
-                                  s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches)))
+                                  s->d_blocksq, s->d_co2[slot], s->d_err, s->s_comp, &launches, kc)))
             return cuda_fail(s, e, "encode");
         prof_end(s, pi, PROF_ENCODE, 2 * amp_bytes);
         if ((e = cudaMemcpyAsync(s->h_co[slot], s->d_co[slot], sizeof(ChunkOut) * gch, cudaMemcpyDeviceToHost,

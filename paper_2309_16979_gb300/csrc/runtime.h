@@ -166,6 +166,10 @@ struct sv_state {
     sv::ChunkOut* d_co2[4] = {};
     sv::ChunkOut* h_co2[4] = {};
     void* d_amps2 = nullptr;
+    // relative bound: per-chunk step exponents of a group and their scratch
+    bool rel = false;
+    int32_t* d_kc = nullptr;
+    unsigned long long* d_mbits = nullptr;
     // device op list
     void* d_ops = nullptr;
     size_t ops_cap = 0;

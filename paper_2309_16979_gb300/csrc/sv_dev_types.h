@@ -50,6 +50,8 @@ __host__ __device__ inline CodecLayout codec_layout(int c)
 struct ChunkOut {
     uint64_t bytes;   // stream length
     uint64_t sumsq;   // sum of q^2 over the chunk (exact; norm^2 = sumsq * Delta^2)
+    int32_t k;        // the chunk's step exponent, Delta = 2^k
+    int32_t pad;
 };
 
 enum : int { kErrCorrupt = 1, kErrRange = 2 };

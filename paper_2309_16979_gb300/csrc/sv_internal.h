@@ -100,7 +100,15 @@ cudaError_t launch_decode(const uint8_t* in, size_t stride, int c, int dtype, in
 template <typename R>
 cudaError_t launch_encode(const void* amps, int c, int dtype, int k, int nchunks, uint8_t* out,
                           size_t stride, uint32_t* sparse, unsigned long long* blocksq,
-                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches);
+                          ChunkOut* chunk_out, int* err, cudaStream_t st, int* launches,
+                          const int32_t* kc = nullptr);
+
+// Relative bound: per-chunk step exponents kc[0..nchunks) of the chunks at
+// amps (2^c amplitudes each) from their largest component (mbits: scratch).
+// launch_encode with kc != nullptr encodes chunk r with step 2^kc[r].
+template <typename R>
+cudaError_t launch_chunk_steps(const void* amps, int c, int nchunks, double eb, unsigned long long* mbits,
+                               int32_t* kc, cudaStream_t st, int* launches);
 
 template <typename R>
 cudaError_t launch_apply(void* amps, const TileDesc& td, const DevOp<R>* ops, int nops,
@@ -126,7 +134,7 @@ cudaError_t launch_apply_phases(void* amps, const TileDesc& td, const Phase* pha
 
 cudaError_t launch_encode_finish(int c, int dtype, int k, int nchunks, uint8_t* out, size_t stride,
                                  const uint32_t* sparse, const unsigned long long* blocksq, ChunkOut* chunk_out,
-                                 cudaStream_t st, int* launches);
+                                 cudaStream_t st, int* launches, const int32_t* kc = nullptr);
 
 template <typename R>
 cudaError_t launch_fill_basis(void* amps, uint64_t count, int64_t one_at, cudaStream_t st);

@@ -112,3 +112,24 @@ def test_corrupt_streams_rejected_on_gpu(sv):
         with pytest.raises(sv.SvError) as ei:
             sv.codec_decode(d, nb, c)
         assert ei.value.code == -4
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("kind", ["random", "smooth", "zero", "constant", "alternating", "unit", "wide", "tiny"])
+@pytest.mark.parametrize("c", [8, 14])
+def test_relative_stream_bytes_match_oracle(sv, dtype, kind, c):
+    """Relative bound: the per-chunk step from the chunk maximum, GPU against
+    the oracle byte for byte, and the bound max(eb m, 2^-61) on the decode."""
+    for eb in (1e-2, 1e-5):
+        x = _planes("random" if kind == "tiny" else kind, c, dtype, seed=c + 1)
+        if kind == "tiny":
+            x = (x * 1e-15).astype(dtype)
+        d = torch.from_numpy(x).cuda()
+        stream, nb = sv.codec_encode(d, eb, relative=True)
+        got = stream[:nb].cpu().numpy().tobytes()
+        assert got == oracle.codec_encode(x, eb, relative=True)
+        back = sv.codec_decode(stream, nb, c, "c64" if dtype == np.complex64 else "c128").cpu().numpy()
+        m = max(np.abs(x.real).max(), np.abs(x.imag).max())
+        bound = max(eb * float(m), 2.0 ** -61)
+        assert np.abs(back.real.astype(np.float64) - x.real.astype(np.float64)).max() <= bound
+        assert np.abs(back.imag.astype(np.float64) - x.imag.astype(np.float64)).max() <= bound

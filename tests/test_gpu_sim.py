@@ -242,3 +242,59 @@ def test_phase_kernel_every_gate_kind_and_control(SV):
     with SV(n, mode="uncompressed", dtype="c128", init_index=77) as s:
         s.apply(gates)
         assert rel_l2(s.state(), want) <= 1e-12
+
+
+def test_relative_bound_keeps_a_spread_state(SV):
+    """QFT-16 of a basis state at eb = 1e-2: every amplitude (2^-8) sits under
+    half the absolute step (2^-7), so the absolute bound collapses the state;
+    the relative bound (step from each chunk's largest component) keeps it."""
+    import paper_2309_16979_gb300 as P
+    n, c, eb = 16, 10, 1e-2
+    x = W.basis_index(n)
+    gates = W.qft(n)
+    want = oracle.run(n, gates, init=x)
+    with pytest.raises(P.SvError):
+        with SV(n, c, eb, init_index=x) as s:
+            s.apply(gates)
+    with SV(n, c, eb, init_index=x, relative_bound=True) as s:
+        s.apply(gates)
+        got = s.state()
+        st = s.stats()
+    # each pass moves a stored component by at most eb times its chunk's
+    # largest component (<= 1)
+    assert np.linalg.norm(got - want) <= compressed_l2_bound(n, eb, st["passes"], len(gates))
+    fid = abs(np.vdot(want, got)) ** 2 / np.vdot(got, got).real
+    assert fid > 1 - 1e-3
+    assert abs(st["norm2"] - np.vdot(got, got).real) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_relative_store_is_byte_exact_with_oracle_codec(SV, dtype):
+    """Relative bound: re-encoding the stored state chunk by chunk with the
+    oracle's relative codec reproduces it exactly (each chunk's step is the
+    one its own maximum gives), and the circuit stays within the bound."""
+    n, c, eb = 14, 9, 1e-4
+    gates = W.random_layers(n, 4, seed=13)
+    want = oracle.run(n, gates, init=3)
+    with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=3, relative_bound=True) as s:
+        s.apply(gates)
+        held = s.state().astype(np.complex64 if dtype == "c64" else np.complex128)
+        st = s.stats()
+    assert np.array_equal(oracle.compress_roundtrip(held, c, eb, relative=True), held)
+    assert np.linalg.norm(held - want) <= compressed_l2_bound(n, eb, st["passes"], len(gates), dtype)
+
+
+def test_relative_bound_adjoint_gradient(SV):
+    """Compressed adjoint gradient with the relative bound: both stores keep
+    their spread amplitudes; the gradient matches the oracle's adjoint to the
+    quantisation level."""
+    n, c = 12, 8
+    gates, npar = W.hea(n, 2)
+    theta = np.array(W.normal_params(npar, seed=3))
+    terms = W.ising(n, seed=4)
+    e_ref, g_ref = oracle.adjoint(n, gates, theta, terms)
+    with SV(n, c, 1e-5, max_group_qubits=3, relative_bound=True) as s:
+        e, g = s.grad(gates, theta, terms)
+    csum = sum(abs(t.coeff) for t in terms)
+    assert abs(e - e_ref) <= 1e-3 * csum
+    assert np.abs(g - g_ref).max() <= 1e-3 * csum
