@@ -40,54 +40,89 @@ template <typename R> struct QLimit;
 template <> struct QLimit<float> { static constexpr float v = 16777215.0f; };     // 2^24 - 1
 template <> struct QLimit<double> { static constexpr double v = 1073741823.0; };  // 2^30 - 1
 
-// Validate and decode block pair bp of the chunk stream s (nbytes long, at
-// most `limit` bytes may be read) into x[plane][m] for j = 8*lane + m.
-// sbuf: this warp's 2 x 264 words of shared memory. Returns false (for the
-// whole warp) if the stream fails validation; x is then undefined.
-template <typename R>
-__device__ __forceinline__ bool decode_pair(const uint8_t* __restrict__ s, uint64_t nbytes, uint64_t limit, int c,
-                                            int dtype, uint32_t bp, uint32_t (*sbuf)[264], R scale, R (&x)[2][8],
-                                            int lane)
+// Decoding one block pair runs in stages, so that a warp can overlap the
+// memory round trips of two pairs: pair_meta (the header and the pair's
+// widths, offsets and anchors, one round trip, validated), pair_load (the
+// lane's share of the packed words into registers), pair_stage (into the
+// warp's shared words), pair_unpack (widths -> residuals -> inclusive scan
+// from the anchor -> q * Delta).
+struct PairMeta {
+    uint32_t w[2], off[2];
+    int32_t anc[2];
+    int k;
+    bool ok;
+};
+
+// block pair bp of the chunk stream s (nbytes long, at most `limit` bytes may
+// be read); ok = false (for the whole warp) when the stream fails validation
+__device__ __forceinline__ PairMeta pair_meta(const uint8_t* __restrict__ s, uint64_t nbytes, uint64_t limit, int c,
+                                              int dtype, uint32_t bp)
 {
+    PairMeta pm;
+    pm.ok = false;
+    pm.k = 0;
+    for (int p = 0; p < 2; p++) pm.w[p] = pm.off[p] = 0, pm.anc[p] = 0;
     const CodecLayout L = codec_layout(c);
-    if (!(nbytes >= L.p_off && nbytes <= limit)) return false;
+    if (!(nbytes >= L.p_off && nbytes <= limit)) return pm;
     // the header and this pair's metadata lie below p_off <= nbytes: all of
-    // them are loaded at once (one memory round trip), then validated
+    // them are loaded at once, then validated
     const uint32_t h0 = ld32(s), h1 = ld32(s + 4), nbh = ld32(s + 12);
     const int k = (int32_t)ld32(s + 8);
     const uint32_t total = ld32(s + 16);
-    uint32_t w[2], off[2], nxt[2];
-    int32_t anc[2];
+    uint32_t nxt[2];
 #pragma unroll
     for (int p = 0; p < 2; p++) {
         const uint32_t b = p ? bp + L.bpc : bp;
-        w[p] = s[L.w_off + b];
-        off[p] = ld32(s + L.o_off + 4ull * b);
+        pm.w[p] = s[L.w_off + b];
+        pm.off[p] = ld32(s + L.o_off + 4ull * b);
         nxt[p] = ld32(s + L.o_off + 4ull * (b + 1));
-        anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
+        pm.anc[p] = (int32_t)ld32(s + L.a_off + 4ull * b);
     }
     bool ok = h0 == kMagic && (h1 & 0xffffu) == 1u && ((h1 >> 16) & 0xffu) == (uint32_t)dtype &&
               (h1 >> 24) == (uint32_t)c && k <= 0 && k >= -60 && nbh == L.nb && L.p_off + 4ull * total <= nbytes;
 #pragma unroll
     for (int p = 0; p < 2; p++)
-        ok = ok && w[p] <= 32u && nxt[p] - off[p] == 8u * w[p] &&
-             L.p_off + 4ull * ((uint64_t)off[p] + 8ull * w[p]) <= nbytes;
+        ok = ok && pm.w[p] <= 32u && nxt[p] - pm.off[p] == 8u * pm.w[p] &&
+             L.p_off + 4ull * ((uint64_t)pm.off[p] + 8ull * pm.w[p]) <= nbytes;
     if (bp == 0) ok = ok && ld32(s + L.o_off) == 0u && ld32(s + L.o_off + 4ull * L.nb) == total;
-    if (!ok) return false;
-    __syncwarp();
+    pm.k = k;
+    pm.ok = ok;
+    return pm;
+}
+
+// the lane's 16-byte words of each plane's packed block (2w <= 64 words)
+__device__ __forceinline__ void pair_load(const uint8_t* __restrict__ s, int c, const PairMeta& pm, uint4 (&v)[2][2],
+                                          int lane)
+{
+    const CodecLayout L = codec_layout(c);
 #pragma unroll
     for (int p = 0; p < 2; p++) {
-        if (w[p] == 0) continue;
-        const uint4* src = reinterpret_cast<const uint4*>(s + L.p_off + 4ull * off[p]);
-        uint4* dst = reinterpret_cast<uint4*>(sbuf[p]);
-        for (uint32_t i = lane; i < 2 * w[p]; i += 32) dst[i] = src[i];
-        if (lane == 0) sbuf[p][8 * w[p]] = 0u;
+        const uint4* src = reinterpret_cast<const uint4*>(s + L.p_off + 4ull * pm.off[p]);
+        if ((uint32_t)lane < 2 * pm.w[p]) v[p][0] = src[lane];
+        if ((uint32_t)lane + 32 < 2 * pm.w[p]) v[p][1] = src[lane + 32];
     }
-    __syncwarp();
-    const R delta = pow2<R>(k);
+}
+
+__device__ __forceinline__ void pair_stage(const PairMeta& pm, const uint4 (&v)[2][2], uint32_t (*sbuf)[264], int lane)
+{
 #pragma unroll
     for (int p = 0; p < 2; p++) {
-        const uint32_t ww = w[p];
+        uint4* dst = reinterpret_cast<uint4*>(sbuf[p]);
+        if ((uint32_t)lane < 2 * pm.w[p]) dst[lane] = v[p][0];
+        if ((uint32_t)lane + 32 < 2 * pm.w[p]) dst[lane + 32] = v[p][1];
+        if (lane == 0) sbuf[p][8 * pm.w[p]] = 0u;
+    }
+}
+
+// x[plane][m] for j = 8*lane + m from the staged words (after a __syncwarp)
+template <typename R>
+__device__ __forceinline__ void pair_unpack(const PairMeta& pm, const uint32_t (*sbuf)[264], R scale, R (&x)[2][8],
+                                            int lane)
+{
+    const R delta = pow2<R>(pm.k);
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const uint32_t ww = pm.w[p];
         const uint32_t mask = ww >= 32u ? FULL : ((1u << ww) - 1u);
         uint32_t v[8];
 #pragma unroll
@@ -110,7 +145,7 @@ __device__ __forceinline__ bool decode_pair(const uint8_t* __restrict__ s, uint6
             const uint32_t t = __shfl_up_sync(FULL, incl, d);
             if (lane >= d) incl += t;
         }
-        const uint32_t base = (uint32_t)anc[p] + (incl - tot);
+        const uint32_t base = (uint32_t)pm.anc[p] + (incl - tot);
 #pragma unroll
         for (int m = 0; m < 8; m++) {
             R val = from_q<R>((int32_t)(base + v[m])) * delta;
@@ -118,6 +153,25 @@ __device__ __forceinline__ bool decode_pair(const uint8_t* __restrict__ s, uint6
             x[p][m] = val;
         }
     }
+}
+
+// Validate and decode block pair bp of the chunk stream s (nbytes long, at
+// most `limit` bytes may be read) into x[plane][m] for j = 8*lane + m.
+// sbuf: this warp's 2 x 264 words of shared memory. Returns false (for the
+// whole warp) if the stream fails validation; x is then undefined.
+template <typename R>
+__device__ __forceinline__ bool decode_pair(const uint8_t* __restrict__ s, uint64_t nbytes, uint64_t limit, int c,
+                                            int dtype, uint32_t bp, uint32_t (*sbuf)[264], R scale, R (&x)[2][8],
+                                            int lane)
+{
+    const PairMeta pm = pair_meta(s, nbytes, limit, c, dtype, bp);
+    if (!pm.ok) return false;
+    uint4 v[2][2];
+    pair_load(s, c, pm, v, lane);
+    __syncwarp();
+    pair_stage(pm, v, sbuf, lane);
+    __syncwarp();
+    pair_unpack<R>(pm, sbuf, scale, x, lane);
     return true;
 }
 
