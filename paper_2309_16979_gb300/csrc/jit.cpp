@@ -1030,8 +1030,8 @@ void jit_key(const Phase* ph, int nph, const PhaseOp<R>* ops, const CtaCtrl* ctl
     const uint8_t hdr[kKeyHeader] = {(uint8_t)sizeof(R), (uint8_t)dec, (uint8_t)enc, (uint8_t)(grad ? 2 : 1),
                                      (uint8_t)td.l};
     put(hdr, kKeyHeader);
-    // the direct stores' offsets are compiled in
-    if (direct_store(ph, nph, enc)) put(td.hpos, (size_t)(td.t - td.l));
+    // the direct stores' and the tile prefetch's offsets are compiled in
+    if (direct_store(ph, nph, enc) || (!grad && prefetches(dec, sizeof(R)))) put(td.hpos, (size_t)(td.t - td.l));
     for (int pi = 0; pi < nph; pi++) {
         const Phase& P = ph[pi];
         put(P.tpos, sizeof P.tpos);
@@ -1288,16 +1288,43 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     if (pf) {
         // tile buffer bo (element offset 0 or 4096) is processed while the
         // other one fills; bo is folded into every phase's base offset
-        // the next tile's base, computed for its prefetch, is carried over
-        src << "__syncthreads();\n"
+        // the next tile's base, computed for its prefetch, is carried over.
+        // The copies' offsets are compiled in (the tile's positions are part
+        // of the kernel's key): amplitude t + 256k of the tile (t = thread)
+        // sits at base + gld + OFF(256k) in HBM and at slot pad(t) + 273k of
+        // the buffer (the padded layout and the local offsets are additive
+        // over disjoint bits)
+        auto sh = [&](int b) { return b < lrow ? b : (int)td.hpos[b - lrow]; };
+        std::string gl;
+        for (int j = 0; j < 8; j++)
+            gl += (j ? " | " : "") + std::string("((uint64_t)((threadIdx.x >> ") + std::to_string(j) + ") & 1u) << " +
+                  std::to_string(sh(j)) + ")";
+        auto fetch = [&](const std::string& buf, const std::string& bse) {
+            std::ostringstream f;
+            f << "{ const T* const g = amps + " << bse << " + gld; const uint32_t d = dld + " << sizeof(R) * 2
+              << "u * (" << buf << ");\n";
+            for (uint32_t k = 0; k < 16; k++) {
+                uint64_t off = 0;
+                for (int i = 0; i < 4; i++)
+                    if ((k >> i) & 1u) off |= 1ull << sh(8 + i);
+                f << "asm volatile(\"cp.async.ca.shared.global [%0], [%1], 8;\\n\" :: \"r\"(d + " << sizeof(R) * 2 * 273u * k
+                  << "u), \"l\"(g + " << hex(off) << "ull) : \"memory\");\n";
+            }
+            f << "asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\"); }\n";
+            return f.str();
+        };
+        src << "const uint64_t gld = " << gl << ";\n"
+            << "const uint32_t dld = (uint32_t)__cvta_generic_to_shared(s) + " << sizeof(R) * 2
+            << "u * (threadIdx.x + (threadIdx.x >> 4));\n"
+            << "__syncthreads();\n"
             << "uint64_t base_n = blockIdx.x < ntiles ? tile::tile_base(rt, td, blockIdx.x) : 0ull;\n"
-            << "if (blockIdx.x < ntiles) tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s, amps, rt, td, base_n);\n"
+            << "if (blockIdx.x < ntiles) " << fetch("0u", "base_n")
             << "uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, bo = tile::kPadElems - bo) {\n"
             << "const uint64_t base = base_n;\n"
             << "tile::cp_async_wait_all();\n__syncthreads();\n"
             << "if (tl + gridDim.x < ntiles) {\nbase_n = tile::tile_base(rt, td, tl + gridDim.x);\n"
-            << "tile::prefetch_tile<T, tile::PadLayout, " << lb << ">(s + (tile::kPadElems - bo), amps, rt, td, base_n);\n}\n";
+            << fetch("tile::kPadElems - bo", "base_n") << "}\n";
     } else {
         src << "const uint32_t bo = 0;\n"
             << "for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {\n__syncthreads();\n"
