@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--group", type=int, default=None)
     p.add_argument("--sets", type=int, default=None, help="parameter sets for c4-grad")
     p.add_argument("--no-extras", action="store_true", help="skip the comparator and baseline legs")
+    p.add_argument("--table1", action="store_true",
+                   help="the paper's Table 1: host<->device copy strategies at 20 and 25 qubits")
     p.add_argument("--jit", type=int, default=1, choices=[0, 1],
                    help="1: sub-pass kernels generated per gate sequence (default); 0: table-driven kernel")
     a = p.parse_args()
@@ -541,6 +543,40 @@ def run_grad(args, rank, world):
             "errors_vs_fp64_gpu_adjoint": errors}
 
 
+# ------------------------------------------------------------- Table 1
+# the paper's numbers (seconds; hardware and precision not stated)
+PAPER_TABLE1 = {20: {"h2d": {"sync": 0.003, "async": 2.7, "buffer": 0.003},
+                     "d2h": {"sync": 0.008, "async": 9.2, "buffer": 0.004}},
+                25: {"h2d": {"sync": 0.080, "async": 77.9, "buffer": 0.110},
+                     "d2h": {"sync": 0.233, "async": 294.4, "buffer": 0.273}}}
+
+
+def run_table1(args):
+    """Sync / async-per-amplitude / buffer+remap copies of a complex128 state
+    (sv_copy_probe), median of 3 (async: the first 2^20 amplitudes timed,
+    scaled to 2^n)."""
+    from paper_2309_16979_gb300 import copy_probe
+    rows, verified = [], True
+    for n in (20, 25):
+        row = {"n_qubits": n}
+        for direction in ("h2d", "d2h"):
+            row[direction] = {}
+            for strategy in ("sync", "async", "buffer"):
+                times = []
+                for _ in range(1 if strategy == "async" else 3):
+                    t, ok = copy_probe(n, strategy, direction, "c128", sample=1 << 20 if strategy == "async" else 0)
+                    times.append(t)
+                    verified = verified and ok
+                row[direction][strategy] = sorted(times)[len(times) // 2]
+            row[direction]["async_over_sync"] = row[direction]["async"] / row[direction]["sync"]
+            row[direction]["buffer_over_sync"] = row[direction]["buffer"] / row[direction]["sync"]
+        rows.append(row)
+    return {"metric": "host<->device copy seconds (Table 1)", "unit": "s", "dtype": "c128", "data": "synthetic",
+            "rows": rows, "all_amplitudes_verified": verified, "paper": PAPER_TABLE1,
+            "note": "async copies the first 2^20 amplitudes one cudaMemcpyAsync each and scales to 2^n; "
+                    "buffer = one bulk copy + a kernel moving every amplitude to its position"}
+
+
 # ------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as the reference arm, on the same config and metric."""
@@ -578,6 +614,10 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world = dist_init()
+    if args.table1:
+        if rank == 0:
+            print(json.dumps(run_table1(args)), flush=True)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)), flush=True)

@@ -372,6 +372,30 @@ int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, 
  * byte-identical to sv_codec_encode's.
  */
 #define SV_NOALLOC_MAX_CHUNK_QUBITS 20
+/* ----------------------------------------------------------- transfers */
+/* The host <-> device copy strategies of Sec. 2 "Online stage" step (2) and
+ * Table 1, timed on a 2^n-amplitude state: SV_COPY_SYNC, one bulk copy;
+ * SV_COPY_ASYNC, one asynchronous copy per amplitude straight to its device
+ * position (timed on the first `sample` amplitudes, 0 = all, and scaled to
+ * 2^n); SV_COPY_BUFFER, one bulk copy into a device staging buffer and a
+ * kernel that moves every amplitude to its position (for SV_COPY_D2H the
+ * kernel gathers first). ASYNC and BUFFER place host amplitude i at device
+ * index i with its low n/2 and high n - n/2 index bits exchanged; SYNC keeps
+ * the order (the least time the bytes take).
+ *   n: 1..34; dtype: SV_C64 / SV_C128; direction: SV_COPY_H2D / SV_COPY_D2H.
+ *   seconds (host): wall time of the copies (host clock, synchronised).
+ *   verified (host, may be NULL): 1 if every moved amplitude arrived at its
+ *            position, 0 otherwise.
+ * Allocates (and frees) 2^n amplitudes of pinned host memory and one or two
+ * device arrays of that size. Errors: SV_ERR_ARG, SV_ERR_HOST_OOM,
+ * SV_ERR_DEVICE_OOM, SV_ERR_CUDA. */
+#define SV_COPY_SYNC 0
+#define SV_COPY_ASYNC 1
+#define SV_COPY_BUFFER 2
+#define SV_COPY_H2D 0
+#define SV_COPY_D2H 1
+int sv_copy_probe(int n, int dtype, int strategy, int direction, uint64_t sample, double* seconds, int* verified);
+
 /* sv_codec_encode with the relative bound of sv_config.relative_bound: the
  * chunk's step follows its largest component magnitude m (k in the stream
  * header), |x - xhat| <= max(eb m, 2^-61). eb >= 2^-23 (complex64) / 2^-29

@@ -180,6 +180,23 @@ def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", 
     return [x.decode() for x in parts]
 
 
+# --------------------------------------------------------------- transfers
+
+COPY_STRATEGIES = {"sync": 0, "async": 1, "buffer": 2}
+
+
+def copy_probe(n: int, strategy: str, direction: str = "h2d", dtype: str = "c128", sample: int = 0):
+    """Seconds to move a 2^n-amplitude state host -> device ("h2d") or back
+    ("d2h") by one of the paper's strategies (sv_copy_probe); returns
+    (seconds, verified)."""
+    sec = C.c_double(0.0)
+    ok = C.c_int(0)
+    _check(load().sv_copy_probe(n, SV_C64 if dtype == "c64" else SV_C128, COPY_STRATEGIES[strategy],
+                                0 if direction == "h2d" else 1, sample, C.byref(sec), C.byref(ok)),
+           "sv_copy_probe", None)
+    return sec.value, bool(ok.value)
+
+
 # ------------------------------------------------------------------ codec
 
 def codec_max_bytes(chunk_qubits: int) -> int:

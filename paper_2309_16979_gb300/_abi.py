@@ -63,7 +63,7 @@ EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "s
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
            "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile",
-           "sv_codec_encode_relative")
+           "sv_codec_encode_relative", "sv_copy_probe")
 
 _lib = None
 
@@ -118,6 +118,9 @@ def load() -> C.CDLL:
     L.sv_codec_encode_noalloc.restype = C.c_int
     L.sv_codec_encode_relative.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
     L.sv_codec_encode_relative.restype = C.c_int
+    L.sv_copy_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_double),
+                                C.POINTER(C.c_int)]
+    L.sv_copy_probe.restype = C.c_int
     L.sv_chunk_stream.argtypes = [P, C.c_uint64, P, SZ, C.POINTER(SZ)]
     L.sv_chunk_stream.restype = C.c_int
     L.sv_jit_sources.argtypes = [C.c_int, C.c_int, C.POINTER(SvConfig), P, SZ, C.c_int, C.c_char_p, SZ,

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "libsvgb300.so")
 BUILD = os.path.join(HERE, "_build")
 
 SOURCES = ["codec.cu", "apply.cu", "apply_phase.cu", "reduce.cu", "noalloc.cu", "plan.cpp", "engine.cpp", "api.cpp",
-           "jit.cpp"]
+           "jit.cpp", "transfer.cu"]
 # device headers embedded into the library for the kernels it generates and
 # compiles at run time (jit.cpp)
 JIT_HEADERS = ["sv_dev_types.h", "codec_dev.cuh", "tile_dev.cuh"]
