@@ -1038,21 +1038,15 @@ static PauliDev pauli_dev(const sv_pauli_term& t, uint64_t xl, uint64_t zl, uint
 
 static uint64_t mask_to_physical(const std::vector<int>& perm, uint64_t m) { return to_physical(perm, m); }
 
+// <psi| sum_t c_t P_t |psi> term group by term group: per distinct high
+// x-mask, chunk pairs (k, k ^ x) staged together (any x; the path for masks
+// wider than a staging group and for term counts beyond the one-sweep kernel).
 template <typename R>
-int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re)
+static int expect_pairs(sv_state* s, const std::vector<sv_pauli_term>& phys, double* out_re)
 {
     *out_re = 0;
+    const size_t nterms = phys.size();
     if (nterms == 0) return SV_OK;
-    const uint64_t dim_mask = (s->n >= 64) ? ~0ull : ((1ull << s->n) - 1);
-    for (size_t i = 0; i < nterms; i++)
-        if ((terms[i].xmask | terms[i].zmask) & ~dim_mask) return fail(s, SV_ERR_ARG, "Pauli mask out of range");
-    // physical masks
-    std::vector<sv_pauli_term> phys(nterms);
-    for (size_t i = 0; i < nterms; i++) {
-        phys[i] = terms[i];
-        phys[i].xmask = mask_to_physical(s->perm, terms[i].xmask);
-        phys[i].zmask = mask_to_physical(s->perm, terms[i].zmask);
-    }
     cudaError_t e;
     const int c = s->mode == SV_UNCOMPRESSED ? s->n : s->c;
     const uint64_t lowmask = (c >= 64) ? ~0ull : ((1ull << c) - 1);
@@ -1147,6 +1141,171 @@ int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_r
     cudaFree(d_part);
     cudaFree(d_acc);
     return r;
+}
+
+// <psi|H|psi> of the compressed store in few streaming sweeps: a sweep with
+// staged high qubits S decodes each chunk group as a local state of c + |S|
+// qubits (S[j] at local bit c + j), on which every term whose high x-mask
+// lies in S is evaluated by one all-terms kernel; the z-mask on the group's
+// fixed high bits is a sign per group. The staged sets are chosen greedily
+// to cover the distinct high x-masks (the Ising chain: two sweeps). Chunk
+// copies to the device alternate between two stream slots so that the next
+// group's copies overlap this group's decode and reduction.
+template <typename R>
+static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, double* out_re)
+{
+    *out_re = 0;
+    const int c = s->c, nh = s->nh, g = std::min(s->gmax, nh);
+    const uint64_t lowmask = (1ull << c) - 1;
+    std::vector<sv_pauli_term> wide;
+    std::vector<size_t> sweepable;
+    for (size_t i = 0; i < phys.size(); i++) {
+        if (__builtin_popcountll(phys[i].xmask >> c) > g) wide.push_back(phys[i]);
+        else sweepable.push_back(i);
+    }
+    // staged sets (bit masks over the nh chunk-index bits), each with its terms
+    std::vector<std::pair<uint64_t, std::vector<size_t>>> sweeps;
+    std::vector<size_t> todo = sweepable;
+    std::stable_sort(todo.begin(), todo.end(), [&](size_t a, size_t b) {
+        return __builtin_popcountll(phys[a].xmask >> c) > __builtin_popcountll(phys[b].xmask >> c);
+    });
+    while (!todo.empty()) {
+        uint64_t S = 0;
+        for (size_t i : todo) {
+            const uint64_t m = phys[i].xmask >> c;
+            if (__builtin_popcountll(S | m) <= g) S |= m;
+        }
+        for (int b = 0; b < nh && __builtin_popcountll(S) < g; b++) S |= 1ull << b;
+        std::vector<size_t> mine, rest;
+        for (size_t i : todo) ((((phys[i].xmask >> c) & ~S) == 0) ? mine : rest).push_back(i);
+        sweeps.push_back({S, mine});
+        todo.swap(rest);
+    }
+    const int nblocks = reduce_blocks_for(1ull << (c + g));
+    PauliDev* d_terms = nullptr;
+    double *d_part = nullptr, *d_acc = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, phys.size()))) ||
+        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) || (e = cudaMalloc(&d_acc, sizeof(double)))) {
+        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+        return cuda_fail(s, e, "cudaMalloc(expect)");
+    }
+    int r = SV_OK;
+    if ((e = cudaMemsetAsync(d_acc, 0, sizeof(double), s->s_comp))) r = cuda_fail(s, e, "memset");
+    uint64_t issued = 0;  // groups issued so far (stream slot = issued & 1)
+    for (size_t sw = 0; sw < sweeps.size() && !r; sw++) {
+        const uint64_t S = sweeps[sw].first;
+        std::vector<int> spos, fpos;
+        for (int b = 0; b < nh; b++) (((S >> b) & 1) ? spos : fpos).push_back(b);
+        std::vector<PauliDev> hd;
+        for (size_t i : sweeps[sw].second) {
+            const sv_pauli_term& t = phys[i];
+            const uint64_t xh = t.xmask >> c, zh = t.zmask >> c;
+            uint64_t xl = t.xmask & lowmask, zl = t.zmask & lowmask;
+            for (size_t j = 0; j < spos.size(); j++) {
+                xl |= ((xh >> spos[j]) & 1ull) << (c + j);
+                zl |= ((zh >> spos[j]) & 1ull) << (c + j);
+            }
+            hd.push_back(pauli_dev(t, xl, zl, t.zmask & ~lowmask & ~(S << c), 1.0));
+        }
+        // the previous sweep's reductions read d_terms: the upload waits for them
+        if ((e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice, s->s_comp)) ||
+            (e = cudaStreamSynchronize(s->s_comp))) {
+            r = cuda_fail(s, e, "upload terms");
+            break;
+        }
+        const int gch = 1 << g;
+        const uint64_t ngroups = 1ull << fpos.size();
+        for (uint64_t gi = 0; gi < ngroups && !r; gi++, issued++) {
+            const int slot = (int)(issued & 1);
+            const uint64_t base = deposit(gi, fpos);
+            // the slot's streams are overwritten once its previous decode is done
+            if (issued >= 2 && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + slot], 0))) {
+                r = cuda_fail(s, e, "wait decode");
+                break;
+            }
+            GroupIn gin{};
+            for (int j = 0; j < gch && !r; j++) {
+                const ChunkRef& cr = s->cur[base | deposit((uint64_t)j, spos)];
+                gin.bytes[j] = (uint32_t)cr.bytes;
+                if ((e = cudaMemcpyAsync(s->d_in[slot] + (size_t)j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                         s->s_h2d)))
+                    r = cuda_fail(s, e, "H2D chunk");
+                s->st.bytes_h2d += cr.bytes;
+            }
+            if (r) break;
+            if ((e = cudaEventRecord(s->ev_h2d[slot], s->s_h2d)) ||
+                (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0)) ||
+                (e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gin, s->d_amps, s->scale, s->d_err,
+                                      s->s_comp)) ||
+                (e = cudaEventRecord(s->ev_h2d[2 + slot], s->s_comp)) ||
+                (e = launch_energy_partials<R>(s->d_amps, c + g, base << c, d_terms, (int)hd.size(), d_part, nblocks,
+                                               s->s_comp)) ||
+                (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp))) {
+                r = cuda_fail(s, e, "expect group");
+                break;
+            }
+            s->st.kernel_launches += 3;
+        }
+    }
+    double acc = 0;
+    const int rs = sync_all(s);
+    if (!r && !rs && (e = cudaMemcpy(&acc, d_acc, sizeof(double), cudaMemcpyDeviceToHost))) r = cuda_fail(s, e, "D2H expect");
+    cudaFree(d_terms);
+    cudaFree(d_part);
+    cudaFree(d_acc);
+    if (r || rs) return r ? r : rs;
+    double rest = 0;
+    if (!wide.empty() && (r = expect_pairs<R>(s, wide, &rest))) return r;
+    *out_re = acc + rest;
+    return check_device_error(s);
+}
+
+template <typename R>
+int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re)
+{
+    *out_re = 0;
+    if (nterms == 0) return SV_OK;
+    const uint64_t dim_mask = (s->n >= 64) ? ~0ull : ((1ull << s->n) - 1);
+    for (size_t i = 0; i < nterms; i++)
+        if ((terms[i].xmask | terms[i].zmask) & ~dim_mask) return fail(s, SV_ERR_ARG, "Pauli mask out of range");
+    // physical masks
+    std::vector<sv_pauli_term> phys(nterms);
+    for (size_t i = 0; i < nterms; i++) {
+        phys[i] = terms[i];
+        phys[i].xmask = mask_to_physical(s->perm, terms[i].xmask);
+        phys[i].zmask = mask_to_physical(s->perm, terms[i].zmask);
+    }
+    if ((int)nterms > max_energy_terms()) return expect_pairs<R>(s, phys, out_re);
+    if (s->mode == SV_COMPRESSED) return expect_streamed<R>(s, phys, out_re);
+    // whole state in HBM: every term in one sweep
+    const int nblocks = reduce_blocks_for(1ull << s->n);
+    std::vector<PauliDev> hd;
+    for (const auto& t : phys) hd.push_back(pauli_dev(t, t.xmask, t.zmask, 0, 1.0));
+    PauliDev* d_terms = nullptr;
+    double *d_part = nullptr, *d_acc = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * nterms)) || (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
+        (e = cudaMalloc(&d_acc, sizeof(double)))) {
+        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+        return cuda_fail(s, e, "cudaMalloc(expect)");
+    }
+    int r = SV_OK;
+    double acc = 0;
+    if ((e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * nterms, cudaMemcpyHostToDevice, s->s_comp)) ||
+        (e = cudaMemsetAsync(d_acc, 0, sizeof(double), s->s_comp)) ||
+        (e = launch_energy_partials<R>(s->d_state, s->n, 0, d_terms, (int)nterms, d_part, nblocks, s->s_comp)) ||
+        (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp)) ||
+        (e = cudaMemcpyAsync(&acc, d_acc, sizeof(double), cudaMemcpyDeviceToHost, s->s_comp)))
+        r = cuda_fail(s, e, "energy");
+    if (!r) r = wait_stream(s, s->s_comp);
+    s->st.kernel_launches += 2;
+    cudaFree(d_terms);
+    cudaFree(d_part);
+    cudaFree(d_acc);
+    if (r) return r;
+    *out_re = acc;
+    return check_device_error(s);
 }
 
 // --------------------------------------------------------------- adjoint

@@ -78,6 +78,67 @@ k_pauli(const typename V2<R>::T* __restrict__ A, const typename V2<R>::T* __rest
     }
 }
 
+// All terms in one sweep: partials[block] = sum_{i in block range}
+// Re conj(psi_i) * sum_t coeff_t * phase_t(i) * psi[i ^ xl_t], i.e. the
+// block's share of <psi|H|psi> over the buffer (phase_t as in k_pauli). Each
+// amplitude is read once, and once more per term with a nonzero x mask (its
+// partner, mostly from cache); the per-amplitude sum over terms runs in the
+// amplitude precision, then FP64 as in k_pauli. Terms staged in shared memory.
+constexpr int kMaxEnergyTerms = 512;
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gbase, const PauliDev* __restrict__ terms,
+         int nterms, double* __restrict__ partials)
+{
+    __shared__ double red[kThreads / 32];
+    __shared__ uint64_t sx[kMaxEnergyTerms], sz[kMaxEnergyTerms];
+    __shared__ R sc[kMaxEnergyTerms];
+    __shared__ int sny[kMaxEnergyTerms];
+    for (int t = threadIdx.x; t < nterms; t += kThreads) {
+        const PauliDev P = terms[t];
+        sx[t] = P.xl;
+        sz[t] = P.zl;
+        // the global-bit sign folded into the coefficient
+        sc[t] = (R)((__popcll(gbase & P.zg) & 1) ? -P.coeff : P.coeff);
+        sny[t] = P.ny & 3;
+    }
+    __syncthreads();
+    const uint64_t per_block = (count + gridDim.x - 1) / gridDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * per_block;
+    const uint64_t i1 = min(count, i0 + per_block);
+    double acc = 0;
+    R sub = (R)0;
+    int cnt = 0;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+        const typename V2<R>::T a = psi[i];
+        R e = (R)0;
+        for (int t = 0; t < nterms; t++) {
+            const typename V2<R>::T b = sx[t] ? psi[i ^ sx[t]] : a;
+            const R re = b.x * a.x + b.y * a.y;
+            const R im = b.x * a.y - b.y * a.x;
+            R v;
+            switch (sny[t]) {  // multiply by i^ny, keep the real part
+                case 0: v = re; break;
+                case 1: v = -im; break;
+                case 2: v = -re; break;
+                default: v = im; break;
+            }
+            if (__popcll(i & sz[t]) & 1) v = -v;
+            e += sc[t] * v;
+        }
+        sub += e;
+        if (++cnt == kPerThread) {
+            acc += (double)sub;
+            sub = (R)0;
+            cnt = 0;
+        }
+    }
+    acc += (double)sub;
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // out[t] += sum over blocks of partials[t * nblocks + b], one CTA per term, fixed order
 __global__ void __launch_bounds__(kThreads)
 k_sum_partials(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
@@ -216,6 +277,19 @@ cudaError_t launch_pauli_partials(const void* A, const void* B, int Lbits, uint6
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_energy_partials(const void* psi, int Lbits, uint64_t gbase, const PauliDev* terms, int nterms,
+                                   double* partials, int nblocks, cudaStream_t st)
+{
+    if (nterms > kMaxEnergyTerms) return cudaErrorInvalidValue;
+    using T = typename V2<R>::T;
+    k_energy<R><<<nblocks, kThreads, 0, st>>>(static_cast<const T*>(psi), 1ull << Lbits, gbase, terms, nterms,
+                                             partials);
+    return cudaGetLastError();
+}
+
+int max_energy_terms() { return kMaxEnergyTerms; }
+
 cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks, double* out, cudaStream_t st)
 {
     k_sum_partials<<<nterms, kThreads, 0, st>>>(partials, nblocks, out);
@@ -267,6 +341,8 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
 #define SV_INST(R)                                                                                              \
     template cudaError_t launch_pauli_partials<R>(const void*, const void*, int, uint64_t, const PauliDev*, int, \
                                                   double*, int, cudaStream_t);                                  \
+    template cudaError_t launch_energy_partials<R>(const void*, int, uint64_t, const PauliDev*, int, double*, int, \
+                                                   cudaStream_t);                                                \
     template cudaError_t launch_gather<R>(const void*, const uint64_t*, const uint64_t*, uint64_t, double*,     \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \

@@ -168,6 +168,13 @@ cudaError_t launch_pauli_partials(const void* A, const void* B, int Lbits, uint6
                                   const PauliDev* terms, int nterms, double* partials, int nblocks,
                                   cudaStream_t st);
 
+// partials[0..nblocks) = per-CTA shares of <psi|H|psi> over a 2^Lbits buffer
+// for all nterms terms (at most max_energy_terms()) in one sweep
+template <typename R>
+cudaError_t launch_energy_partials(const void* psi, int Lbits, uint64_t gbase, const PauliDev* terms, int nterms,
+                                   double* partials, int nblocks, cudaStream_t st);
+int max_energy_terms();
+
 cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks, double* out,
                                 cudaStream_t st);
 

@@ -298,3 +298,30 @@ def test_relative_bound_adjoint_gradient(SV):
     csum = sum(abs(t.coeff) for t in terms)
     assert abs(e - e_ref) <= 1e-3 * csum
     assert np.abs(g - g_ref).max() <= 1e-3 * csum
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 11, 12, 13])
+def test_small_states_uncompressed(SV, n):
+    """States smaller than, equal to and just above one 2^12 tile (the
+    generated kernels need L >= 12; below it the table-driven kernels run)."""
+    gates = W.random_mixed(n, 60, seed=40 + n)
+    want = oracle.run(n, gates, init=1 % (1 << n))
+    with SV(n, mode="uncompressed", dtype="c128", init_index=1 % (1 << n)) as s:
+        s.apply(gates)
+        assert rel_l2(s.state(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("n,c", [(8, 8), (9, 8), (13, 8), (12, 12)])
+def test_degenerate_chunkings(SV, n, c):
+    """One chunk (n = c), one or few high qubits, the smallest chunk (2^8):
+    within the quantisation bound; an empty gate list changes nothing."""
+    gates = W.random_layers(n, 4, seed=50 + n)
+    want = oracle.run(n, gates, init=3)
+    with SV(n, c, 1e-6, init_index=3, max_group_qubits=2 if n - c >= 2 else 0) as s:
+        s.apply(gates)
+        got = s.state()
+        st = s.stats()
+        s.apply([])
+        assert np.array_equal(s.state(), got)
+        assert s.stats()["passes"] == st["passes"]
+    assert np.linalg.norm(got - want) <= compressed_l2_bound(n, 1e-6, st["passes"], len(gates))
