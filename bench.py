@@ -14,9 +14,9 @@ norm) and streams them back.
 Metric: amplitude-gate updates per second = gates * 2^n / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-  python bench.py --workload {c1-layers,c1-ghz,c1-qft,c0-qft,c0-layers,
-                              c2-ghz,c2-qft,c2-clifford,c3-grad,c4-grad,
-                              c2-qft-rel,c2-clifford-rel,c1-layers-rel}
+  python bench.py --workload {layers30,ghz30,qft30,qft16,layers16,
+                              ghz36,qft36,clifford36,grad-hea24,grad-hea32,
+                              qft36-rel,clifford36-rel,layers30-rel}
   (-rel: the relative error bound, each chunk's step from its largest component)
 
 With --gpus N under torchrun every rank runs an independent replica of the
@@ -46,21 +46,21 @@ METRIC = "amp-gate updates/s"
 
 # name -> (n, chunk qubits, eb, dtype, group qubits, circuit, extra)
 WORKLOADS = {
-    "c1-layers": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40),
-    "c1-ghz": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="ghz"),
-    "c1-qft": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="qft"),
-    "c0-qft": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="qft"),
-    "c0-layers": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="layers", depth=20),
-    "c2-ghz": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="ghz"),
-    "c2-qft": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft"),
-    "c2-clifford": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30),
+    "layers30": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40),
+    "ghz30": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="ghz"),
+    "qft30": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="qft"),
+    "qft16": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="qft"),
+    "layers16": dict(n=16, c=10, eb=1e-6, dtype="c128", group=0, circuit="layers", depth=20),
+    "ghz36": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="ghz"),
+    "qft36": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft"),
+    "clifford36": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30),
     # the same with the relative error bound (step from each chunk's largest component)
-    "c2-qft-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft", relative=True),
-    "c2-clifford-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30,
+    "qft36-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="qft", relative=True),
+    "clifford36-rel": dict(n=36, c=26, eb=1e-5, dtype="c64", group=0, circuit="clifford", depth=30,
                             relative=True),
-    "c1-layers-rel": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40, relative=True),
-    "c3-grad": dict(n=24, c=24, eb=0.0, dtype="c64", group=0, circuit="hea", layers=10, mode="uncompressed"),
-    "c4-grad": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16),
+    "layers30-rel": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40, relative=True),
+    "grad-hea24": dict(n=24, c=24, eb=0.0, dtype="c64", group=0, circuit="hea", layers=10, mode="uncompressed"),
+    "grad-hea32": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16),
 }
 
 
@@ -70,13 +70,13 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c1-layers", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="layers30", choices=sorted(WORKLOADS))
     p.add_argument("--eb", type=float, default=None)
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--chunk", type=int, default=None)
     p.add_argument("--depth", type=int, default=None)
     p.add_argument("--group", type=int, default=None)
-    p.add_argument("--sets", type=int, default=None, help="parameter sets for c4-grad")
+    p.add_argument("--sets", type=int, default=None, help="parameter sets for grad-hea32")
     p.add_argument("--no-extras", action="store_true", help="skip the comparator and baseline legs")
     p.add_argument("--table1", action="store_true",
                    help="the paper's Table 1: host<->device copy strategies at 20 and 25 qubits")
@@ -491,7 +491,7 @@ def cpu_baseline(w, gates, target_s=12.0):
 
 
 def run_grad(args, rank, world):
-    """Adjoint gradient seconds per step (configs 3 and 4)."""
+    """Adjoint gradient seconds per step (the HEA workloads: n = 24 in HBM, n = 32 compressed)."""
     import torch
     from paper_2309_16979_gb300 import StateVector
     w = args.w

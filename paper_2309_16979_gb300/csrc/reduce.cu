@@ -107,34 +107,40 @@ k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gba
     const uint64_t per_block = (count + gridDim.x - 1) / gridDim.x;
     const uint64_t i0 = (uint64_t)blockIdx.x * per_block;
     const uint64_t i1 = min(count, i0 + per_block);
+    using T = typename V2<R>::T;
+    // a strip of kStrip amplitudes per thread in registers: each term's
+    // parameters are read from shared memory once per strip
+    constexpr int kStrip = 8;
     double acc = 0;
-    R sub = (R)0;
-    int cnt = 0;
-    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
-        const typename V2<R>::T a = psi[i];
-        R e = (R)0;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += (uint64_t)kThreads * kStrip) {
+        T a[kStrip];
+        R e[kStrip];
+#pragma unroll
+        for (int k = 0; k < kStrip; k++) {
+            const uint64_t j = i + (uint64_t)k * kThreads;
+            a[k] = j < i1 ? psi[j] : T{(R)0, (R)0};
+            e[k] = (R)0;
+        }
         for (int t = 0; t < nterms; t++) {
-            const typename V2<R>::T b = sx[t] ? psi[i ^ sx[t]] : a;
-            const R re = b.x * a.x + b.y * a.y;
-            const R im = b.x * a.y - b.y * a.x;
-            R v;
-            switch (sny[t]) {  // multiply by i^ny, keep the real part
-                case 0: v = re; break;
-                case 1: v = -im; break;
-                case 2: v = -re; break;
-                default: v = im; break;
+            const uint64_t x = sx[t], z = sz[t];
+            const R cf = sc[t];
+            const int ny = sny[t];
+#pragma unroll
+            for (int k = 0; k < kStrip; k++) {
+                const uint64_t j = i + (uint64_t)k * kThreads;
+                const T b = (x && j < i1) ? psi[j ^ x] : a[k];
+                const R re = b.x * a[k].x + b.y * a[k].y;
+                const R im = b.x * a[k].y - b.y * a[k].x;
+                R v = ny == 0 ? re : ny == 1 ? -im : ny == 2 ? -re : im;  // i^ny, real part
+                if (__popcll(j & z) & 1) v = -v;
+                e[k] += cf * v;
             }
-            if (__popcll(i & sz[t]) & 1) v = -v;
-            e += sc[t] * v;
         }
-        sub += e;
-        if (++cnt == kPerThread) {
-            acc += (double)sub;
-            sub = (R)0;
-            cnt = 0;
-        }
+        R sub = (R)0;
+#pragma unroll
+        for (int k = 0; k < kStrip; k++) sub += e[k];
+        acc += (double)sub;
     }
-    acc += (double)sub;
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
