@@ -1272,7 +1272,7 @@ std::string jit_source(const Phase* ph, int nph, const PhaseOp<R>* ops, const Ct
     }
     const bool pf = prefetches(dec, sizeof(R));
     // rows of the tile: whole codec block pairs (8 low bits) in a sub-pass that
-    // decodes or encodes, 32 amplitudes (5) otherwise
+    // decodes or encodes, 16 amplitudes (4 low bits) otherwise
     const std::string lb = std::to_string(lrow);
     std::ostringstream src;
     src << "#include \"tile_dev.cuh\"\nusing namespace sv;\n"
