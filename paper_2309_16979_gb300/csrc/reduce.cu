@@ -114,21 +114,31 @@ k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gba
     double acc = 0;
     for (uint64_t i = i0 + threadIdx.x; i < i1; i += (uint64_t)kThreads * kStrip) {
         T a[kStrip];
-        R e[kStrip];
+        R e[kStrip], n2[kStrip];
 #pragma unroll
         for (int k = 0; k < kStrip; k++) {
             const uint64_t j = i + (uint64_t)k * kThreads;
             a[k] = j < i1 ? psi[j] : T{(R)0, (R)0};
             e[k] = (R)0;
+            n2[k] = a[k].x * a[k].x + a[k].y * a[k].y;
         }
         for (int t = 0; t < nterms; t++) {
             const uint64_t x = sx[t], z = sz[t];
             const R cf = sc[t];
             const int ny = sny[t];
+            if (x == 0) {
+                // a Z string (no Y without an X): |psi_i|^2 with its sign
+#pragma unroll
+                for (int k = 0; k < kStrip; k++) {
+                    const uint64_t j = i + (uint64_t)k * kThreads;
+                    e[k] += ((__popcll(j & z) & 1) ? -cf : cf) * n2[k];
+                }
+                continue;
+            }
 #pragma unroll
             for (int k = 0; k < kStrip; k++) {
                 const uint64_t j = i + (uint64_t)k * kThreads;
-                const T b = (x && j < i1) ? psi[j ^ x] : a[k];
+                const T b = j < i1 ? psi[j ^ x] : a[k];
                 const R re = b.x * a[k].x + b.y * a[k].y;
                 const R im = b.x * a[k].y - b.y * a[k].x;
                 R v = ny == 0 ? re : ny == 1 ? -im : ny == 2 ? -re : im;  // i^ny, real part
