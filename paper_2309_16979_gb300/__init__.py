@@ -5,9 +5,13 @@ streaming, decode, gate application, encode, reductions, the adjoint sweep --
 runs in the CUDA library libsvgb300.so; this module only marshals arguments.
 
     from paper_2309_16979_gb300 import StateVector
-    sv = StateVector(30, chunk_qubits=22, eb=1e-6)
+    sv = StateVector(30, chunk_qubits=22, eb=1e-6)      # relative_bound=True: per-chunk step
     sv.apply(gates)
     e = sv.expect(terms)
+    energy, grad = sv.grad(gates, theta, terms)          # adjoint gradient
+
+Also: codec_encode / codec_decode (one chunk on the device), copy_probe (the
+paper's host <-> device copy strategies), plan and jit_sources (host only).
 """
 from __future__ import annotations
 
@@ -19,8 +23,8 @@ import numpy as np
 from . import _abi
 from ._abi import SV_C64, SV_C128, SV_COMPRESSED, SV_UNCOMPRESSED, SvError, load
 
-__all__ = ["StateVector", "SvError", "codec_encode", "codec_decode", "codec_max_bytes", "load",
-           "SV_C64", "SV_C128", "SV_COMPRESSED", "SV_UNCOMPRESSED"]
+__all__ = ["StateVector", "SvError", "codec_encode", "codec_decode", "codec_max_bytes", "copy_probe", "plan",
+           "jit_sources", "load", "SV_C64", "SV_C128", "SV_COMPRESSED", "SV_UNCOMPRESSED"]
 
 
 def _check(code: int, what: str, handle=None):
