@@ -115,6 +115,12 @@ typedef struct sv_config {
                                      Needs eb >= 2^-23 (complex64) / 2^-29 (complex128), else
                                      SV_ERR_RANGE; the codec then runs in separate kernels (the
                                      chunk maximum precedes the encode) */
+    int32_t remap_qubits;         /* 0 (default): qubits keep their positions (SWAP gates relabel
+                                     them for free); 1: sv_apply_circuit may also move qubits
+                                     between high (chunk-index) and low positions with physical
+                                     SWAPs appended to a pass, when that runs the circuit in fewer
+                                     passes (furthest-next-use rule, sv_plan_remap); logical
+                                     results are unchanged. sv_grad never remaps. */
     uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
@@ -152,6 +158,8 @@ typedef struct sv_stats_t {
     /* host wall time planning passes and looking up / compiling their kernels,
        and blocked waiting for GPU work (always collected) */
     double t_host_prepare_s, t_host_wait_s;
+    /* physical SWAPs added by sv_config.remap_qubits */
+    uint64_t remap_swaps;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
@@ -287,6 +295,40 @@ int sv_jit_sources(int n, int chunk_qubits, const sv_config* cfg, const sv_gate*
 int sv_plan(int n, int chunk_qubits, int max_group_qubits, int tile_qubits, const sv_gate* gates,
             size_t ngates, int32_t* order, int32_t* pass_of, uint64_t* staged, size_t* out_executed,
             size_t* out_passes, size_t* out_subpasses);
+
+/*
+ * sv_plan for a state with sv_config.remap_qubits = 1: the passes
+ * sv_apply_circuit would run with qubit remapping. The partitioning into
+ * stages is the paper's (Sec. 2, "Offline stage"); moving qubits between
+ * stages is not in the paper. At the end of each pass, while a staged high
+ * position holds a qubit that the remaining gates mix before the qubit of
+ * some low position, the two exchange (a physical SWAP in that pass: the
+ * low positions keep the qubits needed soonest), and the later gates run on
+ * the new positions. The remapped plan is used only when it has fewer passes
+ * than sv_plan's (*out_swaps = 0 and sv_plan's plan otherwise).
+ *   order, pass_of: as in sv_plan, over the caller's gates only (the added
+ *                   SWAPs are counted in *out_swaps, not listed).
+ *   staged:         host, >= ngates slots: physical high positions staged by
+ *                   each pass.
+ *   out_swaps:      host: physical SWAPs added.
+ *   swaps:          host, NULL or >= 24 * ngates slots (a pass adds at most
+ *                   8 SWAPs): (pass, low position, high position) of each
+ *                   added SWAP in execution order; it runs after the listed
+ *                   gates of its pass, and every later gate runs on the
+ *                   positions it leaves. Positions start as in sv_plan:
+ *                   qubit q at q, relabelled by the caller's own SWAPs.
+ *   qubits:         host, NULL or >= 4 * ngates slots: for entry k of order,
+ *                   the positions its gate runs on (targets[0], targets[1],
+ *                   controls[0], controls[1]; -1 where the gate has none).
+ *   positions:      host, NULL or >= n slots: the position of every caller
+ *                   qubit after the circuit (the logical-to-physical map the
+ *                   state keeps).
+ * Errors: as sv_plan.
+ */
+int sv_plan_remap(int n, int chunk_qubits, int max_group_qubits, int tile_qubits, const sv_gate* gates,
+                  size_t ngates, int32_t* order, int32_t* pass_of, uint64_t* staged, size_t* out_executed,
+                  size_t* out_passes, size_t* out_subpasses, size_t* out_swaps, int32_t* swaps, int32_t* qubits,
+                  int32_t* positions);
 
 /*
  * Copy the compressed stream of chunk k (physical chunk index, 0 <=

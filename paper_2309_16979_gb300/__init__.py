@@ -42,7 +42,7 @@ class StateVector:
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,
-                 jit: bool = True, relative_bound: bool = False):
+                 jit: bool = True, relative_bound: bool = False, remap_qubits: bool = False):
         L = load()
         cfg = _abi.SvConfig()
         L.sv_config_default(C.byref(cfg))
@@ -60,6 +60,7 @@ class StateVector:
         cfg.fuse_codec = int(fuse_codec)
         cfg.jit = int(jit)
         cfg.relative_bound = int(relative_bound)
+        cfg.remap_qubits = int(remap_qubits)
         h = C.c_void_p()
         _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
         self._h = h
@@ -140,30 +141,48 @@ class StateVector:
         self.close()
 
 
-def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, tile_qubits: int = 0) -> dict:
-    """Host-only pass plan (sv_plan): execution order, pass of each gate,
-    staged high-qubit mask per pass, and pass / sub-pass counts."""
+def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, tile_qubits: int = 0,
+         remap: bool = False) -> dict:
+    """Host-only pass plan (sv_plan, or sv_plan_remap with remap): execution
+    order, pass of each gate, staged high-qubit mask per pass, pass / sub-pass
+    counts, and the physical SWAPs remapping adds as (pass, low position, high
+    position), each after the gates of its pass; with remap also the positions
+    each executed gate runs on (targets, controls; -1 = none) and the final
+    position of every qubit."""
     L = load()
     ng = len(gates)
     arr = _abi.gates_to_c(gates)
     order = np.zeros(max(1, ng), dtype=np.int32)
     pass_of = np.zeros(max(1, ng), dtype=np.int32)
     staged = np.zeros(max(1, ng), dtype=np.uint64)
-    ex, npass, nsub = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
-    _check(L.sv_plan(n, chunk_qubits, max_group_qubits, tile_qubits, C.addressof(arr), ng, order.ctypes.data,
-                     pass_of.ctypes.data, staged.ctypes.data, C.byref(ex), C.byref(npass), C.byref(nsub)),
-           "sv_plan", None)
+    ex, npass, nsub, nswap = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+    args = (n, chunk_qubits, max_group_qubits, tile_qubits, C.addressof(arr), ng, order.ctypes.data,
+            pass_of.ctypes.data, staged.ctypes.data, C.byref(ex), C.byref(npass), C.byref(nsub))
+    swaps = np.zeros(max(1, 24 * ng), dtype=np.int32)
+    qubits = np.full(max(1, 4 * ng), -1, dtype=np.int32)
+    positions = np.arange(n, dtype=np.int32)
+    if remap:
+        _check(L.sv_plan_remap(*args, C.byref(nswap), swaps.ctypes.data, qubits.ctypes.data,
+                               positions.ctypes.data), "sv_plan_remap", None)
+    else:
+        _check(L.sv_plan(*args), "sv_plan", None)
     k = ex.value
-    return {"order": order[:k].tolist(), "pass_of": pass_of[:k].tolist(),
-            "staged": [int(x) for x in staged[:npass.value]], "passes": npass.value, "subpasses": nsub.value}
+    out = {"order": order[:k].tolist(), "pass_of": pass_of[:k].tolist(),
+           "staged": [int(x) for x in staged[:npass.value]], "passes": npass.value, "subpasses": nsub.value,
+           "swaps": [tuple(int(v) for v in swaps[3 * i:3 * i + 3]) for i in range(nswap.value)]}
+    if remap:
+        out["qubits"] = [tuple(int(v) for v in qubits[4 * i:4 * i + 4]) for i in range(k)]
+        out["positions"] = positions.tolist()
+    return out
 
 
 def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", mode: str = "compressed",
                 max_group_qubits: int = 4, tile_qubits: int = 0, fuse_codec: bool = True,
-                adjoint: bool = False) -> list:
+                adjoint: bool = False, remap: bool = False) -> list:
     """Host-only: the CUDA C++ sources of the sub-pass kernels sv_apply_circuit
     (or, with adjoint, the reverse sweep of sv_grad) would generate for this
-    circuit (sv_jit_sources), in launch order."""
+    circuit (sv_jit_sources), in launch order; remap: with
+    sv_config.remap_qubits."""
     L = load()
     cfg = _abi.SvConfig()
     L.sv_config_default(C.byref(cfg))
@@ -172,6 +191,7 @@ def jit_sources(n: int, chunk_qubits: int, gates: Sequence, dtype: str = "c64", 
     cfg.max_group_qubits = max_group_qubits
     cfg.tile_qubits = tile_qubits
     cfg.fuse_codec = int(fuse_codec)
+    cfg.remap_qubits = int(remap)
     arr = _abi.gates_to_c(gates)
     need, nk = C.c_size_t(0), C.c_size_t(0)
     adj = int(adjoint)

@@ -38,7 +38,7 @@ class SvConfig(C.Structure):
                 ("max_group_qubits", C.c_int32), ("tile_qubits", C.c_int32),
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
                 ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("jit", C.c_int32),
-                ("relative_bound", C.c_int32), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
+                ("relative_bound", C.c_int32), ("remap_qubits", C.c_int32), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 
 class SvStats(C.Structure):
@@ -55,7 +55,8 @@ class SvStats(C.Structure):
                 ("jit_kernels_compiled", C.c_uint64), ("jit_launches", C.c_uint64),
                 ("t_jit_compile_s", C.c_double),
                 ("t_h2d_s", C.c_double), ("t_d2h_s", C.c_double), ("t_encode_finish_s", C.c_double),
-                ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double)]
+                ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double),
+                ("remap_swaps", C.c_uint64)]
 
 
 # every entry point declared in include/sv.h
@@ -63,7 +64,7 @@ EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "s
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
            "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile",
-           "sv_codec_encode_relative", "sv_copy_probe")
+           "sv_codec_encode_relative", "sv_copy_probe", "sv_plan_remap")
 
 _lib = None
 
@@ -114,6 +115,9 @@ def load() -> C.CDLL:
     L.sv_plan.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, SZ, P, P, P, C.POINTER(SZ), C.POINTER(SZ),
                           C.POINTER(SZ)]
     L.sv_plan.restype = C.c_int
+    L.sv_plan_remap.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, SZ, P, P, P, C.POINTER(SZ),
+                                C.POINTER(SZ), C.POINTER(SZ), C.POINTER(SZ), P, P, P]
+    L.sv_plan_remap.restype = C.c_int
     L.sv_codec_encode_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]
     L.sv_codec_encode_noalloc.restype = C.c_int
     L.sv_codec_encode_relative.argtypes = [C.c_int, C.c_int, C.c_double, P, P, SZ, C.POINTER(SZ)]

@@ -260,6 +260,7 @@ void sv_config_default(sv_config* cfg)
     cfg->fuse_codec = 1;
     cfg->jit = 1;
     cfg->relative_bound = 0;
+    cfg->remap_qubits = 0;
     cfg->timeout_s = 600.0;
 }
 
@@ -284,6 +285,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     if (cfg.pipeline_slots < 2 || cfg.pipeline_slots > 4) return reject(SV_ERR_ARG, "pipeline_slots must be 2..4");
     if (cfg.tile_qubits && (cfg.tile_qubits < 2 || cfg.tile_qubits > kMaxTileQubits))
         return reject(SV_ERR_ARG, "tile_qubits must be 2..13");
+    if (cfg.remap_qubits != 0 && cfg.remap_qubits != 1) return reject(SV_ERR_ARG, "remap_qubits must be 0 or 1");
     if (!(cfg.timeout_s > 0)) cfg.timeout_s = 600.0;
     int k = 0;
     if (cfg.mode == SV_COMPRESSED) {
@@ -358,7 +360,8 @@ int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t ngates)
     cudaSetDevice(s->cfg.device);
     {
         std::lock_guard<std::mutex> lock(g_apply_mu);
-        r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg) : apply_circuit<double>(s, pg);
+        const bool remap = s->cfg.remap_qubits != 0;
+        r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg, remap) : apply_circuit<double>(s, pg, remap);
     }
     if (!r) {
         s->st.amp_gate_updates += (uint64_t)ngates << s->n;
@@ -427,19 +430,21 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
     return r;
 }
 
-int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_t ngates, int32_t* order,
-            int32_t* pass_of, uint64_t* staged, size_t* out_executed, size_t* out_passes, size_t* out_subpasses)
+static int plan_impl(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_t ngates, int32_t* order,
+                     int32_t* pass_of, uint64_t* staged, size_t* out_executed, size_t* out_passes,
+                     size_t* out_subpasses, bool remap, size_t* out_swaps, int32_t* swaps, int32_t* qubits,
+                     int32_t* positions)
 {
     if (n < 1 || n > 40 || c < 1 || c > n || gmax < 2 || gmax > 8 || (ngates && !gates) || !order || !pass_of ||
-        !staged || !out_executed || !out_passes || !out_subpasses)
+        !staged || !out_executed || !out_passes || !out_subpasses || (remap && !out_swaps))
         return SV_ERR_ARG;
     if (tile_qubits && (tile_qubits < 2 || tile_qubits > kMaxTileQubits)) return SV_ERR_ARG;
     sv_state tmp;
     tmp.n = n;
     tmp.perm.resize(n);
     for (int q = 0; q < n; q++) tmp.perm[q] = q;
-    std::vector<PGate> pg;
-    int r = lower(&tmp, gates, ngates, nullptr, 0, false, pg);
+    std::vector<PGate> input;
+    int r = lower(&tmp, gates, ngates, nullptr, 0, false, input);
     if (r) {
         g_create_error = tmp.err;
         return r;
@@ -448,15 +453,31 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
     std::vector<int32_t> orig;
     for (size_t i = 0; i < ngates; i++)
         if (gates[i].kind != SV_GATE_SWAP) orig.push_back((int32_t)i);
-    const std::vector<PassPlan> passes = plan_passes(pg, n, c, gmax);
-    size_t k = 0, subs = 0;
+    std::vector<PGate> pg;
+    std::vector<int> where, src;
+    const std::vector<PassPlan> passes = plan_circuit(input, n, c, gmax, remap, pg, where, &src);
+    size_t k = 0, subs = 0, ns = 0;
     const int tq = tile_qubits ? tile_qubits : 12;
     for (size_t p = 0; p < passes.size(); p++) {
         uint64_t m = 0;
         for (int q : passes[p].S) m |= 1ull << q;
         staged[p] = m;
         for (int gi : passes[p].gates) {
-            order[k] = orig[gi];
+            if (src[gi] < 0) {  // an added SWAP
+                if (swaps) {
+                    swaps[3 * ns] = (int32_t)p;
+                    swaps[3 * ns + 1] = pg[gi].t[0];
+                    swaps[3 * ns + 2] = pg[gi].t[1];
+                }
+                ns++;
+                continue;
+            }
+            order[k] = orig[src[gi]];
+            if (qubits) {
+                const PGate& G = pg[gi];
+                for (int j = 0; j < 2; j++) qubits[4 * k + j] = j < G.nt ? G.t[j] : -1;
+                for (int j = 0; j < 2; j++) qubits[4 * k + 2 + j] = j < G.nc ? G.c[j] : -1;
+            }
             pass_of[k] = (int32_t)p;
             k++;
         }
@@ -471,7 +492,25 @@ int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_
     *out_executed = k;
     *out_passes = passes.size();
     *out_subpasses = subs;
+    if (out_swaps) *out_swaps = pg.size() - input.size();
+    if (positions)
+        for (int q = 0; q < n; q++) positions[q] = where[tmp.perm[q]];
     return SV_OK;
+}
+
+int sv_plan(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_t ngates, int32_t* order,
+            int32_t* pass_of, uint64_t* staged, size_t* out_executed, size_t* out_passes, size_t* out_subpasses)
+{
+    return plan_impl(n, c, gmax, tile_qubits, gates, ngates, order, pass_of, staged, out_executed, out_passes,
+                     out_subpasses, false, nullptr, nullptr, nullptr, nullptr);
+}
+
+int sv_plan_remap(int n, int c, int gmax, int tile_qubits, const sv_gate* gates, size_t ngates, int32_t* order,
+                  int32_t* pass_of, uint64_t* staged, size_t* out_executed, size_t* out_passes,
+                  size_t* out_subpasses, size_t* out_swaps, int32_t* swaps, int32_t* qubits, int32_t* positions)
+{
+    return plan_impl(n, c, gmax, tile_qubits, gates, ngates, order, pass_of, staged, out_executed, out_passes,
+                     out_subpasses, true, out_swaps, swaps, qubits, positions);
 }
 
 int sv_jit_sources(int n, int c, const sv_config* cfg_in, const sv_gate* gates, size_t ngates, int adjoint, char* buf,

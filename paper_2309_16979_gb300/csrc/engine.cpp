@@ -754,16 +754,20 @@ int run_pass_uncompressed(sv_state* s, void* state, const std::vector<PGate>& ga
 }
 
 template <typename R>
-int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
+int apply_circuit(sv_state* s, const std::vector<PGate>& input, bool remap)
 {
-    if (gates.empty()) return SV_OK;
+    if (input.empty()) return SV_OK;
     if (s->mode == SV_UNCOMPRESSED) {
-        std::vector<int> ids(gates.size());
-        for (size_t i = 0; i < gates.size(); i++) ids[i] = (int)i;
-        return run_pass_uncompressed<R>(s, s->d_state, gates, ids);
+        std::vector<int> ids(input.size());
+        for (size_t i = 0; i < input.size(); i++) ids[i] = (int)i;
+        return run_pass_uncompressed<R>(s, s->d_state, input, ids);
     }
     const auto t0 = std::chrono::steady_clock::now();
-    const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
+    // with remapping the passes run a gate list of their own (the input's
+    // gates on moved positions plus physical SWAPs)
+    std::vector<PGate> gates;
+    std::vector<int> where;
+    const std::vector<PassPlan> passes = plan_circuit(input, s->n, s->c, s->gmax, remap, gates, where);
     // plan every pass first, so that their kernels compile in one parallel batch
     std::vector<DevPass<R>> dps(passes.size());
     std::vector<DevPass<R>*> ptrs;
@@ -775,7 +779,10 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& gates)
     int r = jit_prepare<R>(s, ptrs);
     if (r) return r;
     s->st.t_host_prepare_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return stream_passes<R>(s, passes, dps);
+    if ((r = stream_passes<R>(s, passes, dps))) return r;
+    for (int& p : s->perm) p = where[p];  // logical qubits follow their moves
+    s->st.remap_swaps += gates.size() - input.size();
+    return SV_OK;
 }
 
 template <typename R>
@@ -835,10 +842,13 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
         if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
         dps.push_back(build_dev_pass<R>(subs, s->n, t, l));
     } else {
-        const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
+        std::vector<PGate> rg;
+        std::vector<int> where;
+        const std::vector<PassPlan> passes =
+            plan_circuit(gates, s->n, s->c, s->gmax, s->cfg.remap_qubits != 0, rg, where);
         dps.resize(passes.size());
         for (size_t i = 0; i < passes.size(); i++) {
-            int r = prepare_pass_compressed<R>(s, gates, passes[i], dps[i]);
+            int r = prepare_pass_compressed<R>(s, rg, passes[i], dps[i]);
             if (r) return r;
         }
     }
@@ -1772,7 +1782,7 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     if (r) return r;
     if ((r = init_state<R>(s))) return r;
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
-    if ((r = apply_circuit<R>(s, gates))) return r;  // the forward sweep (the same plan)
+    if ((r = apply_circuit<R>(s, gates, false))) return r;  // the forward sweep (the same plan)
     std::vector<sv_pauli_term> phys(nterms);
     for (size_t i = 0; i < nterms; i++) {
         phys[i] = H[i];
@@ -1840,8 +1850,8 @@ template int grad_compressed<float>(sv_state*, const std::vector<PGate>&, size_t
                                     double*, double*);
 template int grad_compressed<double>(sv_state*, const std::vector<PGate>&, size_t, const sv_pauli_term*, size_t,
                                      double*, double*);
-template int apply_circuit<float>(sv_state*, const std::vector<PGate>&);
-template int apply_circuit<double>(sv_state*, const std::vector<PGate>&);
+template int apply_circuit<float>(sv_state*, const std::vector<PGate>&, bool);
+template int apply_circuit<double>(sv_state*, const std::vector<PGate>&, bool);
 template int jit_sources<float>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&, bool);
 template int jit_sources<double>(sv_state*, const std::vector<PGate>&, std::vector<std::string>&, bool);
 template int init_state<float>(sv_state*);

@@ -17,7 +17,9 @@ void arena_free(Arena& a);
 void tile_shape(int L, int tq, int lq, int& t, int& l);
 
 template <typename R> int init_state(sv_state* s);
-template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& gates);
+// remap: move qubits between high and low positions when that saves passes
+// (plan_circuit); s->perm follows.
+template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& gates, bool remap);
 // host only: the sources of the kernels apply_circuit would generate
 template <typename R>
 int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out, bool adjoint);

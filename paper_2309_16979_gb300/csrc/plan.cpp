@@ -92,61 +92,165 @@ static int count_pass(const std::vector<PGate>& g, const std::vector<int>& remai
     return k;
 }
 
+// One pass over `remaining` (indices into g, in order): the staged set and
+// the gates it applies; the gates it leaves, in order, go to `deferred`.
+static PassPlan plan_one_pass(const std::vector<PGate>& g, const std::vector<int>& remaining, int n, int c, int gsz,
+                              std::vector<int>& deferred)
+{
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t high = (n > c) ? (all & ~((1ull << c) - 1)) : 0;
+    uint64_t S = 0, blocked = 0;
+    // Stage one high qubit at a time, the one that lets the pass apply the
+    // most gates; when none adds any, the scan below stages first-come.
+    for (int cur = count_pass(g, remaining, S, high, all); popc(S) < gsz;) {
+        int best = -1, bestn = cur;
+        for (int q = c; q < n; q++) {
+            if ((S >> q) & 1) continue;
+            const int k = count_pass(g, remaining, S | (1ull << q), high, all);
+            if (k > bestn) {
+                bestn = k;
+                best = q;
+            }
+        }
+        if (best < 0) break;
+        S |= 1ull << best;
+        cur = bestn;
+    }
+    PassPlan pp;
+    deferred.clear();
+    for (int gi : remaining) {
+        const uint64_t qm = qubit_mask(g[gi]);
+        if (qm & blocked) {
+            deferred.push_back(gi);
+            blocked |= qm;
+            continue;
+        }
+        const uint64_t need = mixing_mask(g[gi]) & high & ~S;
+        if (popc(S | need) <= gsz) {
+            S |= need;
+            pp.gates.push_back(gi);
+        } else {
+            deferred.push_back(gi);
+            blocked |= qm;
+        }
+    }
+    // stage exactly gsz high qubits: pad with the lowest unused ones
+    for (int q = c; q < n && popc(S) < gsz; q++) S |= 1ull << q;
+    for (int q = c; q < n; q++)
+        if ((S >> q) & 1) pp.S.push_back(q);
+    return pp;
+}
+
 std::vector<PassPlan> plan_passes(const std::vector<PGate>& g, int n, int c, int gmax)
 {
     std::vector<PassPlan> passes;
-    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
-    const uint64_t high = (n > c) ? (all & ~((1ull << c) - 1)) : 0;
-    const int nh = n - c;
-    const int gsz = std::min(gmax, nh);
-    std::vector<int> remaining(g.size());
+    const int gsz = std::min(gmax, n - c);
+    std::vector<int> remaining(g.size()), deferred;
     for (size_t i = 0; i < g.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
-        uint64_t S = 0, blocked = 0;
-        // Stage one high qubit at a time, the one that lets the pass apply the
-        // most gates; when none adds any, the scan below stages first-come.
-        for (int cur = count_pass(g, remaining, S, high, all); popc(S) < gsz;) {
-            int best = -1, bestn = cur;
-            for (int q = c; q < n; q++) {
-                if ((S >> q) & 1) continue;
-                const int k = count_pass(g, remaining, S | (1ull << q), high, all);
-                if (k > bestn) {
-                    bestn = k;
-                    best = q;
+        passes.push_back(plan_one_pass(g, remaining, n, c, gsz, deferred));
+        remaining.swap(deferred);
+    }
+    return passes;
+}
+
+std::vector<PassPlan> plan_passes_remap(const std::vector<PGate>& g, int n, int c, int gmax, std::vector<PGate>& out,
+                                        std::vector<int>& where, std::vector<int>* src)
+{
+    std::vector<PassPlan> passes;
+    const int gsz = std::min(gmax, n - c);
+    std::vector<PGate> w = g;       // the gates on the current positions
+    std::vector<int> pos(n), at(n);  // pos[q]: position of input qubit q; at[p]: the input qubit at p
+    for (int q = 0; q < n; q++) pos[q] = at[q] = q;
+    std::vector<int> remaining(g.size()), deferred;
+    for (size_t i = 0; i < g.size(); i++) remaining[i] = (int)i;
+    out.clear();
+    if (src) src->clear();
+    constexpr size_t kNever = ~(size_t)0;
+    while (!remaining.empty()) {
+        PassPlan pp = plan_one_pass(w, remaining, n, c, gsz, deferred);
+        std::vector<int> ids;
+        for (int gi : pp.gates) {
+            ids.push_back((int)out.size());
+            out.push_back(w[gi]);
+            if (src) src->push_back(gi);
+        }
+        if (!deferred.empty()) {
+            // next[p]: the first of the gates still to run that mixes position p
+            std::vector<size_t> next(n, kNever);
+            for (size_t k = deferred.size(); k-- > 0;) {
+                const uint64_t mm = mixing_mask(w[deferred[k]]);
+                for (int p = 0; p < n; p++)
+                    if ((mm >> p) & 1) next[p] = k;
+            }
+            // The low positions and the staged ones hold, after this pass,
+            // the qubits mixed soonest (furthest-next-use replacement): pair
+            // the staged position needed soonest with the low one needed
+            // last while the staged one is needed earlier.
+            std::vector<int> hs = pp.S, ls;
+            for (int p = 0; p < c; p++) ls.push_back(p);
+            std::stable_sort(hs.begin(), hs.end(), [&](int a, int b) { return next[a] < next[b]; });
+            std::stable_sort(ls.begin(), ls.end(), [&](int a, int b) { return next[a] > next[b]; });
+            int swapped[2][64], ns = 0;
+            for (size_t k = 0; k < hs.size() && k < ls.size(); k++) {
+                const int h = hs[k], l = ls[k];
+                if (next[h] == kNever || next[h] >= next[l]) break;
+                PGate sw;
+                sw.kind = SV_GATE_SWAP;
+                sw.nt = 2;
+                sw.t[0] = l;
+                sw.t[1] = h;
+                gate_matrix(SV_GATE_SWAP, 0, nullptr, 2, sw.m);
+                ids.push_back((int)out.size());
+                out.push_back(sw);
+                if (src) src->push_back(-1);
+                swapped[0][ns] = l;
+                swapped[1][ns++] = h;
+            }
+            if (ns) {
+                std::vector<int> to(n);  // old position -> new position
+                for (int p = 0; p < n; p++) to[p] = p;
+                for (int k = 0; k < ns; k++) std::swap(to[swapped[0][k]], to[swapped[1][k]]);
+                for (int gi : deferred) {
+                    for (int j = 0; j < w[gi].nt; j++) w[gi].t[j] = to[w[gi].t[j]];
+                    for (int j = 0; j < w[gi].nc; j++) w[gi].c[j] = to[w[gi].c[j]];
+                }
+                for (int k = 0; k < ns; k++) {
+                    const int a = swapped[0][k], b = swapped[1][k];
+                    std::swap(at[a], at[b]);
+                    pos[at[a]] = a;
+                    pos[at[b]] = b;
                 }
             }
-            if (best < 0) break;
-            S |= 1ull << best;
-            cur = bestn;
         }
-        PassPlan pp;
-        std::vector<int> deferred;
-        for (int gi : remaining) {
-            const uint64_t qm = qubit_mask(g[gi]);
-            if (qm & blocked) {
-                deferred.push_back(gi);
-                blocked |= qm;
-                continue;
-            }
-            const uint64_t need = mixing_mask(g[gi]) & high & ~S;
-            if (popc(S | need) <= gsz) {
-                S |= need;
-                pp.gates.push_back(gi);
-            } else {
-                deferred.push_back(gi);
-                blocked |= qm;
-            }
-        }
-        // stage exactly gsz high qubits: pad with the lowest unused ones
-        for (int q = c; q < n && popc(S) < gsz; q++) S |= 1ull << q;
-        for (int q = c; q < n; q++)
-            if ((S >> q) & 1) pp.S.push_back(q);
+        pp.gates = ids;
         passes.push_back(std::move(pp));
         remaining.swap(deferred);
     }
-    if (passes.empty()) {  // empty circuit: nothing to do
-    }
+    where = pos;
     return passes;
+}
+
+std::vector<PassPlan> plan_circuit(const std::vector<PGate>& g, int n, int c, int gmax, bool remap,
+                                   std::vector<PGate>& out, std::vector<int>& where, std::vector<int>* src)
+{
+    std::vector<PassPlan> passes = plan_passes(g, n, c, gmax);
+    out = g;
+    where.resize(n);
+    for (int q = 0; q < n; q++) where[q] = q;
+    if (src) {
+        src->resize(g.size());
+        for (size_t i = 0; i < g.size(); i++) (*src)[i] = (int)i;
+    }
+    if (!remap || passes.size() < 2) return passes;
+    std::vector<PGate> rg;
+    std::vector<int> rw, rs;
+    std::vector<PassPlan> rp = plan_passes_remap(g, n, c, gmax, rg, rw, &rs);
+    if (rp.size() >= passes.size()) return passes;
+    out.swap(rg);
+    where.swap(rw);
+    if (src) src->swap(rs);
+    return rp;
 }
 
 std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& ids, int c,

@@ -62,6 +62,25 @@ struct PassPlan {
 // past gates on disjoint qubits.
 std::vector<PassPlan> plan_passes(const std::vector<PGate>& g, int n, int c, int gmax);
 
+// The same passes with qubit remapping: at the end of each pass, staged high
+// positions whose qubits the remaining gates mix before those of some low
+// positions exchange qubits with them (a physical SWAP applied in the pass),
+// and the gates after it run on the new positions. `out` receives the
+// physical gate list the passes index (the input's gates on their new
+// positions plus the SWAPs), `where[q]` the final position of the qubit at
+// input position q; src (if given) the input index of each entry of `out`,
+// -1 for the SWAPs.
+std::vector<PassPlan> plan_passes_remap(const std::vector<PGate>& g, int n, int c, int gmax, std::vector<PGate>& out,
+                                        std::vector<int>& where, std::vector<int>* src = nullptr);
+
+// The passes a circuit runs as: plan_passes, or with `remap` the remapped
+// passes when they are fewer. `out` receives the gate list the passes index,
+// `where` the final positions (the identity without remapping), src (if
+// given) the input index of each gate of `out` (-1 for an added SWAP).
+std::vector<PassPlan> plan_circuit(const std::vector<PGate>& g, int n, int c, int gmax, bool remap,
+                                   std::vector<PGate>& out, std::vector<int>& where,
+                                   std::vector<int>* src = nullptr);
+
 // Translate a pass's gates to local ops: low qubits 0..c-1 keep their
 // position, S[j] becomes position c + j, other qubits are global.
 std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& ids, int c,

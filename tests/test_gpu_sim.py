@@ -325,3 +325,58 @@ def test_degenerate_chunkings(SV, n, c):
         assert np.array_equal(s.state(), got)
         assert s.stats()["passes"] == st["passes"]
     assert np.linalg.norm(got - want) <= compressed_l2_bound(n, 1e-6, st["passes"], len(gates))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("name", ["layers", "clifford", "mixed"])
+@pytest.mark.parametrize("n,c,g", [(16, 10, 2), (14, 8, 3)])
+def test_remapped_passes_match_oracle(SV, dtype, name, n, c, g):
+    """remap_qubits: physical SWAPs move qubits between chunk-index and
+    in-chunk positions; the state, sampled amplitudes and an expectation read
+    back in logical order match the oracle, with the pass count sv_plan_remap
+    gives."""
+    import paper_2309_16979_gb300 as P
+    gates = _circuits(n)[name]
+    init = W.basis_index(n, seed=7)
+    want = oracle.run(n, gates, init=init)
+    plan = P.plan(n, c, gates, max_group_qubits=g, remap=True)
+    eb = 1e-6
+    with SV(n, c, eb, dtype=dtype, init_index=init, max_group_qubits=g, remap_qubits=True) as s:
+        s.apply(gates)
+        got = s.state()
+        st = s.stats()
+        idx = np.array([0, 1, 5, (1 << n) - 1, 12345 % (1 << n)], dtype=np.uint64)
+        amps = s.amplitudes(idx)
+        terms = W.random_pauli_sum(n, 6, seed=11)
+        e = s.expect(terms)
+    assert st["passes"] == plan["passes"] and st["remap_swaps"] == len(plan["swaps"])
+    bound = compressed_l2_bound(n, eb, st["passes"], len(gates) + st["remap_swaps"], dtype)
+    assert np.linalg.norm(got - want) <= bound, (st["passes"], np.linalg.norm(got - want), bound)
+    assert np.abs(amps - want[idx.astype(np.int64)]).max() <= bound
+    assert abs(e - oracle.expect(n, want, terms)) <= 4 * bound * sum(abs(t.coeff) for t in terms)
+
+
+def test_remapped_calls_accumulate_and_grad_resets(SV):
+    """Two remapped calls in a row compose their moves; sv_grad afterwards
+    starts again from the initial state on the original positions (g = 3:
+    the Ising terms' 6 high x-masks and the identity fit a group of 8
+    chunks)."""
+    n, c, g = 16, 10, 3
+    a, b = W.random_layers(n, 6, seed=4), W.random_mixed(n, 150, seed=6)
+    want = oracle.run(n, a + b, init=3)
+    gates, nparams = W.hea(n, 2)
+    theta = np.array(W.normal_params(nparams, seed=3))
+    H = W.ising(n, seed=4)
+    e_want, g_want = oracle.adjoint(n, gates, theta, H, init=3)
+    with SV(n, c, 1e-7, dtype="c128", init_index=3, max_group_qubits=g, remap_qubits=True) as s:
+        s.apply(a)
+        s.apply(b)
+        got = s.state()
+        st = s.stats()
+        assert st["remap_swaps"] > 0
+        bound = compressed_l2_bound(n, 1e-7, st["passes"], len(a) + len(b) + st["remap_swaps"], "c128")
+        assert np.linalg.norm(got - want) <= bound
+        e, gr = s.grad(gates, theta, H)
+    csum = sum(abs(t.coeff) for t in H)
+    assert abs(e - e_want) <= 1e-4 * csum
+    assert np.abs(gr - g_want).max() <= 1e-4 * csum

@@ -127,3 +127,21 @@ def test_exchange_circuits_reach_every_store_form(jit_sources):
     assert any("T* const gq = " in s for s in srcs)
     assert any("T* const gq0 = " in s for s in srcs)
     assert any("{ const float2 " in s for s in srcs)
+
+
+def test_remapped_circuit_kernels_compile(jit_sources):
+    """With qubit remapping the passes also run physical SWAPs (4x4
+    permutation matrices: moves only); every kernel of such a plan compiles."""
+    import paper_2309_16979_gb300 as P
+    lib = _nvrtc()
+    n, c, g = 16, 10, 2
+    gates = W.random_layers(n, 6, seed=4)
+    assert P.plan(n, c, gates, max_group_qubits=g, remap=True)["swaps"]
+    plain = [s for s in jit_sources(n, c, gates, max_group_qubits=g) if s]
+    srcs = [s for s in jit_sources(n, c, gates, max_group_qubits=g, remap=True) if s]
+    assert srcs and srcs != plain
+    for src in srcs:
+        if src in plain:
+            continue
+        rc, log = _compile(lib, src)
+        assert rc == 0, log
