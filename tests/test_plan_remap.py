@@ -128,3 +128,22 @@ def test_remap_cuts_passes_of_high_heavy_circuits(sv, name, n, c, gmax, most):
     a = sv.plan(n, c, gates, max_group_qubits=gmax)
     b = sv.plan(n, c, gates, max_group_qubits=gmax, remap=True)
     assert b["passes"] <= most < a["passes"], (a["passes"], b["passes"])
+
+
+@pytest.mark.parametrize("n,c,gmax", [(11, 5, 2), (12, 7, 3)])
+def test_remapped_plan_with_caller_swaps(sv, n, c, gmax):
+    """Caller SWAPs relabel qubits before the remapping moves them: the
+    physical circuit the library reports (its own positions for every gate)
+    still equals the logical circuit read back through the final map."""
+    gates = W.random_mixed(n, 200, seed=13)
+    assert any(g.kind == "SWAP" for g in gates)
+    p = sv.plan(n, c, gates, max_group_qubits=gmax, remap=True)
+    assert p["swaps"]
+    assert sorted(p["order"]) == [i for i, g in enumerate(gates) if g.kind != "SWAP"]
+    assert sorted(p["positions"]) == list(range(n))
+    phys = physical_circuit(gates, p)
+    rng = np.random.default_rng(6)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    want = to_physical(oracle.apply_gates(n, psi0, gates), p["positions"], n)
+    got = oracle.apply_gates(n, psi0, [g for g, _ in phys])
+    assert np.abs(got - want).max() < 1e-11
