@@ -6,12 +6,15 @@ runs in the CUDA library libsvgb300.so; this module only marshals arguments.
 
     from paper_2309_16979_gb300 import StateVector
     sv = StateVector(30, chunk_qubits=22, eb=1e-6)      # relative_bound=True: per-chunk step
+                                                         # remap_qubits=True: fewer passes on
+                                                         # circuits that mix high qubits often
     sv.apply(gates)
     e = sv.expect(terms)
     energy, grad = sv.grad(gates, theta, terms)          # adjoint gradient
 
 Also: codec_encode / codec_decode (one chunk on the device), copy_probe (the
-paper's host <-> device copy strategies), plan and jit_sources (host only).
+paper's host <-> device copy strategies), plan (with remap=True: the remapped
+passes) and jit_sources (host only).
 """
 from __future__ import annotations
 
