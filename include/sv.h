@@ -199,7 +199,9 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
  * partitioned into stages; each stage is one pass over all chunks, streamed
  * to the GPU, updated and stored back recompressed).
  *   gates:  host array; copied during the call. SWAPs relabel qubits and
- *           move no data.
+ *           move no data. With sv_config.remap_qubits the call may also add
+ *           physical SWAPs to its passes (sv_plan_remap lists them); logical
+ *           results are the same.
  * Errors: SV_ERR_ARG (invalid gate; the state is unchanged), SV_ERR_RANGE /
  * SV_ERR_CORRUPT / SV_ERR_CUDA / SV_ERR_TIMEOUT (the state is undefined and
  * the handle should be destroyed).
@@ -209,9 +211,15 @@ int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t ngates);
 /*
  * *out_re = sum_j coeff_j <psi|P_j|psi> accumulated in FP64 (the
  * expectation value of a Pauli sum on the stored state; imaginary parts cancel
- * for real coefficients). Masks use logical qubits. Terms whose x-masks
- * differ on the high (inter-chunk) qubits pair different chunks and take one
- * streaming sweep per distinct high x-mask.
+ * for real coefficients). Masks use logical qubits. Compressed states are
+ * streamed from the host store: a sweep stages max_group_qubits high
+ * (inter-chunk) qubits, decodes each chunk group and evaluates every term
+ * whose high x-mask lies in the staged set; the staged sets are chosen
+ * greedily to cover the terms' high x-masks (few sweeps: two for an open
+ * Ising chain at n = 30, chunk_qubits = 22). Terms with more high x bits than
+ * max_group_qubits, or more than 512 terms, take one sweep per distinct high
+ * x-mask over chunk pairs. Errors: SV_ERR_ARG for masks beyond n qubits;
+ * SV_ERR_CORRUPT / SV_ERR_CUDA / SV_ERR_TIMEOUT as sv_apply_circuit.
  */
 int sv_expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
 
@@ -257,8 +265,8 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
  *   n, chunk_qubits: as in sv_create (chunk_qubits ignored when cfg->mode is
  *                    SV_UNCOMPRESSED).
  *   cfg:             NULL for defaults; dtype, mode, max_group_qubits (0 is
- *                    taken as 4 here: no device is queried), tile_qubits and
- *                    fuse_codec are used.
+ *                    taken as 4 here: no device is queried), tile_qubits,
+ *                    fuse_codec and remap_qubits are used.
  *   gates, ngates:   host gate list, validated as in sv_apply_circuit
  *                    (sv_grad when adjoint is set).
  *   adjoint:         0: the kernels of sv_apply_circuit; 1: those of the
@@ -414,6 +422,9 @@ int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, 
  * byte-identical to sv_codec_encode's.
  */
 #define SV_NOALLOC_MAX_CHUNK_QUBITS 20
+int sv_codec_encode_noalloc(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
+                            size_t cap, size_t* h_nbytes);
+
 /* ----------------------------------------------------------- transfers */
 /* The host <-> device copy strategies of Sec. 2 "Online stage" step (2) and
  * Table 1, timed on a 2^n-amplitude state: SV_COPY_SYNC, one bulk copy;
@@ -445,9 +456,6 @@ int sv_copy_probe(int n, int dtype, int strategy, int direction, uint64_t sample
  * decodes with sv_codec_decode. */
 int sv_codec_encode_relative(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
                              size_t cap, size_t* nbytes);
-
-int sv_codec_encode_noalloc(int dtype, int chunk_qubits, double eb, const void* d_amps, void* d_stream,
-                            size_t cap, size_t* h_nbytes);
 
 /*
  * Decode one chunk stream of nbytes bytes (device) into d_amps (device,
