@@ -120,7 +120,10 @@ typedef struct sv_config {
                                      between high (chunk-index) and low positions with physical
                                      SWAPs appended to a pass, when that runs the circuit in fewer
                                      passes (furthest-next-use rule, sv_plan_remap); logical
-                                     results are unchanged. sv_grad never remaps. */
+                                     results are unchanged. sv_grad never remaps. A remapped
+                                     call leaves qubits on new positions, so repeating the same
+                                     circuit runs (and, with jit, compiles) other kernels: best
+                                     for one long circuit per call. */
     uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
