@@ -80,10 +80,19 @@ k_pauli(const typename V2<R>::T* __restrict__ A, const typename V2<R>::T* __rest
 
 // All terms in one sweep: partials[block] = sum_{i in block range}
 // Re conj(psi_i) * sum_t coeff_t * phase_t(i) * psi[i ^ xl_t], i.e. the
-// block's share of <psi|H|psi> over the buffer (phase_t as in k_pauli). Each
-// amplitude is read once, and once more per term with a nonzero x mask (its
-// partner, mostly from cache); the per-amplitude sum over terms runs in the
-// amplitude precision, then FP64 as in k_pauli. Terms staged in shared memory.
+// block's share of <psi|H|psi> over the buffer (phase_t as in k_pauli). The
+// per-amplitude sum over terms runs in the amplitude precision, then FP64 as
+// in k_pauli. Terms staged in shared memory.
+//
+// A thread holds a strip of 8 amplitudes, index i + 256 k (k = 0..7), and a
+// CTA's strips start at multiples of 2048, so bits 8..10 of i are zero and a
+// term's sign (-1)^popcount(j & z) is the sign of i (one popcount per strip)
+// times a per-term table over k. For a term with an x mask, the amplitudes j
+// and j ^ x contribute equal real parts (the term is Hermitian); when the
+// lowest bit of x is one of the strip bits (8..10) or above, only the member
+// of each pair with that bit clear is evaluated, with twice the coefficient
+// (the choice is the same for the whole strip or the whole CTA, so warps do
+// not diverge).
 constexpr int kMaxEnergyTerms = 512;
 
 template <typename R>
@@ -91,28 +100,38 @@ __global__ void __launch_bounds__(kThreads)
 k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gbase, const PauliDev* __restrict__ terms,
          int nterms, double* __restrict__ partials)
 {
+    constexpr int kStrip = 8;
+    constexpr uint64_t kSpan = (uint64_t)kThreads * kStrip;  // 2048 amplitudes: one strip of the CTA
     __shared__ double red[kThreads / 32];
     __shared__ uint64_t sx[kMaxEnergyTerms], sz[kMaxEnergyTerms];
-    __shared__ R sc[kMaxEnergyTerms];
-    __shared__ int sny[kMaxEnergyTerms];
+    __shared__ R sre[kMaxEnergyTerms], sim[kMaxEnergyTerms];
+    __shared__ uint32_t stab[kMaxEnergyTerms];
     for (int t = threadIdx.x; t < nterms; t += kThreads) {
         const PauliDev P = terms[t];
         sx[t] = P.xl;
         sz[t] = P.zl;
-        // the global-bit sign folded into the coefficient
-        sc[t] = (R)((__popcll(gbase & P.zg) & 1) ? -P.coeff : P.coeff);
-        sny[t] = P.ny & 3;
+        // the global-bit sign folded into the coefficient; doubled where one
+        // member of each pair is evaluated
+        double cf = (__popcll(gbase & P.zg) & 1) ? -P.coeff : P.coeff;
+        if (P.xl != 0 && (P.xl & 0xFFull) == 0) cf *= 2.0;
+        // real part of i^ny-weighted conj(psi_j) psi_{j^x} as cr*re + ci*im
+        // (re, im as below; the sign of z on x's bits folded in, as in k_pauli)
+        const int ny = P.ny & 3;
+        sre[t] = (R)(ny == 0 ? cf : ny == 2 ? -cf : 0.0);
+        sim[t] = (R)(ny == 1 ? -cf : ny == 3 ? cf : 0.0);
+        // bit k: parity of z on the strip bits of k
+        uint32_t tab = 0;
+        for (int k = 0; k < kStrip; k++) tab |= (uint32_t)(__popcll(((uint64_t)k << 8) & P.zl) & 1) << k;
+        stab[t] = tab;
     }
     __syncthreads();
-    const uint64_t per_block = (count + gridDim.x - 1) / gridDim.x;
+    const uint64_t per_block = ((count + gridDim.x - 1) / gridDim.x + kSpan - 1) / kSpan * kSpan;
     const uint64_t i0 = (uint64_t)blockIdx.x * per_block;
     const uint64_t i1 = min(count, i0 + per_block);
     using T = typename V2<R>::T;
-    // a strip of kStrip amplitudes per thread in registers: each term's
-    // parameters are read from shared memory once per strip
-    constexpr int kStrip = 8;
     double acc = 0;
-    for (uint64_t i = i0 + threadIdx.x; i < i1; i += (uint64_t)kThreads * kStrip) {
+    for (uint64_t s0 = i0; s0 < i1; s0 += kSpan) {
+        const uint64_t i = s0 + threadIdx.x;
         T a[kStrip];
         R e[kStrip], n2[kStrip];
 #pragma unroll
@@ -123,27 +142,28 @@ k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gba
             n2[k] = a[k].x * a[k].x + a[k].y * a[k].y;
         }
         for (int t = 0; t < nterms; t++) {
-            const uint64_t x = sx[t], z = sz[t];
-            const R cf = sc[t];
-            const int ny = sny[t];
+            const uint64_t x = sx[t];
+            const uint32_t sg = stab[t] ^ ((__popcll(i & sz[t]) & 1) ? 0xFFu : 0u);  // bit k: sign of j_k
+            const R cr = sre[t];
             if (x == 0) {
-                // a Z string (no Y without an X): |psi_i|^2 with its sign
+                // a Z string (no Y without an X): |psi_j|^2 with its sign
 #pragma unroll
-                for (int k = 0; k < kStrip; k++) {
-                    const uint64_t j = i + (uint64_t)k * kThreads;
-                    e[k] += ((__popcll(j & z) & 1) ? -cf : cf) * n2[k];
-                }
+                for (int k = 0; k < kStrip; k++) e[k] += (((sg >> k) & 1u) ? -cr : cr) * n2[k];
                 continue;
             }
+            const uint64_t xb = x & (~x + 1);  // lowest bit of x
+            if (xb >= kSpan && (s0 & xb)) continue;  // the strip s0 ^ xb evaluates these pairs
+            const R ci = sim[t];
 #pragma unroll
             for (int k = 0; k < kStrip; k++) {
-                const uint64_t j = i + (uint64_t)k * kThreads;
-                const T b = j < i1 ? psi[j ^ x] : a[k];
+                const uint64_t kb = (uint64_t)k * kThreads;
+                if (xb >= (uint64_t)kThreads && xb < kSpan && (kb & xb)) continue;  // counted at k ^ (xb >> 8)
+                const uint64_t j = i + kb;
+                const T b = j < i1 ? psi[j ^ x] : T{(R)0, (R)0};
                 const R re = b.x * a[k].x + b.y * a[k].y;
                 const R im = b.x * a[k].y - b.y * a[k].x;
-                R v = ny == 0 ? re : ny == 1 ? -im : ny == 2 ? -re : im;  // i^ny, real part
-                if (__popcll(j & z) & 1) v = -v;
-                e[k] += cf * v;
+                const R v = cr * re + ci * im;
+                e[k] += ((sg >> k) & 1u) ? -v : v;
             }
         }
         R sub = (R)0;

@@ -156,6 +156,28 @@ def test_expectation_values(SV, mode):
     assert abs(got - oracle.expect(n, psi, terms)) <= 2 * err * sum(abs(t.coeff) for t in terms) + 1e-12
 
 
+@pytest.mark.parametrize("mode", ["uncompressed", "compressed"])
+def test_expectation_every_lowest_x_bit(SV, mode):
+    """The all-terms energy kernel evaluates X-type terms whose lowest x bit
+    is 8 or above on one amplitude of each pair: terms with every lowest x
+    bit, with Y factors and z masks, over several strips and CTAs (n = 15),
+    against the oracle on the state the GPU holds."""
+    n = 15
+    gates = W.random_layers(n, 4, seed=8)
+    rng = np.random.default_rng(9)
+    terms = []
+    for b in range(n):
+        z = int(rng.integers(0, 1 << n))
+        terms += [W.PauliTerm(0.7, 1 << b, 0), W.PauliTerm(-0.4, 1 << b, z | (1 << b)),
+                  W.PauliTerm(0.3, (1 << b) | (1 << (n - 1)), z)]
+    terms += W.ising(n, seed=5)
+    with SV(n, 9, 1e-9, mode=mode, dtype="c128", max_group_qubits=3) as s:
+        s.apply(gates)
+        got = s.expect(terms)
+        held = s.state()
+    assert abs(got - oracle.expect(n, held, terms)) <= 1e-12 * sum(abs(t.coeff) for t in terms)
+
+
 def test_expectation_closed_forms(SV):
     n = 14
     with SV(n, 8, 1e-6, max_group_qubits=2) as s:
