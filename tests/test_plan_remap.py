@@ -147,3 +147,24 @@ def test_remapped_plan_with_caller_swaps(sv, n, c, gmax):
     want = to_physical(oracle.apply_gates(n, psi0, gates), p["positions"], n)
     got = oracle.apply_gates(n, psi0, [g for g, _ in phys])
     assert np.abs(got - want).max() < 1e-11
+
+
+def test_remap_plan_degenerate_inputs(sv):
+    """No gates, SWAPs only, all high qubits stageable at once (one pass:
+    nothing to remap), and invalid sizes."""
+    from paper_2309_16979_gb300 import SvError
+    for gates in ([], [W.Gate("SWAP", (0, 9)), W.Gate("SWAP", (3, 11))]):
+        p = sv.plan(12, 8, gates, max_group_qubits=2, remap=True)
+        assert p["passes"] == 0 and p["order"] == [] and p["swaps"] == []
+    swapped = sv.plan(12, 8, [W.Gate("SWAP", (0, 9)), W.Gate("SWAP", (3, 11))], max_group_qubits=2, remap=True)
+    pos = list(range(12))
+    pos[0], pos[9] = 9, 0
+    pos[3], pos[11] = 11, 3
+    assert swapped["positions"] == pos
+    gates = W.random_layers(12, 6, seed=7)
+    p = sv.plan(12, 8, gates, max_group_qubits=4, remap=True)
+    assert p["passes"] == 1 and p["swaps"] == []
+    with pytest.raises(SvError):
+        sv.plan(12, 8, gates, max_group_qubits=1, remap=True)
+    with pytest.raises(SvError):
+        sv.plan(12, 13, gates, max_group_qubits=2, remap=True)
