@@ -47,6 +47,39 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_abi.SvConfig) == 4 + 4 + 8 + 4 * 10 + 8 + 8
 
 
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that
+    the C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    from paper_2309_16979_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sv_gate": _abi.SvGate, "sv_pauli_term": _abi.SvPauliTerm, "sv_config": _abi.SvConfig,
+               "sv_stats_t": _abi.SvStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sv.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, f, v = line.split()
+            got[(cname, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 def test_codec_max_bytes_without_gpu(lib):
     lib.sv_codec_max_bytes.restype = ctypes.c_size_t
     import oracle
