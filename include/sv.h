@@ -163,6 +163,9 @@ typedef struct sv_stats_t {
     double t_host_prepare_s, t_host_wait_s;
     /* physical SWAPs added by sv_config.remap_qubits */
     uint64_t remap_swaps;
+    /* launches of generated two-vector (psi, lambda) kernels by the reverse
+       sweep of sv_grad (included in jit_launches) */
+    uint64_t jit_adjoint_launches;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
@@ -415,7 +418,10 @@ int sv_codec_encode(int dtype, int chunk_qubits, double eb, const void* d_amps, 
  *     the stream is written in place, with no temporary.
  *   - The first call on a device looks up the staging area's device address
  *     for that device (once per device, with that device made current); make
- *     that first call before any stream capture on that device.
+ *     that first call before any stream capture on that device. The address
+ *     is kept for the life of the process: after cudaDeviceReset (or any
+ *     other teardown of the device's primary context) the library image is
+ *     reloaded at a new address and later calls on that device are invalid.
  *   - All calls share the one staging area, which keeps the last call's
  *     contents. Calls are synchronous, so calls from one thread never
  *     overlap; calls from several host threads that overlap on the GPU race

@@ -56,7 +56,7 @@ class SvStats(C.Structure):
                 ("t_jit_compile_s", C.c_double),
                 ("t_h2d_s", C.c_double), ("t_d2h_s", C.c_double), ("t_encode_finish_s", C.c_double),
                 ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double),
-                ("remap_swaps", C.c_uint64)]
+                ("remap_swaps", C.c_uint64), ("jit_adjoint_launches", C.c_uint64)]
 
 
 # every entry point declared in include/sv.h

@@ -1417,6 +1417,7 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
                 e = jit_launch_adjoint<R>(ap.fn[i], s->d_state, s->d_lam, tds[i], 0, d_gpart, ap.par[i], s->s_comp,
                                           &parts);
                 s->st.jit_launches++;
+                s->st.jit_adjoint_launches++;
             } else {
                 e = launch_adjoint<R>(s->d_state, s->d_lam, tds[i], d_ops + offs[i], cnts[i], 0, d_gpart, ntiles,
                                       s->s_comp);
@@ -1694,6 +1695,7 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
                 e = jit_launch_adjoint<R>(ap.fn[i], s->d_amps, s->d_amps2, tds[i], gbase, d_gpart, ap.par[i], s->s_comp,
                                           &parts);
                 s->st.jit_launches++;
+                s->st.jit_adjoint_launches++;
             } else {
                 e = launch_adjoint<R>(s->d_amps, s->d_amps2, tds[i], d_ops + offs[i], cnts[i], gbase, d_gpart, ntiles,
                                       s->s_comp);

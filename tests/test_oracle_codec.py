@@ -126,15 +126,6 @@ def test_corrupt_streams_rejected():
     assert oracle.codec_status_decode(bytes(s), 10) == -4       # wrong chunk size
 
 
-def test_planted_mistake_in_zigzag_is_caught():
-    """Swapping the zigzag sign convention changes the hand-worked stream."""
-    g = _load("codec_ties_c64.json")
-    want = "".join(g["stream_hex"])
-    # a zigzag with z = -2r for r<0 (dropping the -1) would give z1 = 4, z3 = 6
-    wrong_word0 = (0 | (4 << 4) | (8 << 8) | (6 << 12)).to_bytes(4, "little").hex()
-    assert wrong_word0 not in want[160 * 2 // 2:]
-
-
 # ------------------------------------------------------- relative bound
 def test_relative_exponent_brackets_2_eb_m():
     """k = floor(log2(2 eb m)), checked against the power of two it must sit

@@ -58,3 +58,24 @@ def test_noalloc_rejects_out_of_range_sizes(lib):
     assert fn_na(1, 21, 1e-6, d.data_ptr(), out.data_ptr(), out.numel(), C.byref(nb)) == -1
     assert fn_na(1, 12, 1e-6, d.data_ptr(), out.data_ptr(), out.numel() - 16, C.byref(nb)) == -1
     assert fn_na(1, 12, 1e-6, d.data_ptr(), out.data_ptr(), out.numel(), C.byref(nb)) == 0
+
+
+def test_noalloc_range_error_then_clean_call(lib):
+    """An out-of-range value returns SV_ERR_RANGE; the staging area's error
+    word, which persists between calls, must not leak into the next call."""
+    fn_na = lib.sv_codec_encode_noalloc
+    fn_na.argtypes = [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    fn_na.restype = C.c_int
+    c, eb = 12, 1e-7  # step 2^-23: complex64 codes reach 2^24 - 1, i.e. |x| < 2
+    cap = lib.sv_codec_max_bytes(c)
+    bad = np.zeros(1 << c, dtype=np.complex64)
+    bad[77] = 4.0 - 3.0j
+    d_bad = torch.from_numpy(bad).cuda()
+    out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    nb = C.c_size_t(0)
+    torch.cuda.synchronize()
+    assert fn_na(1, c, eb, d_bad.data_ptr(), out.data_ptr(), cap, C.byref(nb)) == -7  # SV_ERR_RANGE
+    rng = np.random.default_rng(7)
+    x = ((rng.standard_normal(1 << c) + 1j * rng.standard_normal(1 << c)) * 2.0 ** (-c / 2)).astype(np.complex64)
+    want = _encode(lib, lib.sv_codec_encode, x, c, eb, 1)
+    assert _encode(lib, fn_na, x, c, eb, 1) == want
