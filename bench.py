@@ -289,7 +289,16 @@ def load_traffic(kind, alg_bytes_per_launch):
     return int(alg_bytes_per_launch * t["bytes_per_amplitude"] / t["algorithmic_bytes_per_amplitude"])
 
 
-def roofline_from_stats(d):
+def roofline_from_stats(d, n=None, amp_bytes=None, step_s=None, link=None, steps=1):
+    """Roofline of the dominant kernel from one profiled step's counters.
+
+    Top level (achieved, frac): the per-pass accounting, where a pass over
+    the state owes 2 * 2^n * s bytes of HBM traffic however many tile sweeps
+    it takes (fused gates ride free); one launch is credited its share,
+    passes * 2 * 2^n * s / launches. "per_sweep" credits every tile sweep
+    with the amplitudes it reads and writes (the kernel's own streaming
+    rate). "step_binding": the slowest of the step's host-link and HBM terms
+    against the measured step time."""
     hbm_peak, peak_kind = measured_peaks()
     kinds = {"apply": ("t_apply_s", "n_apply", "alg_bytes_apply"),
              "decode": ("t_decode_s", "n_decode", "alg_bytes_decode"),
@@ -297,16 +306,42 @@ def roofline_from_stats(d):
     total = sum(d[v[0]] for v in kinds.values())
     top = max(kinds, key=lambda k: d[kinds[k][0]])
     tk, nk, bk = kinds[top]
-    avg_s = d[tk] / max(1, d[nk])
-    bytes_per_launch = d[bk] / max(1, d[nk])
-    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": load_traffic(top, bytes_per_launch),
-            "kernel": ("svj (generated sub-pass kernels)" if top == "apply" and d.get("jit_launches", 0) > 0
-                       else f"k_{top}"),
-            "peak_source": f"{peak_kind} (copy)", "launches": int(d[nk]),
-            "avg_launch_ms": round(avg_s * 1e3, 4), "alg_bytes_per_launch": int(bytes_per_launch),
-            "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, total), 3) for k, v in kinds.items()}}
+    launches = max(1, d[nk])
+    avg_s = d[tk] / launches
+    sweep_bytes = d[bk] / launches
+    sweep_achieved = sweep_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
+    out = {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+           "kernel": ("svj (generated sub-pass kernels)" if top == "apply" and d.get("jit_launches", 0) > 0
+                      else f"k_{top}"),
+           "peak_source": f"{peak_kind} (copy)", "launches": int(d[nk]), "avg_launch_ms": round(avg_s * 1e3, 4),
+           "share_of_kernel_time": {k: round(d[v[0]] / max(1e-12, total), 3) for k, v in kinds.items()},
+           "per_sweep": {"alg_bytes_per_launch": int(sweep_bytes), "achieved": round(sweep_achieved, 1),
+                         "frac": round(sweep_achieved / hbm_peak, 4)}}
+    if top == "apply" and n is not None and amp_bytes is not None and d["passes"] > 0:
+        pass_bytes = d["passes"] * 2.0 * (1 << n) * amp_bytes
+        per_launch = pass_bytes / launches
+        ach = per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+        out.update({"achieved": round(ach, 1), "frac": round(ach / hbm_peak, 4), "accounting": "per pass",
+                    "alg_bytes_per_launch": int(per_launch), "sweeps_per_pass": round(launches / d["passes"], 2)})
+        out["traffic"] = load_traffic(top, sweep_bytes)
+    else:
+        out.update({"achieved": round(sweep_achieved, 1), "frac": round(sweep_achieved / hbm_peak, 4),
+                    "accounting": "per sweep", "alg_bytes_per_launch": int(sweep_bytes),
+                    "traffic": load_traffic(top, sweep_bytes)})
+    if step_s and n is not None:
+        terms = {}
+        if link:
+            terms["h2d_ms"] = d["bytes_h2d"] / steps / (link["h2d"] * 1e9) * 1e3
+            terms["d2h_ms"] = d["bytes_d2h"] / steps / (link["d2h"] * 1e9) * 1e3
+        hbm = (d["passes"] / steps) * 2.0 * (1 << n) * amp_bytes if amp_bytes else 0.0
+        if d["bytes_h2d"]:
+            hbm += (d["bytes_h2d"] + d["bytes_d2h"]) / steps
+        terms["hbm_ms"] = hbm / (hbm_peak * 1e9) * 1e3
+        bind = max(terms, key=terms.get)
+        out["step_binding"] = {"terms_ms": {k: round(v, 2) for k, v in terms.items()}, "binding": bind,
+                               "measured_step_ms": round(step_s * 1e3, 2),
+                               "frac": round(terms[bind] / (step_s * 1e3), 4)}
+    return out
 
 
 STAT_KEYS = ("passes", "subpasses", "groups", "kernel_launches", "bytes_h2d", "bytes_d2h", "t_decode_s", "t_apply_s",
@@ -380,7 +415,8 @@ def run_apply(args, rank, world):
     sp1 = sim.stats()
     sim.set_profile(False)
     dp = {k: sp1[k] - sp0[k] for k in STAT_KEYS}
-    roofline = roofline_from_stats(dp)
+    amp_bytes = 8 if w["dtype"] == "c64" else 16
+    roofline = roofline_from_stats(dp, n=n, amp_bytes=amp_bytes, step_s=t_max / args.steps, link=link)
 
     # e2e: the public calls a user makes (apply + read back <H>), host buffers,
     # every H2D / D2H of the compressed store inside the timed region
@@ -401,7 +437,7 @@ def run_apply(args, rank, world):
     st = sim.stats()
     gpu_launches = int(d["kernel_launches"])
     sim.close()
-    quality = state_quality(w, gates, dev) if rank == 0 and not args.no_extras else {}
+    quality = state_quality(w, gates, terms, dev) if rank == 0 and not args.no_extras else {}
 
     out = {
         "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world, "steps": args.steps,
@@ -431,27 +467,70 @@ def run_apply(args, rank, world):
             ("host_prepare", "t_host_prepare_s"), ("host_wait", "t_host_wait_s"))},
         "stored_state": {"compressed_bytes": st["compressed_bytes"], "raw_bytes": st["raw_bytes"],
                          "ratio": round(st["raw_bytes"] / max(1, st["compressed_bytes"]), 2),
-                         "norm2": st["norm2"], "energy": energy, **quality},
+                         "norm2": st["norm2"], "energy": energy,
+                         "note": "after every warm-up, timed, profiled and e2e application of the circuit "
+                                 "to the same handle: error compounds per pass"},
     }
+    if quality:
+        out["fidelity"] = quality["one_apply_vs_fp64"]
     if rank == 0 and not args.no_extras and w["n"] <= 32:
         out.update(comparator(args, gates, terms, energy, applies=args.warmup + args.steps + 1 + e_steps))
+    if rank == 0 and not args.no_extras and args.workload == "layers30":
+        out["adjoint_grad_s_per_step"] = adjoint_legs(dev)
     return out
 
 
-def state_quality(w, gates, dev):
-    """Closed-form fidelity where the circuit has one: GHZ applied once to
-    |0...0> on a fresh state (the timed steps apply the circuit repeatedly to
-    a seeded basis state, which the GHZ closed form does not describe)."""
+def state_quality(w, gates, terms, dev):
+    """Error of one application of the workload's circuit to its seeded basis
+    state (a fresh handle, as a user's first call), against an FP64
+    reference: the uncompressed complex128 GPU path (pinned to the FP64
+    oracle at 1e-12 relative L2) where 2^n complex128 amplitudes fit in HBM,
+    else the GHZ closed form. Reports the fidelity |<ref|psi>|^2 /
+    (||ref||^2 ||psi||^2), the Ising energy error and the stored norm^2 of
+    the compressed path, and the same for the plain uncompressed path in the
+    workload's own precision (the comparator "at fidelity")."""
     from paper_2309_16979_gb300 import StateVector
     n = w["n"]
-    if w["circuit"] != "ghz":
+    init = W.basis_index(n)
+    kw = dict(dtype=w["dtype"], max_group_qubits=w["group"], device=dev,
+              relative_bound=bool(w.get("relative", False)), host_budget_bytes=host_budget())
+    out = {"reference": None}
+    if w["circuit"] == "ghz":
+        with StateVector(n, w["c"], w["eb"], **kw) as s:
+            s.apply(gates)
+            a = s.amplitudes([0, (1 << n) - 1])
+            st = s.stats()
+        out.update({"reference": "GHZ closed form",
+                    "fidelity": float(abs((a[0] + a[1]) / math.sqrt(2)) ** 2 / max(st["norm2"], 1e-300)),
+                    "norm2": st["norm2"], "passes": st["passes"]})
+        return {"one_apply_vs_fp64": out}
+    if n > 30:
         return {}
-    with StateVector(n, w["c"], w["eb"], dtype=w["dtype"], max_group_qubits=w["group"], device=dev,
-                     relative_bound=bool(w.get("relative", False)), host_budget_bytes=host_budget()) as s:
-        s.apply(gates)
-        a = s.amplitudes([0, (1 << n) - 1])
-        norm2 = s.stats()["norm2"]
-    return {"fidelity_closed_form_one_apply": float(abs((a[0] + a[1]) / math.sqrt(2)) ** 2 / max(norm2, 1e-300))}
+    t0 = time.perf_counter()
+    with StateVector(n, mode="uncompressed", dtype="c128", init_index=init, device=dev) as ref:
+        ref.apply(gates)
+        e_ref = ref.expect(terms)
+        with StateVector(n, w["c"], w["eb"], init_index=init, **kw) as s:
+            s.apply(gates)
+            st = s.stats()
+            e_c = s.expect(terms)
+            nr = ref.inner(ref).real
+            dot, ns = s.inner(ref), st["norm2"]  # <psi|ref>; the stored state's exact FP64 norm^2
+        comp = {"fidelity": float(abs(dot) ** 2 / max(nr * ns, 1e-300)), "infidelity": None,
+                "energy": e_c, "energy_abs_err": abs(e_c - e_ref), "norm2": st["norm2"], "passes": st["passes"],
+                "per_pass_infidelity_estimate": (2.0 / 3.0) * (1 << n) * w["eb"] ** 2
+                if not w.get("relative") else None}
+        comp["infidelity"] = 1.0 - comp["fidelity"]
+        with StateVector(n, mode="uncompressed", dtype=w["dtype"], init_index=init, device=dev) as p:
+            p.apply(gates)
+            e_p = p.expect(terms)
+            dot, npl = p.inner(ref), p.inner(p).real
+        plain = {"fidelity": float(abs(dot) ** 2 / max(nr * npl, 1e-300)), "energy": e_p,
+                 "energy_abs_err": abs(e_p - e_ref), "norm2": npl}
+        plain["infidelity"] = 1.0 - plain["fidelity"]
+    out.update({"reference": "uncompressed complex128 GPU path", "reference_energy": e_ref,
+                "compressed": comp, "plain_uncompressed": plain, "seconds": round(time.perf_counter() - t0, 1)})
+    return {"one_apply_vs_fp64": out}
 
 
 def comparator(args, gates, terms, energy_c, applies):
@@ -479,7 +558,9 @@ def comparator(args, gates, terms, energy_c, applies):
             s1 = p.stats()
         d = {k: s1[k] - s0[k] for k in STAT_KEYS}
         out["plain_uncompressed"] = {"value": units / t, "unit": METRIC, "seconds_per_step": t,
-                                     "subpasses_per_step": d["subpasses"], "roofline": roofline_from_stats(d),
+                                     "subpasses_per_step": d["subpasses"],
+                                     "roofline": roofline_from_stats(d, n=n, amp_bytes=8 if w["dtype"] == "c64" else 16,
+                                                                     step_s=t),
                                      "energy_after_same_applies": e_plain, "energy_compressed": energy_c,
                                      "energy_abs_diff": abs(e_plain - energy_c) if energy_c is not None else None}
     except Exception as ex:  # noqa: BLE001
@@ -488,41 +569,59 @@ def comparator(args, gates, terms, energy_c, applies):
     return out
 
 
-def cpu_baseline(w, gates, target_s=12.0):
-    """FP64 oracle (as it stands) on the host cores: consecutive gates of the
-    workload on the full n-qubit complex128 state; amp-gate updates/s."""
+def oracle_sample(n, gates, psi, first, target_s, threads=None):
+    """The one sampling protocol of both bench arms: the FP64 oracle (as it
+    stands) applies consecutive gates of the workload, starting at gate
+    `first`, to the full 2^n complex128 state, as many as fit in about
+    target_s (timed by the first of them); returns (state, gates applied,
+    seconds, threads used)."""
+    import oracle
+    if threads:
+        oracle.set_num_threads(threads)
+    used = oracle.num_threads()
+    t0 = time.perf_counter()
+    psi = oracle.apply_gates(n, psi, [gates[first % len(gates)]], inplace=True)
+    t1 = time.perf_counter() - t0
+    k = max(1, int(target_s / max(t1, 1e-4)) - 1)
+    sample = [gates[(first + 1 + j) % len(gates)] for j in range(k)]
+    t0 = time.perf_counter()
+    psi = oracle.apply_gates(n, psi, sample, inplace=True)
+    dt = time.perf_counter() - t0 + t1
+    return psi, k + 1, dt, used
+
+
+def cpu_baseline(w, gates, target_s=10.0):
+    """FP64 oracle on the host cores, all of them and one: consecutive gates
+    of the workload on the full n-qubit complex128 state; amp-gate updates/s."""
     import oracle
     n = w["n"]
-    psi = np.zeros(1 << n, dtype=np.complex128)
-    psi[W.basis_index(n)] = 1.0
-    t0 = time.perf_counter()
-    psi = oracle.apply_gates(n, psi, gates[:1])
-    t1 = time.perf_counter() - t0
-    k = max(1, min(len(gates) - 1, int(target_s / max(t1, 1e-3))))
-    t0 = time.perf_counter()
-    psi = oracle.apply_gates(n, psi, gates[1:1 + k])
-    dt = time.perf_counter() - t0
-    return {"value": k * (1 << n) / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"gates 2..{k + 1} of the {len(gates)}-gate workload on the full 2^{n} complex128 state "
-                      f"({dt:.1f} s)"}
+    psi = oracle.basis_state(n, W.basis_index(n))
+    all_cores = oracle.num_threads()
+    psi, k, dt, used = oracle_sample(n, gates, psi, 0, target_s)
+    _, k1, dt1, _ = oracle_sample(n, gates, psi, k, target_s / 2, threads=1)
+    oracle.set_num_threads(all_cores)
+    return {"value": k * (1 << n) / dt, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"gates 1..{k} of the {len(gates)}-gate workload on the full 2^{n} complex128 state "
+                      f"({dt:.1f} s on {used} threads)",
+            "single_thread": {"value": k1 * (1 << n) / dt1, "cores": 1,
+                              "sample": f"gates {k + 1}..{k + k1} ({dt1:.1f} s)"}}
 
 
-def run_grad(args, rank, world):
-    """Adjoint gradient seconds per step (the HEA workloads: n = 24 in HBM, n = 32 compressed)."""
+def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None):
+    """Adjoint gradient seconds per step on an HEA workload, and every timed
+    set's energy and gradient error against the FP64 reference (the
+    uncompressed complex128 GPU adjoint, pinned to the FP64 oracle)."""
     import torch
     from paper_2309_16979_gb300 import StateVector
-    w = args.w
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
     n = w["n"]
     gates, npar = W.hea(n, w["layers"])
     terms = W.ising(n, seed=4)
-    sets = w.get("sets", 1)
-    thetas = [W.normal_params(npar, seed=(3 if sets == 1 else 100 + i)) for i in range(max(1, sets))]
+    sets = w.get("sets", 1) if max_sets is None else min(max_sets, w.get("sets", 1))
+    thetas = [W.normal_params(npar, seed=(3 if w.get("sets", 1) == 1 else 100 + i)) for i in range(max(1, sets))]
     mode = w.get("mode", "compressed")
     sim = StateVector(n, w["c"], w["eb"] or 1e-6, dtype=w["dtype"], mode=mode, max_group_qubits=w["group"], device=dev,
                       host_budget_bytes=host_budget() if mode == "compressed" else 0)
-    for i in range(args.warmup):
+    for i in range(warmup):
         sim.grad(gates, thetas[i % len(thetas)], terms)
     torch.cuda.synchronize()
     barrier(world)
@@ -531,33 +630,65 @@ def run_grad(args, rank, world):
     s0 = sim.stats()
     t0 = time.perf_counter()
     results = []
-    for i in range(args.steps):
+    for i in range(steps):
         results.append(sim.grad(gates, thetas[i % len(thetas)], terms))
     torch.cuda.synchronize()
-    t_local = (time.perf_counter() - t0) / args.steps
+    t_local = (time.perf_counter() - t0) / steps
     clk = clocks.stop()
     barrier(world)
-    t_max, _ = reduce_max_sum(world, t_local, 1.0, device="cuda")
     st = sim.stats()
     launches = int(st["kernel_launches"] - s0["kernel_launches"])
+    adj_launches = int(st["jit_adjoint_launches"] - s0["jit_adjoint_launches"])
+    passes = (st["passes"] - s0["passes"]) / steps
     sim.close()
     errors = []
-    if not args.no_extras and rank == 0:
-        # FP64 reference: the uncompressed complex128 GPU adjoint (pinned to the oracle at small n)
+    if with_errors:
         ref = StateVector(n, mode="uncompressed", dtype="c128", device=dev)
-        for i in range(min(args.steps, len(thetas))):
+        for i in range(min(steps, len(thetas))):
             e_r, g_r = ref.grad(gates, thetas[i], terms)
             e, g = results[i]
-            errors.append({"set": i, "energy_err": abs(e - e_r), "grad_max_err": float(np.abs(g - g_r).max()),
+            errors.append({"set": i, "energy": e, "energy_err": abs(e - e_r),
+                           "grad_max_err": float(np.abs(g - g_r).max()),
                            "grad_rel_l2": float(np.linalg.norm(g - g_r) / max(np.linalg.norm(g_r), 1e-300))})
         ref.close()
+    return {"s_per_step": t_local, "steps": steps, "warmup": warmup, "params": npar, "gates": len(gates),
+            "parameter_sets": len(thetas), "launches_per_step": launches / steps,
+            "generated_adjoint_launches_per_step": adj_launches / steps, "passes_per_step": passes,
+            "clocks": clk, "errors_vs_fp64_gpu_adjoint": errors, "workload": describe(w, len(gates))}
+
+
+def run_grad(args, rank, world):
+    """Adjoint gradient seconds per step (the HEA workloads: n = 24 in HBM, n = 32 compressed)."""
+    import torch
+    w = args.w
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    m = grad_measure(w, args.steps, args.warmup, dev, world, with_errors=not args.no_extras and rank == 0)
+    t_max, _ = reduce_max_sum(world, m["s_per_step"], 1.0, device="cuda")
     return {"metric": "adjoint grad s/step", "value": t_max, "unit": "s/step", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
-            "config": {"workload": describe(w, len(gates)), "n_qubits": n, "params": npar, "gates": len(gates),
-                       "parameter_sets": len(thetas), "parallelism": f"replicas x{world}"},
-            "gpu_launches": launches, "clocks": clk, "passes_total": st["passes"],
-            "errors_vs_fp64_gpu_adjoint": errors}
+            "config": {"workload": m["workload"], "n_qubits": w["n"], "params": m["params"], "gates": m["gates"],
+                       "parameter_sets": m["parameter_sets"], "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(m["launches_per_step"] * args.steps), "clocks": m["clocks"],
+            "passes_per_step": m["passes_per_step"],
+            "generated_adjoint_launches_per_step": m["generated_adjoint_launches_per_step"],
+            "errors_vs_fp64_gpu_adjoint": m["errors_vs_fp64_gpu_adjoint"]}
+
+
+def adjoint_legs(dev):
+    """The metric's second part, adjoint gradient seconds per step, on the two
+    gradient workloads: n = 24 in HBM (480 parameters) and n = 32 on two
+    compressed stores (512 parameters; two of its 16 parameter sets)."""
+    out = {}
+    for name, steps, warmup, max_sets in (("grad-hea24", 5, 2, None), ("grad-hea32", 2, 1, 2)):
+        try:
+            m = grad_measure(WORKLOADS[name], steps, warmup, dev, max_sets=max_sets)
+            m.pop("clocks", None)
+            out[name] = m
+        except Exception as ex:  # noqa: BLE001 -- reported, not hidden
+            out[name] = {"error": str(ex)}
+    return out
 
 
 # ------------------------------------------------------------- Table 1
@@ -596,35 +727,30 @@ def run_table1(args):
 
 # ------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle as the reference arm, on the same config and metric."""
+    """The FP64 CPU oracle as the reference arm, on the same config and metric,
+    sampled as the cpu_baseline leg samples it (consecutive gates of the
+    workload on the full state), about 2 s of gates per step."""
     import oracle
     w = args.w
     n = w["n"]
     gates = make_circuit(w, seed=1) if w["circuit"] != "hea" else W.hea(n, w["layers"])[0]
-    psi = np.zeros(1 << n, dtype=np.complex128)
-    psi[W.basis_index(n)] = 1.0
-    per_step = 4  # gates per step: a bounded sample of the workload
-    times = []
-    g = 0
+    psi = oracle.basis_state(n, W.basis_index(n))
+    first, done, t, used = 0, 0, 0.0, oracle.num_threads()
     for i in range(args.warmup + args.steps):
-        sample = [gates[(g + j) % len(gates)] for j in range(per_step)]
-        g += per_step
-        th = None
-        t0 = time.perf_counter()
-        psi = oracle.apply_gates(n, psi, sample, th)
-        dt = time.perf_counter() - t0
+        psi, k, dt, used = oracle_sample(n, gates, psi, first, 2.0)
+        first += k
         if i >= args.warmup:
-            times.append(dt)
-    t = sum(times)
-    value = args.steps * per_step * (1 << n) / t
+            done += k
+            t += dt
+    value = done * (1 << n) / t
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
             "data": "synthetic",
             "config": {"workload": describe(w, len(gates)) + "; FP64 oracle on the host cores", "n_qubits": n},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{per_step} consecutive gates of the {len(gates)}-gate workload per step "
-                                       f"on the full 2^{n} complex128 state"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": used, "kind": "oracle",
+                             "sample": f"{done} consecutive gates of the {len(gates)}-gate workload over the timed "
+                                       f"steps (about 2 s each) on the full 2^{n} complex128 state"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -124,7 +124,9 @@ typedef struct sv_config {
                                      call leaves qubits on new positions, so repeating the same
                                      circuit runs (and, with jit, compiles) other kernels: best
                                      for one long circuit per call. */
-    uint64_t host_budget_bytes;   /* cap on pinned host memory, 0 = no cap */
+    uint64_t host_budget_bytes;   /* cap on the pinned host memory of the compressed chunk stores
+                                     (sv_stats_t.host_pinned_bytes), 0 = no cap; a call that needs
+                                     more fails with SV_ERR_HOST_OOM */
     double timeout_s;             /* limit of every host wait on GPU work (default 600) */
 } sv_config;
 
@@ -166,6 +168,11 @@ typedef struct sv_stats_t {
     /* launches of generated two-vector (psi, lambda) kernels by the reverse
        sweep of sv_grad (included in jit_launches) */
     uint64_t jit_adjoint_launches;
+    /* pinned host memory held by the compressed chunk stores (the state's and,
+       after a compressed sv_grad, lambda's): one slot per chunk, rewritten in
+       place while a chunk's new stream fits and moved to a slot with 1/8
+       headroom when it grows, plus slots released by such moves */
+    uint64_t host_pinned_bytes;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
@@ -238,6 +245,21 @@ int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out_interl
 
 /* Same as sv_amplitudes for the logical indices first .. first+count-1. */
 int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_interleaved);
+
+/*
+ * *out_re + i *out_im = <a|b> = sum_x conj(a_x) b_x over logical basis
+ * indices x, accumulated in FP64 on the GPU (the paper has no counterpart:
+ * it measures the error the lossy store introduces, as the fidelity
+ * |<ref|psi>|^2 / (||ref||^2 ||psi||^2) against a reference state).
+ *   a: any handle (compressed states are streamed from the host store and
+ *      decoded group by group, as sv_expect reads them; not modified).
+ *   b: an SV_UNCOMPRESSED handle with the same n on the same device (its
+ *      whole state is read in HBM). The two may differ in amplitude type and
+ *      in their logical-to-physical qubit maps.
+ * Errors: SV_ERR_ARG (b compressed, n or device differ, NULL pointers);
+ * SV_ERR_CORRUPT / SV_ERR_CUDA / SV_ERR_TIMEOUT as sv_expect.
+ */
+int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im);
 
 /*
  * Energy and gradient by the adjoint method (Jones & Gacon, arXiv

@@ -153,9 +153,12 @@ def basis_state(n: int, index: int) -> np.ndarray:
 
 
 def apply_gates(n: int, psi: np.ndarray, gates: Sequence,
-                theta: Optional[Sequence[float]] = None) -> np.ndarray:
-    """psi <- U_L ... U_1 psi in FP64 (in place on a complex128 copy)."""
-    out = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+                theta: Optional[Sequence[float]] = None, inplace: bool = False) -> np.ndarray:
+    """psi <- U_L ... U_1 psi in FP64, on a complex128 copy (or, with inplace,
+    on psi itself when it is already a contiguous complex128 array)."""
+    out = np.ascontiguousarray(psi, dtype=np.complex128)
+    if not (inplace and out is psi):
+        out = out.copy()
     th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
     ga = gates_to_c(gates)
     _check(lib().or_apply_gates(n, _ptr(out), C.addressof(ga), len(gates),

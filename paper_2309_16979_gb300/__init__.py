@@ -11,6 +11,7 @@ runs in the CUDA library libsvgb300.so; this module only marshals arguments.
     sv.apply(gates)
     e = sv.expect(terms)
     energy, grad = sv.grad(gates, theta, terms)          # adjoint gradient
+    ov = sv.inner(ref)                                   # <sv|ref>, ref uncompressed
 
 Also: codec_encode / codec_decode (one chunk on the device), copy_probe (the
 paper's host <-> device copy strategies), plan (with remap=True: the remapped
@@ -94,6 +95,13 @@ class StateVector:
         _check(load().sv_amplitudes_range(self._h, first, count, out.ctypes.data), "sv_amplitudes_range",
                self._h)
         return out.view(np.complex128)
+
+    def inner(self, other: "StateVector") -> complex:
+        """<self|other> in FP64 (sv_inner); other must be uncompressed, on the
+        same device, with the same number of qubits."""
+        re, im = C.c_double(0.0), C.c_double(0.0)
+        _check(load().sv_inner(self._h, other._h, C.byref(re), C.byref(im)), "sv_inner", self._h)
+        return complex(re.value, im.value)
 
     def state(self) -> np.ndarray:
         return self.amplitudes_range(0, 1 << self.n)

@@ -56,7 +56,8 @@ class SvStats(C.Structure):
                 ("t_jit_compile_s", C.c_double),
                 ("t_h2d_s", C.c_double), ("t_d2h_s", C.c_double), ("t_encode_finish_s", C.c_double),
                 ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double),
-                ("remap_swaps", C.c_uint64), ("jit_adjoint_launches", C.c_uint64)]
+                ("remap_swaps", C.c_uint64), ("jit_adjoint_launches", C.c_uint64),
+                ("host_pinned_bytes", C.c_uint64)]
 
 
 # every entry point declared in include/sv.h
@@ -64,7 +65,7 @@ EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "s
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
            "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile",
-           "sv_codec_encode_relative", "sv_copy_probe", "sv_plan_remap")
+           "sv_codec_encode_relative", "sv_copy_probe", "sv_plan_remap", "sv_inner")
 
 _lib = None
 
@@ -98,6 +99,8 @@ def load() -> C.CDLL:
     L.sv_amplitudes.restype = C.c_int
     L.sv_amplitudes_range.argtypes = [P, C.c_uint64, SZ, P]
     L.sv_amplitudes_range.restype = C.c_int
+    L.sv_inner.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.sv_inner.restype = C.c_int
     L.sv_grad.argtypes = [P, P, SZ, P, SZ, P, SZ, C.POINTER(C.c_double), P]
     L.sv_grad.restype = C.c_int
     L.sv_stats.argtypes = [P, C.POINTER(SvStats)]

@@ -142,10 +142,8 @@ void release(sv_state* s)
     cudaFree(s->d_ops);
     for (cudaEvent_t ev : s->prof_ev) cudaEventDestroy(ev);
     cudaFree(s->d_amps2);
-    arena_free(s->arena[0]);
-    arena_free(s->arena[1]);
-    arena_free(s->larena[0]);
-    arena_free(s->larena[1]);
+    pool_free(s->pool);
+    pool_free(s->lpool);
     if (s->s_comp) cudaStreamDestroy(s->s_comp);
     if (s->s_h2d) cudaStreamDestroy(s->s_h2d);
     if (s->s_d2h) cudaStreamDestroy(s->s_d2h);
@@ -232,9 +230,8 @@ int create_impl(sv_state* s)
     const uint64_t nchunks = 1ull << s->nh;
     s->carry_at.assign(nchunks, -1);
     s->cur.assign(nchunks, ChunkRef{});
-    s->nxt.assign(nchunks, ChunkRef{});
-    const size_t seg = std::max<size_t>((size_t)1 << 30, 4 * s->stride);
-    s->arena[0].seg_bytes = s->arena[1].seg_bytes = seg;
+    // pinned segments: an eighth of the raw state, at least four slot strides, at most 1 GiB
+    s->pool.seg_bytes = std::min<size_t>((size_t)1 << 30, std::max<size_t>(4 * s->stride, (amp_bytes << s->n) / 8));
     s->st.raw_bytes = amp_bytes << s->n;
     s->st.quant_step = std::ldexp(1.0, s->k);
     return init_state<R>(s);
@@ -387,6 +384,26 @@ int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
     s->err.clear();
     cudaSetDevice(s->cfg.device);
     return s->dtype == SV_C64 ? amplitudes<float>(s, idx, m, out) : amplitudes<double>(s, idx, m, out);
+}
+
+int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im)
+{
+    if (!a || !b || !out_re || !out_im) return SV_ERR_ARG;
+    a->err.clear();
+    if (b->mode != SV_UNCOMPRESSED) return fail(a, SV_ERR_ARG, "sv_inner: the second state must be uncompressed");
+    if (a->n != b->n) return fail(a, SV_ERR_ARG, "sv_inner: the states differ in qubit count");
+    if (a->cfg.device != b->cfg.device) return fail(a, SV_ERR_ARG, "sv_inner: the states are on different devices");
+    cudaSetDevice(a->cfg.device);
+    double out[2] = {0, 0};
+    int r;
+    if (a->dtype == SV_C64)
+        r = b->dtype == SV_C64 ? inner<float, float>(a, b, out) : inner<float, double>(a, b, out);
+    else
+        r = b->dtype == SV_C64 ? inner<double, float>(a, b, out) : inner<double, double>(a, b, out);
+    if (r) return r;
+    *out_re = out[0];
+    *out_im = out[1];
+    return SV_OK;
 }
 
 int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out)
@@ -580,6 +597,7 @@ int sv_stats(const sv_state* s, sv_stats_t* out)
 {
     if (!s || !out) return SV_ERR_ARG;
     *out = s->st;
+    out->host_pinned_bytes = s->pinned_bytes;
     return SV_OK;
 }
 

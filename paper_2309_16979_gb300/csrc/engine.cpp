@@ -9,11 +9,13 @@
 //   d2h  : compressed chunk streams device -> pinned host, issued one group
 //          later, once the sizes are on the host
 // so that while group i is computed, group i+1 is copied in and group i-1
-// copied out. Chunks written by a pass go to the second pinned arena; the
-// arenas swap at the end of the pass.
+// copied out. Every chunk keeps one pinned slot: a pass writes the chunk's
+// new stream over its old one (or into a larger slot when it grew), after
+// the group's copy of the old stream to the device has completed.
 // Uncompressed mode keeps the whole state in HBM and runs the sub-passes
 // over it directly.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -97,38 +99,64 @@ int check_device_error(sv_state* s)
 }
 
 // ------------------------------------------------------------------ store
-uint8_t* arena_alloc(sv_state* s, Arena& a, uint64_t bytes)
+// A slot of at least `need` bytes from the pool: a released slot when one
+// fits without wasting more than half of it, else carved from the last
+// segment, else from a new segment (of seg_bytes, or only `want` when the
+// host budget has no room for a whole one). nullptr when the budget or the
+// host is exhausted.
+static uint8_t* pool_alloc(sv_state* s, HostPool& pool, uint64_t need, uint64_t want, uint64_t& cap)
 {
-    const uint64_t need = (bytes + 255) & ~uint64_t(255);
-    while (true) {
-        if (a.si < a.segs.size()) {
-            Segment& g = a.segs[a.si];
-            if (a.off + need <= g.cap) {
-                uint8_t* p = g.ptr + a.off;
-                a.off += need;
-                return p;
-            }
-            a.si++;
-            a.off = 0;
-            continue;
-        }
-        const size_t cap = std::max<size_t>(a.seg_bytes, need);
-        if (s->cfg.host_budget_bytes && s->pinned_bytes + cap > s->cfg.host_budget_bytes) return nullptr;
+    auto it = pool.free_slots.lower_bound(need);
+    if (it != pool.free_slots.end() && it->first <= 2 * want) {
+        cap = it->first;
+        uint8_t* p = it->second;
+        pool.free_slots.erase(it);
+        return p;
+    }
+    if (pool.segs.empty() || pool.off + want > pool.segs.back().cap) {
+        if (!pool.segs.empty() && pool.segs.back().cap - pool.off >= 256)
+            pool.free_slots.emplace(pool.segs.back().cap - pool.off, pool.segs.back().ptr + pool.off);
+        size_t segb = std::max<size_t>(pool.seg_bytes, want);
+        const uint64_t budget = s->cfg.host_budget_bytes;
+        if (budget && s->pinned_bytes + segb > budget) segb = want;
+        if (budget && s->pinned_bytes + segb > budget) return nullptr;
         void* p = nullptr;
-        if (cudaHostAlloc(&p, cap, cudaHostAllocDefault) != cudaSuccess) {
+        if (cudaHostAlloc(&p, segb, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        s->pinned_bytes += cap;
-        a.segs.push_back({static_cast<uint8_t*>(p), cap});
+        s->pinned_bytes += segb;
+        pool.segs.push_back({static_cast<uint8_t*>(p), segb});
+        pool.off = 0;
     }
+    uint8_t* p = pool.segs.back().ptr + pool.off;
+    pool.off += want;
+    cap = want;
+    return p;
 }
 
-void arena_free(Arena& a)
+uint8_t* store_slot(sv_state* s, HostPool& pool, ChunkRef& ref, uint64_t bytes)
 {
-    for (auto& g : a.segs) cudaFreeHost(g.ptr);
-    a.segs.clear();
-    a.reset();
+    if (ref.ptr && bytes <= ref.cap) {
+        ref.bytes = bytes;
+        return ref.ptr;
+    }
+    const uint64_t need = (bytes + 255) & ~uint64_t(255);
+    const uint64_t want = (bytes + bytes / 8 + 255) & ~uint64_t(255);
+    uint64_t cap = 0;
+    uint8_t* p = pool_alloc(s, pool, need, want, cap);
+    if (!p) return nullptr;
+    if (ref.ptr) pool.free_slots.emplace(ref.cap, ref.ptr);
+    ref = {p, bytes, cap};
+    return p;
+}
+
+void pool_free(HostPool& pool)
+{
+    for (auto& g : pool.segs) cudaFreeHost(g.ptr);
+    pool.segs.clear();
+    pool.free_slots.clear();
+    pool.off = 0;
 }
 
 // ------------------------------------------------------------- profiling
@@ -442,7 +470,8 @@ static inline uint64_t deposit(uint64_t v, const std::vector<int>& pos)
 // Plan one pass for the device: its tile sub-passes, whether the codec
 // fuses into the first / last of them, and their device form.
 template <typename R>
-static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp, DevPass<R>& dp)
+static int prepare_pass_compressed(const sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp,
+                                   DevPass<R>& dp, std::string& err)
 {
     const int c = s->c, g = (int)pp.S.size();
     const int L = c + g;
@@ -450,7 +479,10 @@ static int prepare_pass_compressed(sv_state* s, const std::vector<PGate>& gates,
     tile_shape(L, s->tq, s->lq, t, l);
     const std::vector<HOp> hops = local_ops(gates, pp.gates, c, pp.S, false);
     std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
-    if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");
+    if (subs.empty() && !hops.empty()) {
+        err = "no tile plan for the pass";
+        return SV_ERR_ARG;
+    }
     // Fuse the decode into the first sub-pass when a plan whose first tile
     // holds whole block pairs (local bits 0..7) needs no extra sub-pass, and
     // the encode into the last sub-pass when its tile holds them.
@@ -482,7 +514,7 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
     struct PassInfo {
         std::vector<int> spos, fpos;  // chunk-index bit positions of staged and fixed high qubits
         uint64_t ngroups = 0, done = 0;
-        int g = 0, gch = 0, L = 0, arena = 0;
+        int g = 0, gch = 0, L = 0;
         double norm2 = 0;
     };
     std::vector<PassInfo> pinfo(passes.size());
@@ -497,7 +529,6 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
         P.gch = 1 << P.g;
         P.L = c + P.g;
         P.ngroups = 1ull << P.fpos.size();
-        P.arena = (s->cur_arena + 1 + (int)p) & 1;  // the arena pass p writes
         for (uint64_t gi = 0; gi < P.ngroups; gi++) items.push_back({(int)p, gi});
     }
     // renormalisation feeds a pass's norm into the next pass's decode: no
@@ -655,22 +686,18 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
         int rr = wait_event(s, s->ev_comp[slot]);
         if (rr) return rr;
         cudaError_t e;
-        Arena& out_arena = s->arena[P.arena];
-        // the arena this pass writes held the data of two passes before, whose
-        // copies to the device all precede this group's (stream order)
-        if (P.done == 0) out_arena.reset();
+        // the group's copies of its chunks' previous streams to the device are
+        // complete (the compute event waited on them): their slots can be rewritten
         const int pd2h = prof_begin(s, s->s_d2h);
         for (int j = 0; j < gch; j++) {
             const uint64_t k = slot_chunks[slot][j];
             const ChunkOut co = s->h_co[slot][j];
             if (co.bytes > s->stride) return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
-            uint8_t* dst = arena_alloc(s, out_arena, co.bytes);
+            uint8_t* dst = store_slot(s, s->pool, s->cur[k], co.bytes);
             if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
             if ((e = cudaMemcpyAsync(dst, s->d_out[slot] + (size_t)j * s->stride, co.bytes, cudaMemcpyDeviceToHost,
                                      s->s_d2h)))
                 return cuda_fail(s, e, "D2H chunk");
-            // the pass read chunk k's previous stream before writing it: update in place
-            s->cur[k] = {dst, co.bytes};
             s->st.bytes_d2h += co.bytes;
             if (slot_prof[slot] >= 0) s->prof_rec[slot_prof[slot]].bytes += co.bytes;
             P.norm2 += (double)co.sumsq * std::ldexp(1.0, 2 * co.k);
@@ -706,7 +733,6 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
     if (rs) return rs;
     prof_collect(s);
     if ((r = check_device_error(s))) return r;
-    if (!passes.empty()) s->cur_arena = pinfo.back().arena;
     uint64_t total = 0;
     for (const ChunkRef& cr : s->cur) total += cr.bytes;
     s->st.compressed_bytes = total;
@@ -717,8 +743,10 @@ template <typename R>
 int run_pass_compressed(sv_state* s, const std::vector<PGate>& gates, const PassPlan& pp)
 {
     std::vector<DevPass<R>> dps(1);
-    int r = prepare_pass_compressed<R>(s, gates, pp, dps[0]);
-    if (!r) r = jit_prepare<R>(s, {&dps[0]});
+    std::string err;
+    int r = prepare_pass_compressed<R>(s, gates, pp, dps[0], err);
+    if (r) return fail(s, r, err);
+    r = jit_prepare<R>(s, {&dps[0]});
     if (!r) r = stream_passes<R>(s, {pp}, dps);
     return r;
 }
@@ -771,10 +799,23 @@ int apply_circuit(sv_state* s, const std::vector<PGate>& input, bool remap)
     // plan every pass first, so that their kernels compile in one parallel batch
     std::vector<DevPass<R>> dps(passes.size());
     std::vector<DevPass<R>*> ptrs;
-    for (size_t i = 0; i < passes.size(); i++) {
-        int r = prepare_pass_compressed<R>(s, gates, passes[i], dps[i]);
-        if (r) return r;
-        ptrs.push_back(&dps[i]);
+    {
+        // passes are planned independently: one host thread each (bounded)
+        std::vector<int> codes(passes.size(), SV_OK);
+        std::vector<std::string> errs(passes.size());
+        std::atomic<size_t> next{0};
+        auto worker = [&]() {
+            for (size_t i; (i = next.fetch_add(1)) < passes.size();)
+                codes[i] = prepare_pass_compressed<R>(s, gates, passes[i], dps[i], errs[i]);
+        };
+        const size_t nth = std::min<size_t>(passes.size(), std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (size_t k = 1; k < nth; k++) pool.emplace_back(worker);
+        worker();
+        for (std::thread& th : pool) th.join();
+        for (size_t i = 0; i < passes.size(); i++)
+            if (codes[i]) return fail(s, codes[i], errs[i]);
+        for (size_t i = 0; i < passes.size(); i++) ptrs.push_back(&dps[i]);
     }
     int r = jit_prepare<R>(s, ptrs);
     if (r) return r;
@@ -848,8 +889,9 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
             plan_circuit(gates, s->n, s->c, s->gmax, s->cfg.remap_qubits != 0, rg, where);
         dps.resize(passes.size());
         for (size_t i = 0; i < passes.size(); i++) {
-            int r = prepare_pass_compressed<R>(s, rg, passes[i], dps[i]);
-            if (r) return r;
+            std::string err;
+            int r = prepare_pass_compressed<R>(s, rg, passes[i], dps[i], err);
+            if (r) return fail(s, r, err);
         }
     }
     for (DevPass<R>& dp : dps) {
@@ -907,16 +949,13 @@ int init_state(sv_state* s)
             return cuda_fail(s, e, "D2H init stream");
         s->st.bytes_d2h += streams[j].size();
     }
-    Arena& a = s->arena[s->cur_arena];
-    a.reset();
     const uint64_t init_chunk = init >> c;
     uint64_t total = 0;
     for (uint64_t k = 0; k < nchunks; k++) {
         const std::vector<uint8_t>& src = (nenc == 1 || k == init_chunk) ? streams[nenc - 1] : streams[0];
-        uint8_t* dst = arena_alloc(s, a, src.size());
+        uint8_t* dst = store_slot(s, s->pool, s->cur[k], src.size());
         if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
         std::memcpy(dst, src.data(), src.size());
-        s->cur[k] = {dst, src.size()};
         total += src.size();
     }
     s->st.compressed_bytes = total;
@@ -1030,6 +1069,60 @@ int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
     if (!r) r = check_device_error(s);
     cudaFree(d_loc);
     cudaFree(d_dst);
+    cudaFree(d_out);
+    return r;
+}
+
+// -------------------------------------------------------------- overlap
+// <a|b> in FP64 with b held whole in HBM: a's amplitudes are read where they
+// are (a's state in HBM, or its chunks staged and decoded group by group) and
+// paired with b's amplitude of the same logical index through the two
+// states' qubit maps.
+template <typename RA, typename RB>
+int inner(sv_state* a, const sv_state* b, double* out)
+{
+    IndexMap map;
+    map.n = a->n;
+    for (int q = 0; q < a->n; q++) {
+        map.pos[a->perm[q]] = (int8_t)b->perm[q];
+        if (a->perm[q] != b->perm[q]) map.identity = 0;
+    }
+    const uint64_t run = a->mode == SV_UNCOMPRESSED ? (1ull << a->n) : (1ull << (a->c + std::min(a->gmax, a->nh)));
+    const int nb = reduce_blocks_for(run);
+    double* d_part = nullptr;
+    double* d_out = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_part, sizeof(double) * 2 * nb)) || (e = cudaMalloc(&d_out, sizeof(double) * 2))) {
+        cudaFree(d_part);
+        cudaFree(d_out);
+        return cuda_fail(a, e, "cudaMalloc(inner)");
+    }
+    int r = SV_OK;
+    if ((e = cudaMemsetAsync(d_out, 0, sizeof(double) * 2, a->s_comp))) r = cuda_fail(a, e, "memset");
+    if (!r && a->mode == SV_UNCOMPRESSED) {
+        if ((e = launch_inner<RA, RB>(a->d_state, run, 0, b->d_state, map, d_part, nb, a->s_comp)) ||
+            (e = launch_sum_partials(d_part, 2, nb, d_out, a->s_comp)))
+            r = cuda_fail(a, e, "inner");
+        a->st.kernel_launches += 2;
+    } else if (!r) {
+        const uint64_t nch = 1ull << a->nh, gcap = 1ull << std::min(a->gmax, a->nh);
+        std::vector<uint64_t> ks;
+        for (uint64_t k0 = 0; k0 < nch && !r; k0 += gcap) {
+            ks.clear();
+            for (uint64_t k = k0; k < k0 + gcap; k++) ks.push_back(k);
+            if ((r = stage_chunks<RA>(a, ks))) break;
+            if ((e = launch_inner<RA, RB>(a->d_amps, gcap << a->c, k0 << a->c, b->d_state, map, d_part, nb,
+                                          a->s_comp)) ||
+                (e = launch_sum_partials(d_part, 2, nb, d_out, a->s_comp)))
+                r = cuda_fail(a, e, "inner");
+            a->st.kernel_launches += 2;
+        }
+    }
+    if (!r && (e = cudaMemcpyAsync(out, d_out, sizeof(double) * 2, cudaMemcpyDeviceToHost, a->s_comp)))
+        r = cuda_fail(a, e, "D2H inner");
+    if (!r) r = wait_stream(a, a->s_comp);
+    if (!r) r = check_device_error(a);
+    cudaFree(d_part);
     cudaFree(d_out);
     return r;
 }
@@ -1483,8 +1576,7 @@ static int ensure_lambda_store(sv_state* s)
     }
     const uint64_t nchunks = 1ull << s->nh;
     s->lcur.assign(nchunks, ChunkRef{});
-    s->lnxt.assign(nchunks, ChunkRef{});
-    s->larena[0].seg_bytes = s->larena[1].seg_bytes = s->arena[0].seg_bytes;
+    s->lpool.seg_bytes = s->pool.seg_bytes;
     return SV_OK;
 }
 
@@ -1509,8 +1601,6 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         return fail(s, SV_ERR_ARG, "more distinct high x-masks than chunks in a staging group (raise max_group_qubits)");
     const size_t m = X.size(), nt = phys.size();
     const int nset = 2 * m <= gcap ? 2 : 1;
-    Arena& la = s->larena[s->lcur_arena];
-    la.reset();
     const uint64_t nch = 1ull << s->nh;
     cudaError_t e;
     if (nt) {
@@ -1573,13 +1663,12 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         if (r) return r;
         const uint64_t bytes = s->h_co2[sl][0].bytes;
         if (bytes > s->stride) return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
-        uint8_t* dst = arena_alloc(s, la, bytes);
+        uint8_t* dst = store_slot(s, s->lpool, s->lcur[k], bytes);
         if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the lambda store failed");
         if ((e = cudaMemcpyAsync(dst, s->d_out2[sl], bytes, cudaMemcpyDeviceToHost, s->s_d2h)) ||
             (e = cudaEventRecord(s->ev_d2h[sl], s->s_d2h)))
             return cuda_fail(s, e, "D2H lambda chunk");
         s->st.bytes_d2h += bytes;
-        s->lcur[k] = {dst, bytes};
         return SV_OK;
     };
     int r = SV_OK;
@@ -1647,10 +1736,6 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
     const int gch = 1 << g;
     const int NS = s->nslots;
     std::vector<std::vector<uint64_t>> slot_chunks(NS);
-    Arena& pa = s->arena[1 - s->cur_arena];
-    Arena& la = s->larena[1 - s->lcur_arena];
-    pa.reset();
-    la.reset();
 
     auto issue = [&](uint64_t gi) -> int {
         const int slot = (int)(gi % NS);
@@ -1745,16 +1830,15 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
             const ChunkOut cp = s->h_co[slot][j], cl = s->h_co2[slot][j];
             if (cp.bytes > s->stride || cl.bytes > s->stride)
                 return fail(s, SV_ERR_CORRUPT, "encoded chunk larger than its slot");
-            uint8_t* dp = arena_alloc(s, pa, cp.bytes);
-            uint8_t* dl = arena_alloc(s, la, cl.bytes);
+            // both old streams reached the device before the group's compute event
+            uint8_t* dp = store_slot(s, s->pool, s->cur[k], cp.bytes);
+            uint8_t* dl = store_slot(s, s->lpool, s->lcur[k], cl.bytes);
             if (!dp || !dl) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
             if ((e = cudaMemcpyAsync(dp, s->d_out[slot] + (size_t)j * s->stride, cp.bytes, cudaMemcpyDeviceToHost,
                                      s->s_d2h)) ||
                 (e = cudaMemcpyAsync(dl, s->d_out2[slot] + (size_t)j * s->stride, cl.bytes, cudaMemcpyDeviceToHost,
                                      s->s_d2h)))
                 return cuda_fail(s, e, "D2H chunk");
-            s->nxt[k] = {dp, cp.bytes};
-            s->lnxt[k] = {dl, cl.bytes};
             s->st.bytes_d2h += cp.bytes + cl.bytes;
         }
         prof_end(s, pd2h, PROF_D2H, 0, s->s_d2h);
@@ -1768,10 +1852,6 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
     if ((r = sync_all(s))) return r;
     prof_collect(s);
     if ((r = check_device_error(s))) return r;
-    s->cur.swap(s->nxt);
-    s->lcur.swap(s->lnxt);
-    s->cur_arena = 1 - s->cur_arena;
-    s->lcur_arena = 1 - s->lcur_arena;
     s->st.passes++;
     return SV_OK;
 }
@@ -1859,6 +1939,10 @@ template int jit_sources<double>(sv_state*, const std::vector<PGate>&, std::vect
 template int init_state<float>(sv_state*);
 template int init_state<double>(sv_state*);
 template int amplitudes<float>(sv_state*, const uint64_t*, size_t, double*);
+template int inner<float, float>(sv_state*, const sv_state*, double*);
+template int inner<float, double>(sv_state*, const sv_state*, double*);
+template int inner<double, float>(sv_state*, const sv_state*, double*);
+template int inner<double, double>(sv_state*, const sv_state*, double*);
 template int amplitudes<double>(sv_state*, const uint64_t*, size_t, double*);
 template int expect<float>(sv_state*, const sv_pauli_term*, size_t, double*);
 template int expect<double>(sv_state*, const sv_pauli_term*, size_t, double*);

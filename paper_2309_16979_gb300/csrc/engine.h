@@ -13,7 +13,13 @@ int cuda_fail(sv_state* s, cudaError_t e, const char* where);
 int wait_stream(sv_state* s, cudaStream_t st);
 int sync_all(sv_state* s);
 int check_device_error(sv_state* s);
-void arena_free(Arena& a);
+// Destination of a chunk stream of `bytes` bytes: the chunk's own slot when
+// the stream fits (rewritten in place), else a larger slot with 1/8 headroom
+// (the old slot is released to the pool for reuse). ref is updated; nullptr
+// when pinned memory (or the host budget) is exhausted. Callers write the
+// slot only after every reader of the chunk's previous stream has finished.
+uint8_t* store_slot(sv_state* s, HostPool& pool, ChunkRef& ref, uint64_t bytes);
+void pool_free(HostPool& pool);
 void tile_shape(int L, int tq, int lq, int& t, int& l);
 
 template <typename R> int init_state(sv_state* s);
@@ -24,6 +30,8 @@ template <typename R> int apply_circuit(sv_state* s, const std::vector<PGate>& g
 template <typename R>
 int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::string>& out, bool adjoint);
 template <typename R> int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out);
+// out[0] + i out[1] = <a|b>; b uncompressed on a's device, same n
+template <typename RA, typename RB> int inner(sv_state* a, const sv_state* b, double* out);
 template <typename R> int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_re);
 template <typename R>
 int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,

@@ -9,6 +9,7 @@
 // mix, so they fit any pass. Inside a pass, the same greedy rule splits the
 // gates into tile sub-passes whose mixing qubits fit one on-chip tile.
 #include <algorithm>
+#include <future>
 #include <cmath>
 
 #include "runtime.h"
@@ -377,7 +378,33 @@ static int count_fit(const std::vector<HOp>& ops, const std::vector<int>& remain
     return n;
 }
 
-std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
+// Qubits worth adding to tile T: the mixing positions, outside T, of the
+// first kLookaheadOps remaining ops that T does not admit.
+constexpr int kLookaheadOps = 16;
+static uint64_t lookahead_candidates(const std::vector<HOp>& ops, const std::vector<int>& remaining, uint64_t T,
+                                     uint64_t allL)
+{
+    uint64_t cand = 0;
+    int seen = 0;
+    for (int oi : remaining) {
+        const uint64_t need = ops[oi].mixL & ~T & allL;
+        if (!need) continue;
+        cand |= need;
+        if (++seen >= kLookaheadOps) break;
+    }
+    return cand;
+}
+
+// One sub-pass plan. Tiles grow one qubit at a time:
+//  - lookahead = false: by the qubit that lets the sweep apply the most ops
+//    (pairs of qubits when no single one helps);
+//  - lookahead = true: by the candidate qubit whose best follow-up qubit
+//    admits the most ops (ties broken by the ops the qubit admits alone),
+//    which favours a qubit that is only useful together with another.
+// When no growth helps, the scan below grows the tile first-come in circuit
+// order.
+static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int L, int t, int l, bool fuse,
+                                                int first_l, bool lookahead)
 {
     std::vector<SubPlan> subs;
     const uint64_t low = (l >= 64) ? ~0ull : ((1ull << l) - 1);
@@ -388,10 +415,29 @@ std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, i
     for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
         uint64_t T = subs.empty() ? first_low : low, bL = 0, bG = 0;
-        // Grow the tile one qubit at a time by the qubit that lets the sweep
-        // apply the most ops; when no single qubit adds any (ops that need two
-        // new qubits), the scan below grows it first-come in circuit order.
         for (int cur = count_fit(ops, remaining, T, allL); popc(T) < t;) {
+            if (lookahead) {
+                const uint64_t cand = lookahead_candidates(ops, remaining, T, allL);
+                int best = -1, best2 = cur, best1 = cur;
+                for (int p = 0; p < L; p++) {
+                    if (!((cand >> p) & 1)) continue;
+                    const uint64_t Tp = T | (1ull << p);
+                    const int k1 = count_fit(ops, remaining, Tp, allL);
+                    int k2 = k1;
+                    if (popc(Tp) < t)
+                        for (int q = 0; q < L; q++)
+                            if (q != p && ((cand >> q) & 1)) k2 = std::max(k2, count_fit(ops, remaining, Tp | (1ull << q), allL));
+                    if (k2 > best2 || (k2 == best2 && k1 > best1)) {
+                        best = p;
+                        best2 = k2;
+                        best1 = k1;
+                    }
+                }
+                if (best < 0) break;
+                T |= 1ull << best;
+                cur = best1;
+                continue;
+            }
             int best = -1, bestn = cur;
             for (int p = 0; p < L; p++) {
                 if ((T >> p) & 1) continue;
@@ -457,6 +503,24 @@ std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, i
         remaining.swap(deferred);
     }
     return subs;
+}
+
+// Both growth rules (the lookahead on a second thread when the op list is
+// long enough to repay it); the plan with fewer sub-passes, the plain rule's
+// on a tie.
+std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
+{
+    if (ops.size() < 64) {
+        std::vector<SubPlan> a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false);
+        if (a.size() <= 1) return a;
+        std::vector<SubPlan> b = plan_subpasses_rule(ops, L, t, l, fuse, first_l, true);
+        return (!b.empty() && b.size() < a.size()) ? b : a;
+    }
+    std::future<std::vector<SubPlan>> fb =
+        std::async(std::launch::async, plan_subpasses_rule, std::cref(ops), L, t, l, fuse, first_l, true);
+    std::vector<SubPlan> a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false);
+    std::vector<SubPlan> b = fb.get();
+    return (!b.empty() && b.size() < a.size()) ? b : a;
 }
 
 bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bool keep_first)

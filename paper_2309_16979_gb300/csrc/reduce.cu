@@ -187,6 +187,38 @@ k_sum_partials(const double* __restrict__ partials, int nblocks, double* __restr
     if (threadIdx.x == 0) out[tt] += s;
 }
 
+// <A|B> over a contiguous run of A: each CTA owns one contiguous index range,
+// products in FP64, a fixed reduction tree (deterministic).
+template <typename RA, typename RB>
+__global__ void __launch_bounds__(kThreads)
+k_inner(const typename V2<RA>::T* __restrict__ A, uint64_t count, uint64_t base,
+        const typename V2<RB>::T* __restrict__ B, const IndexMap map, double* __restrict__ partials)
+{
+    __shared__ double red[kThreads / 32];
+    const uint64_t per = (count + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = (uint64_t)blockIdx.x * per, hi = min(count, lo + per);
+    double re = 0, im = 0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+        const uint64_t pa = base + i;
+        uint64_t pb = pa;
+        if (!map.identity) {
+            pb = 0;
+            for (int j = 0; j < map.n; j++) pb |= ((pa >> j) & 1ull) << map.pos[j];
+        }
+        const typename V2<RA>::T a = A[i];
+        const typename V2<RB>::T b = B[pb];
+        const double ar = (double)a.x, ai = (double)a.y, br = (double)b.x, bi = (double)b.y;
+        re += ar * br + ai * bi;
+        im += ar * bi - ai * br;
+    }
+    const double sr = block_sum(re, red);
+    const double si = block_sum(im, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sr;
+        partials[gridDim.x + blockIdx.x] = si;
+    }
+}
+
 template <typename R>
 __global__ void k_gather(const typename V2<R>::T* __restrict__ amps, const uint64_t* __restrict__ local_idx,
                          const uint64_t* __restrict__ dest, uint64_t m, double* __restrict__ out)
@@ -341,6 +373,25 @@ cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uin
     k_gather<R><<<blocks, 256, 0, st>>>(static_cast<const typename V2<R>::T*>(amps), local_idx, dest, m, out);
     return cudaGetLastError();
 }
+
+template <typename RA, typename RB>
+cudaError_t launch_inner(const void* A, uint64_t count, uint64_t base, const void* B, const IndexMap& map,
+                         double* partials, int nblocks, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    k_inner<RA, RB><<<nblocks, kThreads, 0, st>>>(static_cast<const typename V2<RA>::T*>(A), count, base,
+                                                  static_cast<const typename V2<RB>::T*>(B), map, partials);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_inner<float, float>(const void*, uint64_t, uint64_t, const void*, const IndexMap&,
+                                                double*, int, cudaStream_t);
+template cudaError_t launch_inner<float, double>(const void*, uint64_t, uint64_t, const void*, const IndexMap&,
+                                                 double*, int, cudaStream_t);
+template cudaError_t launch_inner<double, float>(const void*, uint64_t, uint64_t, const void*, const IndexMap&,
+                                                 double*, int, cudaStream_t);
+template cudaError_t launch_inner<double, double>(const void*, uint64_t, uint64_t, const void*, const IndexMap&,
+                                                  double*, int, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev* terms, int nterms,

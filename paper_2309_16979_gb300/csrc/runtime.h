@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdint>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "sv.h"
@@ -123,16 +124,21 @@ struct Segment {
     size_t cap = 0;
 };
 
-struct Arena {
+// Pinned host memory of a compressed chunk store: slots carved from large
+// segments, and slots released by chunks that moved to larger ones, kept by
+// capacity for reuse.
+struct HostPool {
     std::vector<Segment> segs;
-    size_t si = 0, off = 0;
-    size_t seg_bytes = 0;
-    void reset() { si = 0; off = 0; }
+    size_t off = 0;        // next free byte of segs.back()
+    size_t seg_bytes = 0;  // size of a new segment (a smaller one when the host budget is nearly spent)
+    std::multimap<size_t, uint8_t*> free_slots;
 };
 
+// One chunk's stream in the store: `bytes` long in a slot of `cap` bytes.
 struct ChunkRef {
     uint8_t* ptr = nullptr;
     uint64_t bytes = 0;
+    uint64_t cap = 0;
 };
 
 }  // namespace sv
@@ -149,9 +155,8 @@ struct sv_state {
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     // compressed store and staging
     size_t stride = 0;              // device slot stride per chunk stream
-    std::vector<sv::ChunkRef> cur, nxt;
-    sv::Arena arena[2];
-    int cur_arena = 0;
+    std::vector<sv::ChunkRef> cur;  // one slot per chunk, rewritten in place by each pass
+    sv::HostPool pool;
     uint64_t pinned_bytes = 0;
     uint8_t* d_in[4] = {};
     uint8_t* d_out[4] = {};
@@ -176,10 +181,9 @@ struct sv_state {
     void* d_state = nullptr;
     void* d_lam = nullptr;
     // compressed adjoint: lambda = H psi as a second compressed chunk store with
-    // its own arenas and staging (allocated at the first compressed sv_grad)
-    std::vector<sv::ChunkRef> lcur, lnxt;
-    sv::Arena larena[2];
-    int lcur_arena = 0;
+    // its own slots and staging (allocated at the first compressed sv_grad)
+    std::vector<sv::ChunkRef> lcur;  // the lambda store of sv_grad, one slot per chunk
+    sv::HostPool lpool;
     uint8_t* d_in2[4] = {};
     uint8_t* d_out2[4] = {};
     sv::ChunkOut* d_co2[4] = {};

@@ -200,4 +200,19 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
 
 int reduce_blocks_for(uint64_t count);
 
+// Where the amplitudes of one state sit in another: physical index bit j of
+// the first is bit pos[j] of the second (identity: the same index).
+struct IndexMap {
+    int32_t n = 0;
+    int32_t identity = 1;
+    int8_t pos[64] = {};
+};
+
+// partials[0 * nblocks + b], partials[1 * nblocks + b] = Re, Im of CTA b's
+// share of sum_i conj(A[i]) * B[map(base + i)], i < count, in FP64; A and B
+// may differ in precision (RA, RB).
+template <typename RA, typename RB>
+cudaError_t launch_inner(const void* A, uint64_t count, uint64_t base, const void* B, const IndexMap& map,
+                         double* partials, int nblocks, cudaStream_t st);
+
 }  // namespace sv

@@ -60,3 +60,33 @@ def test_host_wait_deadline_then_destroy_and_recover(mod):
         s.close()
     assert code == SV_ERR_TIMEOUT
     _fresh_handle_works(mod)
+
+
+def test_store_holds_one_copy_of_the_state(mod):
+    """The pinned store keeps one slot per chunk, rewritten in place: after a
+    circuit that spreads the state, pinned memory is about the compressed
+    size (1/8 headroom per slot, released slots, segment granularity), and a
+    budget of 1.3x that runs the same circuit to the same state. A budget
+    below the compressed size fails in the pass that outgrows it, with
+    SV_ERR_HOST_OOM."""
+    n, c, eb = 20, 12, 1e-6
+    gates = W.random_layers(n, 6)
+    kw = dict(max_group_qubits=3, init_index=5)
+    with mod.StateVector(n, c, eb, **kw) as s:
+        s.apply(gates)
+        st = s.stats()
+        ref = s.state()
+    comp, pinned = st["compressed_bytes"], st["host_pinned_bytes"]
+    seg = max(4 * mod.codec_max_bytes(c), (8 << n) // 8)
+    assert comp > 4096 * (1 << (n - c))  # the state has spread (a basis state: ~340 bytes per chunk)
+    assert pinned <= 1.3 * comp + 2 * seg
+    budget = int(1.3 * comp) + 2 * seg
+    with mod.StateVector(n, c, eb, host_budget_bytes=budget, **kw) as s:
+        s.apply(gates)
+        assert s.stats()["host_pinned_bytes"] <= budget
+        assert np.array_equal(s.state(), ref)
+    with mod.StateVector(n, c, eb, host_budget_bytes=comp // 3, **kw) as s:
+        with pytest.raises(mod.SvError) as ei:
+            s.apply(gates)
+        assert ei.value.code == SV_ERR_HOST_OOM
+    _fresh_handle_works(mod)
