@@ -170,7 +170,7 @@ typedef struct sv_stats_t {
     uint64_t jit_adjoint_launches;
     /* pinned host memory held by the compressed chunk stores (the state's and,
        after a compressed sv_grad, lambda's): one slot per chunk, rewritten in
-       place while a chunk's new stream fits and moved to a slot with 1/8
+       place while a chunk's new stream fits and moved to a slot with 1/32
        headroom when it grows, plus slots released by such moves */
     uint64_t host_pinned_bytes;
 } sv_stats_t;

@@ -230,8 +230,8 @@ int create_impl(sv_state* s)
     const uint64_t nchunks = 1ull << s->nh;
     s->carry_at.assign(nchunks, -1);
     s->cur.assign(nchunks, ChunkRef{});
-    // pinned segments: an eighth of the raw state, at least four slot strides, at most 1 GiB
-    s->pool.seg_bytes = std::min<size_t>((size_t)1 << 30, std::max<size_t>(4 * s->stride, (amp_bytes << s->n) / 8));
+    // pinned segments: an eighth of the raw state, at least four slot strides, at most 4 GiB
+    s->pool.seg_bytes = std::min<size_t>((size_t)4 << 30, std::max<size_t>(4 * s->stride, (amp_bytes << s->n) / 8));
     s->st.raw_bytes = amp_bytes << s->n;
     s->st.quant_step = std::ldexp(1.0, s->k);
     return init_state<R>(s);

@@ -99,23 +99,64 @@ int check_device_error(sv_state* s)
 }
 
 // ------------------------------------------------------------------ store
-// A slot of at least `need` bytes from the pool: a released slot when one
-// fits without wasting more than half of it, else carved from the last
-// segment, else from a new segment (of seg_bytes, or only `want` when the
+static void pool_remove(HostPool& pool, std::map<uint8_t*, std::pair<size_t, int>>::iterator it)
+{
+    auto range = pool.free_by_size.equal_range(it->second.first);
+    for (auto jt = range.first; jt != range.second; ++jt)
+        if (jt->second == it->first) {
+            pool.free_by_size.erase(jt);
+            break;
+        }
+    pool.free_at.erase(it);
+}
+
+static void pool_insert(HostPool& pool, uint8_t* p, size_t bytes, int seg)
+{
+    pool.free_at[p] = {bytes, seg};
+    pool.free_by_size.emplace(bytes, p);
+}
+
+// Return [p, p + bytes) of segment `seg` to the pool, merged with the free
+// blocks that touch it in the same segment.
+static void pool_release(HostPool& pool, uint8_t* p, size_t bytes, int seg)
+{
+    auto next = pool.free_at.lower_bound(p);
+    if (next != pool.free_at.end() && next->first == p + bytes && next->second.second == seg) {
+        bytes += next->second.first;
+        pool_remove(pool, next);
+    }
+    auto it = pool.free_at.lower_bound(p);
+    if (it != pool.free_at.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second.first == p && prev->second.second == seg) {
+            p = prev->first;
+            bytes += prev->second.first;
+            pool_remove(pool, prev);
+        }
+    }
+    pool_insert(pool, p, bytes, seg);
+}
+
+static int pool_segment_of(const HostPool& pool, const uint8_t* p)
+{
+    for (size_t i = 0; i < pool.segs.size(); i++)
+        if (p >= pool.segs[i].ptr && p < pool.segs[i].ptr + pool.segs[i].cap) return (int)i;
+    return -1;
+}
+
+// A slot of `want` bytes (or of at least `need` when only a smaller free
+// block is left): best fit among the free blocks, split when the rest is
+// worth keeping, else from a new segment of seg_bytes (only `want` when the
 // host budget has no room for a whole one). nullptr when the budget or the
 // host is exhausted.
 static uint8_t* pool_alloc(sv_state* s, HostPool& pool, uint64_t need, uint64_t want, uint64_t& cap)
 {
-    auto it = pool.free_slots.lower_bound(need);
-    if (it != pool.free_slots.end() && it->first <= 2 * want) {
-        cap = it->first;
-        uint8_t* p = it->second;
-        pool.free_slots.erase(it);
-        return p;
+    auto it = pool.free_by_size.lower_bound(want);
+    if (it == pool.free_by_size.end()) {
+        it = pool.free_by_size.lower_bound(need);
+        if (it != pool.free_by_size.end()) want = it->first;  // a block between need and want: all of it
     }
-    if (pool.segs.empty() || pool.off + want > pool.segs.back().cap) {
-        if (!pool.segs.empty() && pool.segs.back().cap - pool.off >= 256)
-            pool.free_slots.emplace(pool.segs.back().cap - pool.off, pool.segs.back().ptr + pool.off);
+    if (it == pool.free_by_size.end()) {
         size_t segb = std::max<size_t>(pool.seg_bytes, want);
         const uint64_t budget = s->cfg.host_budget_bytes;
         if (budget && s->pinned_bytes + segb > budget) segb = want;
@@ -127,11 +168,20 @@ static uint8_t* pool_alloc(sv_state* s, HostPool& pool, uint64_t need, uint64_t 
         }
         s->pinned_bytes += segb;
         pool.segs.push_back({static_cast<uint8_t*>(p), segb});
-        pool.off = 0;
+        pool_insert(pool, static_cast<uint8_t*>(p), segb, (int)pool.segs.size() - 1);
+        it = pool.free_by_size.lower_bound(want);
     }
-    uint8_t* p = pool.segs.back().ptr + pool.off;
-    pool.off += want;
-    cap = want;
+    uint8_t* p = it->second;
+    auto at = pool.free_at.find(p);
+    const size_t have = at->second.first;
+    const int seg = at->second.second;
+    pool_remove(pool, at);
+    if (have - want >= 4096) {
+        pool_insert(pool, p + want, have - want, seg);
+        cap = want;
+    } else {
+        cap = have;
+    }
     return p;
 }
 
@@ -142,21 +192,38 @@ uint8_t* store_slot(sv_state* s, HostPool& pool, ChunkRef& ref, uint64_t bytes)
         return ref.ptr;
     }
     const uint64_t need = (bytes + 255) & ~uint64_t(255);
-    const uint64_t want = (bytes + bytes / 8 + 255) & ~uint64_t(255);
+    const uint64_t want = (bytes + bytes / 32 + 255) & ~uint64_t(255);
+    // Release the old slot first, so that it can merge into the block the new
+    // one comes from: its stream has reached the device already, and a copy
+    // still writing it (an earlier pass's, on the device-to-host stream)
+    // precedes every later write into the region on that stream. A slot of
+    // capacity 0 is the shared one and stays.
+    if (ref.ptr && ref.cap) pool_release(pool, ref.ptr, ref.cap, pool_segment_of(pool, ref.ptr));
     uint64_t cap = 0;
     uint8_t* p = pool_alloc(s, pool, need, want, cap);
-    if (!p) return nullptr;
-    if (ref.ptr) pool.free_slots.emplace(ref.cap, ref.ptr);
-    ref = {p, bytes, cap};
+    ref = p ? ChunkRef{p, bytes, cap} : ChunkRef{};
     return p;
+}
+
+void store_release_all(HostPool& pool, std::vector<ChunkRef>& refs)
+{
+    for (ChunkRef& r : refs) {
+        if (r.ptr && r.cap) pool_release(pool, r.ptr, r.cap, pool_segment_of(pool, r.ptr));
+        r = ChunkRef{};
+    }
+    if (pool.shared) pool_release(pool, pool.shared, pool.shared_cap, pool_segment_of(pool, pool.shared));
+    pool.shared = nullptr;
+    pool.shared_cap = 0;
 }
 
 void pool_free(HostPool& pool)
 {
     for (auto& g : pool.segs) cudaFreeHost(g.ptr);
     pool.segs.clear();
-    pool.free_slots.clear();
-    pool.off = 0;
+    pool.free_at.clear();
+    pool.free_by_size.clear();
+    pool.shared = nullptr;
+    pool.shared_cap = 0;
 }
 
 // ------------------------------------------------------------- profiling
@@ -949,14 +1016,31 @@ int init_state(sv_state* s)
             return cuda_fail(s, e, "D2H init stream");
         s->st.bytes_d2h += streams[j].size();
     }
+    // every chunk but the basis amplitude's holds the same all-zero stream:
+    // one shared slot (capacity 0, so the first pass that writes a chunk
+    // gives it a slot of its own); earlier slots return to the pool
     const uint64_t init_chunk = init >> c;
+    store_release_all(s->pool, s->cur);
     uint64_t total = 0;
-    for (uint64_t k = 0; k < nchunks; k++) {
-        const std::vector<uint8_t>& src = (nenc == 1 || k == init_chunk) ? streams[nenc - 1] : streams[0];
-        uint8_t* dst = store_slot(s, s->pool, s->cur[k], src.size());
+    ChunkRef zero{};
+    if (nenc == 2) {
+        uint8_t* dst = store_slot(s, s->pool, zero, streams[0].size());
         if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
-        std::memcpy(dst, src.data(), src.size());
-        total += src.size();
+        std::memcpy(dst, streams[0].data(), streams[0].size());
+        s->pool.shared = zero.ptr;
+        s->pool.shared_cap = zero.cap;
+        zero.cap = 0;
+    }
+    for (uint64_t k = 0; k < nchunks; k++) {
+        if (nenc == 2 && k != init_chunk) {
+            s->cur[k] = zero;
+        } else {
+            const std::vector<uint8_t>& src = streams[nenc - 1];
+            uint8_t* dst = store_slot(s, s->pool, s->cur[k], src.size());
+            if (!dst) return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
+            std::memcpy(dst, src.data(), src.size());
+        }
+        total += s->cur[k].bytes;
     }
     s->st.compressed_bytes = total;
     s->st.norm2 = 1.0;

@@ -14,11 +14,13 @@ int wait_stream(sv_state* s, cudaStream_t st);
 int sync_all(sv_state* s);
 int check_device_error(sv_state* s);
 // Destination of a chunk stream of `bytes` bytes: the chunk's own slot when
-// the stream fits (rewritten in place), else a larger slot with 1/8 headroom
+// the stream fits (rewritten in place), else a larger slot with 1/32 headroom
 // (the old slot is released to the pool for reuse). ref is updated; nullptr
 // when pinned memory (or the host budget) is exhausted. Callers write the
 // slot only after every reader of the chunk's previous stream has finished.
 uint8_t* store_slot(sv_state* s, HostPool& pool, ChunkRef& ref, uint64_t bytes);
+// Return every chunk's slot to the pool (no copy may still read or write them).
+void store_release_all(HostPool& pool, std::vector<ChunkRef>& refs);
 void pool_free(HostPool& pool);
 void tile_shape(int L, int tq, int lq, int& t, int& l);
 

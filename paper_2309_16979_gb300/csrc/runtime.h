@@ -124,14 +124,16 @@ struct Segment {
     size_t cap = 0;
 };
 
-// Pinned host memory of a compressed chunk store: slots carved from large
-// segments, and slots released by chunks that moved to larger ones, kept by
-// capacity for reuse.
+// Pinned host memory of a compressed chunk store: slots carved best-fit from
+// large pinned segments; a released slot merges with free neighbours of the
+// same segment (a slot never spans two pinned allocations).
 struct HostPool {
     std::vector<Segment> segs;
-    size_t off = 0;        // next free byte of segs.back()
     size_t seg_bytes = 0;  // size of a new segment (a smaller one when the host budget is nearly spent)
-    std::multimap<size_t, uint8_t*> free_slots;
+    std::map<uint8_t*, std::pair<size_t, int>> free_at;  // free block -> (bytes, segment)
+    std::multimap<size_t, uint8_t*> free_by_size;
+    uint8_t* shared = nullptr;  // the slot chunks share while they hold the same stream (read only)
+    size_t shared_cap = 0;
 };
 
 // One chunk's stream in the store: `bytes` long in a slot of `cap` bytes.

@@ -34,8 +34,10 @@ def _fresh_handle_works(mod):
 
 
 def test_host_budget_too_small_for_the_store(mod):
+    # a basis state needs two slots (the shared all-zero chunk stream and the
+    # basis amplitude's chunk), a few hundred bytes: 64 bytes cannot hold it
     with pytest.raises(mod.SvError) as ei:
-        mod.StateVector(16, 10, 1e-6, host_budget_bytes=4096)
+        mod.StateVector(16, 10, 1e-6, host_budget_bytes=64)
     assert ei.value.code == SV_ERR_HOST_OOM
     _fresh_handle_works(mod)
 
@@ -65,7 +67,7 @@ def test_host_wait_deadline_then_destroy_and_recover(mod):
 def test_store_holds_one_copy_of_the_state(mod):
     """The pinned store keeps one slot per chunk, rewritten in place: after a
     circuit that spreads the state, pinned memory is about the compressed
-    size (1/8 headroom per slot, released slots, segment granularity), and a
+    size (1/32 headroom per slot, released slots, segment granularity), and a
     budget of 1.3x that runs the same circuit to the same state. A budget
     below the compressed size fails in the pass that outgrows it, with
     SV_ERR_HOST_OOM."""
