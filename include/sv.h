@@ -84,6 +84,18 @@ typedef struct sv_pauli_term {
     uint64_t zmask;
 } sv_pauli_term;
 
+/*
+ * Device memory provider for a handle (sv_config.device_alloc / device_free):
+ * alloc returns `bytes` of device memory on `device` (NULL on failure, which
+ * the calling entry point reports as SV_ERR_DEVICE_OOM); free returns memory
+ * that alloc gave. Both are called on the thread that called the library,
+ * with `ctx` = sv_config.alloc_ctx. The library frees a block only after all
+ * of its own GPU work that uses the block has completed, so a caching
+ * allocator may hand the block out again at once.
+ */
+typedef void* (*sv_device_alloc_fn)(size_t bytes, int device, void* ctx);
+typedef void (*sv_device_free_fn)(void* ptr, int device, void* ctx);
+
 typedef struct sv_config {
     int32_t dtype;                /* SV_C64 (default) or SV_C128 */
     int32_t mode;                 /* SV_COMPRESSED (default) or SV_UNCOMPRESSED */
@@ -124,6 +136,15 @@ typedef struct sv_config {
                                      call leaves qubits on new positions, so repeating the same
                                      circuit runs (and, with jit, compiles) other kernels: best
                                      for one long circuit per call. */
+    sv_device_alloc_fn device_alloc; /* NULL (default): cudaMalloc / cudaFree. Otherwise every device
+                                     allocation of the handle (state, staging, per-call scratch)
+                                     goes through device_alloc / device_free (both must be set) */
+    sv_device_free_fn device_free;
+    void* alloc_ctx;              /* passed to device_alloc / device_free */
+    void* stream;                 /* cudaStream_t of the caller, or NULL. When set, every call on the
+                                     handle first waits (on the GPU) for the work the caller queued
+                                     on it before the call, and the caller's stream then waits for
+                                     the call's GPU work; the library's own streams do the work */
     uint64_t host_budget_bytes;   /* cap on the pinned host memory of the compressed chunk stores
                                      (sv_stats_t.host_pinned_bytes), 0 = no cap; a call that needs
                                      more fails with SV_ERR_HOST_OOM */
@@ -245,6 +266,22 @@ int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out_interl
 
 /* Same as sv_amplitudes for the logical indices first .. first+count-1. */
 int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out_interleaved);
+
+/*
+ * The device memory of an SV_UNCOMPRESSED state, for reading on the GPU
+ * between calls (the paper has no counterpart: it lets a caller use the
+ * state in its own kernels without a copy, e.g. as a torch tensor).
+ *   d_amps:    receives the address of 2^n interleaved complex amplitudes
+ *              (complex64 or complex128 as sv_config.dtype); amplitude i is
+ *              at physical index i.
+ *   positions: host, NULL or n entries: the physical bit position of every
+ *              logical qubit (SWAPs relabel qubits, so logical index x is at
+ *              the physical index with bit positions[q] = bit q of x).
+ * The memory stays owned by the handle and valid until the next call that
+ * applies gates or sv_destroy; writing it is undefined.
+ * Errors: SV_ERR_ARG for compressed handles or NULL arguments.
+ */
+int sv_device_state(sv_state* s, void** d_amps, int32_t* positions);
 
 /*
  * *out_re + i *out_im = <a|b> = sum_x conj(a_x) b_x over logical basis

@@ -46,7 +46,13 @@ class StateVector:
                  tile_qubits: int = 0, pipeline_slots: int = 3, renormalize: bool = False,
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,
-                 jit: bool = True, relative_bound: bool = False, remap_qubits: bool = False):
+                 jit: bool = True, relative_bound: bool = False, remap_qubits: bool = False,
+                 memory: str = "torch"):
+        """memory="torch": the handle's device memory comes from torch's
+        caching allocator (it shows in torch.cuda.memory_allocated()) and its
+        calls order after the work queued on torch's current stream of the
+        device at creation; memory="cuda": the library allocates with
+        cudaMalloc and orders against no caller stream."""
         L = load()
         cfg = _abi.SvConfig()
         L.sv_config_default(C.byref(cfg))
@@ -65,10 +71,16 @@ class StateVector:
         cfg.jit = int(jit)
         cfg.relative_bound = int(relative_bound)
         cfg.remap_qubits = int(remap_qubits)
+        self._callbacks = None
+        if memory == "torch":
+            self._callbacks = _torch_memory(cfg, device)
+        elif memory != "cuda":
+            raise ValueError("memory must be 'torch' or 'cuda'")
         h = C.c_void_p()
         _check(L.sv_create(n, chunk_qubits or n, eb, C.byref(cfg), C.byref(h)), "sv_create", None)
         self._h = h
         self.n = n
+        self.device = device
         self.dtype = dtype
         self.mode = mode
 
@@ -102,6 +114,26 @@ class StateVector:
         re, im = C.c_double(0.0), C.c_double(0.0)
         _check(load().sv_inner(self._h, other._h, C.byref(re), C.byref(im)), "sv_inner", self._h)
         return complex(re.value, im.value)
+
+    def device_tensor(self):
+        """Zero-copy torch view (complex64 / complex128, on the handle's GPU)
+        of an uncompressed state, valid until the next call that applies
+        gates and to be read only (torch has no read-only tensors: writing it
+        is undefined), and the physical bit position of every logical qubit
+        (sv_device_state): logical index x sits at the physical index whose
+        bit positions[q] is bit q of x."""
+        import torch
+        ptr = C.c_void_p()
+        pos = np.zeros(self.n, dtype=np.int32)
+        _check(load().sv_device_state(self._h, C.byref(ptr), pos.ctypes.data), "sv_device_state", self._h)
+        real = "<f4" if self.dtype == "c64" else "<f8"
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (2 << self.n,), "typestr": real, "data": (ptr.value, False),
+                                        "version": 3, "strides": None}
+
+        flat = torch.as_tensor(_View(), device=f"cuda:{self.device}")
+        return flat.view(torch.complex64 if self.dtype == "c64" else torch.complex128), pos.tolist()
 
     def state(self) -> np.ndarray:
         return self.amplitudes_range(0, 1 << self.n)
@@ -150,6 +182,37 @@ class StateVector:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _torch_memory(cfg, device: int):
+    """Fill cfg's allocator and stream from torch: the caching allocator on
+    `device`, torch's current stream there. Returns the ctypes callbacks,
+    which must live as long as the handle. Without CUDA in torch the library
+    keeps its own allocator (sv_create then reports the missing device)."""
+    try:
+        import torch
+    except ImportError:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    stream = torch.cuda.current_stream(device)
+
+    def alloc(nbytes, dev, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream)
+        except Exception:  # noqa: BLE001 -- reported by the library as SV_ERR_DEVICE_OOM
+            return None
+
+    def free(ptr, dev, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:  # noqa: BLE001 -- torch already torn down at interpreter exit
+            pass
+
+    cbs = (_abi.DEVICE_ALLOC_FN(alloc), _abi.DEVICE_FREE_FN(free))
+    cfg.device_alloc, cfg.device_free = cbs
+    cfg.stream = stream.cuda_stream
+    return cbs
 
 
 def plan(n: int, chunk_qubits: int, gates: Sequence, max_group_qubits: int = 4, tile_qubits: int = 0,

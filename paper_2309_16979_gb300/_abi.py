@@ -33,12 +33,18 @@ class SvPauliTerm(C.Structure):
     _fields_ = [("coeff", C.c_double), ("xmask", C.c_uint64), ("zmask", C.c_uint64)]
 
 
+DEVICE_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p)
+DEVICE_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p)
+
+
 class SvConfig(C.Structure):
     _fields_ = [("dtype", C.c_int32), ("mode", C.c_int32), ("init_index", C.c_uint64),
                 ("max_group_qubits", C.c_int32), ("tile_qubits", C.c_int32),
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
                 ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("jit", C.c_int32),
-                ("relative_bound", C.c_int32), ("remap_qubits", C.c_int32), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
+                ("relative_bound", C.c_int32), ("remap_qubits", C.c_int32),
+                ("device_alloc", DEVICE_ALLOC_FN), ("device_free", DEVICE_FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("stream", C.c_void_p), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 
 class SvStats(C.Structure):
@@ -65,7 +71,8 @@ EXPORTS = ("sv_config_default", "sv_create", "sv_apply_circuit", "sv_expect", "s
            "sv_amplitudes_range", "sv_grad", "sv_stats", "sv_last_error", "sv_destroy",
            "sv_codec_max_bytes", "sv_codec_encode", "sv_codec_decode", "sv_plan",
            "sv_codec_encode_noalloc", "sv_chunk_stream", "sv_jit_sources", "sv_set_profile",
-           "sv_codec_encode_relative", "sv_copy_probe", "sv_plan_remap", "sv_inner")
+           "sv_codec_encode_relative", "sv_copy_probe", "sv_plan_remap", "sv_inner",
+           "sv_device_state")
 
 _lib = None
 
@@ -101,6 +108,8 @@ def load() -> C.CDLL:
     L.sv_amplitudes_range.restype = C.c_int
     L.sv_inner.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.sv_inner.restype = C.c_int
+    L.sv_device_state.argtypes = [P, C.POINTER(C.c_void_p), P]
+    L.sv_device_state.restype = C.c_int
     L.sv_grad.argtypes = [P, P, SZ, P, SZ, P, SZ, C.POINTER(C.c_double), P]
     L.sv_grad.restype = C.c_int
     L.sv_stats.argtypes = [P, C.POINTER(SvStats)]

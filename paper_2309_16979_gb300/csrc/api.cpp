@@ -109,39 +109,68 @@ int lower(sv_state* s, const sv_gate* gates, size_t ngates, const double* theta,
     return SV_OK;
 }
 
+// A handle call's GPU work starts after the work the caller queued on its
+// stream before the call, and the caller's stream waits for the call's work.
+struct CallOrder {
+    sv_state* s;
+    explicit CallOrder(sv_state* st) : s(st)
+    {
+        if (!s || !s->cfg.stream || !s->ev_user) return;
+        cudaStream_t u = static_cast<cudaStream_t>(s->cfg.stream);
+        if (cudaEventRecord(s->ev_user, u) == cudaSuccess) {
+            cudaStreamWaitEvent(s->s_comp, s->ev_user, 0);
+            cudaStreamWaitEvent(s->s_h2d, s->ev_user, 0);
+            cudaStreamWaitEvent(s->s_d2h, s->ev_user, 0);
+        }
+        cudaGetLastError();
+    }
+    ~CallOrder()
+    {
+        if (!s || !s->cfg.stream || !s->ev_done) return;
+        cudaStream_t u = static_cast<cudaStream_t>(s->cfg.stream);
+        // every stream's work joins the compute stream, then the caller's waits on it
+        for (cudaStream_t o : {s->s_h2d, s->s_d2h})
+            if (cudaEventRecord(s->ev_user, o) == cudaSuccess) cudaStreamWaitEvent(s->s_comp, s->ev_user, 0);
+        if (cudaEventRecord(s->ev_done, s->s_comp) == cudaSuccess) cudaStreamWaitEvent(u, s->ev_done, 0);
+        cudaGetLastError();
+    }
+};
+
 void release(sv_state* s)
 {
     if (!s) return;
     if (s->s_comp) cudaStreamSynchronize(s->s_comp);
     if (s->s_h2d) cudaStreamSynchronize(s->s_h2d);
     if (s->s_d2h) cudaStreamSynchronize(s->s_d2h);
+    if (s->ev_user) cudaEventDestroy(s->ev_user);
+    if (s->ev_done) cudaEventDestroy(s->ev_done);
     for (int i = 0; i < 4; i++) {
-        cudaFree(s->d_in[i]);
-        cudaFree(s->d_out[i]);
-        cudaFree(s->d_co[i]);
+        dev_free(s, s->d_in[i]);
+        dev_free(s, s->d_out[i]);
+        dev_free(s, s->d_co[i]);
         if (s->h_co[i]) cudaFreeHost(s->h_co[i]);
-        cudaFree(s->d_in2[i]);
-        cudaFree(s->d_out2[i]);
-        cudaFree(s->d_co2[i]);
+        dev_free(s, s->d_in2[i]);
+        dev_free(s, s->d_out2[i]);
+        dev_free(s, s->d_co2[i]);
         if (s->h_co2[i]) cudaFreeHost(s->h_co2[i]);
         if (s->ev_h2d[i]) cudaEventDestroy(s->ev_h2d[i]);
         if (s->ev_comp[i]) cudaEventDestroy(s->ev_comp[i]);
         if (s->ev_d2h[i]) cudaEventDestroy(s->ev_d2h[i]);
     }
-    cudaFree(s->d_carry);
-    cudaFree(s->d_carry_bytes);
-    cudaFree(s->d_kc);
-    cudaFree(s->d_mbits);
+    dev_free(s, s->d_carry);
+    dev_free(s, s->d_carry_bytes);
+    dev_free(s, s->d_kc);
+    dev_free(s, s->d_mbits);
     if (s->ev_prev_d2h) cudaEventDestroy(s->ev_prev_d2h);
-    cudaFree(s->d_amps);
-    cudaFree(s->d_sparse);
-    cudaFree(s->d_blocksq);
-    cudaFree(s->d_err);
-    cudaFree(s->d_state);
-    cudaFree(s->d_lam);
-    cudaFree(s->d_ops);
+    dev_free(s, s->d_amps);
+    dev_free(s, s->d_sparse);
+    dev_free(s, s->d_blocksq);
+    dev_free(s, s->d_err);
+    dev_free(s, s->d_state);
+    dev_free(s, s->d_lam);
+    dev_free(s, s->d_ops);
     for (cudaEvent_t ev : s->prof_ev) cudaEventDestroy(ev);
-    cudaFree(s->d_amps2);
+    dev_free(s, s->d_amps2);
     pool_free(s->pool);
     pool_free(s->lpool);
     if (s->s_comp) cudaStreamDestroy(s->s_comp);
@@ -183,11 +212,11 @@ template <typename R>
 int create_impl(sv_state* s)
 {
     cudaError_t e;
-    if ((e = cudaMalloc(&s->d_err, sizeof(int)))) return cuda_fail(s, e, "cudaMalloc(err)");
+    if ((e = dev_alloc(s, &s->d_err, sizeof(int)))) return cuda_fail(s, e, "cudaMalloc(err)");
     if ((e = cudaMemset(s->d_err, 0, sizeof(int)))) return cuda_fail(s, e, "cudaMemset(err)");
     const size_t amp_bytes = 2 * sizeof(R);
     if (s->mode == SV_UNCOMPRESSED) {
-        if ((e = cudaMalloc(&s->d_state, amp_bytes << s->n)))
+        if ((e = dev_alloc(s, &s->d_state, amp_bytes << s->n)))
             return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the state failed");
         s->st.raw_bytes = amp_bytes << s->n;
         return init_state<R>(s);
@@ -196,15 +225,15 @@ int create_impl(sv_state* s)
     const uint64_t gch = 1ull << gsz;
     const CodecLayout L = codec_layout(s->c);
     s->stride = (L.max_bytes + 255) & ~size_t(255);
-    if ((e = cudaMalloc(&s->d_amps, (amp_bytes << s->c) * gch)) ||
-        (e = cudaMalloc(&s->d_sparse, (size_t)L.nb * 1024 * gch)) ||
-        (e = cudaMalloc(&s->d_blocksq, sizeof(unsigned long long) * L.bpc * gch))) {
+    if ((e = dev_alloc(s, &s->d_amps, (amp_bytes << s->c) * gch)) ||
+        (e = dev_alloc(s, &s->d_sparse, (size_t)L.nb * 1024 * gch)) ||
+        (e = dev_alloc(s, &s->d_blocksq, sizeof(unsigned long long) * L.bpc * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the chunk-group buffers failed");
     }
     for (int i = 0; i < s->nslots; i++) {
-        if ((e = cudaMalloc(&s->d_in[i], s->stride * gch)) || (e = cudaMalloc(&s->d_out[i], s->stride * gch)) ||
-            (e = cudaMalloc(&s->d_co[i], sizeof(ChunkOut) * gch))) {
+        if ((e = dev_alloc(s, &s->d_in[i], s->stride * gch)) || (e = dev_alloc(s, &s->d_out[i], s->stride * gch)) ||
+            (e = dev_alloc(s, &s->d_co[i], sizeof(ChunkOut) * gch))) {
             cudaGetLastError();
             return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the staging slots failed");
         }
@@ -218,11 +247,11 @@ int create_impl(sv_state* s)
             (e = cudaEventCreateWithFlags(&s->ev_comp[i], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&s->ev_d2h[i], cudaEventDisableTiming)))
             return cuda_fail(s, e, "cudaEventCreate");
-    if ((e = cudaMalloc(&s->d_kc, sizeof(int32_t) * gch)) || (e = cudaMalloc(&s->d_mbits, sizeof(uint64_t) * gch))) {
+    if ((e = dev_alloc(s, &s->d_kc, sizeof(int32_t) * gch)) || (e = dev_alloc(s, &s->d_mbits, sizeof(uint64_t) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the chunk step table failed");
     }
-    if ((e = cudaMalloc(&s->d_carry, s->stride * gch)) || (e = cudaMalloc(&s->d_carry_bytes, sizeof(uint64_t) * gch))) {
+    if ((e = dev_alloc(s, &s->d_carry, s->stride * gch)) || (e = dev_alloc(s, &s->d_carry_bytes, sizeof(uint64_t) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the carry buffer failed");
     }
@@ -259,6 +288,10 @@ void sv_config_default(sv_config* cfg)
     cfg->relative_bound = 0;
     cfg->remap_qubits = 0;
     cfg->timeout_s = 600.0;
+    cfg->device_alloc = nullptr;
+    cfg->device_free = nullptr;
+    cfg->alloc_ctx = nullptr;
+    cfg->stream = nullptr;
 }
 
 int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* cfg_in, sv_state** out)
@@ -284,6 +317,8 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
         return reject(SV_ERR_ARG, "tile_qubits must be 2..13");
     if (cfg.remap_qubits != 0 && cfg.remap_qubits != 1) return reject(SV_ERR_ARG, "remap_qubits must be 0 or 1");
     if (!(cfg.timeout_s > 0)) cfg.timeout_s = 600.0;
+    if (!cfg.device_alloc != !cfg.device_free)
+        return reject(SV_ERR_ARG, "device_alloc and device_free must be set together");
     int k = 0;
     if (cfg.mode == SV_COMPRESSED) {
         if (chunk_qubits < 8 || chunk_qubits > n || chunk_qubits > 30)
@@ -332,7 +367,17 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
         release(s);
         return SV_ERR_CUDA;
     }
-    const int r = s->dtype == SV_C64 ? create_impl<float>(s) : create_impl<double>(s);
+    if (cfg.stream && ((e = cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming)) ||
+                       (e = cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming)))) {
+        g_create_error = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
+        release(s);
+        return SV_ERR_CUDA;
+    }
+    int r;
+    {
+        CallOrder order(s);
+        r = s->dtype == SV_C64 ? create_impl<float>(s) : create_impl<double>(s);
+    }
     if (r) {
         g_create_error = s->err;
         release(s);
@@ -356,6 +401,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t ngates)
     }
     cudaSetDevice(s->cfg.device);
     {
+        CallOrder order(s);
         std::lock_guard<std::mutex> lock(g_apply_mu);
         const bool remap = s->cfg.remap_qubits != 0;
         r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg, remap) : apply_circuit<double>(s, pg, remap);
@@ -375,6 +421,7 @@ int sv_expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* ou
     for (size_t i = 0; i < nterms; i++)
         if (!std::isfinite(terms[i].coeff)) return fail(s, SV_ERR_ARG, "coefficient not finite");
     cudaSetDevice(s->cfg.device);
+    CallOrder order(s);
     return s->dtype == SV_C64 ? expect<float>(s, terms, nterms, out_re) : expect<double>(s, terms, nterms, out_re);
 }
 
@@ -383,6 +430,7 @@ int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
     if (!s || (m && (!idx || !out))) return SV_ERR_ARG;
     s->err.clear();
     cudaSetDevice(s->cfg.device);
+    CallOrder order(s);
     return s->dtype == SV_C64 ? amplitudes<float>(s, idx, m, out) : amplitudes<double>(s, idx, m, out);
 }
 
@@ -394,6 +442,7 @@ int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im)
     if (a->n != b->n) return fail(a, SV_ERR_ARG, "sv_inner: the states differ in qubit count");
     if (a->cfg.device != b->cfg.device) return fail(a, SV_ERR_ARG, "sv_inner: the states are on different devices");
     cudaSetDevice(a->cfg.device);
+    CallOrder order(a);
     double out[2] = {0, 0};
     int r;
     if (a->dtype == SV_C64)
@@ -403,6 +452,16 @@ int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im)
     if (r) return r;
     *out_re = out[0];
     *out_im = out[1];
+    return SV_OK;
+}
+
+int sv_device_state(sv_state* s, void** d_amps, int32_t* positions)
+{
+    if (!s || !d_amps) return SV_ERR_ARG;
+    if (s->mode != SV_UNCOMPRESSED) return fail(s, SV_ERR_ARG, "sv_device_state: the state is compressed");
+    *d_amps = s->d_state;
+    if (positions)
+        for (int q = 0; q < s->n; q++) positions[q] = s->perm[q];
     return SV_OK;
 }
 
@@ -436,6 +495,7 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
     int r = lower(s, gates, ngates, theta, nparams, true, pg);
     if (r) return r;
     cudaSetDevice(s->cfg.device);
+    CallOrder order(s);
     std::lock_guard<std::mutex> lock(g_apply_mu);
     if (s->mode == SV_UNCOMPRESSED)
         r = s->dtype == SV_C64 ? grad_uncompressed<float>(s, pg, nparams, H, nterms, energy, grad)

@@ -282,11 +282,11 @@ static int upload_blob(sv_state* s, const std::vector<uint8_t>& blob)
     if (bytes > s->ops_cap) {
         if (s->d_ops) {
             wait_stream(s, s->s_comp);
-            cudaFree(s->d_ops);
+            dev_free(s, s->d_ops);
             s->d_ops = nullptr;
         }
         size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
-        cudaError_t e = cudaMalloc(&s->d_ops, cap);
+        cudaError_t e = dev_alloc(s, &s->d_ops, cap);
         if (e != cudaSuccess) return cuda_fail(s, e, "cudaMalloc(ops)");
         s->ops_cap = cap;
     }
@@ -1091,9 +1091,9 @@ int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
     double* d_out = nullptr;
     cudaError_t e;
     int r = SV_OK;
-    if ((e = cudaMalloc(&d_loc, batch * 8)) || (e = cudaMalloc(&d_dst, batch * 8)) ||
-        (e = cudaMalloc(&d_out, batch * 16))) {
-        cudaFree(d_loc); cudaFree(d_dst); cudaFree(d_out);
+    if ((e = dev_alloc(s, &d_loc, batch * 8)) || (e = dev_alloc(s, &d_dst, batch * 8)) ||
+        (e = dev_alloc(s, &d_out, batch * 16))) {
+        dev_free(s, d_loc); dev_free(s, d_dst); dev_free(s, d_out);
         return cuda_fail(s, e, "cudaMalloc(gather)");
     }
     std::vector<uint64_t> loc, dst;
@@ -1151,9 +1151,9 @@ int amplitudes(sv_state* s, const uint64_t* idx, size_t m, double* out)
         r = wait_stream(s, s->s_comp);
     }
     if (!r) r = check_device_error(s);
-    cudaFree(d_loc);
-    cudaFree(d_dst);
-    cudaFree(d_out);
+    dev_free(s, d_loc);
+    dev_free(s, d_dst);
+    dev_free(s, d_out);
     return r;
 }
 
@@ -1176,9 +1176,9 @@ int inner(sv_state* a, const sv_state* b, double* out)
     double* d_part = nullptr;
     double* d_out = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_part, sizeof(double) * 2 * nb)) || (e = cudaMalloc(&d_out, sizeof(double) * 2))) {
-        cudaFree(d_part);
-        cudaFree(d_out);
+    if ((e = dev_alloc(a, &d_part, sizeof(double) * 2 * nb)) || (e = dev_alloc(a, &d_out, sizeof(double) * 2))) {
+        dev_free(a, d_part);
+        dev_free(a, d_out);
         return cuda_fail(a, e, "cudaMalloc(inner)");
     }
     int r = SV_OK;
@@ -1206,8 +1206,8 @@ int inner(sv_state* a, const sv_state* b, double* out)
         r = cuda_fail(a, e, "D2H inner");
     if (!r) r = wait_stream(a, a->s_comp);
     if (!r) r = check_device_error(a);
-    cudaFree(d_part);
-    cudaFree(d_out);
+    dev_free(a, d_part);
+    dev_free(a, d_out);
     return r;
 }
 
@@ -1245,9 +1245,9 @@ static int expect_pairs(sv_state* s, const std::vector<sv_pauli_term>& phys, dou
     xhs.erase(std::unique(xhs.begin(), xhs.end()), xhs.end());
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr;
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * nterms)) ||
-        (e = cudaMalloc(&d_part, sizeof(double) * nterms * nblocks)) || (e = cudaMalloc(&d_acc, sizeof(double) * nterms))) {
-        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+    if ((e = dev_alloc(s, &d_terms, sizeof(PauliDev) * nterms)) ||
+        (e = dev_alloc(s, &d_part, sizeof(double) * nterms * nblocks)) || (e = dev_alloc(s, &d_acc, sizeof(double) * nterms))) {
+        dev_free(s, d_terms); dev_free(s, d_part); dev_free(s, d_acc);
         return cuda_fail(s, e, "cudaMalloc(expect)");
     }
     int r = SV_OK;
@@ -1324,9 +1324,9 @@ static int expect_pairs(sv_state* s, const std::vector<sv_pauli_term>& phys, dou
         }
     }
     if (!r) r = check_device_error(s);
-    cudaFree(d_terms);
-    cudaFree(d_part);
-    cudaFree(d_acc);
+    dev_free(s, d_terms);
+    dev_free(s, d_part);
+    dev_free(s, d_acc);
     return r;
 }
 
@@ -1372,9 +1372,9 @@ static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, 
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, phys.size()))) ||
-        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) || (e = cudaMalloc(&d_acc, sizeof(double)))) {
-        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+    if ((e = dev_alloc(s, &d_terms, sizeof(PauliDev) * std::max<size_t>(1, phys.size()))) ||
+        (e = dev_alloc(s, &d_part, sizeof(double) * nblocks)) || (e = dev_alloc(s, &d_acc, sizeof(double)))) {
+        dev_free(s, d_terms); dev_free(s, d_part); dev_free(s, d_acc);
         return cuda_fail(s, e, "cudaMalloc(expect)");
     }
     int r = SV_OK;
@@ -1438,9 +1438,9 @@ static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, 
     double acc = 0;
     const int rs = sync_all(s);
     if (!r && !rs && (e = cudaMemcpy(&acc, d_acc, sizeof(double), cudaMemcpyDeviceToHost))) r = cuda_fail(s, e, "D2H expect");
-    cudaFree(d_terms);
-    cudaFree(d_part);
-    cudaFree(d_acc);
+    dev_free(s, d_terms);
+    dev_free(s, d_part);
+    dev_free(s, d_acc);
     if (r || rs) return r ? r : rs;
     double rest = 0;
     if (!wide.empty() && (r = expect_pairs<R>(s, wide, &rest))) return r;
@@ -1472,9 +1472,9 @@ int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_r
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * nterms)) || (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
-        (e = cudaMalloc(&d_acc, sizeof(double)))) {
-        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc);
+    if ((e = dev_alloc(s, &d_terms, sizeof(PauliDev) * nterms)) || (e = dev_alloc(s, &d_part, sizeof(double) * nblocks)) ||
+        (e = dev_alloc(s, &d_acc, sizeof(double)))) {
+        dev_free(s, d_terms); dev_free(s, d_part); dev_free(s, d_acc);
         return cuda_fail(s, e, "cudaMalloc(expect)");
     }
     int r = SV_OK;
@@ -1487,9 +1487,9 @@ int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_r
         r = cuda_fail(s, e, "energy");
     if (!r) r = wait_stream(s, s->s_comp);
     s->st.kernel_launches += 2;
-    cudaFree(d_terms);
-    cudaFree(d_part);
-    cudaFree(d_acc);
+    dev_free(s, d_terms);
+    dev_free(s, d_part);
+    dev_free(s, d_acc);
     if (r) return r;
     *out_re = acc;
     return check_device_error(s);
@@ -1504,7 +1504,7 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
     const int n = s->n;
     const size_t vbytes = sizeof(R) * 2ull << n;
     if (!s->d_lam) {
-        if ((e = cudaMalloc(&s->d_lam, vbytes))) return cuda_fail(s, e, "cudaMalloc(lambda)");
+        if ((e = dev_alloc(s, &s->d_lam, vbytes))) return cuda_fail(s, e, "cudaMalloc(lambda)");
     }
     int r = init_state<R>(s);
     if (r) return r;
@@ -1562,11 +1562,11 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
     }
     const uint64_t ntiles = 1ull << (L - t);
     const size_t nslots_total = slot_params.size();
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms))) ||
-        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
-        (e = cudaMalloc(&d_acc, sizeof(double) * (1 + std::max<size_t>(1, nslots_total)))) ||
-        (e = cudaMalloc(&d_gpart, sizeof(double) * std::max(1, max_slots) * ntiles))) {
-        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc); cudaFree(d_gpart);
+    if ((e = dev_alloc(s, &d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms))) ||
+        (e = dev_alloc(s, &d_part, sizeof(double) * nblocks)) ||
+        (e = dev_alloc(s, &d_acc, sizeof(double) * (1 + std::max<size_t>(1, nslots_total)))) ||
+        (e = dev_alloc(s, &d_gpart, sizeof(double) * std::max(1, max_slots) * ntiles))) {
+        dev_free(s, d_terms); dev_free(s, d_part); dev_free(s, d_acc); dev_free(s, d_gpart);
         return cuda_fail(s, e, "cudaMalloc(grad)");
     }
     do {
@@ -1625,10 +1625,10 @@ int grad_uncompressed(sv_state* s, const std::vector<PGate>& gates, size_t npara
         for (size_t p = 0; p < nparams; p++) grad[p] = 0;
         for (size_t j = 0; j < nslots_total; j++) grad[slot_params[j]] += acc[1 + j];
     } while (0);
-    cudaFree(d_terms);
-    cudaFree(d_part);
-    cudaFree(d_acc);
-    cudaFree(d_gpart);
+    dev_free(s, d_terms);
+    dev_free(s, d_part);
+    dev_free(s, d_acc);
+    dev_free(s, d_gpart);
     if (!r) r = check_device_error(s);
     return r;
 }
@@ -1645,13 +1645,13 @@ static int ensure_lambda_store(sv_state* s)
     const int gsz = std::min(s->gmax, s->nh);
     const uint64_t gch = 1ull << gsz;
     cudaError_t e;
-    if ((e = cudaMalloc(&s->d_amps2, ((sizeof(R) * 2) << s->c) * gch))) {
+    if ((e = dev_alloc(s, &s->d_amps2, ((sizeof(R) * 2) << s->c) * gch))) {
         cudaGetLastError();
         return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the lambda group buffer failed");
     }
     for (int i = 0; i < s->nslots; i++) {
-        if ((e = cudaMalloc(&s->d_in2[i], s->stride * gch)) || (e = cudaMalloc(&s->d_out2[i], s->stride * gch)) ||
-            (e = cudaMalloc(&s->d_co2[i], sizeof(ChunkOut) * gch))) {
+        if ((e = dev_alloc(s, &s->d_in2[i], s->stride * gch)) || (e = dev_alloc(s, &s->d_out2[i], s->stride * gch)) ||
+            (e = dev_alloc(s, &s->d_co2[i], sizeof(ChunkOut) * gch))) {
             cudaGetLastError();
             return fail(s, SV_ERR_DEVICE_OOM, "device allocation of the lambda staging slots failed");
         }
@@ -1972,11 +1972,11 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr, *d_gpart = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms) << s->nh)) ||
-        (e = cudaMalloc(&d_part, sizeof(double) * nblocks)) ||
-        (e = cudaMalloc(&d_acc, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)))) ||
-        (e = cudaMalloc(&d_gpart, sizeof(double) * gpart_cap))) {
-        cudaFree(d_terms); cudaFree(d_part); cudaFree(d_acc); cudaFree(d_gpart);
+    if ((e = dev_alloc(s, &d_terms, sizeof(PauliDev) * std::max<size_t>(1, nterms) << s->nh)) ||
+        (e = dev_alloc(s, &d_part, sizeof(double) * nblocks)) ||
+        (e = dev_alloc(s, &d_acc, sizeof(double) * (1 + std::max<size_t>(1, nparam_gates)))) ||
+        (e = dev_alloc(s, &d_gpart, sizeof(double) * gpart_cap))) {
+        dev_free(s, d_terms); dev_free(s, d_part); dev_free(s, d_acc); dev_free(s, d_gpart);
         return cuda_fail(s, e, "cudaMalloc(grad)");
     }
     std::vector<int> slot_params;
@@ -2004,10 +2004,10 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
         for (size_t p = 0; p < nparams; p++) grad[p] = 0;
         for (size_t j = 0; j < slot_params.size(); j++) grad[slot_params[j]] += acc[1 + j];
     } while (0);
-    cudaFree(d_terms);
-    cudaFree(d_part);
-    cudaFree(d_acc);
-    cudaFree(d_gpart);
+    dev_free(s, d_terms);
+    dev_free(s, d_part);
+    dev_free(s, d_acc);
+    dev_free(s, d_gpart);
     if (!r) r = check_device_error(s);
     return r;
 }

@@ -1,12 +1,30 @@
 // engine.h -- pass execution entry points used by the C ABI (api.cpp).
 #pragma once
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "runtime.h"
 
 namespace sv {
+
+// Device memory of a handle: the caller's provider (sv_config.device_alloc /
+// device_free) when set, else cudaMalloc / cudaFree. dev_free(s, nullptr) is a no-op.
+template <typename T>
+cudaError_t dev_alloc(sv_state* s, T** p, size_t bytes)
+{
+    if (!s->cfg.device_alloc) return cudaMalloc(p, bytes);
+    void* q = s->cfg.device_alloc(std::max<size_t>(1, bytes), s->cfg.device, s->cfg.alloc_ctx);
+    *p = static_cast<T*>(q);
+    return q ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+inline void dev_free(sv_state* s, void* p)
+{
+    if (!p) return;
+    if (s->cfg.device_free) s->cfg.device_free(p, s->cfg.device, s->cfg.alloc_ctx);
+    else cudaFree(p);
+}
 
 int fail(sv_state* s, int code, const std::string& msg);
 int cuda_fail(sv_state* s, cudaError_t e, const char* where);

@@ -155,6 +155,8 @@ struct sv_state {
     int gmax = 4, tq = 12, lq = 5, nslots = 3;
     int nh = 0;                     // high qubits n - c
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    // ordering against the caller's stream (sv_config.stream)
+    cudaEvent_t ev_user = nullptr, ev_done = nullptr;
     // compressed store and staging
     size_t stride = 0;              // device slot stride per chunk stream
     std::vector<sv::ChunkRef> cur;  // one slot per chunk, rewritten in place by each pass
