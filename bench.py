@@ -15,7 +15,7 @@ Metric: amplitude-gate updates per second = gates * 2^n / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload {layers30,ghz30,qft30,qft16,layers16,
-                              ghz36,qft36,clifford36,grad-hea24,grad-hea32,
+                              ghz36,qft36,clifford36,grad-hea24,grad-hea32,grad-hea32-ckpt1,
                               qft36-rel,clifford36-rel,layers30-rel}
   (-rel: the relative error bound, each chunk's step from its largest component)
 
@@ -63,6 +63,9 @@ WORKLOADS = {
     "layers30-rel": dict(n=30, c=22, eb=1e-6, dtype="c64", group=0, circuit="layers", depth=40, relative=True),
     "grad-hea24": dict(n=24, c=24, eb=0.0, dtype="c64", group=0, circuit="hea", layers=10, mode="uncompressed"),
     "grad-hea32": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16),
+    # the same with psi checkpointed after every forward pass (checkpoint_passes = 1)
+    "grad-hea32-ckpt1": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16,
+                             checkpoint=1),
 }
 
 
@@ -129,7 +132,8 @@ def describe(w, ngates, group=None):
     if w["circuit"] == "hea":
         return (f"adjoint gradient, hardware-efficient ansatz n={w['n']}, {w['layers']} layers, 1-D Ising, "
                 f"{w['dtype']}, " + ("uncompressed in HBM" if w.get("mode") == "uncompressed" else
-                                     f"compressed chunks 2^{w['c']}, eb={w['eb']}"))
+                                     f"compressed chunks 2^{w['c']}, eb={w['eb']}")
+                + (f", psi checkpointed every {w['checkpoint']} forward pass(es)" if w.get("checkpoint") else ""))
     name = {"layers": f"random layered circuit depth {w.get('depth')}", "ghz": "GHZ", "qft": "QFT on a seeded basis state",
             "clifford": f"random Clifford+RZ depth {w.get('depth')} (40% of slots on the 10 high qubits)"}[w["circuit"]]
     bound = "relative eb" if w.get("relative") else "eb"
@@ -660,7 +664,8 @@ def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None
     thetas = [W.normal_params(npar, seed=(3 if w.get("sets", 1) == 1 else 100 + i)) for i in range(max(1, sets))]
     mode = w.get("mode", "compressed")
     sim = StateVector(n, w["c"], w["eb"] or 1e-6, dtype=w["dtype"], mode=mode, max_group_qubits=w["group"], device=dev,
-                      host_budget_bytes=host_budget() if mode == "compressed" else 0)
+                      host_budget_bytes=host_budget() if mode == "compressed" else 0,
+                      checkpoint_passes=w.get("checkpoint", 0))
     for i in range(warmup):
         sim.grad(gates, thetas[i % len(thetas)], terms)
     torch.cuda.synchronize()
@@ -680,6 +685,8 @@ def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None
     launches = int(st["kernel_launches"] - s0["kernel_launches"])
     adj_launches = int(st["jit_adjoint_launches"] - s0["jit_adjoint_launches"])
     passes = (st["passes"] - s0["passes"]) / steps
+    ckpt = {"checkpoint_passes": w.get("checkpoint", 0), "checkpoints": st["checkpoints"],
+            "checkpoint_bytes": st["checkpoint_bytes"]}
     sim.close()
     errors = []
     if with_errors:
@@ -694,7 +701,7 @@ def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None
     return {"s_per_step": t_local, "steps": steps, "warmup": warmup, "params": npar, "gates": len(gates),
             "parameter_sets": len(thetas), "launches_per_step": launches / steps,
             "generated_adjoint_launches_per_step": adj_launches / steps, "passes_per_step": passes,
-            "clocks": clk, "errors_vs_fp64_gpu_adjoint": errors, "workload": describe(w, len(gates))}
+            "clocks": clk, "errors_vs_fp64_gpu_adjoint": errors, "workload": describe(w, len(gates)), **ckpt}
 
 
 def run_grad(args, rank, world):
@@ -721,7 +728,8 @@ def adjoint_legs(dev):
     gradient workloads: n = 24 in HBM (480 parameters) and n = 32 on two
     compressed stores (512 parameters; two of its 16 parameter sets)."""
     out = {}
-    for name, steps, warmup, max_sets in (("grad-hea24", 5, 2, None), ("grad-hea32", 2, 1, 2)):
+    for name, steps, warmup, max_sets in (("grad-hea24", 5, 2, None), ("grad-hea32", 2, 1, 2),
+                                          ("grad-hea32-ckpt1", 2, 1, 2)):
         try:
             m = grad_measure(WORKLOADS[name], steps, warmup, dev, max_sets=max_sets)
             m.pop("clocks", None)

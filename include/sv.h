@@ -136,6 +136,13 @@ typedef struct sv_config {
                                      call leaves qubits on new positions, so repeating the same
                                      circuit runs (and, with jit, compiles) other kernels: best
                                      for one long circuit per call. */
+    int32_t checkpoint_passes;    /* compressed sv_grad only. 0 (default): the reverse sweep
+                                     uncomputes psi through the passes (every pass re-encodes it,
+                                     so its error grows over forward and reverse passes); K > 0:
+                                     the forward sweep keeps a copy of the compressed psi after
+                                     every K-th pass (pageable host memory, one compressed state
+                                     per checkpoint, sv_stats_t.checkpoint_bytes) and the reverse
+                                     sweep resumes from it at that pass boundary */
     sv_device_alloc_fn device_alloc; /* NULL (default): cudaMalloc / cudaFree. Otherwise every device
                                      allocation of the handle (state, staging, per-call scratch)
                                      goes through device_alloc / device_free (both must be set) */
@@ -194,6 +201,9 @@ typedef struct sv_stats_t {
        place while a chunk's new stream fits and moved to a slot with 1/32
        headroom when it grows, plus slots released by such moves */
     uint64_t host_pinned_bytes;
+    /* host bytes of the psi checkpoints kept by the last compressed sv_grad
+       (sv_config.checkpoint_passes), and how many there were */
+    uint64_t checkpoint_bytes, checkpoints;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */
@@ -313,8 +323,9 @@ int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im);
  * |coeff|, since |lambda_i| <= ||H|| <= sum |coeff|) and run
  * the reverse sweep pass by pass over both stores (re-encoding both after
  * every pass); lambda is built one chunk at a time from the source chunks
- * k ^ xh of every distinct high x-mask xh, which must number at most
- * 2^max_group_qubits (SV_ERR_ARG otherwise).
+ * k ^ xh of every distinct high x-mask xh, staged 2^max_group_qubits at a
+ * time (more distinct masks take several batches per chunk, accumulated on
+ * the device before the chunk is encoded once).
  * On return the stored state is psi_0 as left by the reverse sweep (|init_index>
  * up to rounding and, when compressed, quantisation error); call sv_create or
  * sv_apply_circuit from a known state to continue.

@@ -288,6 +288,7 @@ void sv_config_default(sv_config* cfg)
     cfg->relative_bound = 0;
     cfg->remap_qubits = 0;
     cfg->timeout_s = 600.0;
+    cfg->checkpoint_passes = 0;
     cfg->device_alloc = nullptr;
     cfg->device_free = nullptr;
     cfg->alloc_ctx = nullptr;
@@ -317,6 +318,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
         return reject(SV_ERR_ARG, "tile_qubits must be 2..13");
     if (cfg.remap_qubits != 0 && cfg.remap_qubits != 1) return reject(SV_ERR_ARG, "remap_qubits must be 0 or 1");
     if (!(cfg.timeout_s > 0)) cfg.timeout_s = 600.0;
+    if (cfg.checkpoint_passes < 0) return reject(SV_ERR_ARG, "checkpoint_passes must be >= 0");
     if (!cfg.device_alloc != !cfg.device_free)
         return reject(SV_ERR_ARG, "device_alloc and device_free must be set together");
     int k = 0;

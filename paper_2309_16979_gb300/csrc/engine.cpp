@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <thread>
 
 #include "engine.h"
@@ -1666,10 +1667,14 @@ static int ensure_lambda_store(sv_state* s)
 
 // lambda = H psi, one output chunk at a time from the staged source chunks
 // k ^ xh (one per distinct high x-mask); adds Re<psi_k|lambda_k> to *d_energy.
-// Two staging sets alternate: chunk k+1's sources cross the host link while
-// chunk k is decoded, multiplied and encoded, and chunk k's stream returns
-// to the host while chunk k+1 computes. d_terms holds every output chunk's
-// term table (2^(n-c) x phys.size() entries).
+// When the distinct high x-masks outnumber the chunks a staging group holds,
+// they are taken in batches: every batch stages chunk k itself in slot 0 and
+// as many other sources as fit, and lambda_k accumulates over the batches in
+// device memory before it is encoded once. With a single batch that fits
+// twice, two staging sets alternate: chunk k+1's sources cross the host link
+// while chunk k is decoded, multiplied and encoded, and chunk k's stream
+// returns to the host while chunk k+1 computes. d_terms holds every batch's
+// term table for every output chunk (2^(n-c) x phys.size() entries).
 template <typename R>
 static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, PauliDev* d_terms, double* d_part,
                         int nblocks, double* d_energy)
@@ -1679,25 +1684,48 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
     std::vector<uint64_t> X{0};
     for (const auto& t : phys) X.push_back(t.xmask >> c);
     std::sort(X.begin(), X.end());
-    X.erase(std::unique(X.begin(), X.end()), X.end());
+    X.erase(std::unique(X.begin(), X.end()), X.end());  // X[0] = 0: chunk k itself
     const size_t gcap = (size_t)1 << std::min(s->gmax, s->nh);
-    if (X.size() > gcap)
-        return fail(s, SV_ERR_ARG, "more distinct high x-masks than chunks in a staging group (raise max_group_qubits)");
-    const size_t m = X.size(), nt = phys.size();
-    const int nset = 2 * m <= gcap ? 2 : 1;
+    if (gcap < 2 && X.size() > 1) return fail(s, SV_ERR_ARG, "staging groups too small for lambda = H psi");
+    // batches of source slots: batch 0 = X[0 .. gcap), later ones X[0] and the next gcap - 1
+    std::vector<std::vector<size_t>> batch{{}};
+    for (size_t j = 0; j < X.size(); j++) {
+        if (batch.back().size() == gcap) batch.push_back({0});
+        batch.back().push_back(j);
+    }
+    const size_t nb = batch.size(), nt = phys.size();
+    std::vector<int> batch_of(X.size(), -1), slot_of(X.size(), -1);
+    for (size_t b = 0; b < nb; b++)
+        for (size_t i = 0; i < batch[b].size(); i++)
+            if (batch_of[batch[b][i]] < 0) {
+                batch_of[batch[b][i]] = (int)b;
+                slot_of[batch[b][i]] = (int)i;
+            }
+    const size_t m = batch[0].size();
+    const int nset = (nb == 1 && 2 * m <= gcap) ? 2 : 1;
     const uint64_t nch = 1ull << s->nh;
+    // term table of (chunk k, batch b) at d_terms + toff[b] + k * tcnt[b]
+    std::vector<size_t> toff(nb, 0), tcnt(nb, 0);
+    for (size_t i = 0; i < nt; i++) {
+        const size_t j = std::lower_bound(X.begin(), X.end(), phys[i].xmask >> c) - X.begin();
+        tcnt[batch_of[j]]++;
+    }
+    for (size_t b = 1; b < nb; b++) toff[b] = toff[b - 1] + nch * tcnt[b - 1];
     cudaError_t e;
     if (nt) {
         std::vector<PauliDev> hd(nch * nt);
-        for (uint64_t k = 0; k < nch; k++)
+        for (uint64_t k = 0; k < nch; k++) {
+            std::vector<size_t> fill(nb, 0);
             for (size_t i = 0; i < nt; i++) {
                 const uint64_t xh = phys[i].xmask >> c;
-                const size_t slot = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
+                const size_t j = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
+                const int b = batch_of[j];
                 const int hs = __builtin_popcountll((k ^ xh) & (phys[i].zmask >> c)) & 1;
-                PauliDev& d = hd[k * nt + i];
+                PauliDev& d = hd[toff[b] + k * tcnt[b] + fill[b]++];
                 d = pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, 0, hs ? -1.0 : 1.0);
-                d.pad = (int32_t)slot;
+                d.pad = slot_of[j];
             }
+        }
         if ((e = cudaMemcpy(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice)))
             return cuda_fail(s, e, "upload terms");
     }
@@ -1707,28 +1735,35 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         const size_t base = (size_t)sl * m;
         uint8_t* in = s->d_in[0] + base * s->stride;
         uint8_t* amps = static_cast<uint8_t*>(s->d_amps) + (base << c) * amp_bytes;
-        // the set's streams are overwritten once its previous decode is done
-        if (k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
-            return cuda_fail(s, e, "wait decode");
-        GroupIn gin{};
-        for (size_t j = 0; j < m; j++) {
-            const ChunkRef& cr = s->cur[k ^ X[j]];
-            gin.bytes[j] = (uint32_t)cr.bytes;
-            if ((e = cudaMemcpyAsync(in + j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
-                return cuda_fail(s, e, "H2D chunk");
-            s->st.bytes_h2d += cr.bytes;
-        }
-        if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)))
-            return cuda_fail(s, e, "record h2d");
-        if ((e = launch_decode<R>(in, s->stride, c, s->dtype, (int)m, gin, amps, s->scale, s->d_err, s->s_comp)) ||
-            (e = cudaEventRecord(s->ev_h2d[2 + sl], s->s_comp)))
-            return cuda_fail(s, e, "decode");
-        // the set's output stream is overwritten once its copy to the host is done
-        if (k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[sl], 0)))
-            return cuda_fail(s, e, "wait d2h");
         int launches = 0;
-        if ((e = launch_ham_chunk<R>(amps, s->d_amps2, c, d_terms + k * nt, (int)nt, s->s_comp)) ||
-            (e = launch_dot<R>(amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
+        for (size_t b = 0; b < nb; b++) {
+            // the set's streams are overwritten once its previous decode is done
+            if ((k >= (uint64_t)nset || b > 0) && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
+                return cuda_fail(s, e, "wait decode");
+            GroupIn gin{};
+            for (size_t i = 0; i < batch[b].size(); i++) {
+                const ChunkRef& cr = s->cur[k ^ X[batch[b][i]]];
+                gin.bytes[i] = (uint32_t)cr.bytes;
+                if ((e = cudaMemcpyAsync(in + i * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
+                    return cuda_fail(s, e, "H2D chunk");
+                s->st.bytes_h2d += cr.bytes;
+            }
+            if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)))
+                return cuda_fail(s, e, "record h2d");
+            if ((e = launch_decode<R>(in, s->stride, c, s->dtype, (int)batch[b].size(), gin, amps, s->scale, s->d_err,
+                                      s->s_comp)) ||
+                (e = cudaEventRecord(s->ev_h2d[2 + sl], s->s_comp)))
+                return cuda_fail(s, e, "decode");
+            // the set's output stream is overwritten once its copy to the host is done
+            if (b == 0 && k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[sl], 0)))
+                return cuda_fail(s, e, "wait d2h");
+            if ((e = launch_ham_chunk<R>(amps, s->d_amps2, c, d_terms + toff[b] + k * tcnt[b], (int)tcnt[b], b > 0,
+                                         s->s_comp)))
+                return cuda_fail(s, e, "lambda chunk");
+            launches += 2;
+        }
+        // slot 0 of the last batch holds psi_k
+        if ((e = launch_dot<R>(amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
             (s->rel && (e = launch_chunk_steps<R>(s->d_amps2, c, 1, s->eb, s->d_mbits, s->d_kc, s->s_comp,
                                                   &launches))) ||
@@ -1738,7 +1773,7 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
             (e = cudaMemcpyAsync(s->h_co2[sl], s->d_co2[sl], sizeof(ChunkOut), cudaMemcpyDeviceToHost, s->s_comp)) ||
             (e = cudaEventRecord(s->ev_comp[sl], s->s_comp)))
             return cuda_fail(s, e, "lambda chunk");
-        s->st.kernel_launches += 4 + launches;
+        s->st.kernel_launches += 2 + launches;
         return SV_OK;
     };
     auto finish = [&](uint64_t k) -> int {
@@ -1940,6 +1975,42 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
     return SV_OK;
 }
 
+// psi checkpoints of the compressed adjoint: a copy of every chunk stream of
+// the store, taken and put back with host threads (no GPU work is in flight
+// on the store at either point: the passes around them have synchronised).
+using Checkpoint = std::vector<std::vector<uint8_t>>;
+
+static void parallel_chunks(uint64_t nch, const std::function<void(uint64_t)>& fn)
+{
+    const uint64_t nth = std::min<uint64_t>(nch, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    std::atomic<uint64_t> next{0};
+    auto worker = [&]() {
+        for (uint64_t k; (k = next.fetch_add(1)) < nch;) fn(k);
+    };
+    std::vector<std::thread> pool;
+    for (uint64_t i = 1; i < nth; i++) pool.emplace_back(worker);
+    worker();
+    for (std::thread& th : pool) th.join();
+}
+
+static void checkpoint_take(sv_state* s, Checkpoint& cp)
+{
+    cp.assign(s->cur.size(), {});
+    parallel_chunks(s->cur.size(), [&](uint64_t k) {
+        cp[k].assign(s->cur[k].ptr, s->cur[k].ptr + s->cur[k].bytes);
+    });
+}
+
+static int checkpoint_restore(sv_state* s, const Checkpoint& cp)
+{
+    // slots first (the pool is not thread-safe), then the copies
+    for (uint64_t k = 0; k < cp.size(); k++)
+        if (!store_slot(s, s->pool, s->cur[k], cp[k].size()))
+            return fail(s, SV_ERR_HOST_OOM, "pinned host allocation for the compressed store failed");
+    parallel_chunks(cp.size(), [&](uint64_t k) { std::memcpy(s->cur[k].ptr, cp[k].data(), cp[k].size()); });
+    return SV_OK;
+}
+
 template <typename R>
 int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams, const sv_pauli_term* H,
                     size_t nterms, double* energy, double* grad)
@@ -1948,7 +2019,25 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     if (r) return r;
     if ((r = init_state<R>(s))) return r;
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
-    if ((r = apply_circuit<R>(s, gates, false))) return r;  // the forward sweep (the same plan)
+    // the forward sweep (the same plan); with checkpoints pass by pass, keeping
+    // psi after every K-th pass (ckpt[i]: psi after (i + 1) K passes)
+    const size_t K = (size_t)std::max(0, s->cfg.checkpoint_passes);
+    std::vector<Checkpoint> ckpt;
+    s->st.checkpoint_bytes = 0;
+    s->st.checkpoints = 0;
+    if (K == 0 || passes.size() <= K) {
+        if ((r = apply_circuit<R>(s, gates, false))) return r;
+    } else {
+        for (size_t p = 0; p < passes.size(); p++) {
+            if ((r = run_pass_compressed<R>(s, gates, passes[p]))) return r;
+            if ((p + 1) % K == 0 && p + 1 < passes.size()) {
+                ckpt.emplace_back();
+                checkpoint_take(s, ckpt.back());
+                for (const auto& v : ckpt.back()) s->st.checkpoint_bytes += v.size();
+                s->st.checkpoints++;
+            }
+        }
+    }
     std::vector<sv_pauli_term> phys(nterms);
     for (size_t i = 0; i < nterms; i++) {
         phys[i] = H[i];
@@ -1990,9 +2079,13 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
         while (std::ldexp(1.0, up) < csum && up < 40) up++;
         s->kl = std::min(0, s->k + up);
         if ((r = build_lambda<R>(s, phys, d_terms, d_part, nblocks, d_acc))) break;
-        for (size_t p = passes.size(); p-- > 0;)
+        for (size_t p = passes.size(); p-- > 0;) {
             if ((r = run_pass_adjoint_compressed<R>(s, inv, passes[p], d_gpart, gpart_cap, d_acc, slot_params)))
                 break;
+            // psi after p passes, as the forward sweep left it, replaces the uncomputed one
+            if (K && p > 0 && p % K == 0 && p / K - 1 < ckpt.size() && (r = checkpoint_restore(s, ckpt[p / K - 1])))
+                break;
+        }
         if (r) break;
         std::vector<double> acc(1 + slot_params.size());
         if ((e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s->s_comp))) {

@@ -271,13 +271,18 @@ k_hamiltonian(const typename V2<R>::T* __restrict__ psi, typename V2<R>::T* __re
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_ham_chunk(const typename V2<R>::T* __restrict__ psi_slots, typename V2<R>::T* __restrict__ lam, int c,
-            const PauliDev* __restrict__ terms, int nterms)
+            const PauliDev* __restrict__ terms, int nterms, int accumulate)
 {
     using T = typename V2<R>::T;
     const uint64_t count = 1ull << c;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
          k += (uint64_t)gridDim.x * blockDim.x) {
         R ar = (R)0, ai = (R)0;
+        if (accumulate) {
+            const T l = lam[k];
+            ar = l.x;
+            ai = l.y;
+        }
         for (int tt = 0; tt < nterms; tt++) {
             const PauliDev& P = terms[tt];
             const uint64_t src = k ^ P.xl;
@@ -407,13 +412,13 @@ cudaError_t launch_hamiltonian(const void* psi, void* lam, int n, const PauliDev
 
 template <typename R>
 cudaError_t launch_ham_chunk(const void* psi_slots, void* lam, int c, const PauliDev* terms, int nterms,
-                             cudaStream_t st)
+                             bool accumulate, cudaStream_t st)
 {
     using T = typename V2<R>::T;
     const uint64_t count = 1ull << c;
     const unsigned blocks = (unsigned)std::min<uint64_t>((count + kThreads - 1) / kThreads, 152ull * 32);
     k_ham_chunk<R><<<blocks, kThreads, 0, st>>>(static_cast<const T*>(psi_slots), static_cast<T*>(lam), c, terms,
-                                               nterms);
+                                               nterms, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -434,7 +439,7 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
                                           cudaStream_t);                                                        \
     template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \
     template cudaError_t launch_dot<R>(const void*, const void*, uint64_t, double*, int, cudaStream_t);     \
-    template cudaError_t launch_ham_chunk<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);
+    template cudaError_t launch_ham_chunk<R>(const void*, void*, int, const PauliDev*, int, bool, cudaStream_t);
 SV_INST(float)
 SV_INST(double)
 #undef SV_INST

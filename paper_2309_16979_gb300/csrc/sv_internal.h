@@ -190,9 +190,11 @@ template <typename R>
 cudaError_t launch_adjoint(void* psi, void* lam, const TileDesc& td, const DevOp<R>* ops, int nops,
                            uint64_t gbase, double* gpart, uint64_t tile_stride, cudaStream_t st);
 
+// lam (+)= sum_t coeff_t P_t psi over one output chunk of 2^c amplitudes from
+// staged source slots (term t reads slot terms[t].pad); accumulate: add to lam
 template <typename R>
 cudaError_t launch_ham_chunk(const void* psi_slots, void* lam, int c, const PauliDev* terms, int nterms,
-                             cudaStream_t st);
+                             bool accumulate, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* partials,

@@ -106,11 +106,59 @@ def test_compressed_adjoint_agrees_with_uncompressed_gpu(SV):
     assert abs(e_c - e_u) < 1e-4 and np.abs(g_c - g_u).max() < 1e-4
 
 
-def test_compressed_adjoint_rejects_too_many_high_x_masks(SV):
-    from paper_2309_16979_gb300 import SvError
+@pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
+def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb):
+    """lambda = H psi when the terms' distinct high x-masks (0, 1, 2, 4, 8, 9
+    over 4 high qubits) outnumber the 4 chunks a staging group holds: two
+    batches per output chunk, accumulated before one encode. Same bound as
+    the single-batch case."""
     n, c = 12, 8
-    gates, npar = W.hea(n, 1)
-    terms = [W.PauliTerm(1.0, 1 << q, 0) for q in range(n)] + [W.PauliTerm(0.5, (1 << 11) | (1 << 8), 0)]
-    with SV(n, c, 1e-6, max_group_qubits=2) as s:
-        with pytest.raises(SvError):
-            s.grad(gates, W.normal_params(npar), terms)
+    gates, npar = W.hea(n, 2)
+    theta = W.normal_params(npar, seed=12)
+    terms = [W.PauliTerm(0.3 + 0.05 * q, 1 << q, 0) for q in range(n)] + \
+        [W.PauliTerm(0.5, (1 << 11) | (1 << 8), 1 << 3), W.PauliTerm(-0.7, (1 << 9) | 3, (1 << 9) | (1 << 2))]
+    e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=6)
+    with SV(n, c, eb, dtype=dtype, init_index=6, max_group_qubits=2) as s:
+        e, gr = s.grad(gates, theta, terms)
+        P = s.stats()["passes"]
+    scale = sum(abs(t.coeff) for t in terms)
+    q = np.sqrt(2.0 * (1 << n)) * eb
+    arith = 0.0 if dtype == "c128" else 64 * 2.0 ** -24 * len(gates) * scale
+    assert abs(e - e_o) <= scale * P * q + arith + 1e-12
+    assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
+
+
+@pytest.mark.parametrize("dtype,eb", [("c64", 1e-4), ("c128", 1e-7)])
+def test_compressed_adjoint_checkpoints(SV, dtype, eb):
+    """checkpoint_passes = 1: the forward sweep keeps psi after each of its 7
+    passes but the last, and the reverse sweep resumes from them, so psi's
+    error comes from the forward passes only (plus one reverse re-encoding)
+    instead of growing over forward and reverse sweeps. Both runs obey the
+    uncompute bound against the oracle, the energy (taken before the reverse
+    sweep) is the same, and the reverse sweep did use the checkpoints (the
+    gradients differ). Lambda's store, re-encoded in every reverse pass with
+    a step 2^ceil(log2 sum|c|) times psi's, is not checkpointed, so the
+    gradient error need not shrink."""
+    n, c, g = 14, 8, 2
+    gates, npar = W.hea(n, 2)
+    theta = W.normal_params(npar, seed=21)
+    terms = W.ising(n)
+    e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=9)
+    out = {}
+    for K in (0, 1):
+        with SV(n, c, eb, dtype=dtype, init_index=9, max_group_qubits=g, checkpoint_passes=K) as s:
+            e, gr = s.grad(gates, theta, terms)
+            st = s.stats()
+        out[K] = (e, gr, st)
+    P = out[0][2]["passes"]
+    assert out[0][2]["checkpoints"] == 0 and out[1][2]["checkpoints"] == P // 2 - 1 > 0
+    assert out[1][2]["checkpoint_bytes"] > 0
+    scale = sum(abs(t.coeff) for t in terms)
+    q = np.sqrt(2.0 * (1 << n)) * eb
+    arith = 0.0 if dtype == "c128" else 64 * 2.0 ** -24 * len(gates) * scale
+    for K in (0, 1):
+        e, gr, _ = out[K]
+        assert abs(e - e_o) <= scale * P * q + arith + 1e-12
+        assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
+    assert out[0][0] == out[1][0]
+    assert not np.array_equal(out[0][1], out[1][1])
