@@ -443,7 +443,7 @@ def run_apply(args, rank, world):
     st = sim.stats()
     gpu_launches = int(d["kernel_launches"])
     sim.close()
-    quality = state_quality(w, gates, terms, dev) if rank == 0 and not args.no_extras else {}
+    quality = state_quality(w, gates, terms, dev, args.remap) if rank == 0 and not args.no_extras else {}
 
     out = {
         "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world, "steps": args.steps,
@@ -481,12 +481,14 @@ def run_apply(args, rank, world):
         out["fidelity"] = quality["one_apply_vs_fp64"]
     if rank == 0 and not args.no_extras and w["n"] <= 32:
         out.update(comparator(args, gates, terms, energy, applies=args.warmup + args.steps + 1 + e_steps))
-    if rank == 0 and not args.no_extras and args.workload == "layers30":
+    default = args.workload == "layers30" and all(v is None for v in (args.eb, args.n, args.chunk, args.depth,
+                                                                      args.group))
+    if rank == 0 and not args.no_extras and default:
         out["adjoint_grad_s_per_step"] = adjoint_legs(dev)
     return out
 
 
-def state_quality(w, gates, terms, dev):
+def state_quality(w, gates, terms, dev, remap=False):
     """Error of one application of the workload's circuit to its seeded basis
     state (a fresh handle, as a user's first call), against an FP64
     reference: the uncompressed complex128 GPU path (pinned to the FP64
@@ -499,7 +501,7 @@ def state_quality(w, gates, terms, dev):
     n = w["n"]
     init = W.basis_index(n)
     kw = dict(dtype=w["dtype"], max_group_qubits=w["group"], device=dev,
-              relative_bound=bool(w.get("relative", False)), host_budget_bytes=host_budget())
+              relative_bound=bool(w.get("relative", False)), host_budget_bytes=host_budget(), remap_qubits=remap)
     out = {"reference": None}
     if w["circuit"] == "ghz":
         with StateVector(n, w["c"], w["eb"], **kw) as s:
