@@ -317,7 +317,9 @@ int sv_inner(sv_state* a, const sv_state* b, double* out_re, double* out_im);
  * grad[p] += Im<lambda_k|G_k|psi_k> in FP64 for every gate k with
  * param_index p (G = X, Y, Z for RX, RY, RZ).
  *   theta: host, nparams values. H: host Pauli terms. energy: host double.
- *   grad:  host, nparams doubles (overwritten).
+ *   grad:  host, nparams doubles (overwritten), or NULL for the energy alone
+ *          (the forward sweep and sv_expect: no lambda, no reverse sweep; the
+ *          stored state is then psi(theta)).
  * Compressed states keep lambda as a second compressed chunk store (its
  * quantisation step is the state's times the smallest power of two >= sum
  * |coeff|, since |lambda_i| <= ||H|| <= sum |coeff|) and run

@@ -139,6 +139,17 @@ class StateVector:
     def state(self) -> np.ndarray:
         return self.amplitudes_range(0, 1 << self.n)
 
+    def energy(self, gates: Sequence, theta: Sequence[float], terms: Sequence) -> float:
+        """<H> of the parameterised circuit at theta from |init_index>, with no
+        gradient (sv_grad with grad = NULL); the state is left at psi(theta)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        ga = _abi.gates_to_c(gates)
+        ta = _abi.terms_to_c(terms)
+        e = C.c_double(0.0)
+        _check(load().sv_grad(self._h, C.addressof(ga), len(gates), th.ctypes.data, th.size, C.addressof(ta),
+                              len(terms), C.byref(e), None), "sv_grad", self._h)
+        return e.value
+
     def grad(self, gates: Sequence, theta: Sequence[float], terms: Sequence):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         g = np.zeros(th.size, dtype=np.float64)

@@ -487,7 +487,7 @@ int sv_amplitudes_range(sv_state* s, uint64_t first, size_t count, double* out)
 int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* theta, size_t nparams,
             const sv_pauli_term* H, size_t nterms, double* energy, double* grad)
 {
-    if (!s || (ngates && !gates) || (nparams && (!theta || !grad)) || (nterms && !H) || !energy) return SV_ERR_ARG;
+    if (!s || (ngates && !gates) || (nparams && !theta) || (nterms && !H) || !energy) return SV_ERR_ARG;
     s->err.clear();
     for (size_t p = 0; p < nparams; p++)
         if (!std::isfinite(theta[p])) return fail(s, SV_ERR_ARG, "theta not finite");
@@ -499,7 +499,12 @@ int sv_grad(sv_state* s, const sv_gate* gates, size_t ngates, const double* thet
     cudaSetDevice(s->cfg.device);
     CallOrder order(s);
     std::lock_guard<std::mutex> lock(g_apply_mu);
-    if (s->mode == SV_UNCOMPRESSED)
+    if (!grad) {
+        // energy only: the forward sweep from |init_index> and the expectation
+        r = s->dtype == SV_C64 ? init_state<float>(s) : init_state<double>(s);
+        if (!r) r = s->dtype == SV_C64 ? apply_circuit<float>(s, pg, false) : apply_circuit<double>(s, pg, false);
+        if (!r) r = s->dtype == SV_C64 ? expect<float>(s, H, nterms, energy) : expect<double>(s, H, nterms, energy);
+    } else if (s->mode == SV_UNCOMPRESSED)
         r = s->dtype == SV_C64 ? grad_uncompressed<float>(s, pg, nparams, H, nterms, energy, grad)
                                : grad_uncompressed<double>(s, pg, nparams, H, nterms, energy, grad);
     else

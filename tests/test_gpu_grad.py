@@ -70,6 +70,32 @@ def test_autograd_function(SV):
     assert np.abs(theta.grad.numpy() - 2 * g_o).max() < 1e-11
 
 
+@pytest.mark.parametrize("mode", ["uncompressed", "compressed"])
+def test_energy_without_gradient(SV, mode):
+    """sv_grad with grad = NULL (StateVector.energy, and the autograd wrapper
+    under no_grad): the forward sweep and the expectation only -- no reverse
+    sweep launches -- with the energy sv_grad reports."""
+    torch = pytest.importorskip("torch")
+    from paper_2309_16979_gb300.autograd import expectation
+    n, layers = 14, 2
+    gates, npar = W.hea(n, layers)
+    theta = W.normal_params(npar, seed=31)
+    terms = W.ising(n)
+    with SV(n, 10, 1e-9, dtype="c128", mode=mode, max_group_qubits=2) as s:
+        e_full, _ = s.grad(gates, theta, terms)
+        a = s.stats()
+        e = s.energy(gates, theta, terms)
+        with torch.no_grad():
+            e_t = expectation(torch.tensor(theta, dtype=torch.float64, requires_grad=True), s, gates, terms)
+        b = s.stats()
+    assert b["jit_adjoint_launches"] == a["jit_adjoint_launches"]
+    e_o, _ = oracle.adjoint(n, gates, theta, terms)
+    scale = sum(abs(t.coeff) for t in terms)
+    # compressed: every pass re-quantises psi (L2 move <= sqrt(2 * 2^n) eb each)
+    tol = 1e-11 if mode == "uncompressed" else scale * b["passes"] * np.sqrt(2.0 * (1 << n)) * 1e-9 + 1e-12
+    assert abs(e - e_o) <= tol and abs(e_t.item() - e) <= 1e-15 and abs(e_full - e_o) <= tol
+
+
 @pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
 def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
     """psi and lambda both as compressed chunk stores. Each re-encoding of psi
