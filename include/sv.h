@@ -204,6 +204,9 @@ typedef struct sv_stats_t {
     /* host bytes of the psi checkpoints kept by the last compressed sv_grad
        (sv_config.checkpoint_passes), and how many there were */
     uint64_t checkpoint_bytes, checkpoints;
+    /* host wall time of the last sv_grad's forward sweep, lambda = H psi, and
+       reverse sweep (each ends with its GPU work complete) */
+    double t_grad_forward_s, t_grad_lambda_s, t_grad_reverse_s;
 } sv_stats_t;
 
 typedef struct sv_state sv_state; /* opaque, owned by the library */

@@ -64,7 +64,8 @@ class SvStats(C.Structure):
                 ("t_host_prepare_s", C.c_double), ("t_host_wait_s", C.c_double),
                 ("remap_swaps", C.c_uint64), ("jit_adjoint_launches", C.c_uint64),
                 ("host_pinned_bytes", C.c_uint64), ("checkpoint_bytes", C.c_uint64),
-                ("checkpoints", C.c_uint64)]
+                ("checkpoints", C.c_uint64), ("t_grad_forward_s", C.c_double), ("t_grad_lambda_s", C.c_double),
+                ("t_grad_reverse_s", C.c_double)]
 
 
 # every entry point declared in include/sv.h

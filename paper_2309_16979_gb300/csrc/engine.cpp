@@ -2021,6 +2021,7 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
     const std::vector<PassPlan> passes = plan_passes(gates, s->n, s->c, s->gmax);
     // the forward sweep (the same plan); with checkpoints pass by pass, keeping
     // psi after every K-th pass (ckpt[i]: psi after (i + 1) K passes)
+    const auto tf0 = std::chrono::steady_clock::now();
     const size_t K = (size_t)std::max(0, s->cfg.checkpoint_passes);
     std::vector<Checkpoint> ckpt;
     s->st.checkpoint_bytes = 0;
@@ -2078,7 +2079,11 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
         int up = 0;
         while (std::ldexp(1.0, up) < csum && up < 40) up++;
         s->kl = std::min(0, s->k + up);
+        const auto tl0 = std::chrono::steady_clock::now();
+        s->st.t_grad_forward_s = std::chrono::duration<double>(tl0 - tf0).count();
         if ((r = build_lambda<R>(s, phys, d_terms, d_part, nblocks, d_acc))) break;
+        const auto tr0 = std::chrono::steady_clock::now();
+        s->st.t_grad_lambda_s = std::chrono::duration<double>(tr0 - tl0).count();
         for (size_t p = passes.size(); p-- > 0;) {
             if ((r = run_pass_adjoint_compressed<R>(s, inv, passes[p], d_gpart, gpart_cap, d_acc, slot_params)))
                 break;
@@ -2093,6 +2098,7 @@ int grad_compressed(sv_state* s, const std::vector<PGate>& gates, size_t nparams
             break;
         }
         if ((r = wait_stream(s, s->s_comp))) break;
+        s->st.t_grad_reverse_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - tr0).count();
         *energy = acc[0];
         for (size_t p = 0; p < nparams; p++) grad[p] = 0;
         for (size_t j = 0; j < slot_params.size(); j++) grad[slot_params[j]] += acc[1 + j];

@@ -10,6 +10,9 @@
 // gates into tile sub-passes whose mixing qubits fit one on-chip tile.
 #include <algorithm>
 #include <future>
+#include <string>
+#include <unordered_map>
+#include <mutex>
 #include <cmath>
 
 #include "runtime.h"
@@ -403,10 +406,14 @@ static uint64_t lookahead_candidates(const std::vector<HOp>& ops, const std::vec
 //    which favours a qubit that is only useful together with another.
 // When no growth helps, the scan below grows the tile first-come in circuit
 // order.
+// groups[s][k]: the indices in `ops` of the ops fused into op k of sub-pass s
+using FuseGroups = std::vector<std::vector<std::vector<int>>>;
+
 static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int L, int t, int l, bool fuse,
-                                                int first_l, bool lookahead)
+                                                int first_l, bool lookahead, FuseGroups& groups)
 {
     std::vector<SubPlan> subs;
+    groups.clear();
     const uint64_t low = (l >= 64) ? ~0ull : ((1ull << l) - 1);
     const int fl = first_l > 0 ? std::min(first_l, t) : l;
     const uint64_t first_low = (fl >= 64) ? ~0ull : ((1ull << fl) - 1);
@@ -472,6 +479,7 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
             cur = bestn;
         }
         SubPlan sp;
+        std::vector<std::vector<int>> grp;
         std::vector<int> deferred;
         for (int oi : remaining) {
             const HOp& o = ops[oi];
@@ -484,8 +492,12 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
             const uint64_t need = o.mixL & ~T;
             if (popc(T | need) <= t) {
                 T |= need;
-                if (fuse && !sp.ops.empty() && try_fuse(sp.ops.back(), o)) continue;
+                if (fuse && !sp.ops.empty() && try_fuse(sp.ops.back(), o)) {
+                    grp.back().push_back(oi);
+                    continue;
+                }
                 sp.ops.push_back(o);
+                grp.push_back({oi});
             } else {
                 deferred.push_back(oi);
                 bL |= o.qL;
@@ -495,32 +507,100 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
         if (sp.ops.empty() && !deferred.empty() && deferred.size() == remaining.size()) {
             // no op fits a tile (cannot happen when t - l >= 2): stop instead of looping
             subs.clear();
+            groups.clear();
             return subs;
         }
         for (int p = 0; p < L && popc(T) < t; p++) T |= 1ull << p;
         sp.T = T;
         subs.push_back(std::move(sp));
+        groups.push_back(std::move(grp));
         remaining.swap(deferred);
     }
     return subs;
 }
+
+// Plans depend on the ops' structure only (kinds, positions, controls, what
+// they touch, whether they carry a parameter), never on their matrices, so
+// a process-wide cache keyed by that structure replays a plan for a circuit
+// seen before -- the same circuit re-applied, or new angles -- by fusing the
+// current ops' matrices along the cached groups. Bounded: cleared when full.
+namespace {
+struct PlanRecipe {
+    std::vector<uint64_t> T;
+    FuseGroups groups;
+};
+std::mutex g_plan_mu;
+std::unordered_map<std::string, PlanRecipe> g_plan_cache;
+constexpr size_t kPlanCacheMax = 512;
+
+std::string plan_key(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
+{
+    std::string k;
+    k.reserve(16 + ops.size() * 72);
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    const int32_t hdr[5] = {L, t, l, fuse ? 1 : 0, first_l};
+    put(hdr, sizeof(hdr));
+    for (const HOp& o : ops) {
+        const int32_t a[6] = {o.type, o.t[0], o.t[1], o.dsrc[0], o.dsrc[1], o.param >= 0 ? 1 : 0};
+        const uint64_t b[5] = {o.cL, o.cG, o.qL, o.qG, o.mixL};
+        put(a, sizeof(a));
+        put(b, sizeof(b));
+    }
+    return k;
+}
+
+bool replay(const std::vector<HOp>& ops, const PlanRecipe& rc, std::vector<SubPlan>& subs)
+{
+    subs.clear();
+    for (size_t s = 0; s < rc.T.size(); s++) {
+        SubPlan sp;
+        sp.T = rc.T[s];
+        for (const std::vector<int>& g : rc.groups[s]) {
+            HOp o = ops[g[0]];
+            for (size_t k = 1; k < g.size(); k++)
+                if (!try_fuse(o, ops[g[k]])) return false;
+            sp.ops.push_back(o);
+        }
+        subs.push_back(std::move(sp));
+    }
+    return true;
+}
+}  // namespace
 
 // Both growth rules (the lookahead on a second thread when the op list is
 // long enough to repay it); the plan with fewer sub-passes, the plain rule's
 // on a tie.
 std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
 {
-    if (ops.size() < 64) {
-        std::vector<SubPlan> a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false);
-        if (a.size() <= 1) return a;
-        std::vector<SubPlan> b = plan_subpasses_rule(ops, L, t, l, fuse, first_l, true);
-        return (!b.empty() && b.size() < a.size()) ? b : a;
+    const std::string key = plan_key(ops, L, t, l, fuse, first_l);
+    std::vector<SubPlan> subs;
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        auto it = g_plan_cache.find(key);
+        if (it != g_plan_cache.end() && replay(ops, it->second, subs)) return subs;
     }
-    std::future<std::vector<SubPlan>> fb =
-        std::async(std::launch::async, plan_subpasses_rule, std::cref(ops), L, t, l, fuse, first_l, true);
-    std::vector<SubPlan> a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false);
-    std::vector<SubPlan> b = fb.get();
-    return (!b.empty() && b.size() < a.size()) ? b : a;
+    FuseGroups ga, gb;
+    std::vector<SubPlan> a, b;
+    if (ops.size() < 64) {
+        a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false, ga);
+        if (a.size() > 1) b = plan_subpasses_rule(ops, L, t, l, fuse, first_l, true, gb);
+    } else {
+        std::future<std::vector<SubPlan>> fb = std::async(std::launch::async, [&]() {
+            return plan_subpasses_rule(ops, L, t, l, fuse, first_l, true, gb);
+        });
+        a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false, ga);
+        b = fb.get();
+    }
+    const bool use_b = !b.empty() && b.size() < a.size();
+    PlanRecipe rc;
+    for (const SubPlan& sp : use_b ? b : a) rc.T.push_back(sp.T);
+    rc.groups = use_b ? std::move(gb) : std::move(ga);
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        if (g_plan_cache.size() >= kPlanCacheMax) g_plan_cache.clear();
+        g_plan_cache[key] = std::move(rc);
+    }
+    return use_b ? b : a;
 }
 
 bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bool keep_first)

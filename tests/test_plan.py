@@ -95,3 +95,32 @@ def test_subpass_counts_small_tiles_terminate(sv):
     for tile in (2, 3, 5, 8, 13):
         p = sv.plan(n, 10, gates, max_group_qubits=3, tile_qubits=tile)
         assert p["subpasses"] >= p["passes"] >= 1
+
+
+def test_plan_cache_replays_the_fresh_plan():
+    """Sub-pass plans are cached by the ops' structure and replayed with the
+    current matrices: the kernels generated for a circuit seen before (and
+    for the same circuit with new angles) equal those of a fresh process."""
+    import os
+    import subprocess
+    import sys
+    from paper_2309_16979_gb300 import jit_sources
+    ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n, c = 20, 14
+    g1 = W.random_layers(n, 12, seed=5)
+    g2 = [W.Gate(x.kind, x.targets, x.controls, theta=x.theta * 0.731 + 0.2) if x.kind in W.ANGLE_KINDS else x
+          for x in g1]
+    code = ("import sys, json; sys.path.insert(0, %r); import workloads as W; "
+            "from paper_2309_16979_gb300 import jit_sources; "
+            "g = W.random_layers(%d, 12, seed=5); "
+            "g = [W.Gate(x.kind, x.targets, x.controls, theta=x.theta * 0.731 + 0.2) if x.kind in W.ANGLE_KINDS else x "
+            "for x in g]; print(json.dumps(jit_sources(%d, %d, g, max_group_qubits=3)))") % (ROOT, n, n, c)
+    fresh = subprocess.run([sys.executable, "-c", code], check=True, capture_output=True, text=True).stdout
+    import json
+    jit_sources(n, c, g1, max_group_qubits=3)  # fills the cache with g1's structure
+    cached = jit_sources(n, c, g2, max_group_qubits=3)
+    assert cached == json.loads(fresh)
+    for adjoint in (False, True):
+        a = jit_sources(n, c, g1, max_group_qubits=3, adjoint=adjoint)
+        b = jit_sources(n, c, g1, max_group_qubits=3, adjoint=adjoint)
+        assert a == b
