@@ -701,6 +701,7 @@ def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None
                            "grad_rel_l2": float(np.linalg.norm(g - g_r) / max(np.linalg.norm(g_r), 1e-300))})
         ref.close()
     return {"s_per_step": t_local, "steps": steps, "warmup": warmup, "params": npar, "gates": len(gates),
+            "group_qubits": st["group_qubits"],
             "parameter_sets": len(thetas), "launches_per_step": launches / steps,
             "generated_adjoint_launches_per_step": adj_launches / steps, "passes_per_step": passes,
             "clocks": clk, "errors_vs_fp64_gpu_adjoint": errors, "workload": describe(w, len(gates)), **ckpt}

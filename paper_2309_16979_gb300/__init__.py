@@ -74,7 +74,7 @@ class StateVector:
         cfg.checkpoint_passes = int(checkpoint_passes)
         self._callbacks = None
         if memory == "torch":
-            self._callbacks = _torch_memory(cfg, device)
+            self._callbacks = _torch_memory(cfg, device, release_cached=max_group_qubits == 0)
         elif memory != "cuda":
             raise ValueError("memory must be 'torch' or 'cuda'")
         h = C.c_void_p()
@@ -196,17 +196,23 @@ class StateVector:
         self.close()
 
 
-def _torch_memory(cfg, device: int):
+def _torch_memory(cfg, device: int, release_cached: bool = False):
     """Fill cfg's allocator and stream from torch: the caching allocator on
     `device`, torch's current stream there. Returns the ctypes callbacks,
     which must live as long as the handle. Without CUDA in torch the library
-    keeps its own allocator (sv_create then reports the missing device)."""
+    keeps its own allocator (sv_create then reports the missing device).
+    release_cached: hand torch's cached free blocks back to the driver first,
+    so that the library's automatic group size, which it takes from the
+    device's free memory, sees them."""
     try:
         import torch
     except ImportError:
         return None
     if not torch.cuda.is_available():
         return None
+    if release_cached:
+        with torch.cuda.device(device):
+            torch.cuda.empty_cache()
     stream = torch.cuda.current_stream(device)
 
     def alloc(nbytes, dev, ctx):
