@@ -702,6 +702,8 @@ def grad_measure(w, steps, warmup, dev, world=1, with_errors=True, max_sets=None
         ref.close()
     return {"s_per_step": t_local, "steps": steps, "warmup": warmup, "params": npar, "gates": len(gates),
             "group_qubits": st["group_qubits"],
+            "last_step_s": {k: round(st[f"t_grad_{k}_s"], 4) for k in ("forward", "lambda", "reverse")}
+            if mode == "compressed" else None,
             "parameter_sets": len(thetas), "launches_per_step": launches / steps,
             "generated_adjoint_launches_per_step": adj_launches / steps, "passes_per_step": passes,
             "clocks": clk, "errors_vs_fp64_gpu_adjoint": errors, "workload": describe(w, len(gates)), **ckpt}
@@ -721,7 +723,8 @@ def run_grad(args, rank, world):
             "config": {"workload": m["workload"], "n_qubits": w["n"], "params": m["params"], "gates": m["gates"],
                        "parameter_sets": m["parameter_sets"], "parallelism": f"replicas x{world}"},
             "gpu_launches": int(m["launches_per_step"] * args.steps), "clocks": m["clocks"],
-            "passes_per_step": m["passes_per_step"],
+            "passes_per_step": m["passes_per_step"], "group_qubits": m["group_qubits"],
+            "last_step_s": m["last_step_s"],
             "generated_adjoint_launches_per_step": m["generated_adjoint_launches_per_step"],
             "errors_vs_fp64_gpu_adjoint": m["errors_vs_fp64_gpu_adjoint"]}
 

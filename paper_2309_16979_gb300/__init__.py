@@ -47,7 +47,7 @@ class StateVector:
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,
                  jit: bool = True, relative_bound: bool = False, remap_qubits: bool = False,
-                 checkpoint_passes: int = 0, memory: str = "torch"):
+                 checkpoint_passes: int = 0, lambda_cache: bool = True, memory: str = "torch"):
         """memory="torch": the handle's device memory comes from torch's
         caching allocator (it shows in torch.cuda.memory_allocated()) and its
         calls order after the work queued on torch's current stream of the
@@ -72,6 +72,7 @@ class StateVector:
         cfg.relative_bound = int(relative_bound)
         cfg.remap_qubits = int(remap_qubits)
         cfg.checkpoint_passes = int(checkpoint_passes)
+        cfg.lambda_cache = int(lambda_cache)
         self._callbacks = None
         if memory == "torch":
             self._callbacks = _torch_memory(cfg, device, release_cached=max_group_qubits == 0)

@@ -43,7 +43,7 @@ class SvConfig(C.Structure):
                 ("pipeline_slots", C.c_int32), ("renormalize", C.c_int32), ("device", C.c_int32),
                 ("profile", C.c_int32), ("fuse_codec", C.c_int32), ("jit", C.c_int32),
                 ("relative_bound", C.c_int32), ("remap_qubits", C.c_int32),
-                ("checkpoint_passes", C.c_int32), ("device_alloc", DEVICE_ALLOC_FN), ("device_free", DEVICE_FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("checkpoint_passes", C.c_int32), ("lambda_cache", C.c_int32), ("device_alloc", DEVICE_ALLOC_FN), ("device_free", DEVICE_FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p), ("host_budget_bytes", C.c_uint64), ("timeout_s", C.c_double)]
 
 

@@ -289,6 +289,7 @@ void sv_config_default(sv_config* cfg)
     cfg->remap_qubits = 0;
     cfg->timeout_s = 600.0;
     cfg->checkpoint_passes = 0;
+    cfg->lambda_cache = 1;
     cfg->device_alloc = nullptr;
     cfg->device_free = nullptr;
     cfg->alloc_ctx = nullptr;

@@ -353,11 +353,13 @@ __global__ void k_copy_streams(const uint8_t* __restrict__ src, const ChunkOut* 
 }
 
 __global__ void k_gather_streams(const uint8_t* __restrict__ src, const uint64_t* __restrict__ bytes,
-                                 uint8_t* __restrict__ dst, size_t stride, StreamMoves mv)
+                                 size_t src_stride, uint8_t* __restrict__ dst, size_t dst_stride, StreamMoves mv)
 {
     const int i = blockIdx.y;
-    const uint64_t nb = bytes[mv.src[i]] < stride ? bytes[mv.src[i]] : stride;
-    copy_stream(src + (size_t)mv.src[i] * stride, dst + (size_t)mv.dst[i] * stride, nb);
+    uint64_t nb = bytes[mv.src[i]];
+    nb = nb < src_stride ? nb : src_stride;
+    nb = nb < dst_stride ? nb : dst_stride;
+    copy_stream(src + (size_t)mv.src[i] * src_stride, dst + (size_t)mv.dst[i] * dst_stride, nb);
 }
 
 }  // namespace
@@ -370,12 +372,12 @@ cudaError_t launch_copy_streams(const uint8_t* src, const ChunkOut* co, uint8_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, uint8_t* dst, size_t stride,
-                                  const StreamMoves& mv, cudaStream_t st)
+cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, size_t src_stride, uint8_t* dst,
+                                  size_t dst_stride, const StreamMoves& mv, cudaStream_t st)
 {
     if (mv.n <= 0) return cudaSuccess;
     if (mv.n > kMaxGroupChunks) return cudaErrorInvalidValue;
-    k_gather_streams<<<dim3(64, mv.n), 256, 0, st>>>(src, bytes, dst, stride, mv);
+    k_gather_streams<<<dim3(64, mv.n), 256, 0, st>>>(src, bytes, src_stride, dst, dst_stride, mv);
     return cudaGetLastError();
 }
 

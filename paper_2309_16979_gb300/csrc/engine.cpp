@@ -664,7 +664,7 @@ static int stream_passes(sv_state* s, const std::vector<PassPlan>& passes, std::
         if ((e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[slot], 0))) return cuda_fail(s, e, "wait h2d");
         if (s->slot_used[slot] && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[slot], 0)))
             return cuda_fail(s, e, "wait d2h");
-        if (mv.n && (e = launch_gather_streams(s->d_carry, s->d_carry_bytes, s->d_in[slot], s->stride, mv, s->s_comp)))
+        if (mv.n && (e = launch_gather_streams(s->d_carry, s->d_carry_bytes, s->stride, s->d_in[slot], s->stride, mv, s->s_comp)))
             return cuda_fail(s, e, "gather streams");
         if (mv.n) s->st.kernel_launches++;
         const uint64_t amp_bytes = (sizeof(R) * 2ull) << L;
@@ -1730,6 +1730,57 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
             return cuda_fail(s, e, "upload terms");
     }
     const size_t amp_bytes = sizeof(R) * 2;
+    // Every source chunk serves X.size() output chunks. When the whole
+    // compressed psi fits beside the staging buffers, it crosses the host
+    // link once into a device copy (chunk k at k * cstride) and each output
+    // chunk's sources are gathered from there on the device; otherwise each
+    // output chunk copies its sources from the host store.
+    uint8_t* d_cache = nullptr;
+    uint64_t* d_cbytes = nullptr;
+    size_t cstride = 0;
+    if (s->cfg.lambda_cache && X.size() > 1 && nch <= 65536) {
+        for (const ChunkRef& cr : s->cur) cstride = std::max<size_t>(cstride, cr.bytes);
+        cstride = (cstride + 255) & ~size_t(255);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        cudaGetLastError();
+        const bool fits = s->cfg.device_alloc || (double)cstride * nch <= 0.5 * (double)free_b;
+        if (fits && (dev_alloc(s, &d_cache, cstride * nch) || dev_alloc(s, &d_cbytes, sizeof(uint64_t) * nch))) {
+            cudaGetLastError();
+            dev_free(s, d_cache);
+            dev_free(s, d_cbytes);
+            d_cache = nullptr;
+            d_cbytes = nullptr;
+        }
+        if (d_cache) {
+            std::vector<uint64_t> lens(nch);
+            for (uint64_t k = 0; k < nch; k++) {
+                const ChunkRef& cr = s->cur[k];
+                lens[k] = cr.bytes;
+                if ((e = cudaMemcpyAsync(d_cache + k * cstride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
+                    return cuda_fail(s, e, "H2D psi cache");
+                s->st.bytes_h2d += cr.bytes;
+            }
+            if ((e = cudaMemcpyAsync(d_cbytes, lens.data(), sizeof(uint64_t) * nch, cudaMemcpyHostToDevice,
+                                     s->s_h2d)) ||
+                (e = cudaEventRecord(s->ev_h2d[0], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[0], 0)) ||
+                (e = cudaStreamSynchronize(s->s_h2d)))  // lens is a host temporary
+                return cuda_fail(s, e, "H2D psi cache");
+        }
+    }
+    struct CacheFree {
+        sv_state* s;
+        uint8_t*& a;
+        uint64_t*& b;
+        ~CacheFree()
+        {
+            if (a || b) {
+                cudaStreamSynchronize(s->s_comp);  // the gathers that read them
+                dev_free(s, a);
+                dev_free(s, b);
+            }
+        }
+    } cache_free{s, d_cache, d_cbytes};
     auto issue = [&](uint64_t k) -> int {
         const int sl = nset == 2 ? (int)(k & 1) : 0;
         const size_t base = (size_t)sl * m;
@@ -1737,19 +1788,35 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         uint8_t* amps = static_cast<uint8_t*>(s->d_amps) + (base << c) * amp_bytes;
         int launches = 0;
         for (size_t b = 0; b < nb; b++) {
-            // the set's streams are overwritten once its previous decode is done
-            if ((k >= (uint64_t)nset || b > 0) && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
-                return cuda_fail(s, e, "wait decode");
             GroupIn gin{};
-            for (size_t i = 0; i < batch[b].size(); i++) {
-                const ChunkRef& cr = s->cur[k ^ X[batch[b][i]]];
-                gin.bytes[i] = (uint32_t)cr.bytes;
-                if ((e = cudaMemcpyAsync(in + i * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
-                    return cuda_fail(s, e, "H2D chunk");
-                s->st.bytes_h2d += cr.bytes;
+            if (d_cache) {
+                // sources from the device copy of psi (compute stream: after the set's previous decode)
+                StreamMoves mv;
+                for (size_t i = 0; i < batch[b].size(); i++) {
+                    const uint64_t src = k ^ X[batch[b][i]];
+                    gin.bytes[i] = (uint32_t)s->cur[src].bytes;
+                    mv.src[mv.n] = (uint16_t)src;
+                    mv.dst[mv.n] = (uint16_t)i;
+                    mv.n++;
+                }
+                if ((e = launch_gather_streams(d_cache, d_cbytes, cstride, in, s->stride, mv, s->s_comp)))
+                    return cuda_fail(s, e, "gather sources");
+                launches++;
+            } else {
+                // the set's streams are overwritten once its previous decode is done
+                if ((k >= (uint64_t)nset || b > 0) && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
+                    return cuda_fail(s, e, "wait decode");
+                for (size_t i = 0; i < batch[b].size(); i++) {
+                    const ChunkRef& cr = s->cur[k ^ X[batch[b][i]]];
+                    gin.bytes[i] = (uint32_t)cr.bytes;
+                    if ((e = cudaMemcpyAsync(in + i * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice, s->s_h2d)))
+                        return cuda_fail(s, e, "H2D chunk");
+                    s->st.bytes_h2d += cr.bytes;
+                }
+                if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) ||
+                    (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)))
+                    return cuda_fail(s, e, "record h2d");
             }
-            if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)))
-                return cuda_fail(s, e, "record h2d");
             if ((e = launch_decode<R>(in, s->stride, c, s->dtype, (int)batch[b].size(), gin, amps, s->scale, s->d_err,
                                       s->s_comp)) ||
                 (e = cudaEventRecord(s->ev_h2d[2 + sl], s->s_comp)))

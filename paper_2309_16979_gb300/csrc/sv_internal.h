@@ -150,8 +150,10 @@ struct StreamMoves {
 };
 cudaError_t launch_copy_streams(const uint8_t* src, const ChunkOut* co, uint8_t* dst, uint64_t* bytes, size_t stride,
                                 int n, cudaStream_t st);
-cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, uint8_t* dst, size_t stride,
-                                  const StreamMoves& mv, cudaStream_t st);
+// stream mv.src[i] (at src + mv.src[i] * src_stride, bytes[mv.src[i]] long)
+// -> dst + mv.dst[i] * dst_stride
+cudaError_t launch_gather_streams(const uint8_t* src, const uint64_t* bytes, size_t src_stride, uint8_t* dst,
+                                  size_t dst_stride, const StreamMoves& mv, cudaStream_t st);
 
 // sum_t coeff_t <A| P_t |B> pieces; see reduce.cu
 struct PauliDev {

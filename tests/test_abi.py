@@ -44,7 +44,7 @@ def test_struct_sizes_match_header_layout():
     from paper_2309_16979_gb300 import _abi
     assert ctypes.sizeof(_abi.SvGate) == 4 * 4 + 8 + 8 + 8 + 32 * 8
     assert ctypes.sizeof(_abi.SvPauliTerm) == 24
-    assert ctypes.sizeof(_abi.SvConfig) == 4 + 4 + 8 + 4 * 11 + 4 + 4 * 8 + 8 + 8  # 4 bytes of padding
+    assert ctypes.sizeof(_abi.SvConfig) == 4 + 4 + 8 + 4 * 12 + 4 * 8 + 8 + 8
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):

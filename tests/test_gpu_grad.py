@@ -112,6 +112,10 @@ def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
     with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g) as s:
         e, gr = s.grad(gates, theta, terms)
         st = s.stats()
+    with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g, lambda_cache=False) as s:
+        e2, gr2 = s.grad(gates, theta, terms)
+    # the device copy of psi only changes where lambda's sources come from
+    assert e2 == e and np.array_equal(gr2, gr)
     P = st["passes"]  # forward + reverse passes
     scale = sum(abs(t.coeff) for t in terms)
     q = np.sqrt(2.0 * (1 << n)) * eb
@@ -132,8 +136,9 @@ def test_compressed_adjoint_agrees_with_uncompressed_gpu(SV):
     assert abs(e_c - e_u) < 1e-4 and np.abs(g_c - g_u).max() < 1e-4
 
 
+@pytest.mark.parametrize("cache", [True, False])
 @pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
-def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb):
+def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb, cache):
     """lambda = H psi when the terms' distinct high x-masks (0, 1, 2, 4, 8, 9
     over 4 high qubits) outnumber the 4 chunks a staging group holds: two
     batches per output chunk, accumulated before one encode. Same bound as
@@ -144,7 +149,7 @@ def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb):
     terms = [W.PauliTerm(0.3 + 0.05 * q, 1 << q, 0) for q in range(n)] + \
         [W.PauliTerm(0.5, (1 << 11) | (1 << 8), 1 << 3), W.PauliTerm(-0.7, (1 << 9) | 3, (1 << 9) | (1 << 2))]
     e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=6)
-    with SV(n, c, eb, dtype=dtype, init_index=6, max_group_qubits=2) as s:
+    with SV(n, c, eb, dtype=dtype, init_index=6, max_group_qubits=2, lambda_cache=cache) as s:
         e, gr = s.grad(gates, theta, terms)
         P = s.stats()["passes"]
     scale = sum(abs(t.coeff) for t in terms)
