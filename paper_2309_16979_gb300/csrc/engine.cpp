@@ -1339,6 +1339,115 @@ static int expect_pairs(sv_state* s, const std::vector<sv_pauli_term>& phys, dou
 // to cover the distinct high x-masks (the Ising chain: two sweeps). Chunk
 // copies to the device alternate between two stream slots so that the next
 // group's copies overlap this group's decode and reduction.
+// The terms of one sweep over a 2^L buffer, grouped for k_energy_tiles: each
+// set's terms have x-masks whose bits above local bit 7 fit the set's four
+// tile positions, so their partners are read from the tile in shared
+// memory; the rest (more than four such bits, or buffers under 2^12
+// amplitudes) go to k_energy. hd is reordered: the sets' terms first,
+// contiguous, then the rest.
+struct EnergyPlan {
+    std::vector<EnergyTiles> tiles;
+    std::vector<int> off, cnt;
+    int rest_off = 0, rest_cnt = 0;
+};
+
+static EnergyPlan energy_plan(std::vector<PauliDev>& hd, int L)
+{
+    EnergyPlan ep;
+    const int nt = (int)hd.size();
+    std::vector<int> rest, order(nt);
+    std::vector<uint64_t> H;                   // each set's tile positions above bit 7
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < nt; i++) order[i] = i;
+    if (L >= kEnergyTileBits) {
+        auto need = [&](int i) { return hd[i].xl & ~0xFFull; };
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return __builtin_popcountll(need(a)) > __builtin_popcountll(need(b)); });
+        std::vector<int> free_terms;
+        for (int i : order) {
+            const uint64_t nd = need(i);
+            if (__builtin_popcountll(nd) > 4) {
+                rest.push_back(i);
+                continue;
+            }
+            if (!nd) {
+                free_terms.push_back(i);
+                continue;
+            }
+            int best = -1, best_ov = -1;
+            for (size_t k = 0; k < H.size(); k++) {
+                if (__builtin_popcountll(H[k] | nd) > 4) continue;
+                const int ov = __builtin_popcountll(H[k] & nd);
+                if (ov > best_ov) {
+                    best = (int)k;
+                    best_ov = ov;
+                }
+            }
+            if (best < 0) {
+                H.push_back(nd);
+                members.push_back({i});
+            } else {
+                H[best] |= nd;
+                members[best].push_back(i);
+            }
+        }
+        if (!free_terms.empty()) {
+            if (H.empty()) {
+                H.push_back(0);
+                members.push_back({});
+            }
+            for (int i : free_terms) members[0].push_back(i);
+        }
+    } else {
+        rest = order;
+    }
+    std::vector<PauliDev> out;
+    for (size_t k = 0; k < H.size(); k++) {
+        uint64_t h = H[k];
+        for (int p = 8; p < L && __builtin_popcountll(h) < 4; p++) h |= 1ull << p;
+        EnergyTiles et{};
+        int j = 0, o = 0;
+        for (int p = 0; p < L; p++) {
+            if ((h >> p) & 1) et.hp[j++] = (int8_t)p;
+            else if (p >= 8) et.op[o++] = (int8_t)p;
+        }
+        et.nout = o;
+        ep.tiles.push_back(et);
+        ep.off.push_back((int)out.size());
+        for (int i : members[k]) out.push_back(hd[i]);
+        ep.cnt.push_back((int)out.size() - ep.off.back());
+    }
+    ep.rest_off = (int)out.size();
+    for (int i : rest) out.push_back(hd[i]);
+    ep.rest_cnt = (int)out.size() - ep.rest_off;
+    hd.swap(out);
+    return ep;
+}
+
+// <psi|H|psi> partial sums of a 2^L buffer added to *d_acc on stream st.
+template <typename R>
+static cudaError_t energy_sweep(sv_state* s, const void* psi, int L, uint64_t gbase, const EnergyPlan& ep,
+                                const PauliDev* d_terms, double* d_part, int nblocks, double* d_acc)
+{
+    cudaError_t e;
+    for (size_t k = 0; k < ep.tiles.size(); k++) {
+        if (!ep.cnt[k]) continue;
+        if ((e = launch_energy_tiles<R>(psi, L, gbase, ep.tiles[k], d_terms + ep.off[k], ep.cnt[k], d_part, nblocks,
+                                        s->s_comp)) ||
+            (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp)))
+            return e;
+        s->st.kernel_launches += 2;
+    }
+    if (ep.rest_cnt) {
+        if ((e = launch_energy_partials<R>(psi, L, gbase, d_terms + ep.rest_off, ep.rest_cnt, d_part, nblocks,
+                                           s->s_comp)) ||
+            (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp)))
+            return e;
+        s->st.kernel_launches += 2;
+    }
+    return cudaSuccess;
+}
+
 template <typename R>
 static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, double* out_re)
 {
@@ -1396,6 +1505,7 @@ static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, 
             }
             hd.push_back(pauli_dev(t, xl, zl, t.zmask & ~lowmask & ~(S << c), 1.0));
         }
+        const EnergyPlan ep = energy_plan(hd, c + g);
         // the previous sweep's reductions read d_terms: the upload waits for them
         if ((e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice, s->s_comp)) ||
             (e = cudaStreamSynchronize(s->s_comp))) {
@@ -1427,13 +1537,11 @@ static int expect_streamed(sv_state* s, const std::vector<sv_pauli_term>& phys, 
                 (e = launch_decode<R>(s->d_in[slot], s->stride, c, s->dtype, gch, gin, s->d_amps, s->scale, s->d_err,
                                       s->s_comp)) ||
                 (e = cudaEventRecord(s->ev_h2d[2 + slot], s->s_comp)) ||
-                (e = launch_energy_partials<R>(s->d_amps, c + g, base << c, d_terms, (int)hd.size(), d_part, nblocks,
-                                               s->s_comp)) ||
-                (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp))) {
+                (e = energy_sweep<R>(s, s->d_amps, c + g, base << c, ep, d_terms, d_part, nblocks, d_acc))) {
                 r = cuda_fail(s, e, "expect group");
                 break;
             }
-            s->st.kernel_launches += 3;
+            s->st.kernel_launches += 1;
         }
     }
     double acc = 0;
@@ -1470,6 +1578,7 @@ int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_r
     const int nblocks = reduce_blocks_for(1ull << s->n);
     std::vector<PauliDev> hd;
     for (const auto& t : phys) hd.push_back(pauli_dev(t, t.xmask, t.zmask, 0, 1.0));
+    const EnergyPlan ep = energy_plan(hd, s->n);
     PauliDev* d_terms = nullptr;
     double *d_part = nullptr, *d_acc = nullptr;
     cudaError_t e;
@@ -1482,12 +1591,10 @@ int expect(sv_state* s, const sv_pauli_term* terms, size_t nterms, double* out_r
     double acc = 0;
     if ((e = cudaMemcpyAsync(d_terms, hd.data(), sizeof(PauliDev) * nterms, cudaMemcpyHostToDevice, s->s_comp)) ||
         (e = cudaMemsetAsync(d_acc, 0, sizeof(double), s->s_comp)) ||
-        (e = launch_energy_partials<R>(s->d_state, s->n, 0, d_terms, (int)nterms, d_part, nblocks, s->s_comp)) ||
-        (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp)) ||
+        (e = energy_sweep<R>(s, s->d_state, s->n, 0, ep, d_terms, d_part, nblocks, d_acc)) ||
         (e = cudaMemcpyAsync(&acc, d_acc, sizeof(double), cudaMemcpyDeviceToHost, s->s_comp)))
         r = cuda_fail(s, e, "energy");
     if (!r) r = wait_stream(s, s->s_comp);
-    s->st.kernel_launches += 2;
     dev_free(s, d_terms);
     dev_free(s, d_part);
     dev_free(s, d_acc);

@@ -175,6 +175,102 @@ k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gba
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The same sum as k_energy for terms whose x-masks lie in a tile's bits
+// (local bits 0..7 and et.hp[0..3]): a CTA loads a tile of 4096 amplitudes
+// (16 rows of 256 contiguous ones) into shared memory and every term's
+// partner is read there, so the buffer is read once for all these terms
+// instead of once more per term. Both members of a pair are evaluated (the
+// coefficient is not doubled). Thread t holds tile positions t + 256k,
+// k = 0..15; a tile position's local index is the tile base | t | the
+// offsets of k's bits on hp. Per tile, products in the amplitude precision;
+// across tiles FP64; a fixed reduction tree.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint64_t gbase, const EnergyTiles et,
+               const PauliDev* __restrict__ terms, int nterms, double* __restrict__ partials)
+{
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char tile_smem[];  // 4096 amplitudes
+    T* const tile = reinterpret_cast<T*>(tile_smem);
+    __shared__ double red[kThreads / 32];
+    __shared__ uint32_t sxt[kMaxEnergyTerms];   // x-mask on tile bits (bit 8 + i <-> hp[i])
+    __shared__ uint64_t szl[kMaxEnergyTerms];   // z-mask on local bits
+    __shared__ uint32_t srow[kMaxEnergyTerms];  // bit k: parity of z on k's row offset; bit 16: on t's bits
+    __shared__ R sre[kMaxEnergyTerms], sim[kMaxEnergyTerms];
+    const uint32_t t = threadIdx.x;
+    uint64_t rowoff[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        uint64_t o = 0;
+        for (int i = 0; i < 4; i++)
+            if ((k >> i) & 1) o |= 1ull << et.hp[i];
+        rowoff[k] = o;
+    }
+    for (int q = t; q < nterms; q += kThreads) {
+        const PauliDev P = terms[q];
+        uint32_t xt = (uint32_t)(P.xl & 0xFFull);
+        for (int i = 0; i < 4; i++) xt |= (uint32_t)((P.xl >> et.hp[i]) & 1ull) << (8 + i);
+        sxt[q] = xt;
+        szl[q] = P.zl;
+        const double cf = (__popcll(gbase & P.zg) & 1) ? -P.coeff : P.coeff;
+        const int ny = P.ny & 3;
+        sre[q] = (R)(ny == 0 ? cf : ny == 2 ? -cf : 0.0);
+        sim[q] = (R)(ny == 1 ? -cf : ny == 3 ? cf : 0.0);
+        uint32_t tab = 0;
+        for (int k = 0; k < 16; k++) {
+            uint64_t o = 0;
+            for (int i = 0; i < 4; i++)
+                if ((k >> i) & 1) o |= 1ull << et.hp[i];
+            tab |= (uint32_t)(__popcll(o & P.zl) & 1) << k;
+        }
+        srow[q] = tab;
+    }
+    double acc = 0;
+    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        uint64_t tb = 0;
+        for (int i = 0; i < et.nout; i++)
+            if ((tl >> i) & 1ull) tb |= 1ull << et.op[i];
+        T a[16];
+        R n2[16], e[16];
+        __syncthreads();  // the previous tile's partner reads are done
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            a[k] = psi[tb + t + rowoff[k]];
+            tile[t + 256u * k] = a[k];
+            n2[k] = a[k].x * a[k].x + a[k].y * a[k].y;
+            e[k] = (R)0;
+        }
+        __syncthreads();
+        const uint64_t jt = tb | t;
+        for (int q = 0; q < nterms; q++) {
+            const uint32_t xt = sxt[q];
+            const uint32_t sg = (__popcll(jt & szl[q]) & 1) ? ~srow[q] : srow[q];  // bit k: sign of position k
+            const R cr = sre[q];
+            if (xt == 0) {
+#pragma unroll
+                for (int k = 0; k < 16; k++) e[k] += (((sg >> k) & 1u) ? -cr : cr) * n2[k];
+                continue;
+            }
+            const R ci = sim[q];
+            const uint32_t pt = t ^ (xt & 0xFFu), pk = xt >> 8;
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const T b = tile[pt + 256u * ((uint32_t)k ^ pk)];
+                const R re = b.x * a[k].x + b.y * a[k].y;
+                const R im = b.x * a[k].y - b.y * a[k].x;
+                const R v = cr * re + ci * im;
+                e[k] += ((sg >> k) & 1u) ? -v : v;
+            }
+        }
+        R sub = (R)0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) sub += e[k];
+        acc += (double)sub;
+    }
+    const double sblk = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sblk;
+}
+
 // out[t] += sum over blocks of partials[t * nblocks + b], one CTA per term, fixed order
 __global__ void __launch_bounds__(kThreads)
 k_sum_partials(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
@@ -370,6 +466,26 @@ cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks,
 }
 
 template <typename R>
+cudaError_t launch_energy_tiles(const void* psi, int Lbits, uint64_t gbase, const EnergyTiles& et,
+                                const PauliDev* terms, int nterms, double* partials, int nblocks, cudaStream_t st)
+{
+    if (Lbits < kEnergyTileBits || nterms > kMaxEnergyTerms) return cudaErrorInvalidValue;
+    const uint64_t ntiles = 1ull << (Lbits - kEnergyTileBits);
+    const int smem = (int)(sizeof(typename V2<R>::T) << kEnergyTileBits);
+    static thread_local int attr_device = -1;  // the attribute is per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_energy_tiles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_device = dev;
+    }
+    k_energy_tiles<R><<<nblocks, kThreads, smem, st>>>(static_cast<const typename V2<R>::T*>(psi), ntiles, gbase, et,
+                                                      terms, nterms, partials);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uint64_t* dest, uint64_t m,
                           double* out, cudaStream_t st)
 {
@@ -435,6 +551,8 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
                                                   double*, int, cudaStream_t);                                  \
     template cudaError_t launch_energy_partials<R>(const void*, int, uint64_t, const PauliDev*, int, double*, int, \
                                                    cudaStream_t);                                                \
+    template cudaError_t launch_energy_tiles<R>(const void*, int, uint64_t, const EnergyTiles&, const PauliDev*, \
+                                                int, double*, int, cudaStream_t);                               \
     template cudaError_t launch_gather<R>(const void*, const uint64_t*, const uint64_t*, uint64_t, double*,     \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \

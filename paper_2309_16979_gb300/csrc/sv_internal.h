@@ -180,6 +180,23 @@ int max_energy_terms();
 cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks, double* out,
                                 cudaStream_t st);
 
+// Tiles of 4096 amplitudes of a 2^Lbits buffer for k_energy_tiles: local bits
+// 0..7 and the four local positions hp[0..3] (all >= 8); op[0..nout) are the
+// other positions, ascending (the tile index's bits, low first).
+struct EnergyTiles {
+    int8_t hp[4];
+    int8_t op[kMaxLocalQubits];
+    int32_t nout;
+};
+constexpr int kEnergyTileBits = 12;
+
+// partials[0..nblocks) = per-CTA shares of sum_t <psi|P_t|psi> over the
+// buffer for terms whose x-masks lie in the tiles' bits (at most
+// max_energy_terms()); partners read from the tile in shared memory
+template <typename R>
+cudaError_t launch_energy_tiles(const void* psi, int Lbits, uint64_t gbase, const EnergyTiles& et,
+                                const PauliDev* terms, int nterms, double* partials, int nblocks, cudaStream_t st);
+
 template <typename R>
 cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uint64_t* dest,
                           uint64_t m, double* out, cudaStream_t st);

@@ -402,3 +402,29 @@ def test_remapped_calls_accumulate_and_grad_resets(SV):
     csum = sum(abs(t.coeff) for t in H)
     assert abs(e - e_want) <= 1e-4 * csum
     assert np.abs(gr - g_want).max() <= 1e-4 * csum
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation_tile_sets_and_remainder(SV, dtype):
+    """Terms whose x bits above local bit 7 fit four tile positions are
+    evaluated from shared-memory tiles, several tile sets per sweep; terms
+    with five or more such bits by the strip kernel; one sum. n = 18, in HBM
+    and as compressed groups of 2^15 amplitudes, against the oracle on the
+    state the GPU holds."""
+    n = 18
+    gates = W.random_layers(n, 4, seed=12)
+    rng = np.random.default_rng(13)
+    terms = [W.PauliTerm(0.5 - 0.03 * q, 1 << q, int(rng.integers(0, 1 << n))) for q in range(n)]
+    terms += [W.PauliTerm(0.2, (1 << 9) | (1 << 12) | (1 << 15) | 5, 1 << 16)]       # 3 high bits + low
+    wide = 0
+    for q in (8, 10, 11, 13, 14, 17):
+        wide |= 1 << q
+    terms += [W.PauliTerm(-0.35, wide, 3), W.PauliTerm(0.15, wide | 1, wide)]       # 6 high bits: remainder
+    terms += W.ising(n, seed=6) + W.random_pauli_sum(n, 12, seed=14)
+    tol = 1e-12 if dtype == "c128" else 2e-6
+    for mode in ("uncompressed", "compressed"):
+        with SV(n, 12, 1e-9 if dtype == "c128" else 1e-6, mode=mode, dtype=dtype, max_group_qubits=3) as s:
+            s.apply(gates)
+            got = s.expect(terms)
+            held = s.state()
+        assert abs(got - oracle.expect(n, held, terms)) <= tol * sum(abs(t.coeff) for t in terms), mode
