@@ -364,40 +364,82 @@ k_hamiltonian(const typename V2<R>::T* __restrict__ psi, typename V2<R>::T* __re
 // s << c); term t reads slot terms[t].pad, its low x-mask flips local bits,
 // and the sign from its z-mask on the source chunk's high bits is already in
 // its coefficient.
+// Each thread builds a strip of 8 outputs (k = strip base + thread + 256 m),
+// so the 8 source reads of a term are in flight together; the terms are
+// staged in shared memory in batches, and every output sums its terms in
+// their order.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_ham_chunk(const typename V2<R>::T* __restrict__ psi_slots, typename V2<R>::T* __restrict__ lam, int c,
             const PauliDev* __restrict__ terms, int nterms, int accumulate)
 {
     using T = typename V2<R>::T;
+    constexpr int kStrip = 8, kBatch = 256;
+    __shared__ uint64_t sxl[kBatch], szl[kBatch];
+    __shared__ R sc[kBatch];
+    __shared__ int32_t spn[kBatch];  // pad << 2 | ny
     const uint64_t count = 1ull << c;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        R ar = (R)0, ai = (R)0;
-        if (accumulate) {
-            const T l = lam[k];
-            ar = l.x;
-            ai = l.y;
-        }
-        for (int tt = 0; tt < nterms; tt++) {
-            const PauliDev& P = terms[tt];
-            const uint64_t src = k ^ P.xl;
-            const T v = psi_slots[((uint64_t)P.pad << c) + src];
-            R vr = v.x, vi = v.y, tr;
-            switch (P.ny & 3) {
-                case 1: tr = vr; vr = -vi; vi = tr; break;
-                case 2: vr = -vr; vi = -vi; break;
-                case 3: tr = vr; vr = vi; vi = -tr; break;
-                default: break;
+    const uint64_t span = (uint64_t)kThreads * kStrip;
+    for (uint64_t s0 = (uint64_t)blockIdx.x * span; s0 < count; s0 += (uint64_t)gridDim.x * span) {
+        R ar[kStrip], ai[kStrip];
+#pragma unroll
+        for (int m = 0; m < kStrip; m++) {
+            const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
+            ar[m] = ai[m] = (R)0;
+            if (accumulate && k < count) {
+                const T l = lam[k];
+                ar[m] = l.x;
+                ai[m] = l.y;
             }
-            const R cf = (__popcll(src & P.zl) & 1) ? (R)(-P.coeff) : (R)P.coeff;
-            ar += cf * vr;
-            ai += cf * vi;
         }
-        T o;
-        o.x = ar;
-        o.y = ai;
-        lam[k] = o;
+        for (int b0 = 0; b0 < nterms; b0 += kBatch) {
+            const int nb = min(kBatch, nterms - b0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < nb; q += kThreads) {
+                const PauliDev& P = terms[b0 + q];
+                sxl[q] = P.xl;
+                szl[q] = P.zl;
+                sc[q] = (R)P.coeff;
+                spn[q] = (P.pad << 2) | (P.ny & 3);
+            }
+            __syncthreads();
+            for (int q = 0; q < nb; q++) {
+                const uint64_t xl = sxl[q], zl = szl[q];
+                const R cf0 = sc[q];
+                const int pn = spn[q], ny = pn & 3;
+                const T* const src_slot = psi_slots + ((uint64_t)(pn >> 2) << c);
+                T v[kStrip];
+#pragma unroll
+                for (int m = 0; m < kStrip; m++) {
+                    const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
+                    v[m] = k < count ? src_slot[k ^ xl] : T{(R)0, (R)0};
+                }
+#pragma unroll
+                for (int m = 0; m < kStrip; m++) {
+                    const uint64_t src = (s0 + threadIdx.x + (uint64_t)m * kThreads) ^ xl;
+                    R vr = v[m].x, vi = v[m].y, tr;
+                    switch (ny) {
+                        case 1: tr = vr; vr = -vi; vi = tr; break;
+                        case 2: vr = -vr; vi = -vi; break;
+                        case 3: tr = vr; vr = vi; vi = -tr; break;
+                        default: break;
+                    }
+                    const R cf = (__popcll(src & zl) & 1) ? -cf0 : cf0;
+                    ar[m] += cf * vr;
+                    ai[m] += cf * vi;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kStrip; m++) {
+            const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
+            if (k < count) {
+                T o;
+                o.x = ar[m];
+                o.y = ai[m];
+                lam[k] = o;
+            }
+        }
     }
 }
 
@@ -532,7 +574,7 @@ cudaError_t launch_ham_chunk(const void* psi_slots, void* lam, int c, const Paul
 {
     using T = typename V2<R>::T;
     const uint64_t count = 1ull << c;
-    const unsigned blocks = (unsigned)std::min<uint64_t>((count + kThreads - 1) / kThreads, 152ull * 32);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((count + kThreads * 8 - 1) / (kThreads * 8), 152ull * 8);
     k_ham_chunk<R><<<blocks, kThreads, 0, st>>>(static_cast<const T*>(psi_slots), static_cast<T*>(lam), c, terms,
                                                nterms, accumulate ? 1 : 0);
     return cudaGetLastError();
