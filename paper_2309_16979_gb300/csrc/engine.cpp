@@ -95,6 +95,7 @@ int check_device_error(sv_state* s)
         wait_stream(s, s->s_comp);
         if (h & kErrCorrupt) return fail(s, SV_ERR_CORRUPT, "compressed chunk stream failed validation");
         if (h & kErrRange) return fail(s, SV_ERR_RANGE, "amplitude outside the quantiser range or not finite");
+        if (h & kErrWait) return fail(s, SV_ERR_TIMEOUT, "a kernel's wait for its copies exceeded its limit");
     }
     return SV_OK;
 }
@@ -1433,7 +1434,7 @@ static cudaError_t energy_sweep(sv_state* s, const void* psi, int L, uint64_t gb
     for (size_t k = 0; k < ep.tiles.size(); k++) {
         if (!ep.cnt[k]) continue;
         if ((e = launch_energy_tiles<R>(psi, L, gbase, ep.tiles[k], d_terms + ep.off[k], ep.cnt[k], d_part, nblocks,
-                                        s->s_comp)) ||
+                                        s->d_err, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_acc, s->s_comp)))
             return e;
         s->st.kernel_launches += 2;

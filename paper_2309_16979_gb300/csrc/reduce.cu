@@ -175,27 +175,74 @@ k_energy(const typename V2<R>::T* __restrict__ psi, uint64_t count, uint64_t gba
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// Bulk (TMA) copies into shared memory completing on an mbarrier, and a
+// bounded wait for them.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bytes (a multiple of 16; both addresses 16-byte aligned) from global to shared
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// true once the barrier's phase of this parity has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 // The same sum as k_energy for terms whose x-masks lie in a tile's bits
-// (local bits 0..7 and et.hp[0..3]): a CTA loads a tile of 4096 amplitudes
-// (16 rows of 256 contiguous ones) into shared memory and every term's
+// (local bits 0..7 and et.hp[0..3]): a CTA holds a tile of 4096 amplitudes
+// (16 rows of 256 contiguous ones) in shared memory and every term's
 // partner is read there, so the buffer is read once for all these terms
 // instead of once more per term. Both members of a pair are evaluated (the
 // coefficient is not doubled). Thread t holds tile positions t + 256k,
 // k = 0..15; a tile position's local index is the tile base | t | the
-// offsets of k's bits on hp. Per tile, products in the amplitude precision;
-// across tiles FP64; a fixed reduction tree.
+// offsets of k's bits on hp. Tiles arrive as 16 bulk row copies on an
+// mbarrier, double-buffered: the CTA's next tile is in flight while the
+// current one is evaluated. Per tile, products in the amplitude precision;
+// across tiles FP64; a fixed reduction tree. A wait that exceeds its limit
+// sets kErrWait and ends the CTA's work.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint64_t gbase, const EnergyTiles et,
-               const PauliDev* __restrict__ terms, int nterms, double* __restrict__ partials)
+               const PauliDev* __restrict__ terms, int nterms, double* __restrict__ partials, int* __restrict__ err)
 {
     using T = typename V2<R>::T;
-    extern __shared__ __align__(16) unsigned char tile_smem[];  // 4096 amplitudes
-    T* const tile = reinterpret_cast<T*>(tile_smem);
+    constexpr uint32_t kTile = 1u << kEnergyTileBits;
+    extern __shared__ __align__(128) unsigned char tile_smem[];  // two tiles of 4096 amplitudes
+    T* const buf = reinterpret_cast<T*>(tile_smem);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int ok_s;
     __shared__ double red[kThreads / 32];
     __shared__ uint32_t sxt[kMaxEnergyTerms];   // x-mask on tile bits (bit 8 + i <-> hp[i])
     __shared__ uint64_t szl[kMaxEnergyTerms];   // z-mask on local bits
-    __shared__ uint32_t srow[kMaxEnergyTerms];  // bit k: parity of z on k's row offset; bit 16: on t's bits
+    __shared__ uint32_t srow[kMaxEnergyTerms];  // bit k: parity of z on k's row offset
     __shared__ R sre[kMaxEnergyTerms], sim[kMaxEnergyTerms];
     const uint32_t t = threadIdx.x;
     uint64_t rowoff[16];
@@ -205,6 +252,25 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
         for (int i = 0; i < 4; i++)
             if ((k >> i) & 1) o |= 1ull << et.hp[i];
         rowoff[k] = o;
+    }
+    auto tile_base = [&](uint64_t tl) {
+        uint64_t tb = 0;
+        for (int i = 0; i < et.nout; i++)
+            if ((tl >> i) & 1ull) tb |= 1ull << et.op[i];
+        return tb;
+    };
+    // thread 0 issues a tile's 16 row copies into buffer b
+    auto issue = [&](uint64_t tl, int b) {
+        const uint64_t tb = tile_base(tl);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of b came first
+        mbar_expect_tx(&bar[b], kTile * (uint32_t)sizeof(T));
+        for (int k = 0; k < 16; k++)
+            bulk_load(buf + b * kTile + 256u * k, psi + tb + rowoff[k], 256u * (uint32_t)sizeof(T), &bar[b]);
+    };
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int q = t; q < nterms; q += kThreads) {
         const PauliDev P = terms[q];
@@ -217,31 +283,42 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
         sre[q] = (R)(ny == 0 ? cf : ny == 2 ? -cf : 0.0);
         sim[q] = (R)(ny == 1 ? -cf : ny == 3 ? cf : 0.0);
         uint32_t tab = 0;
-        for (int k = 0; k < 16; k++) {
-            uint64_t o = 0;
-            for (int i = 0; i < 4; i++)
-                if ((k >> i) & 1) o |= 1ull << et.hp[i];
-            tab |= (uint32_t)(__popcll(o & P.zl) & 1) << k;
-        }
+        for (int k = 0; k < 16; k++) tab |= (uint32_t)(__popcll(rowoff[k] & P.zl) & 1) << k;
         srow[q] = tab;
     }
+    __syncthreads();
+    bool pending[2] = {false, false};  // thread 0: a copy into the buffer not yet waited for
+    if (t == 0 && blockIdx.x < ntiles) {
+        issue(blockIdx.x, 0);
+        pending[0] = true;
+    }
     double acc = 0;
-    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-        uint64_t tb = 0;
-        for (int i = 0; i < et.nout; i++)
-            if ((tl >> i) & 1ull) tb |= 1ull << et.op[i];
+    uint32_t it = 0;
+    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, it++) {
+        const int b = (int)(it & 1);
+        const uint32_t parity = (it >> 1) & 1u;
+        if (t == 0) {
+            // the other buffer was last read in the previous iteration (a barrier ago)
+            if (tl + gridDim.x < ntiles) {
+                issue(tl + gridDim.x, b ^ 1);
+                pending[b ^ 1] = true;
+            }
+            ok_s = mbar_wait(&bar[b], parity, kWaitPolls) ? 1 : 0;
+            pending[b] = !ok_s;
+        }
+        __syncthreads();
+        if (!ok_s) break;
+        if (t != 0) mbar_wait(&bar[b], parity, kWaitPolls);  // complete already: this thread's acquire
+        const T* const tile = buf + b * kTile;
+        const uint64_t jt = tile_base(tl) | t;
         T a[16];
         R n2[16], e[16];
-        __syncthreads();  // the previous tile's partner reads are done
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-            a[k] = psi[tb + t + rowoff[k]];
-            tile[t + 256u * k] = a[k];
+            a[k] = tile[t + 256u * k];
             n2[k] = a[k].x * a[k].x + a[k].y * a[k].y;
             e[k] = (R)0;
         }
-        __syncthreads();
-        const uint64_t jt = tb | t;
         for (int q = 0; q < nterms; q++) {
             const uint32_t xt = sxt[q];
             const uint32_t sg = (__popcll(jt & szl[q]) & 1) ? ~srow[q] : srow[q];  // bit k: sign of position k
@@ -255,9 +332,9 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
             const uint32_t pt = t ^ (xt & 0xFFu), pk = xt >> 8;
 #pragma unroll
             for (int k = 0; k < 16; k++) {
-                const T b = tile[pt + 256u * ((uint32_t)k ^ pk)];
-                const R re = b.x * a[k].x + b.y * a[k].y;
-                const R im = b.x * a[k].y - b.y * a[k].x;
+                const T bb = tile[pt + 256u * ((uint32_t)k ^ pk)];
+                const R re = bb.x * a[k].x + bb.y * a[k].y;
+                const R im = bb.x * a[k].y - bb.y * a[k].x;
                 const R v = cr * re + ci * im;
                 e[k] += ((sg >> k) & 1u) ? -v : v;
             }
@@ -266,6 +343,13 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
 #pragma unroll
         for (int k = 0; k < 16; k++) sub += e[k];
         acc += (double)sub;
+        __syncthreads();  // this buffer's reads are done before it is refilled
+    }
+    if (t == 0 && (pending[0] || pending[1])) {
+        atomicOr(err, kErrWait);
+        // copies still in flight must land before the CTA's shared memory goes away
+        for (int b = 0; b < 2; b++)
+            if (pending[b]) mbar_wait(&bar[b], ((it + (b != (int)(it & 1))) >> 1) & 1u, kWaitPolls);
     }
     const double sblk = block_sum(acc, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = sblk;
@@ -509,11 +593,12 @@ cudaError_t launch_sum_partials(const double* partials, int nterms, int nblocks,
 
 template <typename R>
 cudaError_t launch_energy_tiles(const void* psi, int Lbits, uint64_t gbase, const EnergyTiles& et,
-                                const PauliDev* terms, int nterms, double* partials, int nblocks, cudaStream_t st)
+                                const PauliDev* terms, int nterms, double* partials, int nblocks, int* err,
+                                cudaStream_t st)
 {
     if (Lbits < kEnergyTileBits || nterms > kMaxEnergyTerms) return cudaErrorInvalidValue;
     const uint64_t ntiles = 1ull << (Lbits - kEnergyTileBits);
-    const int smem = (int)(sizeof(typename V2<R>::T) << kEnergyTileBits);
+    const int smem = (int)(2 * sizeof(typename V2<R>::T) << kEnergyTileBits);  // two tile buffers
     static thread_local int attr_device = -1;  // the attribute is per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -523,7 +608,7 @@ cudaError_t launch_energy_tiles(const void* psi, int Lbits, uint64_t gbase, cons
         attr_device = dev;
     }
     k_energy_tiles<R><<<nblocks, kThreads, smem, st>>>(static_cast<const typename V2<R>::T*>(psi), ntiles, gbase, et,
-                                                      terms, nterms, partials);
+                                                      terms, nterms, partials, err);
     return cudaGetLastError();
 }
 
@@ -594,7 +679,7 @@ cudaError_t launch_dot(const void* A, const void* B, uint64_t count, double* par
     template cudaError_t launch_energy_partials<R>(const void*, int, uint64_t, const PauliDev*, int, double*, int, \
                                                    cudaStream_t);                                                \
     template cudaError_t launch_energy_tiles<R>(const void*, int, uint64_t, const EnergyTiles&, const PauliDev*, \
-                                                int, double*, int, cudaStream_t);                               \
+                                                int, double*, int, int*, cudaStream_t);                         \
     template cudaError_t launch_gather<R>(const void*, const uint64_t*, const uint64_t*, uint64_t, double*,     \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_hamiltonian<R>(const void*, void*, int, const PauliDev*, int, cudaStream_t);    \

@@ -54,7 +54,9 @@ struct ChunkOut {
     int32_t pad;
 };
 
-enum : int { kErrCorrupt = 1, kErrRange = 2 };
+// kErrWait: a kernel gave up waiting for its own asynchronous copies (an
+// iteration limit on every spin-wait) and skipped the rest of its work
+enum : int { kErrCorrupt = 1, kErrRange = 2, kErrWait = 4 };
 
 // Register-phase form of a sub-pass (tiles of exactly kPhaseTileQubits
 // qubits, 256 threads, 16 amplitudes per thread): a phase keeps 4 tile

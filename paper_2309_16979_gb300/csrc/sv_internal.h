@@ -192,10 +192,13 @@ constexpr int kEnergyTileBits = 12;
 
 // partials[0..nblocks) = per-CTA shares of sum_t <psi|P_t|psi> over the
 // buffer for terms whose x-masks lie in the tiles' bits (at most
-// max_energy_terms()); partners read from the tile in shared memory
+// max_energy_terms()); partners read from the tile in shared memory, tiles
+// brought in by bulk copies. psi must be 16-byte aligned. A wait for the
+// copies that exceeds its limit sets kErrWait in *err.
 template <typename R>
 cudaError_t launch_energy_tiles(const void* psi, int Lbits, uint64_t gbase, const EnergyTiles& et,
-                                const PauliDev* terms, int nterms, double* partials, int nblocks, cudaStream_t st);
+                                const PauliDev* terms, int nterms, double* partials, int nblocks, int* err,
+                                cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_gather(const void* amps, const uint64_t* local_idx, const uint64_t* dest,
