@@ -394,7 +394,7 @@ static DevPass<R> build_dev_pass(const std::vector<SubPlan>& subs, int L, int t,
         // sub-passes that fuse the codec use rows of whole block pairs (l = 8)
         const bool codec_rows = dp.use_phases && ((si == 0 && dp.fuse_decode) || (si + 1 == subs.size() && dp.fuse_encode));
         TileDesc td = tile_desc(sp.T, L, t, codec_rows ? 8 : l);
-        if (dp.use_phases) order_tile_bits<R>(sp, td);
+        if (dp.use_phases) order_tile_bits<R>(sp, td, false);
         dp.td.push_back(td);
         dp.off.push_back((int)dp.ops.size());
         dp.ph_off.push_back((int)dp.phases.size());
@@ -460,7 +460,7 @@ static int jit_adjoint_plan(sv_state* s, const std::vector<SubPlan>& subs, int L
     std::vector<std::string> keys(subs.size());
     for (size_t i = 0; i < subs.size(); i++) {
         TileDesc td = tile_desc(subs[i].T, L, t, l);
-        order_tile_bits<R>(subs[i], td);
+        order_tile_bits<R>(subs[i], td, true);
         ap.td.push_back(td);
         ap.gslot.push_back((int)(slot_params.size() + sp_local.size()));
         const size_t before = sp_local.size();
@@ -926,7 +926,7 @@ int jit_sources(sv_state* s, const std::vector<PGate>& gates, std::vector<std::s
             const std::vector<SubPlan> subs = plan_subpasses(local_ops(inv, rids, c, pp.S, true), L, t, l, true);
             for (const SubPlan& sp : subs) {
                 TileDesc td = tile_desc(sp.T, L, t, l);
-                order_tile_bits<R>(sp, td);
+                order_tile_bits<R>(sp, td, true);
                 std::vector<Phase> ph;
                 std::vector<PhaseOp<R>> ops;
                 std::vector<CtaCtrl> ctl;

@@ -708,6 +708,35 @@ static int classify_2x2(const cd* m)
     return PK_GENERIC;
 }
 
+// The register sets and op placement of a sub-pass's phases depend on its
+// ops' structure and the tile's numbering only, not on their matrices; the
+// enumerated plan costs a few hundred placements per phase, so a
+// process-wide cache (bounded, cleared when full) keeps them per structure.
+namespace {
+struct PhasePick {
+    uint32_t Rm;
+    std::vector<int> placed;
+};
+std::mutex g_phase_mu;
+std::unordered_map<std::string, std::vector<PhasePick>> g_phase_cache;
+constexpr size_t kPhaseCacheMax = 4096;
+
+std::string phase_key(const SubPlan& sp, const TileDesc& td, bool adjoint)
+{
+    std::string k;
+    k.reserve(16 + sp.ops.size() * 24);
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    const int32_t hdr[3] = {td.t, td.l, adjoint ? 1 : 0};
+    put(hdr, sizeof(hdr));
+    put(td.hpos, (size_t)(td.t - td.l));
+    for (const HOp& o : sp.ops) {
+        const uint64_t b[3] = {o.qL, o.qG, o.mixL};
+        put(b, sizeof(b));
+    }
+    return k;
+}
+}  // namespace
+
 template <typename R>
 void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phases, std::vector<PhaseOp<R>>& out,
                 std::vector<CtaCtrl>& ctl, std::vector<R>& d2m, std::vector<int32_t>* grad,
@@ -725,36 +754,131 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
         for (int p = 0; p < 64; p++)
             if ((o.mixL >> p) & 1) mix[i] |= 1u << tbit[p];
     }
-    std::vector<int> remaining(nops);
-    for (int i = 0; i < nops; i++) remaining[i] = i;
-    while (!remaining.empty()) {
-        uint32_t Rm = 0;
+    // ops a phase with register bits `regs` applies, in order: those whose
+    // mixing bits lie in regs and that no deferred op before them blocks
+    auto place_with = [&](const std::vector<int>& rem, uint32_t regs, std::vector<int>* placed,
+                          std::vector<int>* deferred) {
         uint64_t bL = 0, bG = 0;
-        std::vector<int> placed, deferred;
-        for (int oi : remaining) {
+        int n = 0;
+        for (int oi : rem) {
             const HOp& o = sp.ops[oi];
-            if ((o.qL & bL) || (o.qG & bG)) {
-                deferred.push_back(oi);
+            if ((o.qL & bL) || (o.qG & bG) || (mix[oi] & ~regs)) {
+                if (deferred) deferred->push_back(oi);
                 bL |= o.qL;
                 bG |= o.qG;
                 continue;
             }
-            if (popc(Rm | mix[oi]) <= kPhaseRegBits) {
-                Rm |= mix[oi];
-                placed.push_back(oi);
-            } else {
-                deferred.push_back(oi);
-                bL |= o.qL;
-                bG |= o.qG;
-            }
+            if (placed) placed->push_back(oi);
+            n++;
         }
-        // unused register bits: the lowest tile bits, except in the last phase,
-        // which leaves tile bits 0..3 to thread bits 0..3 (its stores can then
-        // go from registers straight to HBM in whole 32-byte sectors)
-        if (deferred.empty())
-            for (int b = td.t - 1; b >= 0 && popc(Rm) < kPhaseRegBits; b--) Rm |= 1u << b;
-        else
-            for (int b = 0; b < td.t && popc(Rm) < kPhaseRegBits; b++) Rm |= 1u << b;
+        return n;
+    };
+    // The phases' register bits and ops. First-come: ops in order while their
+    // mixing bits fit kPhaseRegBits. Enumerated: per phase, the set of
+    // kPhaseRegBits of the remaining ops' bits that applies the most ops (the
+    // first-come set reproduces itself under place_with, so it is among the
+    // candidates and wins ties).
+    auto plan_phases = [&](bool enumerate) {
+        std::vector<PhasePick> out;
+        std::vector<int> remaining(nops);
+        for (int i = 0; i < nops; i++) remaining[i] = i;
+        while (!remaining.empty()) {
+            uint32_t Rm = 0;
+            uint64_t bL = 0, bG = 0;
+            std::vector<int> placed, deferred;
+            for (int oi : remaining) {
+                const HOp& o = sp.ops[oi];
+                if ((o.qL & bL) || (o.qG & bG)) {
+                    deferred.push_back(oi);
+                    bL |= o.qL;
+                    bG |= o.qG;
+                    continue;
+                }
+                if (popc(Rm | mix[oi]) <= kPhaseRegBits) {
+                    Rm |= mix[oi];
+                    placed.push_back(oi);
+                } else {
+                    deferred.push_back(oi);
+                    bL |= o.qL;
+                    bG |= o.qG;
+                }
+            }
+            uint32_t U = 0;
+            for (int oi : remaining) U |= mix[oi];
+            if (enumerate && popc(U) > kPhaseRegBits) {
+                int best = (int)placed.size();
+                uint32_t bestR = 0;
+                // candidates in local-position order, so that the pick (ties
+                // included) does not depend on how the tile numbers its high bits
+                std::vector<int> ub;
+                for (int p = 0; p < 64; p++)
+                    if (tbit[p] >= 0 && ((U >> tbit[p]) & 1)) ub.push_back(tbit[p]);
+                const int m = (int)ub.size();
+                for (int a = 0; a < m; a++)
+                    for (int b = a + 1; b < m; b++)
+                        for (int c2 = b + 1; c2 < m; c2++)
+                            for (int d = c2 + 1; d < m; d++) {
+                                const uint32_t regs = (1u << ub[a]) | (1u << ub[b]) | (1u << ub[c2]) | (1u << ub[d]);
+                                const int k = place_with(remaining, regs, nullptr, nullptr);
+                                if (k > best) {
+                                    best = k;
+                                    bestR = regs;
+                                }
+                            }
+                if (bestR) {
+                    placed.clear();
+                    deferred.clear();
+                    place_with(remaining, bestR, &placed, &deferred);
+                    Rm = bestR;
+                }
+            }
+            // unused register bits: the lowest tile bits, except in the last phase,
+            // which leaves tile bits 0..3 to thread bits 0..3 (its stores can then
+            // go from registers straight to HBM in whole 32-byte sectors) and takes
+            // the tile's highest local positions, again whatever their numbering
+            if (deferred.empty()) {
+                for (int p = 63; p >= 0 && popc(Rm) < kPhaseRegBits; p--)
+                    if (tbit[p] >= 0) Rm |= 1u << tbit[p];
+            } else {
+                for (int b = 0; b < td.t && popc(Rm) < kPhaseRegBits; b++) Rm |= 1u << b;
+            }
+            out.push_back({Rm, std::move(placed)});
+            remaining.swap(deferred);
+        }
+        return out;
+    };
+    // Forward sub-passes take the enumerated phases when they cost less,
+    // counting one shared-memory round trip per phase and one more for a last
+    // phase that cannot store straight to HBM (tile bits 0 and 1 in its
+    // registers). Adjoint sub-passes keep first-come (measured slower with the
+    // larger phases: their gradient partials sit between the ops).
+    const std::string key = phase_key(sp, td, grad != nullptr);
+    std::vector<PhasePick> picks;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_phase_mu);
+        auto it = g_phase_cache.find(key);
+        if (it != g_phase_cache.end()) {
+            picks = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        picks = plan_phases(false);
+        if (!grad) {
+            std::vector<PhasePick> alt = plan_phases(true);
+            auto cost = [](const std::vector<PhasePick>& v) {
+                return v.size() + (v.empty() || (v.back().Rm & 3u) ? 1 : 0);
+            };
+            if (cost(alt) < cost(picks)) picks.swap(alt);
+        }
+        std::lock_guard<std::mutex> lock(g_phase_mu);
+        if (g_phase_cache.size() >= kPhaseCacheMax) g_phase_cache.clear();
+        g_phase_cache[key] = picks;
+    }
+    for (const PhasePick& pick : picks) {
+        const uint32_t Rm = pick.Rm;
+        const std::vector<int>& placed = pick.placed;
         Phase ph{};
         int reg_of[32];
         for (int b = 0; b < 32; b++) reg_of[b] = -1;
@@ -860,7 +984,6 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
         }
         ph.op_count = (int)out.size() - ph.op_begin;
         phases.push_back(ph);
-        remaining.swap(deferred);
     }
 }
 
@@ -873,7 +996,7 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
 // registers does not depend on the numbering; a deterministic search over
 // orders of the high bits keeps the first with the fewest such phases.
 template <typename R>
-void order_tile_bits(const SubPlan& sp, TileDesc& td)
+void order_tile_bits(const SubPlan& sp, TileDesc& td, bool adjoint)
 {
     const int nh = td.t - td.l;
     if (td.t != kPhaseTileQubits || nh < 2) return;
@@ -881,7 +1004,8 @@ void order_tile_bits(const SubPlan& sp, TileDesc& td)
     std::vector<PhaseOp<R>> ops;
     std::vector<CtaCtrl> ctl;
     std::vector<R> d2m;
-    dev_phases<R>(sp, td, ph, ops, ctl, d2m);
+    std::vector<int32_t> grad;  // the adjoint's phases are planned as its sub-passes' are
+    dev_phases<R>(sp, td, ph, ops, ctl, d2m, adjoint ? &grad : nullptr);
     // each phase's register qubits as local positions
     std::vector<uint64_t> reg(ph.size(), 0);
     for (size_t i = 0; i < ph.size(); i++)
@@ -928,8 +1052,8 @@ void order_tile_bits(const SubPlan& sp, TileDesc& td)
     for (int i = 0; i < nh; i++) td.hpos[i] = keep[i];
 }
 
-template void order_tile_bits<float>(const SubPlan&, TileDesc&);
-template void order_tile_bits<double>(const SubPlan&, TileDesc&);
+template void order_tile_bits<float>(const SubPlan&, TileDesc&, bool);
+template void order_tile_bits<double>(const SubPlan&, TileDesc&, bool);
 
 template void dev_phases<float>(const SubPlan&, const TileDesc&, std::vector<Phase>&, std::vector<PhaseOp<float>>&,
                                 std::vector<CtaCtrl>&, std::vector<float>&, std::vector<int32_t>*, std::vector<int>*);

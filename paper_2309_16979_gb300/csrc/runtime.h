@@ -102,9 +102,10 @@ bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bo
 // Tile descriptor and device ops of one sub-pass.
 TileDesc tile_desc(uint64_t T, int L, int t, int l);
 // Renumber the high bits of a 2^12 tile against shared-memory bank
-// conflicts of its register phases (plan.cpp).
+// conflicts of its register phases (plan.cpp); adjoint: the phases are
+// those of an adjoint sub-pass.
 template <typename R>
-void order_tile_bits(const SubPlan& sp, TileDesc& td);
+void order_tile_bits(const SubPlan& sp, TileDesc& td, bool adjoint);
 template <typename R>
 void dev_ops(const SubPlan& sp, const TileDesc& td, std::vector<DevOp<R>>& out, int* grad_slot_base,
              std::vector<int>* slot_params);
