@@ -77,18 +77,77 @@ static uint64_t mixing_mask(const PGate& g)
     return m;
 }
 
+// A 2x2 matrix commutes with Z when it is diagonal and with X when it is
+// symmetric under exchanging its basis states (a I + b X). Exact tests: a
+// matrix that misses them by rounding is taken as general.
+static bool commutes_z(const cd* m) { return m[1] == cd(0) && m[2] == cd(0); }
+static bool commutes_x(const cd* m) { return m[0] == m[3] && m[1] == m[2]; }
+
+// Gates or ops left for later (deferred) block a following one only where
+// they do not commute with it: it may run ahead of deferred ones when on
+// every qubit it shares with them, it and all of them commute with Z there,
+// or it and all of them commute with X there. (Two operators that both
+// commute with Z, or both with X, on each qubit they share are sums of
+// projectors on those qubits times operators on disjoint qubits, so they
+// commute.) A pass's global qubits are controls or diagonal sources only,
+// so in the sub-pass and phase planners they never block.
+struct Blocked {
+    uint64_t any = 0;  // local positions some deferred op touches
+    uint64_t nz = 0;   // ... where some deferred op does not commute with Z
+    uint64_t nx = 0;   // ... where some deferred op does not commute with X
+    bool commute = true;  // false: any shared qubit blocks
+    // q: the qubits an op touches; z, x: where it commutes with Z / X
+    bool blocks(uint64_t q, uint64_t z, uint64_t x) const
+    {
+        return (q & any & (commute ? ~((z & ~nz) | (x & ~nx)) : ~0ull)) != 0;
+    }
+    void add(uint64_t q, uint64_t z, uint64_t x)
+    {
+        any |= q;
+        nz |= q & ~z;
+        nx |= q & ~x;
+    }
+    bool blocks(const HOp& o) const { return blocks(o.qL, o.zL, o.xL); }
+    void add(const HOp& o) { add(o.qL, o.zL, o.xL); }
+    bool all(uint64_t allL) const { return ((commute ? nz & nx : any) & allL) == allL; }
+};
+
+// Qubits where gate g commutes with Z / with X: controls and diagonal
+// targets with Z; a single dense target as its matrix does, or, for a
+// parameterised gate, as its generator does at every angle (RX: X; RY:
+// neither), since a gradient needs the order to hold at all angles.
+static void commute_masks(const PGate& g, uint64_t& zm, uint64_t& xm)
+{
+    zm = xm = 0;
+    for (int i = 0; i < g.nc; i++) zm |= 1ull << g.c[i];
+    if (g.diag) {
+        for (int i = 0; i < g.nt; i++) zm |= 1ull << g.t[i];
+        return;
+    }
+    if (g.nt != 1) return;
+    const uint64_t b = 1ull << g.t[0];
+    if (g.param >= 0) {
+        if (g.kind == SV_GATE_RX) xm |= b;
+        return;
+    }
+    if (commutes_z(g.m)) zm |= b;
+    if (commutes_x(g.m)) xm |= b;
+}
+
 // Gates one pass staging the high qubits S would apply, scanning the remaining
 // gates in order; a gate that cannot run blocks its qubits for later ones.
 static int count_pass(const std::vector<PGate>& g, const std::vector<int>& remaining, uint64_t S, uint64_t high,
                       uint64_t all)
 {
-    uint64_t blocked = 0;
+    Blocked bk;
     int k = 0;
     for (int gi : remaining) {
         const uint64_t qm = qubit_mask(g[gi]);
-        if ((qm & blocked) || (mixing_mask(g[gi]) & high & ~S)) {
-            blocked |= qm;
-            if ((blocked & all) == all) break;
+        uint64_t zm, xm;
+        commute_masks(g[gi], zm, xm);
+        if (bk.blocks(qm, zm, xm) || (mixing_mask(g[gi]) & high & ~S)) {
+            bk.add(qm, zm, xm);
+            if (bk.all(all)) break;
             continue;
         }
         k++;
@@ -103,7 +162,8 @@ static PassPlan plan_one_pass(const std::vector<PGate>& g, const std::vector<int
 {
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
     const uint64_t high = (n > c) ? (all & ~((1ull << c) - 1)) : 0;
-    uint64_t S = 0, blocked = 0;
+    uint64_t S = 0;
+    Blocked bk;
     // Stage one high qubit at a time, the one that lets the pass apply the
     // most gates; when none adds any, the scan below stages first-come.
     for (int cur = count_pass(g, remaining, S, high, all); popc(S) < gsz;) {
@@ -124,9 +184,11 @@ static PassPlan plan_one_pass(const std::vector<PGate>& g, const std::vector<int
     deferred.clear();
     for (int gi : remaining) {
         const uint64_t qm = qubit_mask(g[gi]);
-        if (qm & blocked) {
+        uint64_t zm, xm;
+        commute_masks(g[gi], zm, xm);
+        if (bk.blocks(qm, zm, xm)) {
             deferred.push_back(gi);
-            blocked |= qm;
+            bk.add(qm, zm, xm);
             continue;
         }
         const uint64_t need = mixing_mask(g[gi]) & high & ~S;
@@ -135,7 +197,7 @@ static PassPlan plan_one_pass(const std::vector<PGate>& g, const std::vector<int
             pp.gates.push_back(gi);
         } else {
             deferred.push_back(gi);
-            blocked |= qm;
+            bk.add(qm, zm, xm);
         }
     }
     // stage exactly gsz high qubits: pad with the lowest unused ones
@@ -273,7 +335,7 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
         HOp op;
         for (int i = 0; i < G.nc; i++) {
             const int p = loc(G.c[i]);
-            if (p >= 0) { op.cL |= 1ull << p; op.qL |= 1ull << p; }
+            if (p >= 0) { op.cL |= 1ull << p; op.qL |= 1ull << p; op.zL |= 1ull << p; }
             else { op.cG |= 1ull << G.c[i]; op.qG |= 1ull << G.c[i]; }
         }
         if (G.diag) {
@@ -281,7 +343,7 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
             for (int i = 0; i < G.nt; i++) {
                 const int p = loc(G.t[i]);
                 op.dsrc[i] = p >= 0 ? p : kGlobalSrc + G.t[i];
-                if (p >= 0) op.qL |= 1ull << p;
+                if (p >= 0) { op.qL |= 1ull << p; op.zL |= 1ull << p; }
                 else op.qG |= 1ull << G.t[i];
             }
             const int K = 1 << G.nt;
@@ -296,6 +358,10 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
                 op.mixL |= 1ull << p;
             }
             for (int i = 0; i < 16; i++) op.m[i] = G.m[i];
+            if (G.nt == 1) {
+                if (commutes_z(op.m)) op.zL |= op.mixL;
+                if (commutes_x(op.m)) op.xL |= op.mixL;
+            }
         }
         if (adjoint && G.param >= 0) {
             op.param = G.param;
@@ -303,6 +369,12 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
             const int p = loc(G.t[0]);
             op.mixL |= 1ull << p;  // the generator's pairs must be tile-local
             if (op.type == OP_DIAG) op.t[0] = p;
+            // a gradient needs the ordering to hold at every angle: the
+            // generator decides (RX: X-like, RZ: diagonal, RY: neither),
+            // not the matrix at this angle (RX(0) is also diagonal)
+            const uint64_t b = 1ull << p;
+            op.zL = (op.zL & ~b) | (op.gen == 3 ? b : 0);
+            op.xL = (op.xL & ~b) | (op.gen == 1 ? b : 0);
         }
         out.push_back(op);
     }
@@ -355,6 +427,9 @@ static bool try_fuse(HOp& a, const HOp& b)
         a.dsrc[0] = a.dsrc[1] = -1;
         a.mixL |= 1ull << pa;
         for (int i = 0; i < 4; i++) a.m[i] = M[i];
+        const uint64_t bit = 1ull << pa;
+        a.zL = (a.zL & ~bit) | (commutes_z(M) ? bit : 0);
+        a.xL = (a.xL & ~bit) | (commutes_x(M) ? bit : 0);
     }
     a.qL |= b.qL;
     a.qG |= b.qG;
@@ -364,16 +439,17 @@ static bool try_fuse(HOp& a, const HOp& b)
 // Ops one sweep with tile set T would apply (no growth of T), scanning the
 // remaining ops in order; an op that cannot run blocks its qubits for later
 // ones. The scan stops once every local qubit is blocked.
-static int count_fit(const std::vector<HOp>& ops, const std::vector<int>& remaining, uint64_t T, uint64_t allL)
+static int count_fit(const std::vector<HOp>& ops, const std::vector<int>& remaining, uint64_t T, uint64_t allL,
+                     bool commute)
 {
-    uint64_t bL = 0, bG = 0;
+    Blocked bk;
+    bk.commute = commute;
     int n = 0;
     for (int oi : remaining) {
         const HOp& o = ops[oi];
-        if ((o.qL & bL) || (o.qG & bG) || (o.mixL & ~T)) {
-            bL |= o.qL;
-            bG |= o.qG;
-            if ((bL & allL) == allL) break;
+        if (bk.blocks(o) || (o.mixL & ~T)) {
+            bk.add(o);
+            if (bk.all(allL)) break;
             continue;
         }
         n++;
@@ -410,7 +486,7 @@ static uint64_t lookahead_candidates(const std::vector<HOp>& ops, const std::vec
 using FuseGroups = std::vector<std::vector<std::vector<int>>>;
 
 static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int L, int t, int l, bool fuse,
-                                                int first_l, bool lookahead, FuseGroups& groups)
+                                                int first_l, bool lookahead, bool commute, FuseGroups& groups)
 {
     std::vector<SubPlan> subs;
     groups.clear();
@@ -421,19 +497,21 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
     std::vector<int> remaining(ops.size());
     for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
     while (!remaining.empty()) {
-        uint64_t T = subs.empty() ? first_low : low, bL = 0, bG = 0;
-        for (int cur = count_fit(ops, remaining, T, allL); popc(T) < t;) {
+        uint64_t T = subs.empty() ? first_low : low;
+        Blocked bk;
+        bk.commute = commute;
+        for (int cur = count_fit(ops, remaining, T, allL, commute); popc(T) < t;) {
             if (lookahead) {
                 const uint64_t cand = lookahead_candidates(ops, remaining, T, allL);
                 int best = -1, best2 = cur, best1 = cur;
                 for (int p = 0; p < L; p++) {
                     if (!((cand >> p) & 1)) continue;
                     const uint64_t Tp = T | (1ull << p);
-                    const int k1 = count_fit(ops, remaining, Tp, allL);
+                    const int k1 = count_fit(ops, remaining, Tp, allL, commute);
                     int k2 = k1;
                     if (popc(Tp) < t)
                         for (int q = 0; q < L; q++)
-                            if (q != p && ((cand >> q) & 1)) k2 = std::max(k2, count_fit(ops, remaining, Tp | (1ull << q), allL));
+                            if (q != p && ((cand >> q) & 1)) k2 = std::max(k2, count_fit(ops, remaining, Tp | (1ull << q), allL, commute));
                     if (k2 > best2 || (k2 == best2 && k1 > best1)) {
                         best = p;
                         best2 = k2;
@@ -448,7 +526,7 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
             int best = -1, bestn = cur;
             for (int p = 0; p < L; p++) {
                 if ((T >> p) & 1) continue;
-                const int k = count_fit(ops, remaining, T | (1ull << p), allL);
+                const int k = count_fit(ops, remaining, T | (1ull << p), allL, commute);
                 if (k > bestn) {
                     bestn = k;
                     best = p;
@@ -466,7 +544,7 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
                 if ((T >> p) & 1) continue;
                 for (int q = p + 1; q < L; q++) {
                     if ((T >> q) & 1) continue;
-                    const int k = count_fit(ops, remaining, T | (1ull << p) | (1ull << q), allL);
+                    const int k = count_fit(ops, remaining, T | (1ull << p) | (1ull << q), allL, commute);
                     if (k > bestn) {
                         bestn = k;
                         b0 = p;
@@ -483,10 +561,9 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
         std::vector<int> deferred;
         for (int oi : remaining) {
             const HOp& o = ops[oi];
-            if ((o.qL & bL) || (o.qG & bG)) {
+            if (bk.blocks(o)) {
                 deferred.push_back(oi);
-                bL |= o.qL;
-                bG |= o.qG;
+                bk.add(o);
                 continue;
             }
             const uint64_t need = o.mixL & ~T;
@@ -500,8 +577,7 @@ static std::vector<SubPlan> plan_subpasses_rule(const std::vector<HOp>& ops, int
                 grp.push_back({oi});
             } else {
                 deferred.push_back(oi);
-                bL |= o.qL;
-                bG |= o.qG;
+                bk.add(o);
             }
         }
         if (sp.ops.empty() && !deferred.empty() && deferred.size() == remaining.size()) {
@@ -536,13 +612,13 @@ constexpr size_t kPlanCacheMax = 512;
 std::string plan_key(const std::vector<HOp>& ops, int L, int t, int l, bool fuse, int first_l)
 {
     std::string k;
-    k.reserve(16 + ops.size() * 72);
+    k.reserve(20 + ops.size() * 80);
     auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
     const int32_t hdr[5] = {L, t, l, fuse ? 1 : 0, first_l};
     put(hdr, sizeof(hdr));
     for (const HOp& o : ops) {
         const int32_t a[6] = {o.type, o.t[0], o.t[1], o.dsrc[0], o.dsrc[1], o.param >= 0 ? 1 : 0};
-        const uint64_t b[5] = {o.cL, o.cG, o.qL, o.qG, o.mixL};
+        const uint64_t b[7] = {o.cL, o.cG, o.qL, o.qG, o.mixL, o.zL, o.xL};
         put(a, sizeof(a));
         put(b, sizeof(b));
     }
@@ -579,28 +655,32 @@ std::vector<SubPlan> plan_subpasses(const std::vector<HOp>& ops, int L, int t, i
         auto it = g_plan_cache.find(key);
         if (it != g_plan_cache.end() && replay(ops, it->second, subs)) return subs;
     }
-    FuseGroups ga, gb;
-    std::vector<SubPlan> a, b;
+    // rules: (lookahead, commute) = (no, no), (yes, no), (no, yes), (yes, yes)
+    FuseGroups gr[4];
+    std::vector<SubPlan> pl[4];
+    auto run = [&](int i) { return plan_subpasses_rule(ops, L, t, l, fuse, first_l, (i & 1) != 0, (i & 2) != 0, gr[i]); };
     if (ops.size() < 64) {
-        a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false, ga);
-        if (a.size() > 1) b = plan_subpasses_rule(ops, L, t, l, fuse, first_l, true, gb);
+        pl[0] = run(0);
+        if (pl[0].size() > 1)
+            for (int i = 1; i < 4; i++) pl[i] = run(i);
     } else {
-        std::future<std::vector<SubPlan>> fb = std::async(std::launch::async, [&]() {
-            return plan_subpasses_rule(ops, L, t, l, fuse, first_l, true, gb);
-        });
-        a = plan_subpasses_rule(ops, L, t, l, fuse, first_l, false, ga);
-        b = fb.get();
+        std::future<std::vector<SubPlan>> f[3];
+        for (int i = 1; i < 4; i++) f[i - 1] = std::async(std::launch::async, run, i);
+        pl[0] = run(0);
+        for (int i = 1; i < 4; i++) pl[i] = f[i - 1].get();
     }
-    const bool use_b = !b.empty() && b.size() < a.size();
+    int use = 0;
+    for (int i = 1; i < 4; i++)
+        if (!pl[i].empty() && pl[i].size() < pl[use].size()) use = i;
     PlanRecipe rc;
-    for (const SubPlan& sp : use_b ? b : a) rc.T.push_back(sp.T);
-    rc.groups = use_b ? std::move(gb) : std::move(ga);
+    for (const SubPlan& sp : pl[use]) rc.T.push_back(sp.T);
+    rc.groups = std::move(gr[use]);
     {
         std::lock_guard<std::mutex> lock(g_plan_mu);
         if (g_plan_cache.size() >= kPlanCacheMax) g_plan_cache.clear();
         g_plan_cache[key] = std::move(rc);
     }
-    return use_b ? b : a;
+    return pl[use];
 }
 
 bool replan_tail(std::vector<SubPlan>& subs, int L, int t, int l, int last_l, bool keep_first)
@@ -724,13 +804,13 @@ constexpr size_t kPhaseCacheMax = 4096;
 std::string phase_key(const SubPlan& sp, const TileDesc& td, bool adjoint)
 {
     std::string k;
-    k.reserve(16 + sp.ops.size() * 24);
+    k.reserve(16 + sp.ops.size() * 32);
     auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
     const int32_t hdr[3] = {td.t, td.l, adjoint ? 1 : 0};
     put(hdr, sizeof(hdr));
     put(td.hpos, (size_t)(td.t - td.l));
     for (const HOp& o : sp.ops) {
-        const uint64_t b[3] = {o.qL, o.qG, o.mixL};
+        const uint64_t b[4] = {o.qL, o.mixL, o.zL, o.xL};
         put(b, sizeof(b));
     }
     return k;
@@ -758,14 +838,13 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
     // mixing bits lie in regs and that no deferred op before them blocks
     auto place_with = [&](const std::vector<int>& rem, uint32_t regs, std::vector<int>* placed,
                           std::vector<int>* deferred) {
-        uint64_t bL = 0, bG = 0;
+        Blocked bk;
         int n = 0;
         for (int oi : rem) {
             const HOp& o = sp.ops[oi];
-            if ((o.qL & bL) || (o.qG & bG) || (mix[oi] & ~regs)) {
+            if (bk.blocks(o) || (mix[oi] & ~regs)) {
                 if (deferred) deferred->push_back(oi);
-                bL |= o.qL;
-                bG |= o.qG;
+                bk.add(o);
                 continue;
             }
             if (placed) placed->push_back(oi);
@@ -784,14 +863,13 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
         for (int i = 0; i < nops; i++) remaining[i] = i;
         while (!remaining.empty()) {
             uint32_t Rm = 0;
-            uint64_t bL = 0, bG = 0;
+            Blocked bk;
             std::vector<int> placed, deferred;
             for (int oi : remaining) {
                 const HOp& o = sp.ops[oi];
-                if ((o.qL & bL) || (o.qG & bG)) {
+                if (bk.blocks(o)) {
                     deferred.push_back(oi);
-                    bL |= o.qL;
-                    bG |= o.qG;
+                    bk.add(o);
                     continue;
                 }
                 if (popc(Rm | mix[oi]) <= kPhaseRegBits) {
@@ -799,8 +877,7 @@ void dev_phases(const SubPlan& sp, const TileDesc& td, std::vector<Phase>& phase
                     placed.push_back(oi);
                 } else {
                     deferred.push_back(oi);
-                    bL |= o.qL;
-                    bG |= o.qG;
+                    bk.add(o);
                 }
             }
             uint32_t U = 0;

@@ -45,6 +45,10 @@ struct HOp {
     int gen = 0;                   // adjoint: 1 X, 2 Y, 3 Z
     uint64_t qL = 0, qG = 0;       // every qubit the op touches (for ordering)
     uint64_t mixL = 0;             // local positions that must be tile bits
+    // local positions where the op commutes with Z (controls, diagonal
+    // sources, diagonal targets) / with X (X-like targets: X, RX, CNOT's
+    // target); global qubits are only ever controls or diagonal sources
+    uint64_t zL = 0, xL = 0;
 };
 
 struct SubPlan {

@@ -137,7 +137,7 @@ def test_remapped_circuit_kernels_compile(jit_sources):
     import paper_2309_16979_gb300 as P
     lib = _nvrtc()
     n, c, g = 16, 10, 2
-    gates = W.random_layers(n, 6, seed=4)
+    gates = W.random_layers(n, 6, seed=5)
     assert P.plan(n, c, gates, max_group_qubits=g, remap=True)["swaps"]
     plain = [s for s in jit_sources(n, c, gates, max_group_qubits=g) if s]
     srcs = [s for s in jit_sources(n, c, gates, max_group_qubits=g, remap=True) if s]

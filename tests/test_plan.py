@@ -124,3 +124,30 @@ def test_plan_cache_replays_the_fresh_plan():
         a = jit_sources(n, c, g1, max_group_qubits=3, adjoint=adjoint)
         b = jit_sources(n, c, g1, max_group_qubits=3, adjoint=adjoint)
         assert a == b
+
+
+def test_commuting_gates_run_ahead_of_deferred_ones(sv):
+    """A gate may run in an earlier pass than a deferred gate it shares
+    qubits with when, on every shared qubit, both commute with Z (controls,
+    diagonal gates) or both with X (CNOT's target, RX); a gate that breaks
+    both families waits. Here g = 2 stages qubits 10 and 13 first (the
+    gates on them outnumber the rest), so H(11), the CNOT it blocks and the
+    CNOT onto 12 wait for a later pass."""
+    n, c = 16, 10
+    gates = [W.Gate("H", (q,)) for q in (10, 13, 10, 13, 10, 13, 10, 13)]
+    gates += [W.Gate("H", (11,)), W.Gate("CNOT", (5,), (11,)),
+              W.Gate("RX", (5,), theta=0.3),   # 10: X family on 5, like the CNOT's target: runs ahead
+              W.Gate("RZ", (5,), theta=0.7),   # 11: Z family against the target's X: waits
+              W.Gate("CNOT", (12,), (4,)),     # 12: mixes 12, deferred in pass 0
+              W.Gate("RZ", (4,), theta=0.2),   # 13: Z family, like the CNOT's control: runs ahead
+              W.Gate("H", (4,))]               # 14: neither: waits
+    p = sv.plan(n, c, gates, max_group_qubits=2)
+    assert p["staged"][0] == (1 << 10) | (1 << 13)
+    pass_of = dict(zip(p["order"], p["pass_of"]))
+    assert {k for k, v in pass_of.items() if v == 0} == set(range(8)) | {10, 13}
+    assert pass_of[11] >= pass_of[9] >= pass_of[8] > 0 and pass_of[14] >= pass_of[12] > 0
+    rng = np.random.default_rng(3)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    a = oracle.apply_gates(n, psi0, gates)
+    b = oracle.apply_gates(n, psi0, [gates[i] for i in p["order"]])
+    assert np.abs(a - b).max() < 1e-12
