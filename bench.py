@@ -16,7 +16,7 @@ Metric: amplitude-gate updates per second = gates * 2^n / step time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload {layers30,ghz30,qft30,qft16,layers16,
                               ghz36,qft36,clifford36,grad-hea24,grad-hea32,grad-hea32-ckpt1,
-                              qft36-rel,clifford36-rel,layers30-rel}
+                              grad-hea28,qft36-rel,clifford36-rel,layers30-rel}
   (-rel: the relative error bound, each chunk's step from its largest component)
 
 With --gpus N under torchrun every rank runs an independent replica of the
@@ -66,6 +66,8 @@ WORKLOADS = {
     # the same with psi checkpointed after every forward pass (checkpoint_passes = 1)
     "grad-hea32-ckpt1": dict(n=32, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=8, sets=16,
                              checkpoint=1),
+    # a small compressed gradient with config 4's chunks (16 chunks of 2^24): profiling case
+    "grad-hea28": dict(n=28, c=24, eb=1e-6, dtype="c64", group=0, circuit="hea", layers=2),
 }
 
 

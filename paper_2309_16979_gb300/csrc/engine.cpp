@@ -1821,10 +1821,19 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
     for (size_t b = 1; b < nb; b++) toff[b] = toff[b - 1] + nch * tcnt[b - 1];
     cudaError_t e;
     if (nt) {
+        // each table lists the terms that read one source (slot, low x-mask)
+        // together: the kernel loads a source once per run of such terms
+        std::vector<size_t> ord(nt);
+        for (size_t i = 0; i < nt; i++) ord[i] = i;
+        auto slot_key = [&](size_t i) {
+            const size_t j = std::lower_bound(X.begin(), X.end(), phys[i].xmask >> c) - X.begin();
+            return std::make_pair(slot_of[j], phys[i].xmask & lowmask);
+        };
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return slot_key(a) < slot_key(b); });
         std::vector<PauliDev> hd(nch * nt);
         for (uint64_t k = 0; k < nch; k++) {
             std::vector<size_t> fill(nb, 0);
-            for (size_t i = 0; i < nt; i++) {
+            for (size_t i : ord) {
                 const uint64_t xh = phys[i].xmask >> c;
                 const size_t j = std::lower_bound(X.begin(), X.end(), xh) - X.begin();
                 const int b = batch_of[j];

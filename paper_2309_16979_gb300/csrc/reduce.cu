@@ -447,11 +447,17 @@ k_hamiltonian(const typename V2<R>::T* __restrict__ psi, typename V2<R>::T* __re
 // k ^ xh of every distinct high x-mask are staged side by side (slot s at
 // s << c); term t reads slot terms[t].pad, its low x-mask flips local bits,
 // and the sign from its z-mask on the source chunk's high bits is already in
-// its coefficient.
-// Each thread builds a strip of 8 outputs (k = strip base + thread + 256 m),
-// so the 8 source reads of a term are in flight together; the terms are
-// staged in shared memory in batches, and every output sums its terms in
-// their order.
+// its coefficient. The host orders the terms so that those reading the same
+// source (slot and low x-mask) are consecutive: a run of them loads its
+// source amplitudes once, sums its terms' coefficients c i^ny (-1)^|src & z|
+// per output, and adds coefficient x source at the run's end.
+// Each thread builds a strip of 8 outputs k = b + 256 m (b: the strip base
+// plus the thread, bits 8..10 clear), so the 8 source reads of a run are in
+// flight together while its coefficients are summed, and a term's sign
+// (-1)^|(k ^ x) & z| splits into (-1)^|x & z|, taken when the term is
+// staged, (-1)^|b & z|, once per thread, and a pattern over m from z's bits
+// 8..10, staged with the term: most terms have none and add one coefficient
+// to all 8 outputs.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_ham_chunk(const typename V2<R>::T* __restrict__ psi_slots, typename V2<R>::T* __restrict__ lam, int c,
@@ -459,68 +465,115 @@ k_ham_chunk(const typename V2<R>::T* __restrict__ psi_slots, typename V2<R>::T* 
 {
     using T = typename V2<R>::T;
     constexpr int kStrip = 8, kBatch = 256;
+    static_assert(kThreads == 256 && kStrip == 8, "the sign pattern covers bits 8..10 of the output index");
     __shared__ uint64_t sxl[kBatch], szl[kBatch];
-    __shared__ R sc[kBatch];
-    __shared__ int32_t spn[kBatch];  // pad << 2 | ny
+    __shared__ R sc[kBatch];            // c (-1)^|x & z| (-1)^[ny >= 2]
+    __shared__ int32_t spad[kBatch];
+    __shared__ uint32_t sfl[kBatch];    // sign pattern over m << 1 | ny odd
     const uint64_t count = 1ull << c;
     const uint64_t span = (uint64_t)kThreads * kStrip;
     for (uint64_t s0 = (uint64_t)blockIdx.x * span; s0 < count; s0 += (uint64_t)gridDim.x * span) {
-        R ar[kStrip], ai[kStrip];
+        const uint64_t kb = s0 + threadIdx.x;
+        R ar[kStrip], ai[kStrip];  // lambda
+        R fr[kStrip], fi[kStrip];  // the current run's coefficient per output
+        T v[kStrip];               // the current run's source amplitudes
 #pragma unroll
         for (int m = 0; m < kStrip; m++) {
-            const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
-            ar[m] = ai[m] = (R)0;
+            const uint64_t k = kb + (uint64_t)m * kThreads;
+            ar[m] = ai[m] = fr[m] = fi[m] = (R)0;
+            v[m] = T{(R)0, (R)0};
             if (accumulate && k < count) {
                 const T l = lam[k];
                 ar[m] = l.x;
                 ai[m] = l.y;
             }
         }
+        int rpad = -1;      // the current run's slot (-1: none yet)
+        uint64_t rxl = 0;   // and low x-mask
+        bool rim = false;   // whether its coefficients have imaginary parts
+        const bool whole = s0 + span <= count;
         for (int b0 = 0; b0 < nterms; b0 += kBatch) {
             const int nb = min(kBatch, nterms - b0);
             __syncthreads();
             for (int q = threadIdx.x; q < nb; q += kThreads) {
                 const PauliDev& P = terms[b0 + q];
+                R cf = (R)P.coeff;
+                if (__popcll(P.xl & P.zl) & 1) cf = -cf;
+                if (P.ny & 2) cf = -cf;
+                uint32_t pat = 0;
+#pragma unroll
+                for (int m = 0; m < kStrip; m++)
+                    pat |= (uint32_t)(__popcll(((uint64_t)m * kThreads) & P.zl) & 1) << m;
                 sxl[q] = P.xl;
                 szl[q] = P.zl;
-                sc[q] = (R)P.coeff;
-                spn[q] = (P.pad << 2) | (P.ny & 3);
+                sc[q] = cf;
+                spad[q] = P.pad;
+                sfl[q] = (pat << 1) | (uint32_t)(P.ny & 1);
             }
             __syncthreads();
             for (int q = 0; q < nb; q++) {
                 const uint64_t xl = sxl[q], zl = szl[q];
-                const R cf0 = sc[q];
-                const int pn = spn[q], ny = pn & 3;
-                const T* const src_slot = psi_slots + ((uint64_t)(pn >> 2) << c);
-                T v[kStrip];
+                const int pad = spad[q];
+                const uint32_t fl = sfl[q], pat = fl >> 1;
+                if (pad != rpad || xl != rxl) {
+                    // a new source: finish the run before it, load this one
+                    if (rpad >= 0 && rim) {
 #pragma unroll
-                for (int m = 0; m < kStrip; m++) {
-                    const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
-                    v[m] = k < count ? src_slot[k ^ xl] : T{(R)0, (R)0};
-                }
+                        for (int m = 0; m < kStrip; m++) {
+                            ar[m] += fr[m] * v[m].x - fi[m] * v[m].y;
+                            ai[m] += fr[m] * v[m].y + fi[m] * v[m].x;
+                            fr[m] = fi[m] = (R)0;
+                        }
+                    } else if (rpad >= 0) {
 #pragma unroll
-                for (int m = 0; m < kStrip; m++) {
-                    const uint64_t src = (s0 + threadIdx.x + (uint64_t)m * kThreads) ^ xl;
-                    R vr = v[m].x, vi = v[m].y, tr;
-                    switch (ny) {
-                        case 1: tr = vr; vr = -vi; vi = tr; break;
-                        case 2: vr = -vr; vi = -vi; break;
-                        case 3: tr = vr; vr = vi; vi = -tr; break;
-                        default: break;
+                        for (int m = 0; m < kStrip; m++) {
+                            ar[m] += fr[m] * v[m].x;
+                            ai[m] += fr[m] * v[m].y;
+                            fr[m] = (R)0;
+                        }
                     }
-                    const R cf = (__popcll(src & zl) & 1) ? -cf0 : cf0;
-                    ar[m] += cf * vr;
-                    ai[m] += cf * vi;
+                    rpad = pad;
+                    rxl = xl;
+                    rim = false;
+                    const T* const src_slot = psi_slots + ((uint64_t)pad << c);
+                    if (whole && !(xl & (7ull << 8))) {
+                        // k ^ x = (b ^ x) + 256 m: one base, constant offsets
+                        const T* const sp = src_slot + (kb ^ xl);
+#pragma unroll
+                        for (int m = 0; m < kStrip; m++) v[m] = sp[m * kThreads];
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < kStrip; m++) {
+                            const uint64_t k = kb + (uint64_t)m * kThreads;
+                            v[m] = k < count ? src_slot[k ^ xl] : T{(R)0, (R)0};
+                        }
+                    }
+                }
+                const R w = (__popcll(kb & zl) & 1) ? -sc[q] : sc[q];
+                if (pat == 0 && !(fl & 1)) {
+#pragma unroll
+                    for (int m = 0; m < kStrip; m++) fr[m] += w;
+                } else if (pat == 0) {
+                    rim = true;
+#pragma unroll
+                    for (int m = 0; m < kStrip; m++) fi[m] += w;
+                } else if (!(fl & 1)) {
+#pragma unroll
+                    for (int m = 0; m < kStrip; m++) fr[m] += ((pat >> m) & 1) ? -w : w;
+                } else {
+                    rim = true;
+#pragma unroll
+                    for (int m = 0; m < kStrip; m++) fi[m] += ((pat >> m) & 1) ? -w : w;
                 }
             }
         }
 #pragma unroll
         for (int m = 0; m < kStrip; m++) {
-            const uint64_t k = s0 + threadIdx.x + (uint64_t)m * kThreads;
+            const uint64_t k = kb + (uint64_t)m * kThreads;
             if (k < count) {
                 T o;
-                o.x = ar[m];
-                o.y = ai[m];
+                o.x = ar[m] + (fr[m] * v[m].x - fi[m] * v[m].y);
+                o.y = ai[m] + (fr[m] * v[m].y + fi[m] * v[m].x);
                 lam[k] = o;
             }
         }

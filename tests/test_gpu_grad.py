@@ -159,6 +159,35 @@ def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb, c
     assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
 
 
+@pytest.mark.parametrize("n,c", [(12, 8), (15, 11)])
+@pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
+def test_compressed_lambda_runs_of_terms_sharing_a_source(SV, dtype, eb, n, c):
+    """lambda = H psi sums, per output, the terms that read the same source
+    (high and low x-mask) as one coefficient times one source amplitude.
+    Here several x-masks (low, high, both, none; some on local bits 8..10,
+    where a thread's 8 outputs differ) each carry terms with different
+    z-masks (some on bits 8..10, some overlapping the x-mask: Y factors, odd
+    and even counts), listed in an order that interleaves the sources. With
+    c = 11 the chunks are at least one 2048-output strip long."""
+    gates, npar = W.hea(n, 2)
+    theta = W.normal_params(npar, seed=14)
+    xs = [0, 1 << 2, (1 << (c + 1)) | (1 << 1), (1 << (c + 2)) | (1 << 9), (1 << c) | (1 << (c + 3)) | 5]
+    zs = [0, 1 << 2, (1 << (c + 1)) | (1 << 3), (1 << 1) | (1 << (c + 3)), 0b11100000111 | (1 << c),
+          (1 << (c + 1)) | 2]
+    terms = [W.PauliTerm(0.1 + 0.07 * i - 0.03 * j, x, z) for j, z in enumerate(zs) for i, x in enumerate(xs)]
+    assert any(bin(t.xmask & t.zmask).count("1") % 2 for t in terms)
+    assert any(bin(t.xmask & t.zmask).count("1") == 2 for t in terms)
+    e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=5)
+    with SV(n, c, eb, dtype=dtype, init_index=5, max_group_qubits=3) as s:
+        e, gr = s.grad(gates, theta, terms)
+        P = s.stats()["passes"]
+    scale = sum(abs(t.coeff) for t in terms)
+    q = np.sqrt(2.0 * (1 << n)) * eb
+    arith = 0.0 if dtype == "c128" else 64 * 2.0 ** -24 * len(gates) * scale
+    assert abs(e - e_o) <= scale * P * q + arith + 1e-12
+    assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
+
+
 @pytest.mark.parametrize("dtype,eb", [("c64", 1e-4), ("c128", 1e-7)])
 def test_compressed_adjoint_checkpoints(SV, dtype, eb):
     """checkpoint_passes = 1: the forward sweep keeps psi after each of its 7
