@@ -445,7 +445,12 @@ def run_apply(args, rank, world):
     st = sim.stats()
     gpu_launches = int(d["kernel_launches"])
     sim.close()
-    quality = state_quality(w, gates, terms, dev, args.remap) if rank == 0 and not args.no_extras else {}
+    default = args.workload == "layers30" and all(v is None for v in (args.eb, args.n, args.chunk, args.depth,
+                                                                      args.group))
+    # the same workload with one group holding every chunk (one pass per call)
+    single = n - c if default and 2 <= n - c <= 8 and not args.remap else None
+    quality = state_quality(w, gates, terms, dev, args.remap, extra_groups=(single,) if single else ()) \
+        if rank == 0 and not args.no_extras else {}
 
     out = {
         "metric": METRIC, "value": value, "unit": "amp-gate updates/s", "n_gpus": world, "steps": args.steps,
@@ -483,14 +488,48 @@ def run_apply(args, rank, world):
         out["fidelity"] = quality["one_apply_vs_fp64"]
     if rank == 0 and not args.no_extras and w["n"] <= 32:
         out.update(comparator(args, gates, terms, energy, applies=args.warmup + args.steps + 1 + e_steps))
-    default = args.workload == "layers30" and all(v is None for v in (args.eb, args.n, args.chunk, args.depth,
-                                                                      args.group))
+    if rank == 0 and not args.no_extras and single:
+        out["single_group"] = single_group_leg(args, w, gates, units_per_step, single, dev,
+                                               quality.get("one_apply_vs_fp64", {}).get(f"group_qubits_{single}"))
     if rank == 0 and not args.no_extras and default:
         out["adjoint_grad_s_per_step"] = adjoint_legs(dev)
     return out
 
 
-def state_quality(w, gates, terms, dev, remap=False):
+def single_group_leg(args, w, gates, units_per_step, g, dev, quality):
+    """The headline workload with max_group_qubits = n - c: one group holds
+    every chunk, so each call is one pass (all chunks in, the fused sweeps,
+    all chunks out) instead of several passes of 2^g-chunk groups streamed
+    through a copy / compute pipeline. Timed like the headline (CUDA events
+    over the same steps after the same warm-up)."""
+    import torch
+    from paper_2309_16979_gb300 import StateVector
+    n, c = w["n"], w["c"]
+    try:
+        with StateVector(n, c, w["eb"], dtype=w["dtype"], init_index=W.basis_index(n), max_group_qubits=g,
+                         host_budget_bytes=host_budget(), device=dev, jit=bool(args.jit)) as sim:
+            for _ in range(args.warmup):
+                sim.apply(gates)
+            s0 = sim.stats()
+            torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                sim.apply(gates)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3 / args.steps
+            s1 = sim.stats()
+        return {"value": units_per_step / t, "unit": METRIC, "ms_per_step": t * 1e3, "group_qubits": g,
+                "passes_per_step": (s1["passes"] - s0["passes"]) / args.steps,
+                "subpasses_per_step": (s1["subpasses"] - s0["subpasses"]) / args.steps,
+                "one_apply_vs_fp64": quality}
+    except Exception as ex:  # noqa: BLE001 -- reported, not hidden
+        return {"error": str(ex)}
+
+
+def state_quality(w, gates, terms, dev, remap=False, extra_groups=()):
     """Error of one application of the workload's circuit to its seeded basis
     state (a fresh handle, as a user's first call), against an FP64
     reference: the uncompressed complex128 GPU path (pinned to the FP64
@@ -498,7 +537,8 @@ def state_quality(w, gates, terms, dev, remap=False):
     else the GHZ closed form. Reports the fidelity |<ref|psi>|^2 /
     (||ref||^2 ||psi||^2), the Ising energy error and the stored norm^2 of
     the compressed path, and the same for the plain uncompressed path in the
-    workload's own precision (the comparator "at fidelity")."""
+    workload's own precision (the comparator "at fidelity"); extra_groups:
+    group sizes whose compressed path is measured the same way."""
     from paper_2309_16979_gb300 import StateVector
     n = w["n"]
     init = W.basis_index(n)
@@ -531,6 +571,16 @@ def state_quality(w, gates, terms, dev, remap=False):
                 "per_pass_infidelity_estimate": (2.0 / 3.0) * (1 << n) * w["eb"] ** 2
                 if not w.get("relative") else None}
         comp["infidelity"] = 1.0 - comp["fidelity"]
+        extra = {}
+        for g in extra_groups:
+            with StateVector(n, w["c"], w["eb"], init_index=init, **dict(kw, max_group_qubits=g)) as s:
+                s.apply(gates)
+                st = s.stats()
+                e_g = s.expect(terms)
+                dot, ns = s.inner(ref), st["norm2"]
+            f = float(abs(dot) ** 2 / max(nr * ns, 1e-300))
+            extra[f"group_qubits_{g}"] = {"fidelity": f, "infidelity": 1.0 - f, "energy": e_g,
+                                          "energy_abs_err": abs(e_g - e_ref), "passes": st["passes"]}
         with StateVector(n, mode="uncompressed", dtype=w["dtype"], init_index=init, device=dev) as p:
             p.apply(gates)
             e_p = p.expect(terms)
@@ -539,7 +589,8 @@ def state_quality(w, gates, terms, dev, remap=False):
                  "energy_abs_err": abs(e_p - e_ref), "norm2": npl}
         plain["infidelity"] = 1.0 - plain["fidelity"]
     out.update({"reference": "uncompressed complex128 GPU path", "reference_energy": e_ref,
-                "compressed": comp, "plain_uncompressed": plain, "seconds": round(time.perf_counter() - t0, 1)})
+                "compressed": comp, "plain_uncompressed": plain, **extra,
+                "seconds": round(time.perf_counter() - t0, 1)})
     return {"one_apply_vs_fp64": out}
 
 
