@@ -125,14 +125,24 @@ __device__ __forceinline__ void pair_unpack(const PairMeta& pm, const uint32_t (
         const uint32_t ww = pm.w[p];
         const uint32_t mask = ww >= 32u ? FULL : ((1u << ww) - 1u);
         uint32_t v[8];
+        // the lane's 8 values are its 8 ww consecutive bits from bit 8 lane ww:
+        // read word by word into a 64-bit accumulator as they are needed
+        const uint32_t pos = 8u * (uint32_t)lane * ww;
+        uint32_t wi = pos >> 5;
+        uint64_t acc = ww ? (uint64_t)(sbuf[p][wi] >> (pos & 31)) : 0ull;
+        uint32_t nb = 32u - (pos & 31);
+        wi++;
 #pragma unroll
         for (int m = 0; m < 8; m++) {
             const uint32_t j = 8u * lane + m;
-            uint32_t z = 0;
-            if (ww) {
-                const uint32_t pos = j * ww;
-                z = __funnelshift_r(sbuf[p][pos >> 5], sbuf[p][(pos >> 5) + 1], pos & 31) & mask;
+            if (nb < ww) {
+                acc |= (uint64_t)sbuf[p][wi] << nb;
+                nb += 32u;
+                wi++;
             }
+            const uint32_t z = (uint32_t)acc & mask;
+            acc >>= ww;
+            nb -= ww;
             const uint32_t rr = (z >> 1) ^ (0u - (z & 1u));
             v[m] = (j == 0) ? 0u : rr;
         }
@@ -202,10 +212,6 @@ __device__ __forceinline__ void encode_pair(const R (&x)[2][8], int c, int k, ui
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, kErrRange);
-    __syncwarp();
-    uint32_t* pkw = &pk[0][0];
-    for (int i = lane; i < 2 * 260; i += 32) pkw[i] = 0u;
-    __syncwarp();
     uint32_t wpl[2];
     int32_t anchor[2];
 #pragma unroll
@@ -222,7 +228,35 @@ __device__ __forceinline__ void encode_pair(const R (&x)[2][8], int c, int k, ui
         }
         mx = __reduce_max_sync(FULL, mx);
         const uint32_t w = mx ? 32u - (uint32_t)__clz(mx) : 0u;
-        if (w) {
+        // value j = 8 lane + m takes bits [j w, (j + 1) w) of the block's words
+        if (w >= 4) {
+            // a lane's 8 w >= 32 bits complete at least one word: it packs them
+            // in a 64-bit accumulator and stores each word it completes; its
+            // first word's low bits (when it starts inside a word) belong to
+            // the previous lane, whose leftover (the accumulator's final
+            // partial word) is shuffled up and OR-ed in after the stores
+            const uint32_t pos = 8u * (uint32_t)lane * w;
+            uint32_t wi = pos >> 5, nb = pos & 31;
+            uint64_t acc = 0;
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                acc |= (uint64_t)z[m] << nb;
+                nb += w;
+                if (nb >= 32u) {
+                    pk[p][wi] = (uint32_t)acc;
+                    acc >>= 32;
+                    nb -= 32u;
+                    wi++;
+                }
+            }
+            // lane 31 ends on the block's last bit (256 w is a multiple of 32)
+            const uint32_t prev = __shfl_up_sync(FULL, (uint32_t)acc, 1);
+            __syncwarp();
+            if (lane > 0 && (pos & 31)) pk[p][pos >> 5] |= prev;
+        } else if (w) {
+            // fewer than 32 bits a lane: words shared by several lanes
+            for (uint32_t i = (uint32_t)lane; i <= 8u * w; i += 32) pk[p][i] = 0u;
+            __syncwarp();
 #pragma unroll
             for (int m = 0; m < 8; m++) {
                 const uint32_t pos = (8u * lane + m) * w;
