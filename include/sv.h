@@ -143,10 +143,14 @@ typedef struct sv_config {
                                      every K-th pass (pageable host memory, one compressed state
                                      per checkpoint, sv_stats_t.checkpoint_bytes) and the reverse
                                      sweep resumes from it at that pass boundary */
-    int32_t lambda_cache;         /* compressed sv_grad only. 1 (default): while lambda = H psi is
-                                     built, a device copy of the compressed psi (when it fits) serves
-                                     every output chunk's source chunks, so psi crosses the host link
-                                     once; 0: each output chunk copies its sources from the host store */
+    int32_t lambda_cache;         /* compressed sv_grad only, how lambda = H psi gets each output
+                                     chunk's source chunks. 1 (default): psi decoded once into device
+                                     memory when 2^n amplitudes fit in half the free device memory (or
+                                     the device_alloc callback grants them), else as 2; 2: a device copy
+                                     of the compressed psi (when it fits), decoded per source, so psi
+                                     crosses the host link once; 0: copied from the host store per
+                                     output chunk. The results are the same bit for bit. Other values:
+                                     SV_ERR_ARG */
     sv_device_alloc_fn device_alloc; /* NULL (default): cudaMalloc / cudaFree. Otherwise every device
                                      allocation of the handle (state, staging, per-call scratch)
                                      goes through device_alloc / device_free (both must be set) */

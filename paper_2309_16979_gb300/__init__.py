@@ -47,7 +47,7 @@ class StateVector:
                  host_budget_bytes: int = 0, timeout_s: float = 600.0, device: int = 0,
                  profile: bool = False, fuse_codec: bool = True,
                  jit: bool = True, relative_bound: bool = False, remap_qubits: bool = False,
-                 checkpoint_passes: int = 0, lambda_cache: bool = True, memory: str = "torch"):
+                 checkpoint_passes: int = 0, lambda_cache: int = 1, memory: str = "torch"):
         """memory="torch": the handle's device memory comes from torch's
         caching allocator (it shows in torch.cuda.memory_allocated()) and its
         calls order after the work queued on torch's current stream of the

@@ -320,6 +320,7 @@ int sv_create(int n, int chunk_qubits, double abs_error_bound, const sv_config* 
     if (cfg.remap_qubits != 0 && cfg.remap_qubits != 1) return reject(SV_ERR_ARG, "remap_qubits must be 0 or 1");
     if (!(cfg.timeout_s > 0)) cfg.timeout_s = 600.0;
     if (cfg.checkpoint_passes < 0) return reject(SV_ERR_ARG, "checkpoint_passes must be >= 0");
+    if (cfg.lambda_cache < 0 || cfg.lambda_cache > 2) return reject(SV_ERR_ARG, "lambda_cache must be 0, 1 or 2");
     if (!cfg.device_alloc != !cfg.device_free)
         return reject(SV_ERR_ARG, "device_alloc and device_free must be set together");
     int k = 0;

@@ -1781,8 +1781,11 @@ static int ensure_lambda_store(sv_state* s)
 // device memory before it is encoded once. With a single batch that fits
 // twice, two staging sets alternate: chunk k+1's sources cross the host link
 // while chunk k is decoded, multiplied and encoded, and chunk k's stream
-// returns to the host while chunk k+1 computes. d_terms holds every batch's
-// term table for every output chunk (2^(n-c) x phys.size() entries).
+// returns to the host while chunk k+1 computes. With lambda_cache 1 and room
+// on the device for the whole decoded psi, psi is instead decoded once and
+// each output chunk reads its sources there, and its output staging sets
+// alternate the same way. d_terms holds every batch's term table for every
+// output chunk (2^(n-c) x phys.size() entries).
 template <typename R>
 static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, PauliDev* d_terms, double* d_part,
                         int nblocks, double* d_energy)
@@ -1795,10 +1798,40 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
     X.erase(std::unique(X.begin(), X.end()), X.end());  // X[0] = 0: chunk k itself
     const size_t gcap = (size_t)1 << std::min(s->gmax, s->nh);
     if (gcap < 2 && X.size() > 1) return fail(s, SV_ERR_ARG, "staging groups too small for lambda = H psi");
-    // batches of source slots: batch 0 = X[0 .. gcap), later ones X[0] and the next gcap - 1
+    const uint64_t nch = 1ull << s->nh;
+    const size_t amp_bytes = sizeof(R) * 2;
+    cudaError_t e;
+    // lambda_cache 1: when the whole decoded psi fits in half the free device
+    // memory (or the caller's allocator grants it), psi is decoded into it
+    // once and every output chunk reads its sources there (ψ decoded once
+    // instead of once per source); a term's slot is then its source chunk.
+    void* d_full = nullptr;
+    if (s->cfg.lambda_cache == 1 && X.size() > 1) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        cudaGetLastError();
+        const size_t full_bytes = amp_bytes << s->n;
+        if ((s->cfg.device_alloc || (double)full_bytes <= 0.5 * (double)free_b) && dev_alloc(s, &d_full, full_bytes)) {
+            cudaGetLastError();
+            d_full = nullptr;
+        }
+    }
+    struct FullFree {
+        sv_state* s;
+        void*& p;
+        ~FullFree()
+        {
+            if (p) {
+                cudaStreamSynchronize(s->s_comp);  // the kernels that read it
+                dev_free(s, p);
+            }
+        }
+    } full_free{s, d_full};
+    // batches of source slots: batch 0 = X[0 .. gcap), later ones X[0] and the
+    // next gcap - 1; one batch of every source when psi is decoded in full
     std::vector<std::vector<size_t>> batch{{}};
     for (size_t j = 0; j < X.size(); j++) {
-        if (batch.back().size() == gcap) batch.push_back({0});
+        if (!d_full && batch.back().size() == gcap) batch.push_back({0});
         batch.back().push_back(j);
     }
     const size_t nb = batch.size(), nt = phys.size();
@@ -1810,8 +1843,7 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
                 slot_of[batch[b][i]] = (int)i;
             }
     const size_t m = batch[0].size();
-    const int nset = (nb == 1 && 2 * m <= gcap) ? 2 : 1;
-    const uint64_t nch = 1ull << s->nh;
+    const int nset = (d_full || (nb == 1 && 2 * m <= gcap)) ? 2 : 1;
     // term table of (chunk k, batch b) at d_terms + toff[b] + k * tcnt[b]
     std::vector<size_t> toff(nb, 0), tcnt(nb, 0);
     for (size_t i = 0; i < nt; i++) {
@@ -1819,7 +1851,6 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         tcnt[batch_of[j]]++;
     }
     for (size_t b = 1; b < nb; b++) toff[b] = toff[b - 1] + nch * tcnt[b - 1];
-    cudaError_t e;
     if (nt) {
         // each table lists the terms that read one source (slot, low x-mask)
         // together: the kernel loads a source once per run of such terms
@@ -1840,13 +1871,37 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
                 const int hs = __builtin_popcountll((k ^ xh) & (phys[i].zmask >> c)) & 1;
                 PauliDev& d = hd[toff[b] + k * tcnt[b] + fill[b]++];
                 d = pauli_dev(phys[i], phys[i].xmask & lowmask, phys[i].zmask & lowmask, 0, hs ? -1.0 : 1.0);
-                d.pad = slot_of[j];
+                d.pad = d_full ? (int32_t)(k ^ xh) : slot_of[j];
             }
         }
         if ((e = cudaMemcpy(d_terms, hd.data(), sizeof(PauliDev) * hd.size(), cudaMemcpyHostToDevice)))
             return cuda_fail(s, e, "upload terms");
     }
-    const size_t amp_bytes = sizeof(R) * 2;
+    if (d_full) {
+        // psi decoded once, group by group through the two staging sets
+        for (uint64_t k0 = 0, bi = 0; k0 < nch; k0 += gcap, bi++) {
+            const int sl = (int)(bi & 1);
+            const uint64_t mm = std::min<uint64_t>(gcap, nch - k0);
+            if (bi >= 2 && (e = cudaStreamWaitEvent(s->s_h2d, s->ev_h2d[2 + sl], 0)))
+                return cuda_fail(s, e, "wait decode");
+            GroupIn gin{};
+            for (uint64_t j = 0; j < mm; j++) {
+                const ChunkRef& cr = s->cur[k0 + j];
+                gin.bytes[j] = (uint32_t)cr.bytes;
+                if ((e = cudaMemcpyAsync(s->d_in[sl] + j * s->stride, cr.ptr, cr.bytes, cudaMemcpyHostToDevice,
+                                         s->s_h2d)))
+                    return cuda_fail(s, e, "H2D chunk");
+                s->st.bytes_h2d += cr.bytes;
+            }
+            if ((e = cudaEventRecord(s->ev_h2d[sl], s->s_h2d)) || (e = cudaStreamWaitEvent(s->s_comp, s->ev_h2d[sl], 0)) ||
+                (e = launch_decode<R>(s->d_in[sl], s->stride, c, s->dtype, (int)mm, gin,
+                                      static_cast<uint8_t*>(d_full) + ((k0 << c) * amp_bytes), s->scale, s->d_err,
+                                      s->s_comp)) ||
+                (e = cudaEventRecord(s->ev_h2d[2 + sl], s->s_comp)))
+                return cuda_fail(s, e, "decode psi");
+            s->st.kernel_launches++;
+        }
+    }
     // Every source chunk serves X.size() output chunks. When the whole
     // compressed psi fits beside the staging buffers, it crosses the host
     // link once into a device copy (chunk k at k * cstride) and each output
@@ -1855,7 +1910,7 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
     uint8_t* d_cache = nullptr;
     uint64_t* d_cbytes = nullptr;
     size_t cstride = 0;
-    if (s->cfg.lambda_cache && X.size() > 1 && nch <= 65536) {
+    if (!d_full && s->cfg.lambda_cache && X.size() > 1 && nch <= 65536) {
         for (const ChunkRef& cr : s->cur) cstride = std::max<size_t>(cstride, cr.bytes);
         cstride = (cstride + 255) & ~size_t(255);
         size_t free_b = 0, total_b = 0;
@@ -1904,7 +1959,16 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
         uint8_t* in = s->d_in[0] + base * s->stride;
         uint8_t* amps = static_cast<uint8_t*>(s->d_amps) + (base << c) * amp_bytes;
         int launches = 0;
-        for (size_t b = 0; b < nb; b++) {
+        if (d_full) {
+            // the set's output stream is overwritten once its copy to the host is done
+            if (k >= (uint64_t)nset && (e = cudaStreamWaitEvent(s->s_comp, s->ev_d2h[sl], 0)))
+                return cuda_fail(s, e, "wait d2h");
+            if ((e = launch_ham_chunk<R>(d_full, s->d_amps2, c, d_terms + k * nt, (int)nt, 0, s->s_comp)))
+                return cuda_fail(s, e, "lambda chunk");
+            launches++;
+            amps = static_cast<uint8_t*>(d_full) + (k << c) * amp_bytes;  // psi_k
+        }
+        for (size_t b = 0; b < (d_full ? 0 : nb); b++) {
             GroupIn gin{};
             if (d_cache) {
                 // sources from the device copy of psi (compute stream: after the set's previous decode)
@@ -1946,7 +2010,7 @@ static int build_lambda(sv_state* s, const std::vector<sv_pauli_term>& phys, Pau
                 return cuda_fail(s, e, "lambda chunk");
             launches += 2;
         }
-        // slot 0 of the last batch holds psi_k
+        // psi_k: slot 0 of the last batch, or its place in the decoded psi
         if ((e = launch_dot<R>(amps, s->d_amps2, 1ull << c, d_part, nblocks, s->s_comp)) ||
             (e = launch_sum_partials(d_part, 1, nblocks, d_energy, s->s_comp)) ||
             (s->rel && (e = launch_chunk_steps<R>(s->d_amps2, c, 1, s->eb, s->d_mbits, s->d_kc, s->s_comp,

@@ -112,10 +112,12 @@ def test_compressed_adjoint_within_quantisation_bound(SV, dtype, eb):
     with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g) as s:
         e, gr = s.grad(gates, theta, terms)
         st = s.stats()
-    with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g, lambda_cache=False) as s:
-        e2, gr2 = s.grad(gates, theta, terms)
-    # the device copy of psi only changes where lambda's sources come from
-    assert e2 == e and np.array_equal(gr2, gr)
+    # lambda's sources from the host store (0) or a device copy of the
+    # compressed psi (2) instead of the decoded psi (1): the same bits
+    for cache in (0, 2):
+        with SV(n, c, eb, dtype=dtype, init_index=3, max_group_qubits=g, lambda_cache=cache) as s:
+            e2, gr2 = s.grad(gates, theta, terms)
+        assert e2 == e and np.array_equal(gr2, gr), cache
     P = st["passes"]  # forward + reverse passes
     scale = sum(abs(t.coeff) for t in terms)
     q = np.sqrt(2.0 * (1 << n)) * eb
@@ -136,13 +138,15 @@ def test_compressed_adjoint_agrees_with_uncompressed_gpu(SV):
     assert abs(e_c - e_u) < 1e-4 and np.abs(g_c - g_u).max() < 1e-4
 
 
-@pytest.mark.parametrize("cache", [True, False])
+@pytest.mark.parametrize("cache", [0, 1, 2])
 @pytest.mark.parametrize("dtype,eb", [("c128", 1e-9), ("c64", 1e-6)])
 def test_compressed_adjoint_with_more_high_x_masks_than_a_group(SV, dtype, eb, cache):
     """lambda = H psi when the terms' distinct high x-masks (0, 1, 2, 4, 8, 9
     over 4 high qubits) outnumber the 4 chunks a staging group holds: two
-    batches per output chunk, accumulated before one encode. Same bound as
-    the single-batch case."""
+    batches per output chunk, accumulated before one encode, when the
+    sources are staged (lambda_cache 0: from the host, 2: from a device copy
+    of the compressed psi); one pass over the decoded psi with 1. Same bound
+    as the single-batch case."""
     n, c = 12, 8
     gates, npar = W.hea(n, 2)
     theta = W.normal_params(npar, seed=12)
