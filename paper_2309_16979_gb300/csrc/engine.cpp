@@ -2063,6 +2063,12 @@ static int run_pass_adjoint_compressed(sv_state* s, const std::vector<PGate>& in
     int t, l;
     tile_shape(L, std::min(s->tq, 12), s->lq, t, l);
     std::vector<int> rids(pp.gates.rbegin(), pp.gates.rend());
+    for (int gi : rids) {
+        // a partial is evaluated on the tile: the target must be in the pass's group
+        const int q = inv[gi].t[0];
+        if (inv[gi].param >= 0 && q >= c && std::find(pp.S.begin(), pp.S.end(), q) == pp.S.end())
+            return fail(s, SV_ERR_ARG, "parameterised gate on a qubit its pass does not stage");
+    }
     const std::vector<HOp> hops = local_ops(inv, rids, c, pp.S, true);
     const std::vector<SubPlan> subs = plan_subpasses(hops, L, t, l, true);
     if (subs.empty() && !hops.empty()) return fail(s, SV_ERR_ARG, "no tile plan for the pass");

@@ -69,9 +69,12 @@ static uint64_t qubit_mask(const PGate& g)
     return m;
 }
 
+// Qubits a pass must stage for gate g: the targets it mixes, and the target of
+// a parameterised gate of a gradient even when it is diagonal (the reverse
+// sweep evaluates its generator's partial on the tile, as a register bit).
 static uint64_t mixing_mask(const PGate& g)
 {
-    if (g.diag) return 0;
+    if (g.diag && g.param < 0) return 0;
     uint64_t m = 0;
     for (int i = 0; i < g.nt; i++) m |= 1ull << g.t[i];
     return m;
@@ -366,7 +369,7 @@ std::vector<HOp> local_ops(const std::vector<PGate>& g, const std::vector<int>& 
         if (adjoint && G.param >= 0) {
             op.param = G.param;
             op.gen = G.kind == SV_GATE_RX ? 1 : G.kind == SV_GATE_RY ? 2 : 3;
-            const int p = loc(G.t[0]);
+            const int p = loc(G.t[0]);  // >= 0: the pass planner stages a parameterised gate's target
             op.mixL |= 1ull << p;  // the generator's pairs must be tile-local
             if (op.type == OP_DIAG) op.t[0] = p;
             // a gradient needs the ordering to hold at every angle: the

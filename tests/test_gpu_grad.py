@@ -192,6 +192,31 @@ def test_compressed_lambda_runs_of_terms_sharing_a_source(SV, dtype, eb, n, c):
     assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + arith + 1e-12
 
 
+def test_compressed_adjoint_diagonal_parameters_on_high_qubits(SV):
+    """Parameterised RZ gates on the chunk-index (high) qubits ahead of any
+    gate that mixes them: a diagonal gate needs no staged qubit to run, but
+    the reverse sweep takes each parameter's partial on the tile, so the
+    gradient's passes stage those targets too (the library refuses a plan
+    that does not). Energy and gradient against the oracle."""
+    n, c, g = 13, 8, 2
+    gates = [W.Gate("RZ", (q,), param=q - c) for q in range(c, n)]          # params 0..4 on high qubits
+    gates += [W.Gate("H", (q,)) for q in range(c)]
+    gates += [W.Gate("CNOT", (q + 1,), (q,)) for q in range(n - 1)]
+    gates += [W.Gate("RZ", (q,), param=5 + q) for q in range(n)]
+    gates += [W.Gate("RX", (q,), param=5 + n + q) for q in range(n)]
+    npar = 5 + 2 * n
+    theta = W.normal_params(npar, seed=31)
+    terms = W.ising(n)
+    e_o, g_o = oracle.adjoint(n, gates, theta, terms, init=9)
+    with SV(n, c, 1e-9, dtype="c128", init_index=9, max_group_qubits=g) as s:
+        e, gr = s.grad(gates, theta, terms)
+        P = s.stats()["passes"]
+    scale = sum(abs(t.coeff) for t in terms)
+    q = np.sqrt(2.0 * (1 << n)) * 1e-9
+    assert abs(e - e_o) <= scale * P * q + 1e-12
+    assert np.abs(gr - g_o).max() <= scale * (P + 2 * (P + 1)) * q + 1e-12
+
+
 @pytest.mark.parametrize("dtype,eb", [("c64", 1e-4), ("c128", 1e-7)])
 def test_compressed_adjoint_checkpoints(SV, dtype, eb):
     """checkpoint_passes = 1: the forward sweep keeps psi after each of its 7
