@@ -284,7 +284,9 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
         sim[q] = (R)(ny == 1 ? -cf : ny == 3 ? cf : 0.0);
         uint32_t tab = 0;
         for (int k = 0; k < 16; k++) tab |= (uint32_t)(__popcll(rowoff[k] & P.zl) & 1) << k;
-        srow[q] = tab;
+        uint32_t r = 0;  // z on the four row positions
+        for (int i = 0; i < 4; i++) r |= (uint32_t)((P.zl >> et.hp[i]) & 1ull) << i;
+        srow[q] = tab | (r << 16);
     }
     __syncthreads();
     bool pending[2] = {false, false};  // thread 0: a copy into the buffer not yet waited for
@@ -319,15 +321,27 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
             n2[k] = a[k].x * a[k].x + a[k].y * a[k].y;
             e[k] = (R)0;
         }
+        // diagonal terms: c (-1)^|j & z| with j = jt + row offset of k splits
+        // into (-1)^|jt & z| and (-1)^|k & r| (r: z on the row positions), so
+        // they sum per r into dc[r] and a 16-point Walsh-Hadamard transform
+        // gives every row's coefficient at once
+        R dc[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) dc[k] = (R)0;
         for (int q = 0; q < nterms; q++) {
             const uint32_t xt = sxt[q];
-            const uint32_t sg = (__popcll(jt & szl[q]) & 1) ? ~srow[q] : srow[q];  // bit k: sign of position k
             const R cr = sre[q];
             if (xt == 0) {
-#pragma unroll
-                for (int k = 0; k < 16; k++) e[k] += (((sg >> k) & 1u) ? -cr : cr) * n2[k];
+                const R v = (__popcll(jt & szl[q]) & 1) ? -cr : cr;
+                switch (srow[q] >> 16) {
+#define SV_DC(i) case i: dc[i] += v; break;
+                    SV_DC(0) SV_DC(1) SV_DC(2) SV_DC(3) SV_DC(4) SV_DC(5) SV_DC(6) SV_DC(7)
+                    SV_DC(8) SV_DC(9) SV_DC(10) SV_DC(11) SV_DC(12) SV_DC(13) SV_DC(14) SV_DC(15)
+#undef SV_DC
+                }
                 continue;
             }
+            const uint32_t sg = (__popcll(jt & szl[q]) & 1) ? ~srow[q] : srow[q];  // bit k: sign of position k
             const R ci = sim[q];
             const uint32_t pt = t ^ (xt & 0xFFu), pk = xt >> 8;
 #pragma unroll
@@ -339,9 +353,19 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
                 e[k] += ((sg >> k) & 1u) ? -v : v;
             }
         }
+#pragma unroll
+        for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+            for (int i = 0; i < 16; i += 2 * h)
+#pragma unroll
+                for (int j = i; j < i + h; j++) {
+                    const R a0 = dc[j], a1 = dc[j + h];
+                    dc[j] = a0 + a1;
+                    dc[j + h] = a0 - a1;
+                }
         R sub = (R)0;
 #pragma unroll
-        for (int k = 0; k < 16; k++) sub += e[k];
+        for (int k = 0; k < 16; k++) sub += e[k] + dc[k] * n2[k];
         acc += (double)sub;
         __syncthreads();  // this buffer's reads are done before it is refilled
     }
