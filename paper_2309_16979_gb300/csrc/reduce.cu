@@ -342,16 +342,44 @@ k_energy_tiles(const typename V2<R>::T* __restrict__ psi, uint64_t ntiles, uint6
                 continue;
             }
             const uint32_t sg = (__popcll(jt & szl[q]) & 1) ? ~srow[q] : srow[q];  // bit k: sign of position k
-            const R ci = sim[q];
+            // Both members of a pair (position and partner) add the same
+            // real value (P is Hermitian), so one member per pair adds it
+            // twice: with a row bit flipped (pk != 0), the rows whose lowest
+            // flipped row bit is clear; else the rows whose bit 0 equals the
+            // thread's lowest flipped thread bit. Each thread takes 8 rows.
+            const R c2r = cr + cr, c2i = sim[q] + sim[q];
             const uint32_t pt = t ^ (xt & 0xFFu), pk = xt >> 8;
+#define SV_PAIR(k, own)                                                      \
+    {                                                                        \
+        const T bb = tile[pt + 256u * ((uint32_t)(k) ^ pk)];                 \
+        const T aa = (own);                                                  \
+        const R re = bb.x * aa.x + bb.y * aa.y;                              \
+        const R im = bb.x * aa.y - bb.y * aa.x;                              \
+        const R v = c2r * re + c2i * im;                                     \
+        e[m] += ((sg >> (k)) & 1u) ? -v : v;                                 \
+    }
+#define SV_ROWPAIRS(PB)                                                      \
+    _Pragma("unroll") for (int m = 0; m < 8; m++) {                          \
+        const int k = ((m >> (PB)) << ((PB) + 1)) | (m & ((1 << (PB)) - 1)); \
+        SV_PAIR(k, a[k])                                                     \
+    }
+            if (pk) {
+                switch (__ffs(pk) - 1) {
+                    case 0: SV_ROWPAIRS(0) break;
+                    case 1: SV_ROWPAIRS(1) break;
+                    case 2: SV_ROWPAIRS(2) break;
+                    default: SV_ROWPAIRS(3) break;
+                }
+            } else {
+                const uint32_t tb = (t >> (__ffs(xt & 0xFFu) - 1)) & 1u;
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
-                const T bb = tile[pt + 256u * ((uint32_t)k ^ pk)];
-                const R re = bb.x * a[k].x + bb.y * a[k].y;
-                const R im = bb.x * a[k].y - bb.y * a[k].x;
-                const R v = cr * re + ci * im;
-                e[k] += ((sg >> k) & 1u) ? -v : v;
+                for (int m = 0; m < 8; m++) {
+                    const uint32_t k = 2u * (uint32_t)m + tb;
+                    SV_PAIR(k, tb ? a[2 * m + 1] : a[2 * m])
+                }
             }
+#undef SV_ROWPAIRS
+#undef SV_PAIR
         }
 #pragma unroll
         for (int h = 1; h < 16; h <<= 1)
