@@ -95,3 +95,25 @@ def test_create_without_gpu_fails_cleanly(lib):
     from paper_2309_16979_gb300 import StateVector, SvError
     with pytest.raises(SvError):
         StateVector(10, 8, 1e-6)
+
+
+@pytest.mark.parametrize("kw,word", [
+    (dict(lambda_cache=3), "lambda_cache"),
+    (dict(lambda_cache=-1), "lambda_cache"),
+    (dict(checkpoint_passes=-1), "checkpoint_passes"),
+    (dict(max_group_qubits=9), "max_group_qubits"),
+    (dict(max_group_qubits=1), "max_group_qubits"),
+    (dict(pipeline_slots=1), "pipeline_slots"),
+    (dict(pipeline_slots=5), "pipeline_slots"),
+    (dict(tile_qubits=14), "tile_qubits"),
+    (dict(init_index=1 << 10), "init_index"),
+])
+def test_create_rejects_bad_config_before_any_gpu_call(kw, word):
+    """sv_create checks its arguments before it touches a device: each bad
+    field gives SV_ERR_ARG (-1) and a message naming it, with or without a
+    GPU."""
+    from paper_2309_16979_gb300 import StateVector, SvError
+    with pytest.raises(SvError) as ei:
+        StateVector(10, 8, 1e-6, memory="cuda", **kw)
+    assert ei.value.code == -1
+    assert word in str(ei.value)
